@@ -1,0 +1,1364 @@
+/*
+ * FP64 CPU oracle of the batched rigid-body step -- TEST INFRASTRUCTURE ONLY.
+ * See oracle.h for the interface and the published methods each stage follows.
+ *
+ * Everything here is plain, sequential FP64: one env at a time, stages in the
+ * order broadphase -> narrowphase -> colouring once per step, then for every
+ * substep gravity -> prep -> warm start -> position iterations -> integration
+ * -> relax (velocity) iterations.  Rows of one colour touch disjoint dynamic
+ * bodies, so solving them in constraint-list order equals solving them in
+ * parallel; that is what lets a parallel GPU solver agree with this file.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* small vector algebra                                                       */
+/* ------------------------------------------------------------------------- */
+typedef struct { double x, y, z; } v3;
+typedef struct { double x, y, z, w; } qt;          /* Hamilton, (x,y,z,w) */
+typedef struct { double m[3][3]; } m3;
+
+static v3 V(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static v3 add(v3 a, v3 b) { return V(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 sub(v3 a, v3 b) { return V(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 scl(v3 a, double s) { return V(a.x * s, a.y * s, a.z * s); }
+static double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross(v3 a, v3 b) {
+    return V(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double norm(v3 a) { return sqrt(dot(a, a)); }
+static v3 neg(v3 a) { return V(-a.x, -a.y, -a.z); }
+static double comp(v3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+static v3 unit_axis(int i) { return V(i == 0, i == 1, i == 2); }
+static v3 with_comp(v3 a, int i, double s) {
+    if (i == 0) a.x = s; else if (i == 1) a.y = s; else a.z = s;
+    return a;
+}
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+static qt Q(double x, double y, double z, double w) { qt r = {x, y, z, w}; return r; }
+static qt qmul(qt a, qt b) {
+    /* (a_v, a_w)(b_v, b_w) = (a_w b_v + b_w a_v + a_v x b_v, a_w b_w - a_v.b_v) */
+    v3 av = V(a.x, a.y, a.z), bv = V(b.x, b.y, b.z);
+    v3 r = add(add(scl(bv, a.w), scl(av, b.w)), cross(av, bv));
+    return Q(r.x, r.y, r.z, a.w * b.w - dot(av, bv));
+}
+static qt qconj(qt a) { return Q(-a.x, -a.y, -a.z, a.w); }
+static qt qnormalize(qt a) {
+    double n = sqrt(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+    return Q(a.x / n, a.y / n, a.z / n, a.w / n);
+}
+static m3 qmat(qt q) {
+    m3 R;
+    double x = q.x, y = q.y, z = q.z, w = q.w;
+    R.m[0][0] = 1 - 2 * (y * y + z * z); R.m[0][1] = 2 * (x * y - z * w); R.m[0][2] = 2 * (x * z + y * w);
+    R.m[1][0] = 2 * (x * y + z * w); R.m[1][1] = 1 - 2 * (x * x + z * z); R.m[1][2] = 2 * (y * z - x * w);
+    R.m[2][0] = 2 * (x * z - y * w); R.m[2][1] = 2 * (y * z + x * w); R.m[2][2] = 1 - 2 * (x * x + y * y);
+    return R;
+}
+static v3 mv(const m3* R, v3 a) {
+    return V(R->m[0][0] * a.x + R->m[0][1] * a.y + R->m[0][2] * a.z,
+             R->m[1][0] * a.x + R->m[1][1] * a.y + R->m[1][2] * a.z,
+             R->m[2][0] * a.x + R->m[2][1] * a.y + R->m[2][2] * a.z);
+}
+static v3 mtv(const m3* R, v3 a) { /* R^T a */
+    return V(R->m[0][0] * a.x + R->m[1][0] * a.y + R->m[2][0] * a.z,
+             R->m[0][1] * a.x + R->m[1][1] * a.y + R->m[2][1] * a.z,
+             R->m[0][2] * a.x + R->m[1][2] * a.y + R->m[2][2] * a.z);
+}
+static v3 mcol(const m3* R, int j) { return V(R->m[0][j], R->m[1][j], R->m[2][j]); }
+static v3 qrot(qt q, v3 a) { m3 R = qmat(q); return mv(&R, a); }
+
+/* Axis used to build a basis orthogonal to a unit vector n: the first index
+ * i (0, 1, 2) whose |n_i| is within 0.1 of the smallest |n_j|.  Near an axis
+ * direction this never flips between nearly equal tiny components, and for a
+ * normal in a coordinate plane it picks the axis normal to that plane. */
+static int basis_axis(v3 a) {
+    double c[3] = {fabs(a.x), fabs(a.y), fabs(a.z)};
+    double mn = fmin(c[0], fmin(c[1], c[2]));
+    for (int i = 0; i < 3; i++) if (c[i] <= mn + 0.1) return i;
+    return 2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* world data                                                                 */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int type; double p[3]; double mass; int dyn;
+    double inv_mass; double inv_I[3]; double mu; unsigned group, mask;
+    v3 x; qt q; v3 v; v3 w;
+    m3 invIw;                         /* world inverse inertia, per substep */
+} Body;
+
+typedef struct {
+    int type, parent, child;
+    v3 fpP; qt fqP; v3 fpC; qt fqC;
+    double lower, upper, kp, kd, target;
+} Joint;
+
+typedef struct { v3 cA, cB, n; double d; v3 aA, aB; } CPoint;
+typedef struct { int a, b, np; CPoint p[4]; } Manifold;
+
+enum { RK_NORMAL = 0, RK_FRICTION = 1, RK_EQ = 2, RK_LIMIT = 3, RK_DRIVE = 4 };
+
+typedef struct {
+    int kind, a, b;                   /* a, b: env-local bodies, -1 = world */
+    v3 lin, angA, angB;
+    double k;                         /* J M^-1 J^T */
+    double bias, relax_bias;
+    double lambda, gamma, mu;
+    int partner;                      /* friction: index of its normal row */
+    int pt;                           /* contact point / limit side, for relax bias */
+} Row;
+
+typedef struct { int kind, idx, a, b, color, row0, nrows; } Constraint;
+
+typedef struct {
+    int nb, nj;
+    Body* bodies; Joint* joints;
+    int npairs; int (*pairs)[2];
+    int nman; Manifold* man;
+    int ntie; int (*tiepairs)[2];
+    int ncons; Constraint* cons; int* order; int ncolors;
+    int nrows; Row* rows;
+    unsigned status; long long ties;
+    long long cnt[OC_NUM];
+} Env;
+
+struct oracle_world {
+    int E; Env* envs;
+    double dt; int substeps, pos_iters, vel_iters; v3 g; double margin, vmax;
+    int contact_cap, pair_cap;
+    int nb_total, nj_total;
+    long long* body_off; long long* joint_off;
+};
+
+static const double TIE_EPS = 1e-5;    /* lengths (m) */
+static const double TIE_DIR = 1e-6;    /* unit-vector components */
+/* a decision is tie-adjacent when its deciding quantity is within 1e-5 of
+ * the threshold but not structurally equal to it (exactly equal values, such
+ * as the zero components of an axis-aligned normal, break the same way in
+ * any precision) */
+static void tie_w(Env* e, double a, double b, double w) { if (a != b && fabs(a - b) < w) e->ties++; }
+static void tie(Env* e, double a, double b) { tie_w(e, a, b, TIE_EPS); }
+/* tie check of the basis_axis choice */
+static void tie_basis(Env* e, v3 a) {
+    double c[3] = {fabs(a.x), fabs(a.y), fabs(a.z)};
+    double mn = fmin(c[0], fmin(c[1], c[2]));
+    for (int i = 0; i < 3; i++) tie_w(e, c[i], mn + 0.1, TIE_DIR);
+}
+
+/* ------------------------------------------------------------------------- */
+/* shapes and mass                                                            */
+/* ------------------------------------------------------------------------- */
+void oracle_inertia(const double* d, double* out) {
+    int type = (int)d[0];
+    double m = d[4];
+    if (type == OR_SPHERE) {
+        double r = d[1];
+        out[0] = out[1] = out[2] = 0.4 * m * r * r;
+    } else if (type == OR_BOX) {
+        double hx = d[1], hy = d[2], hz = d[3];
+        out[0] = m / 3.0 * (hy * hy + hz * hz);
+        out[1] = m / 3.0 * (hx * hx + hz * hz);
+        out[2] = m / 3.0 * (hx * hx + hy * hy);
+    } else if (type == OR_CAPSULE) {
+        /* uniform solid: cylinder of length 2l plus two hemispheres whose
+         * centroids sit 3r/8 beyond the segment ends (parallel-axis theorem) */
+        double r = d[1], l = d[2];
+        double vc = M_PI * r * r * 2.0 * l, vs = 4.0 / 3.0 * M_PI * r * r * r;
+        double mc = m * vc / (vc + vs), ms = m * vs / (vc + vs);
+        double izz = mc * r * r / 2.0 + ms * 0.4 * r * r;
+        double ixx = mc * (r * r / 4.0 + l * l / 3.0) + ms * (0.4 * r * r + l * l + 0.75 * l * r);
+        out[0] = out[1] = ixx; out[2] = izz;
+    } else {
+        out[0] = out[1] = out[2] = 0.0;
+    }
+}
+
+static void body_from_desc(Body* b, const double* d) {
+    memset(b, 0, sizeof(*b));
+    b->type = (int)d[0];
+    b->p[0] = d[1]; b->p[1] = d[2]; b->p[2] = d[3];
+    b->mass = d[4];
+    b->dyn = (b->type != OR_PLANE) && d[4] > 0.0;
+    b->x = V(d[5], d[6], d[7]);
+    b->q = qnormalize(Q(d[8], d[9], d[10], d[11]));
+    b->mu = d[18];
+    b->group = (unsigned)d[20]; b->mask = (unsigned)d[21];
+    if (b->dyn) {
+        double I[3];
+        oracle_inertia(d, I);
+        b->inv_mass = 1.0 / b->mass;
+        for (int i = 0; i < 3; i++) b->inv_I[i] = 1.0 / I[i];
+        b->v = V(d[12], d[13], d[14]);
+        b->w = V(d[15], d[16], d[17]);
+    } else {
+        b->inv_mass = 0.0;
+        b->v = V(0, 0, 0); b->w = V(0, 0, 0);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* broadphase: brute force over i < j                                         */
+/* ------------------------------------------------------------------------- */
+static void aabb(const Body* b, double half_margin, v3* lo, v3* hi) {
+    m3 R = qmat(b->q);
+    v3 e;
+    if (b->type == OR_SPHERE) {
+        e = V(b->p[0], b->p[0], b->p[0]);
+    } else if (b->type == OR_BOX) {
+        /* half-widths of a rotated box: |R| h */
+        e = V(fabs(R.m[0][0]) * b->p[0] + fabs(R.m[0][1]) * b->p[1] + fabs(R.m[0][2]) * b->p[2],
+              fabs(R.m[1][0]) * b->p[0] + fabs(R.m[1][1]) * b->p[1] + fabs(R.m[1][2]) * b->p[2],
+              fabs(R.m[2][0]) * b->p[0] + fabs(R.m[2][1]) * b->p[1] + fabs(R.m[2][2]) * b->p[2]);
+    } else { /* capsule: segment +- l z_local, then +- r */
+        v3 ax = mcol(&R, 2);
+        double l = b->p[1], r = b->p[0];
+        e = V(fabs(ax.x) * l + r, fabs(ax.y) * l + r, fabs(ax.z) * l + r);
+    }
+    e = add(e, V(half_margin, half_margin, half_margin));
+    *lo = sub(b->x, e); *hi = add(b->x, e);
+}
+
+static int joint_connected(const Env* e, int i, int j) {
+    for (int k = 0; k < e->nj; k++) {
+        int p = e->joints[k].parent, c = e->joints[k].child;
+        if ((p == i && c == j) || (p == j && c == i)) return 1;
+    }
+    return 0;
+}
+
+static void broadphase(const oracle_world* w, Env* e) {
+    e->npairs = 0;
+    for (int i = 0; i < e->nb; i++) {
+        for (int j = i + 1; j < e->nb; j++) {
+            const Body* A = &e->bodies[i]; const Body* B = &e->bodies[j];
+            e->cnt[OC_PAIRS_TESTED]++;
+            if (!A->dyn && !B->dyn) continue;
+            if (!((A->group & B->mask) && (B->group & A->mask))) continue;
+            if (joint_connected(e, i, j)) continue;
+            int overlap = 1;
+            if (A->type != OR_PLANE && B->type != OR_PLANE) {
+                v3 la, ha, lb, hb;
+                aabb(A, 0.5 * w->margin, &la, &ha);
+                aabb(B, 0.5 * w->margin, &lb, &hb);
+                overlap = la.x <= hb.x && lb.x <= ha.x && la.y <= hb.y && lb.y <= ha.y &&
+                          la.z <= hb.z && lb.z <= ha.z;
+            }
+            if (!overlap) continue;
+            if (e->npairs >= w->pair_cap) { e->status |= OR_ST_PAIR_OVERFLOW; continue; }
+            e->pairs[e->npairs][0] = i; e->pairs[e->npairs][1] = j;
+            e->npairs++;
+        }
+    }
+    e->cnt[OC_PAIRS_CANDIDATE] += e->npairs;
+}
+
+/* ------------------------------------------------------------------------- */
+/* narrowphase                                                                */
+/* Convention: A is the lower shape rank (sphere < capsule < box < plane),    */
+/* the lower index on equal ranks; n points from B toward A;                  */
+/* d = n.(cA - cB) (< 0: penetration); a point is kept iff d < margin.       */
+/* ------------------------------------------------------------------------- */
+typedef struct { v3 cA, cB, n; double d; } Cand;
+typedef struct { int n; Cand c[8]; } CandSet;
+
+typedef struct { v3 x; m3 R; qt q; int type; double p[3]; } Shape;
+
+static Shape shape_of(const Body* b) {
+    Shape s; s.x = b->x; s.q = b->q; s.R = qmat(b->q); s.type = b->type;
+    s.p[0] = b->p[0]; s.p[1] = b->p[1]; s.p[2] = b->p[2];
+    return s;
+}
+
+static void push(CandSet* cs, v3 cA, v3 cB, v3 n, double d) {
+    if (cs->n < 8) { Cand* c = &cs->c[cs->n++]; c->cA = cA; c->cB = cB; c->n = n; c->d = d; }
+}
+
+/* two spheres (centres a, b; radii ra, rb); n = +z when centres coincide */
+static void sphere_pair(CandSet* cs, v3 a, double ra, v3 b, double rb) {
+    v3 dl = sub(a, b);
+    double dist = norm(dl);
+    v3 n = dist < 1e-9 ? V(0, 0, 1) : scl(dl, 1.0 / dist);
+    push(cs, sub(a, scl(n, ra)), add(b, scl(n, rb)), n, dist - ra - rb);
+}
+
+/* closest point to p on segment [s0, s1] (clamped projection) */
+static v3 closest_on_segment(v3 p, v3 s0, v3 s1) {
+    v3 d = sub(s1, s0);
+    double dd = dot(d, d);
+    double t = dd > 0 ? clampd(dot(sub(p, s0), d) / dd, 0.0, 1.0) : 0.0;
+    return add(s0, scl(d, t));
+}
+
+/* closest points of segments p0+s d1 and q0+t d2 (Ericson 2005, 5.1.9), with
+ * the denominator |d1|^2|d2|^2 - (d1.d2)^2 written as |d1 x d2|^2 */
+static void closest_segments(v3 p0, v3 p1, v3 q0, v3 q1, v3* cp, v3* cq) {
+    v3 d1 = sub(p1, p0), d2 = sub(q1, q0), r = sub(p0, q0);
+    double a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+    double s, t;
+    if (a <= 1e-18 && e <= 1e-18) { s = t = 0.0; }
+    else if (a <= 1e-18) { s = 0.0; t = clampd(f / e, 0.0, 1.0); }
+    else {
+        double c = dot(d1, r);
+        if (e <= 1e-18) { t = 0.0; s = clampd(-c / a, 0.0, 1.0); }
+        else {
+            double b = dot(d1, d2);
+            v3 cr = cross(d1, d2);
+            double denom = dot(cr, cr);
+            s = denom > 0.0 ? clampd((b * f - c * e) / denom, 0.0, 1.0) : 0.0;
+            t = (b * s + f) / e;
+            if (t < 0.0) { t = 0.0; s = clampd(-c / a, 0.0, 1.0); }
+            else if (t > 1.0) { t = 1.0; s = clampd((b - c) / a, 0.0, 1.0); }
+        }
+    }
+    *cp = add(p0, scl(d1, s));
+    *cq = add(q0, scl(d2, t));
+}
+
+static void capsule_ends(const Shape* s, v3* e0, v3* e1) {
+    v3 ax = mcol(&s->R, 2);
+    *e0 = sub(s->x, scl(ax, s->p[1]));
+    *e1 = add(s->x, scl(ax, s->p[1]));
+}
+
+/* sphere - sphere */
+static void np_ss(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e; (void)m;
+    sphere_pair(cs, A->x, A->p[0], B->x, B->p[0]);
+}
+
+/* sphere - plane */
+static void np_sp(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e; (void)m;
+    v3 N = mcol(&B->R, 2);
+    double dist = dot(N, sub(A->x, B->x));
+    push(cs, sub(A->x, scl(N, A->p[0])), sub(A->x, scl(N, dist)), N, dist - A->p[0]);
+}
+
+/* sphere - capsule */
+static void np_sc(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e; (void)m;
+    v3 b0, b1;
+    capsule_ends(B, &b0, &b1);
+    v3 q = closest_on_segment(A->x, b0, b1);
+    sphere_pair(cs, A->x, A->p[0], q, B->p[0]);
+}
+
+/* sphere - box: clamp the centre into the box; if inside, leave through the
+ * face of least penetration (lowest axis, + before - on ties) */
+static void np_sb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)m;
+    double r = A->p[0];
+    v3 c = mtv(&B->R, sub(A->x, B->x));
+    double h[3] = {B->p[0], B->p[1], B->p[2]};
+    double cc[3] = {c.x, c.y, c.z};
+    int inside = fabs(cc[0]) <= h[0] && fabs(cc[1]) <= h[1] && fabs(cc[2]) <= h[2];
+    for (int i = 0; i < 3; i++) tie(e, fabs(cc[i]), h[i]);
+    if (!inside) {
+        double q[3];
+        for (int i = 0; i < 3; i++) q[i] = clampd(cc[i], -h[i], h[i]);
+        v3 ql = V(q[0], q[1], q[2]);
+        v3 dl = sub(c, ql);
+        double dist = norm(dl);
+        v3 nl = dist > 0 ? scl(dl, 1.0 / dist) : V(0, 0, 1);
+        v3 n = mv(&B->R, nl);
+        v3 cB = add(B->x, mv(&B->R, ql));
+        push(cs, sub(A->x, scl(n, r)), cB, n, dist - r);
+    } else {
+        int bi = 0; double bs = 1.0; double best = 1e300;
+        for (int i = 0; i < 3; i++) {
+            for (int sgn = 1; sgn >= -1; sgn -= 2) {
+                double depth = h[i] - sgn * cc[i];
+                if (depth < best) { best = depth; bi = i; bs = sgn; }
+            }
+        }
+        v3 nl = scl(unit_axis(bi), bs);
+        v3 ql = with_comp(c, bi, bs * h[bi]);
+        v3 n = mv(&B->R, nl);
+        push(cs, sub(A->x, scl(n, r)), add(B->x, mv(&B->R, ql)), n, -best - r);
+    }
+}
+
+/* capsule - plane: both segment ends */
+static void np_cp(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e; (void)m;
+    v3 N = mcol(&B->R, 2);
+    v3 ends[2];
+    capsule_ends(A, &ends[0], &ends[1]);
+    for (int k = 0; k < 2; k++) {
+        double dist = dot(N, sub(ends[k], B->x));
+        push(cs, sub(ends[k], scl(N, A->p[0])), sub(ends[k], scl(N, dist)), N, dist - A->p[0]);
+    }
+}
+
+/* capsule - capsule: near-parallel overlapping axes give two points at the
+ * ends of the overlap interval, otherwise the closest points of the segments */
+static void np_cc(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)m;
+    v3 a0, a1, b0, b1;
+    capsule_ends(A, &a0, &a1);
+    capsule_ends(B, &b0, &b1);
+    v3 dA = sub(a1, a0), dB = sub(b1, b0);
+    double la = norm(dA), lb = norm(dB);
+    double cr = norm(cross(dA, dB));
+    tie_w(e, cr, 1e-3 * la * lb, TIE_DIR * la * lb);
+    if (la > 0 && lb > 0 && cr < 1e-3 * la * lb) {
+        v3 u = scl(dA, 1.0 / la);
+        double t0 = dot(sub(b0, a0), u), t1 = dot(sub(b1, a0), u);
+        double lo = fmax(0.0, fmin(t0, t1)), hi = fmin(la, fmax(t0, t1));
+        if (lo <= hi) {
+            tie_w(e, hi - lo, 1e-6, 1e-7);
+            int cnt = (hi - lo) < 1e-6 ? 1 : 2;
+            double xs[2] = {lo, hi};
+            for (int k = 0; k < cnt; k++) {
+                v3 pa = add(a0, scl(u, xs[k]));
+                v3 pb = closest_on_segment(pa, b0, b1);
+                sphere_pair(cs, pa, A->p[0], pb, B->p[0]);
+            }
+            return;
+        }
+    }
+    v3 pa, pb;
+    closest_segments(a0, a1, b0, b1, &pa, &pb);
+    sphere_pair(cs, pa, A->p[0], pb, B->p[0]);
+}
+
+/* segment - box exact closest points in the box frame: the squared distance
+ * along the segment is convex and piecewise quadratic between the parameters
+ * where a coordinate crosses a slab face; minimise on each piece. */
+static double segment_box_closest(v3 s0, v3 u, const double h[3], double* tbest) {
+    double ts[8]; int nt = 0;
+    ts[nt++] = 0.0; ts[nt++] = 1.0;
+    double s0c[3] = {s0.x, s0.y, s0.z}, uc[3] = {u.x, u.y, u.z};
+    for (int j = 0; j < 3; j++) {
+        if (uc[j] == 0.0) continue;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            double t = (sg * h[j] - s0c[j]) / uc[j];
+            if (t > 0.0 && t < 1.0) ts[nt++] = t;
+        }
+    }
+    for (int i = 1; i < nt; i++) { /* insertion sort */
+        double x = ts[i]; int k = i - 1;
+        while (k >= 0 && ts[k] > x) { ts[k + 1] = ts[k]; k--; }
+        ts[k + 1] = x;
+    }
+    double best = 1e300; double bt = 0.0;
+    for (int i = 0; i + 1 < nt; i++) {
+        double ta = ts[i], tb = ts[i + 1];
+        double tm = 0.5 * (ta + tb);
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < 3; j++) {
+            double x = s0c[j] + tm * uc[j];
+            double cj = x > h[j] ? h[j] : (x < -h[j] ? -h[j] : x);
+            if (cj != x) { num += (s0c[j] - cj) * uc[j]; den += uc[j] * uc[j]; }
+        }
+        double cand[3] = {ta, tb, den > 0.0 ? clampd(-num / den, ta, tb) : ta};
+        for (int k = 0; k < 3; k++) {
+            double t = cand[k], f = 0.0;
+            for (int j = 0; j < 3; j++) {
+                double x = s0c[j] + t * uc[j];
+                double cj = x > h[j] ? h[j] : (x < -h[j] ? -h[j] : x);
+                f += (x - cj) * (x - cj);
+            }
+            if (f < best) { best = f; bt = t; }
+        }
+    }
+    *tbest = bt;
+    return sqrt(best);
+}
+
+/* capsule - box: SAT over the 3 box faces and the 3 crosses of box edges with
+ * the segment, in the box frame.  Face case clips the segment to the face's
+ * side slabs (<= 2 points); edge case gives one point. */
+static void np_cb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    double r = A->p[0];
+    v3 a0, a1;
+    capsule_ends(A, &a0, &a1);
+    v3 s0 = mtv(&B->R, sub(a0, B->x)), s1 = mtv(&B->R, sub(a1, B->x));
+    v3 u = sub(s1, s0);
+    v3 mid = scl(add(s0, s1), 0.5);
+    double h[3] = {B->p[0], B->p[1], B->p[2]};
+    double ul = norm(u);
+    v3 uh = ul > 0 ? scl(u, 1.0 / ul) : V(0, 0, 0);
+    double sep[6]; v3 ax[6]; int valid[6];
+    for (int i = 0; i < 6; i++) {
+        v3 L;
+        valid[i] = 1;
+        if (i < 3) L = unit_axis(i);
+        else {
+            v3 c = cross(unit_axis(i - 3), uh);
+            double cn = norm(c);
+            tie_w(e, cn, 1e-5, TIE_DIR);
+            if (cn < 1e-5) { valid[i] = 0; sep[i] = -1e300; continue; }
+            L = scl(c, 1.0 / cn);
+        }
+        if (dot(mid, L) < 0) L = neg(L);
+        double hb = h[0] * fabs(L.x) + h[1] * fabs(L.y) + h[2] * fabs(L.z);
+        double p0 = dot(s0, L), p1 = dot(s1, L);
+        sep[i] = fmin(p0, p1) - hb - r;
+        ax[i] = L;
+    }
+    double maxsep = -1e300;
+    for (int i = 0; i < 6; i++) if (valid[i] && sep[i] > maxsep) maxsep = sep[i];
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
+    int bf = 0;
+    for (int i = 1; i < 3; i++) if (sep[i] > sep[bf]) bf = i;
+    int be = -1;
+    for (int i = 3; i < 6; i++) if (valid[i] && (be < 0 || sep[i] > sep[be])) be = i;
+    if (be >= 0) tie(e, sep[be], sep[bf] + 1e-4);
+    if (be >= 0 && sep[be] > sep[bf] + 1e-4) {
+        /* edge case: the box edge parallel to e_i at the support toward L */
+        v3 L = ax[be];
+        int i = be - 3;
+        double c[3];
+        for (int k = 0; k < 3; k++) c[k] = (comp(L, k) >= 0 ? 1.0 : -1.0) * h[k];
+        v3 q0 = V(c[0], c[1], c[2]), q1 = q0;
+        q0 = with_comp(q0, i, -h[i]); q1 = with_comp(q1, i, h[i]);
+        v3 ps, pe;
+        closest_segments(s0, s1, q0, q1, &ps, &pe);
+        v3 n = mv(&B->R, L);
+        v3 cA = add(B->x, mv(&B->R, sub(ps, scl(L, r))));
+        v3 cB = add(B->x, mv(&B->R, pe));
+        push(cs, cA, cB, n, dot(L, sub(ps, pe)) - r);
+        return;
+    }
+    /* face case on axis bf, oriented sigma */
+    int k = bf;
+    double sigma = comp(ax[k], k) >= 0 ? 1.0 : -1.0;
+    double tlo = 0.0, thi = 1.0; int empty = 0;
+    for (int j = 0; j < 3; j++) {
+        if (j == k) continue;
+        double sj = comp(s0, j), uj = comp(u, j);
+        if (uj == 0.0) { if (fabs(sj) > h[j]) empty = 1; continue; }
+        double ta = (-h[j] - sj) / uj, tb = (h[j] - sj) / uj;
+        tlo = fmax(tlo, fmin(ta, tb)); thi = fmin(thi, fmax(ta, tb));
+    }
+    if (tlo > thi) empty = 1;
+    v3 nl = scl(unit_axis(k), sigma);
+    v3 n = mv(&B->R, nl);
+    if (!empty) {
+        double ts[2] = {tlo, thi};
+        int cnt = tlo == thi ? 1 : 2;
+        for (int a = 0; a < cnt; a++) {
+            v3 q = add(s0, scl(u, ts[a]));
+            double dist = sigma * comp(q, k) - h[k];
+            v3 qb = with_comp(q, k, sigma * h[k]);
+            v3 qa = sub(q, scl(nl, r));
+            push(cs, add(B->x, mv(&B->R, qa)), add(B->x, mv(&B->R, qb)), n, dist - r);
+        }
+        return;
+    }
+    /* the segment misses the face's slab: one point from the exact closest
+     * points of segment and box */
+    double t;
+    double dist = segment_box_closest(s0, u, h, &t);
+    v3 q = add(s0, scl(u, t));
+    v3 qb = V(clampd(q.x, -h[0], h[0]), clampd(q.y, -h[1], h[1]), clampd(q.z, -h[2], h[2]));
+    v3 dl = sub(q, qb);
+    v3 nn = dist > 1e-12 ? scl(dl, 1.0 / dist) : nl;
+    v3 nw = mv(&B->R, nn);
+    push(cs, add(B->x, mv(&B->R, sub(q, scl(nn, r)))), add(B->x, mv(&B->R, qb)), nw, dist - r);
+}
+
+/* box - plane: the 8 vertices, bit0/1/2 of the index choose +-hx/hy/hz */
+static void np_bp(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e; (void)m;
+    v3 N = mcol(&B->R, 2);
+    for (int i = 0; i < 8; i++) {
+        v3 lv = V((i & 1) ? A->p[0] : -A->p[0], (i & 2) ? A->p[1] : -A->p[1],
+                  (i & 4) ? A->p[2] : -A->p[2]);
+        v3 v = add(A->x, mv(&A->R, lv));
+        double dist = dot(N, sub(v, B->x));
+        push(cs, v, sub(v, scl(N, dist)), N, dist);
+    }
+}
+
+/* Sutherland-Hodgman against dir.(x - c) <= hh */
+static int clip_plane(const v3* in, int nin, v3* out, v3 dir, v3 c, double hh, Env* e) {
+    int nout = 0;
+    if (nin == 0) return 0;
+    v3 prev = in[nin - 1];
+    double fp = dot(dir, sub(prev, c)) - hh;
+    for (int i = 0; i < nin; i++) {
+        v3 cur = in[i];
+        double fc = dot(dir, sub(cur, c)) - hh;
+        tie(e, fc, 0.0);
+        if (fc <= 0.0) {
+            if (fp > 0.0) out[nout++] = add(prev, scl(sub(cur, prev), fp / (fp - fc)));
+            out[nout++] = cur;
+        } else if (fp <= 0.0) {
+            out[nout++] = add(prev, scl(sub(cur, prev), fp / (fp - fc)));
+        }
+        prev = cur; fp = fc;
+    }
+    return nout;
+}
+
+/* box - box: SAT over 15 axes (A faces, B faces, A_i x B_j row-major),
+ * face case with incident-face clipping, or one edge-edge point */
+static void np_bb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    v3 a[3], b[3];
+    for (int i = 0; i < 3; i++) { a[i] = mcol(&A->R, i); b[i] = mcol(&B->R, i); }
+    const double* hA = A->p; const double* hB = B->p;
+    v3 dl = sub(A->x, B->x);
+    double sep[15]; v3 ax[15]; int valid[15];
+    for (int k = 0; k < 15; k++) {
+        v3 L;
+        valid[k] = 1;
+        if (k < 3) L = a[k];
+        else if (k < 6) L = b[k - 3];
+        else {
+            v3 c = cross(a[(k - 6) / 3], b[(k - 6) % 3]);
+            double cn = norm(c);
+            tie_w(e, cn, 1e-5, TIE_DIR);
+            if (cn < 1e-5) { valid[k] = 0; sep[k] = -1e300; continue; }
+            L = scl(c, 1.0 / cn);
+        }
+        if (dot(dl, L) < 0) L = neg(L);
+        double ra = hA[0] * fabs(dot(a[0], L)) + hA[1] * fabs(dot(a[1], L)) + hA[2] * fabs(dot(a[2], L));
+        double rb = hB[0] * fabs(dot(b[0], L)) + hB[1] * fabs(dot(b[1], L)) + hB[2] * fabs(dot(b[2], L));
+        sep[k] = dot(dl, L) - ra - rb;
+        ax[k] = L;
+    }
+    double maxsep = -1e300;
+    for (int k = 0; k < 15; k++) if (valid[k] && sep[k] > maxsep) maxsep = sep[k];
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
+    int fa = 0, fb = 3, be = -1;
+    for (int k = 1; k < 3; k++) if (sep[k] > sep[fa]) fa = k;
+    for (int k = 4; k < 6; k++) if (sep[k] > sep[fb]) fb = k;
+    for (int k = 6; k < 15; k++) if (valid[k] && (be < 0 || sep[k] > sep[be])) be = k;
+    double sf = fmax(sep[fa], sep[fb]);
+    if (be >= 0) tie(e, sep[be], sf + 1e-4);
+    if (be >= 0 && sep[be] > sf + 1e-4) {
+        v3 L = ax[be];
+        int i = (be - 6) / 3, j = (be - 6) % 3;
+        /* A's edge parallel to a_i at A's support toward -L; B's toward +L */
+        v3 ca = A->x, cb = B->x;
+        for (int k = 0; k < 3; k++) {
+            if (k != i) ca = add(ca, scl(a[k], (dot(a[k], L) > 0 ? -1.0 : 1.0) * hA[k]));
+            if (k != j) cb = add(cb, scl(b[k], (dot(b[k], L) >= 0 ? 1.0 : -1.0) * hB[k]));
+        }
+        v3 pa, pb;
+        closest_segments(sub(ca, scl(a[i], hA[i])), add(ca, scl(a[i], hA[i])),
+                         sub(cb, scl(b[j], hB[j])), add(cb, scl(b[j], hB[j])), &pa, &pb);
+        push(cs, pa, pb, L, dot(L, sub(pa, pb)));
+        return;
+    }
+    tie(e, sep[fb], sep[fa] + 1e-4);
+    int refB = sep[fb] > sep[fa] + 1e-4;
+    const Shape* Rf = refB ? B : A;   /* reference box */
+    const Shape* In = refB ? A : B;   /* incident box */
+    int k = refB ? fb - 3 : fa;
+    v3 n = ax[refB ? fb : fa];                    /* B -> A */
+    v3 nref = refB ? n : neg(n);                  /* outward normal of the reference face */
+    v3 r[3], ic[3];
+    for (int t = 0; t < 3; t++) { r[t] = mcol(&Rf->R, t); ic[t] = mcol(&In->R, t); }
+    v3 cref = add(Rf->x, scl(nref, Rf->p[k]));
+    int ju = (k + 1) % 3, jv = (k + 2) % 3;
+    v3 uu = r[ju], vv = r[jv];
+    double hu = Rf->p[ju], hv = Rf->p[jv];
+    /* incident face: minimal dot(face normal, nref); order +x,-x,+y,-y,+z,-z */
+    int fi = 0; double fs = 1.0, best = 1e300, second = 1e300;
+    for (int t = 0; t < 3; t++) {
+        for (int sg = 1; sg >= -1; sg -= 2) {
+            double dd = sg * dot(ic[t], nref);
+            if (dd < best) { second = best; best = dd; fi = t; fs = sg; }
+            else if (dd < second) second = dd;
+        }
+    }
+    tie(e, best, second);
+    int i1 = (fi + 1) % 3, i2 = (fi + 2) % 3;
+    v3 fc = add(In->x, scl(ic[fi], fs * In->p[fi]));
+    v3 e1 = scl(ic[i1], In->p[i1]), e2 = scl(ic[i2], In->p[i2]);
+    v3 poly[8], tmp[8];
+    poly[0] = add(add(fc, e1), e2);
+    poly[1] = add(sub(fc, e1), e2);
+    poly[2] = sub(sub(fc, e1), e2);
+    poly[3] = sub(add(fc, e1), e2);
+    int np = 4;
+    np = clip_plane(poly, np, tmp, uu, cref, hu, e);
+    np = clip_plane(tmp, np, poly, neg(uu), cref, hu, e);
+    np = clip_plane(poly, np, tmp, vv, cref, hv, e);
+    np = clip_plane(tmp, np, poly, neg(vv), cref, hv, e);
+    for (int t = 0; t < np; t++) {
+        v3 x = poly[t];
+        double dist = dot(nref, sub(x, cref));
+        v3 xp = sub(x, scl(nref, dist));
+        if (refB) push(cs, x, xp, n, dist);
+        else push(cs, xp, x, n, dist);
+    }
+}
+
+/* reduce > 4 candidates to 4, selection order p1..p4 (positions: cB) */
+static int reduce4(Env* e, const Cand* c, int n, int* sel) {
+    int used[8] = {0};
+    int i1 = 0;
+    for (int k = 1; k < n; k++) if (c[k].d < c[i1].d) i1 = k;
+    for (int k = 0; k < n; k++) if (k != i1) tie(e, c[k].d, c[i1].d);
+    used[i1] = 1;
+    double best, second; int i2 = -1;
+    best = -1.0; second = -1.0;
+    for (int k = 0; k < n; k++) {
+        if (used[k]) continue;
+        double s = dot(sub(c[k].cB, c[i1].cB), sub(c[k].cB, c[i1].cB));
+        if (s > best) { second = best; best = s; i2 = k; } else if (s > second) second = s;
+    }
+    tie(e, best, second);
+    used[i2] = 1;
+    v3 e12 = sub(c[i2].cB, c[i1].cB);
+    int i3 = -1; best = -1.0; second = -1.0;
+    for (int k = 0; k < n; k++) {
+        if (used[k]) continue;
+        double s = norm(cross(e12, sub(c[k].cB, c[i1].cB)));
+        if (s > best) { second = best; best = s; i3 = k; } else if (s > second) second = s;
+    }
+    tie(e, best, second);
+    used[i3] = 1;
+    int i4 = -1; best = -1.0; second = -1.0;
+    v3 P1 = c[i1].cB, P2 = c[i2].cB, P3 = c[i3].cB;
+    for (int k = 0; k < n; k++) {
+        if (used[k]) continue;
+        v3 P = c[k].cB;
+        double s = norm(cross(sub(P2, P1), sub(P, P1))) + norm(cross(sub(P3, P2), sub(P, P2))) +
+                   norm(cross(sub(P1, P3), sub(P, P3)));
+        if (s > best) { second = best; best = s; i4 = k; } else if (s > second) second = s;
+    }
+    tie(e, best, second);
+    sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
+    return 4;
+}
+
+/* Narrowphase of the ordered pair (A, B); returns kept points in `out`.
+ * *margin_tie is set when a candidate's d lies within 1e-5 of the margin. */
+static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, int* margin_tie) {
+    CandSet cs; cs.n = 0;
+    int ta = A->type, tb = B->type;
+    int slot = -1;
+    if (ta == OR_SPHERE && tb == OR_SPHERE) { np_ss(e, A, B, m, &cs); slot = OC_NP_SS; }
+    else if (ta == OR_SPHERE && tb == OR_CAPSULE) { np_sc(e, A, B, m, &cs); slot = OC_NP_SC; }
+    else if (ta == OR_SPHERE && tb == OR_BOX) { np_sb(e, A, B, m, &cs); slot = OC_NP_SB; }
+    else if (ta == OR_SPHERE && tb == OR_PLANE) { np_sp(e, A, B, m, &cs); slot = OC_NP_SP; }
+    else if (ta == OR_CAPSULE && tb == OR_CAPSULE) { np_cc(e, A, B, m, &cs); slot = OC_NP_CC; }
+    else if (ta == OR_CAPSULE && tb == OR_BOX) { np_cb(e, A, B, m, &cs); slot = OC_NP_CB; }
+    else if (ta == OR_CAPSULE && tb == OR_PLANE) { np_cp(e, A, B, m, &cs); slot = OC_NP_CP; }
+    else if (ta == OR_BOX && tb == OR_BOX) { np_bb(e, A, B, m, &cs); slot = OC_NP_BB; }
+    else if (ta == OR_BOX && tb == OR_PLANE) { np_bp(e, A, B, m, &cs); slot = OC_NP_BP; }
+    if (slot >= 0) e->cnt[slot]++;
+    Cand kept[8]; int nk = 0;
+    *margin_tie = 0;
+    for (int i = 0; i < cs.n; i++) {
+        if (fabs(cs.c[i].d - m) < TIE_EPS) { *margin_tie = 1; e->ties++; }
+        if (cs.c[i].d < m) kept[nk++] = cs.c[i];
+    }
+    if (nk <= 4) {
+        for (int i = 0; i < nk; i++) out[i] = kept[i];
+        return nk;
+    }
+    int sel[4];
+    reduce4(e, kept, nk, sel);
+    for (int i = 0; i < 4; i++) out[i] = kept[sel[i]];
+    return 4;
+}
+
+static void narrowphase(const oracle_world* w, Env* e) {
+    e->nman = 0; e->ntie = 0;
+    int total = 0, stop = 0;
+    for (int p = 0; p < e->npairs; p++) {
+        int i = e->pairs[p][0], j = e->pairs[p][1];
+        const Body* Bi = &e->bodies[i]; const Body* Bj = &e->bodies[j];
+        /* order by shape rank, then index */
+        int a = i, b = j;
+        if (Bj->type < Bi->type) { a = j; b = i; }
+        Shape A = shape_of(&e->bodies[a]), B = shape_of(&e->bodies[b]);
+        Cand pts[4]; int mt;
+        int np = collide(e, &A, &B, w->margin, pts, &mt);
+        if (mt) { e->tiepairs[e->ntie][0] = i; e->tiepairs[e->ntie][1] = j; e->ntie++; }
+        if (np == 0) continue;
+        /* keep the longest prefix of manifolds (pair order) within capacity */
+        if (stop || total + np > w->contact_cap) { stop = 1; e->status |= OR_ST_CONTACT_OVERFLOW; continue; }
+        Manifold* M = &e->man[e->nman++];
+        M->a = a; M->b = b; M->np = np;
+        const Body* BA = &e->bodies[a]; const Body* BB = &e->bodies[b];
+        m3 RA = qmat(BA->q), RB = qmat(BB->q);
+        for (int k = 0; k < np; k++) {
+            CPoint* c = &M->p[k];
+            c->cA = pts[k].cA; c->cB = pts[k].cB; c->n = pts[k].n; c->d = pts[k].d;
+            c->aA = mtv(&RA, sub(c->cA, BA->x));   /* body-local anchors */
+            c->aB = mtv(&RB, sub(c->cB, BB->x));
+        }
+        total += np;
+    }
+    e->cnt[OC_CONTACT_POINTS] += total;
+}
+
+/* ------------------------------------------------------------------------- */
+/* colouring                                                                  */
+/* ------------------------------------------------------------------------- */
+int oracle_color(int n, const int* a, const int* b, const int* dyn, int* colors) {
+    /* used[body] bitmask of colours already taken by constraints on it */
+    int maxb = 0;
+    for (int i = 0; i < n; i++) { if (a[i] + 1 > maxb) maxb = a[i] + 1; if (b[i] + 1 > maxb) maxb = b[i] + 1; }
+    uint64_t* used = (uint64_t*)calloc((size_t)(maxb > 0 ? maxb : 1), sizeof(uint64_t));
+    int ncol = 0, overflow = 0;
+    for (int i = 0; i < n; i++) {
+        uint64_t mask = 0;
+        int da = a[i] >= 0 && dyn[a[i]], db = b[i] >= 0 && dyn[b[i]];
+        if (da) mask |= used[a[i]];
+        if (db) mask |= used[b[i]];
+        int c = 0;
+        while (c < 64 && (mask >> c) & 1ull) c++;
+        if (c == 64) { colors[i] = -1; overflow = 1; continue; }
+        colors[i] = c;
+        if (da) used[a[i]] |= 1ull << c;
+        if (db) used[b[i]] |= 1ull << c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(used);
+    return overflow ? -1 : ncol;
+}
+
+static void build_constraints(Env* e) {
+    int n = e->nj + e->nman;
+    e->ncons = n;
+    int* a = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int* b = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int* dyn = (int*)malloc(sizeof(int) * (e->nb > 0 ? e->nb : 1));
+    int* col = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int i = 0; i < e->nb; i++) dyn[i] = e->bodies[i].dyn;
+    int row = 0;
+    for (int i = 0; i < e->nj; i++) {
+        Constraint* c = &e->cons[i];
+        c->kind = 0; c->idx = i; c->a = e->joints[i].parent; c->b = e->joints[i].child;
+        c->row0 = row; c->nrows = 8; row += 8;
+        a[i] = c->a; b[i] = c->b;
+    }
+    for (int m = 0; m < e->nman; m++) {
+        Constraint* c = &e->cons[e->nj + m];
+        c->kind = 1; c->idx = m; c->a = e->man[m].a; c->b = e->man[m].b;
+        c->row0 = row; c->nrows = 3 * e->man[m].np; row += c->nrows;
+        a[e->nj + m] = c->a; b[e->nj + m] = c->b;
+    }
+    e->nrows = row;
+    int nc = oracle_color(n, a, b, dyn, col);
+    if (nc < 0) {
+        e->status |= OR_ST_COLOR_OVERFLOW;
+        nc = 64;
+    }
+    e->ncolors = nc;
+    for (int i = 0; i < n; i++) e->cons[i].color = col[i];
+    /* solve order: by colour, constraint-list order inside a colour;
+     * constraints left without a colour are not solved */
+    int k = 0;
+    for (int c = 0; c < nc; c++)
+        for (int i = 0; i < n; i++)
+            if (e->cons[i].color == c) e->order[k++] = i;
+    for (int i = k; i < n; i++) e->order[i] = -1;
+    e->cnt[OC_CONSTRAINTS] += n;
+    e->cnt[OC_COLORS] += nc;
+    free(a); free(b); free(dyn); free(col);
+}
+
+/* ------------------------------------------------------------------------- */
+/* constraint rows (per substep)                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct { v3 x; qt q; m3 R; v3 v, w; double im; m3 iI; int dyn; } BodyView;
+
+static BodyView view(const Env* e, int i) {
+    BodyView bv;
+    if (i < 0) {
+        bv.x = V(0, 0, 0); bv.q = Q(0, 0, 0, 1); bv.R = qmat(bv.q);
+        bv.v = V(0, 0, 0); bv.w = V(0, 0, 0); bv.im = 0.0; bv.dyn = 0;
+        memset(&bv.iI, 0, sizeof(bv.iI));
+        return bv;
+    }
+    const Body* b = &e->bodies[i];
+    bv.x = b->x; bv.q = b->q; bv.R = qmat(b->q); bv.v = b->v; bv.w = b->w;
+    bv.im = b->inv_mass; bv.iI = b->invIw; bv.dyn = b->dyn;
+    return bv;
+}
+
+static void world_inertia(Body* b) {
+    memset(&b->invIw, 0, sizeof(b->invIw));
+    if (!b->dyn) return;
+    m3 R = qmat(b->q);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++) s += R.m[i][k] * b->inv_I[k] * R.m[j][k];
+            b->invIw.m[i][j] = s;
+        }
+}
+
+static double row_k(const BodyView* A, const BodyView* B, const Row* r) {
+    return (A->im + B->im) * dot(r->lin, r->lin) + dot(r->angA, mv(&A->iI, r->angA)) +
+           dot(r->angB, mv(&B->iI, r->angB));
+}
+
+static void set_point_row(Row* r, v3 e, v3 rA, v3 rB) {
+    r->lin = e; r->angA = cross(rA, e); r->angB = cross(e, rB);
+}
+static void set_ang_row(Row* r, v3 jA, v3 jB) {
+    r->lin = V(0, 0, 0); r->angA = jA; r->angB = jB;
+}
+
+/* tangent basis: t1 = normalize(n x e_k), k = basis_axis(n), t2 = n x t1 */
+static void tangents(v3 n, v3* t1, v3* t2) {
+    int k = basis_axis(n);
+    v3 c = cross(n, unit_axis(k));
+    *t1 = scl(c, 1.0 / norm(c));
+    *t2 = cross(n, *t1);
+}
+
+/* joint kinematics shared by prep and relax: anchors, axis and coordinate */
+typedef struct { v3 wP, wC, rP, rC, a, c; double phi; qt qPw, qCw; } JointGeo;
+
+static double wrap_pi(double x) {
+    while (x > M_PI) x -= 2.0 * M_PI;
+    while (x <= -M_PI) x += 2.0 * M_PI;
+    return x;
+}
+
+static JointGeo joint_geo(const Joint* j, const BodyView* P, const BodyView* C) {
+    JointGeo g;
+    g.rP = mv(&P->R, j->fpP); g.rC = mv(&C->R, j->fpC);
+    g.wP = add(P->x, g.rP); g.wC = add(C->x, g.rC);
+    g.qPw = qmul(P->q, j->fqP); g.qCw = qmul(C->q, j->fqC);
+    g.a = qrot(g.qPw, V(1, 0, 0));
+    g.c = qrot(g.qCw, V(1, 0, 0));
+    if (j->type == OR_REVOLUTE) {
+        qt qrel = qmul(qconj(g.qPw), g.qCw);
+        g.phi = wrap_pi(2.0 * atan2(qrel.x, qrel.w));
+    } else {
+        g.phi = dot(g.a, sub(g.wC, g.wP));
+    }
+    return g;
+}
+
+static double contact_bias(double d, double h, double vmax) {
+    return d >= 0.0 ? d / h : fmax(d / h, -vmax);
+}
+
+static void prep(const oracle_world* w, Env* e, double h) {
+    for (int i = 0; i < e->nb; i++) { world_inertia(&e->bodies[i]); if (e->bodies[i].dyn) e->cnt[OC_BODY_INERTIA]++; }
+    for (int ci = 0; ci < e->ncons; ci++) {
+        Constraint* c = &e->cons[ci];
+        BodyView A = view(e, c->a), B = view(e, c->b);
+        Row* R = &e->rows[c->row0];
+        if (c->kind == 1) {
+            Manifold* M = &e->man[c->idx];
+            double mu = 0.5 * (e->bodies[M->a].mu + e->bodies[M->b].mu);
+            for (int k = 0; k < M->np; k++) {
+                CPoint* p = &M->p[k];
+                v3 rA = mv(&A.R, p->aA), rB = mv(&B.R, p->aB);
+                double d = dot(p->n, sub(add(A.x, rA), add(B.x, rB)));
+                v3 t1, t2;
+                tangents(p->n, &t1, &t2);
+                tie_basis(e, p->n);
+                Row* rn = &R[k];
+                rn->kind = RK_NORMAL; set_point_row(rn, p->n, rA, rB);
+                rn->bias = contact_bias(d, h, w->vmax); rn->pt = k;
+                Row* rt1 = &R[M->np + 2 * k];
+                Row* rt2 = &R[M->np + 2 * k + 1];
+                rt1->kind = rt2->kind = RK_FRICTION;
+                set_point_row(rt1, t1, rA, rB); set_point_row(rt2, t2, rA, rB);
+                rt1->bias = rt2->bias = 0.0;
+                rt1->partner = rt2->partner = c->row0 + k;
+                rt1->mu = rt2->mu = mu;
+            }
+            for (int r = 0; r < c->nrows; r++) {
+                R[r].a = c->a; R[r].b = c->b;
+                R[r].k = row_k(&A, &B, &R[r]);
+                if (R[r].kind == RK_NORMAL) R[r].mu = mu;
+            }
+        } else {
+            Joint* j = &e->joints[c->idx];
+            JointGeo g = joint_geo(j, &A, &B);
+            int r = 0;
+            if (j->type == OR_REVOLUTE) {
+                for (int t = 0; t < 3; t++) {
+                    v3 ee = unit_axis(t);
+                    R[r].kind = RK_EQ; set_point_row(&R[r], ee, g.rP, g.rC);
+                    R[r].bias = dot(ee, sub(g.wP, g.wC)) / h; r++;
+                }
+                int k = basis_axis(g.a);
+                tie_basis(e, g.a);
+                v3 b1 = cross(g.a, unit_axis(k)); b1 = scl(b1, 1.0 / norm(b1));
+                v3 b2 = cross(g.a, b1);
+                v3 axc = cross(g.a, g.c);
+                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b1), b1); R[r].bias = dot(b1, axc) / h; r++;
+                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b2), b2); R[r].bias = dot(b2, axc) / h; r++;
+                R[r].kind = RK_LIMIT; set_ang_row(&R[r], neg(g.a), g.a); R[r].pt = 0;
+                R[r].bias = contact_bias(g.phi - j->lower, h, w->vmax); r++;
+                R[r].kind = RK_LIMIT; set_ang_row(&R[r], g.a, neg(g.a)); R[r].pt = 1;
+                R[r].bias = contact_bias(j->upper - g.phi, h, w->vmax); r++;
+                R[r].kind = RK_DRIVE; set_ang_row(&R[r], neg(g.a), g.a);
+            } else {
+                int k = basis_axis(g.a);
+                tie_basis(e, g.a);
+                v3 b1 = cross(g.a, unit_axis(k)); b1 = scl(b1, 1.0 / norm(b1));
+                v3 b2 = cross(g.a, b1);
+                R[r].kind = RK_EQ; set_point_row(&R[r], b1, g.rP, g.rC);
+                R[r].bias = dot(b1, sub(g.wP, g.wC)) / h; r++;
+                R[r].kind = RK_EQ; set_point_row(&R[r], b2, g.rP, g.rC);
+                R[r].bias = dot(b2, sub(g.wP, g.wC)) / h; r++;
+                qt qe = qmul(g.qPw, qconj(g.qCw));
+                double sg = qe.w >= 0.0 ? 1.0 : -1.0;
+                v3 th = V(2.0 * sg * qe.x, 2.0 * sg * qe.y, 2.0 * sg * qe.z);
+                for (int t = 0; t < 3; t++) {
+                    v3 ee = unit_axis(t);
+                    R[r].kind = RK_EQ; set_ang_row(&R[r], ee, neg(ee)); R[r].bias = comp(th, t) / h; r++;
+                }
+                R[r].kind = RK_LIMIT; set_point_row(&R[r], neg(g.a), g.rP, g.rC); R[r].pt = 0;
+                R[r].bias = contact_bias(g.phi - j->lower, h, w->vmax); r++;
+                R[r].kind = RK_LIMIT; set_point_row(&R[r], g.a, g.rP, g.rC); R[r].pt = 1;
+                R[r].bias = contact_bias(j->upper - g.phi, h, w->vmax); r++;
+                R[r].kind = RK_DRIVE; set_point_row(&R[r], neg(g.a), g.rP, g.rC);
+            }
+            /* PD drive as an implicit spring-damper (soft constraint):
+             * gamma = 1/(h (h kp + kd)), b = kp C / (h kp + kd) */
+            Row* dr = &R[7];
+            double den = h * j->kp + j->kd;
+            double C = g.phi - j->target;
+            if (den > 0.0) { dr->gamma = 1.0 / (h * den); dr->bias = j->kp * C / den; }
+            else { dr->gamma = 0.0; dr->bias = 0.0; }
+            for (int t = 0; t < 8; t++) {
+                R[t].a = c->a; R[t].b = c->b;
+                R[t].k = row_k(&A, &B, &R[t]);
+            }
+            if (den <= 0.0) dr->k = 0.0;  /* no drive */
+        }
+        e->cnt[OC_ROWS_PREP] += c->nrows;
+    }
+}
+
+/* relax bias: contact normals and limits from the integrated poses */
+static void relax_bias(Env* e, double h) {
+    for (int ci = 0; ci < e->ncons; ci++) {
+        Constraint* c = &e->cons[ci];
+        BodyView A = view(e, c->a), B = view(e, c->b);
+        Row* R = &e->rows[c->row0];
+        if (c->kind == 1) {
+            Manifold* M = &e->man[c->idx];
+            for (int k = 0; k < M->np; k++) {
+                CPoint* p = &M->p[k];
+                v3 rA = mv(&A.R, p->aA), rB = mv(&B.R, p->aB);
+                double d = dot(p->n, sub(add(A.x, rA), add(B.x, rB)));
+                R[k].relax_bias = fmax(d, 0.0) / h;
+            }
+            for (int r = M->np; r < c->nrows; r++) R[r].relax_bias = 0.0;
+        } else {
+            Joint* j = &e->joints[c->idx];
+            JointGeo g = joint_geo(j, &A, &B);
+            for (int r = 0; r < 8; r++) R[r].relax_bias = 0.0;
+            R[5].relax_bias = fmax(g.phi - j->lower, 0.0) / h;
+            R[6].relax_bias = fmax(j->upper - g.phi, 0.0) / h;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* solver                                                                     */
+/* ------------------------------------------------------------------------- */
+static void apply_impulse(Env* e, const Row* r, double dl) {
+    if (r->a >= 0 && e->bodies[r->a].dyn) {
+        Body* A = &e->bodies[r->a];
+        A->v = add(A->v, scl(r->lin, A->inv_mass * dl));
+        A->w = add(A->w, scl(mv(&A->invIw, r->angA), dl));
+    }
+    if (r->b >= 0 && e->bodies[r->b].dyn) {
+        Body* B = &e->bodies[r->b];
+        B->v = sub(B->v, scl(r->lin, B->inv_mass * dl));
+        B->w = add(B->w, scl(mv(&B->invIw, r->angB), dl));
+    }
+}
+
+static double row_jv(const Env* e, const Row* r) {
+    v3 va = V(0, 0, 0), wa = V(0, 0, 0), vb = V(0, 0, 0), wb = V(0, 0, 0);
+    if (r->a >= 0) { va = e->bodies[r->a].v; wa = e->bodies[r->a].w; }
+    if (r->b >= 0) { vb = e->bodies[r->b].v; wb = e->bodies[r->b].w; }
+    return dot(r->lin, sub(va, vb)) + dot(r->angA, wa) + dot(r->angB, wb);
+}
+
+static void solve_row(Env* e, Row* r, int relax) {
+    if (r->k <= 0.0) return;               /* inert row (no dynamic body) */
+    if (relax && r->kind == RK_DRIVE) return;
+    double jv = row_jv(e, r);
+    double old = r->lambda, nl;
+    int ndyn = (r->a >= 0 && e->bodies[r->a].dyn) + (r->b >= 0 && e->bodies[r->b].dyn);
+    e->cnt[ndyn == 2 ? OC_ROW_SOLVE_2DYN : OC_ROW_SOLVE_1DYN]++;
+    double bias = relax ? r->relax_bias : r->bias;
+    switch (r->kind) {
+    case RK_NORMAL:
+    case RK_LIMIT:
+        nl = fmax(old - (jv + bias) / r->k, 0.0);
+        break;
+    case RK_FRICTION: {
+        double lim = r->mu * e->rows[r->partner].lambda;
+        nl = clampd(old - jv / r->k, -lim, lim);
+        break;
+    }
+    case RK_EQ:
+        nl = old - (jv + (relax ? 0.0 : r->bias)) / r->k;
+        break;
+    default: /* RK_DRIVE: dl = -(Jv + b + gamma lambda) / (1/m + gamma) */
+        nl = old - (jv + r->bias + r->gamma * old) / (r->k + r->gamma);
+        break;
+    }
+    r->lambda = nl;
+    apply_impulse(e, r, nl - old);
+}
+
+static void sweep(Env* e, int relax) {
+    for (int o = 0; o < e->ncons; o++) {
+        int ci = e->order[o];
+        if (ci < 0) break;
+        Constraint* c = &e->cons[ci];
+        for (int r = 0; r < c->nrows; r++) solve_row(e, &e->rows[c->row0 + r], relax);
+    }
+}
+
+static void warm_start(Env* e) {
+    for (int o = 0; o < e->ncons; o++) {
+        int ci = e->order[o];
+        if (ci < 0) break;
+        Constraint* c = &e->cons[ci];
+        for (int r = 0; r < c->nrows; r++) {
+            Row* row = &e->rows[c->row0 + r];
+            if (row->k <= 0.0) continue;
+            apply_impulse(e, row, row->lambda);
+            e->cnt[OC_WARM_APPLY]++;
+        }
+    }
+}
+
+/* symplectic Euler: x += h v; q <- normalize(q + h/2 [w,0] q) */
+static void integrate(Env* e, double h) {
+    for (int i = 0; i < e->nb; i++) {
+        Body* b = &e->bodies[i];
+        if (!b->dyn) continue;
+        b->x = add(b->x, scl(b->v, h));
+        qt wq = qmul(Q(b->w.x, b->w.y, b->w.z, 0.0), b->q);
+        b->q = qnormalize(Q(b->q.x + 0.5 * h * wq.x, b->q.y + 0.5 * h * wq.y,
+                            b->q.z + 0.5 * h * wq.z, b->q.w + 0.5 * h * wq.w));
+        e->cnt[OC_BODY_INTEGRATE]++;
+    }
+}
+
+static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
+    /* drive targets: NaN keeps the previous target */
+    if (act) for (int j = 0; j < e->nj && j < A; j++) if (!isnan(act[j])) e->joints[j].target = act[j];
+    broadphase(w, e);
+    narrowphase(w, e);
+    build_constraints(e);
+    for (int r = 0; r < e->nrows; r++) memset(&e->rows[r], 0, sizeof(Row));
+    double h = w->dt / w->substeps;
+    for (int s = 0; s < w->substeps; s++) {
+        for (int i = 0; i < e->nb; i++)
+            if (e->bodies[i].dyn) e->bodies[i].v = add(e->bodies[i].v, scl(w->g, h));
+        prep(w, e, h);
+        warm_start(e);
+        for (int it = 0; it < w->pos_iters; it++) sweep(e, 0);
+        integrate(e, h);
+        relax_bias(e, h);
+        for (int it = 0; it < w->vel_iters; it++) sweep(e, 1);
+    }
+    e->cnt[OC_STEPS]++;
+}
+
+/* ------------------------------------------------------------------------- */
+/* world API                                                                  */
+/* ------------------------------------------------------------------------- */
+oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
+                            const long long* joint_off, const double* joints, const double* params) {
+    oracle_world* w = (oracle_world*)calloc(1, sizeof(oracle_world));
+    w->E = n_envs;
+    w->dt = params[0]; w->substeps = (int)params[1]; w->pos_iters = (int)params[2];
+    w->vel_iters = (int)params[3]; w->g = V(params[4], params[5], params[6]);
+    w->margin = params[7]; w->vmax = params[8];
+    w->contact_cap = (int)params[9]; w->pair_cap = (int)params[10];
+    w->nb_total = (int)body_off[n_envs]; w->nj_total = (int)joint_off[n_envs];
+    w->body_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
+    w->joint_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
+    memcpy(w->body_off, body_off, sizeof(long long) * (n_envs + 1));
+    memcpy(w->joint_off, joint_off, sizeof(long long) * (n_envs + 1));
+    w->envs = (Env*)calloc((size_t)(n_envs > 0 ? n_envs : 1), sizeof(Env));
+    for (int ei = 0; ei < n_envs; ei++) {
+        Env* e = &w->envs[ei];
+        e->nb = (int)(body_off[ei + 1] - body_off[ei]);
+        e->nj = (int)(joint_off[ei + 1] - joint_off[ei]);
+        e->bodies = (Body*)calloc((size_t)(e->nb > 0 ? e->nb : 1), sizeof(Body));
+        e->joints = (Joint*)calloc((size_t)(e->nj > 0 ? e->nj : 1), sizeof(Joint));
+        for (int i = 0; i < e->nb; i++) body_from_desc(&e->bodies[i], bodies + 22 * (body_off[ei] + i));
+        for (int i = 0; i < e->nj; i++) {
+            const double* d = joints + 22 * (joint_off[ei] + i);
+            Joint* j = &e->joints[i];
+            j->type = (int)d[0]; j->parent = (int)d[1]; j->child = (int)d[2];
+            j->fpP = V(d[3], d[4], d[5]); j->fqP = qnormalize(Q(d[6], d[7], d[8], d[9]));
+            j->fpC = V(d[10], d[11], d[12]); j->fqC = qnormalize(Q(d[13], d[14], d[15], d[16]));
+            j->lower = d[17]; j->upper = d[18]; j->kp = d[19]; j->kd = d[20]; j->target = d[21];
+        }
+        int maxp = e->nb * (e->nb - 1) / 2;
+        int pc = w->pair_cap < maxp ? w->pair_cap : maxp;
+        e->pairs = malloc(sizeof(int[2]) * (size_t)(pc > 0 ? pc : 1));
+        e->tiepairs = malloc(sizeof(int[2]) * (size_t)(maxp > 0 ? maxp : 1));
+        e->man = (Manifold*)malloc(sizeof(Manifold) * (size_t)(pc > 0 ? pc : 1));
+        int nc = e->nj + pc;
+        e->cons = (Constraint*)malloc(sizeof(Constraint) * (size_t)(nc > 0 ? nc : 1));
+        e->order = (int*)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+        int nr = 8 * e->nj + 3 * w->contact_cap;
+        e->rows = (Row*)calloc((size_t)(nr > 0 ? nr : 1), sizeof(Row));
+    }
+    return w;
+}
+
+void oracle_destroy(oracle_world* w) {
+    if (!w) return;
+    for (int i = 0; i < w->E; i++) {
+        Env* e = &w->envs[i];
+        free(e->bodies); free(e->joints); free(e->pairs); free(e->tiepairs); free(e->man);
+        free(e->cons); free(e->order); free(e->rows);
+    }
+    free(w->envs); free(w->body_off); free(w->joint_off); free(w);
+}
+
+typedef struct { oracle_world* w; const double* act; int A, n_steps, e0, e1; } Job;
+
+static void* run_job(void* p) {
+    Job* j = (Job*)p;
+    for (int k = 0; k < j->n_steps; k++)
+        for (int ei = j->e0; ei < j->e1; ei++)
+            env_step(j->w, &j->w->envs[ei],
+                     j->act ? j->act + ((size_t)k * j->w->E + ei) * j->A : NULL, j->A);
+    return NULL;
+}
+
+int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int n_threads) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > w->E) n_threads = w->E > 0 ? w->E : 1;
+    Job* jobs = (Job*)calloc((size_t)n_threads, sizeof(Job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; t++) {
+        jobs[t].w = w; jobs[t].act = actions; jobs[t].A = A; jobs[t].n_steps = n_steps;
+        jobs[t].e0 = (int)((long long)w->E * t / n_threads);
+        jobs[t].e1 = (int)((long long)w->E * (t + 1) / n_threads);
+    }
+    if (n_threads == 1) run_job(&jobs[0]);
+    else {
+        for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, run_job, &jobs[t]);
+        for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+    }
+    free(jobs); free(th);
+    return 0;
+}
+
+void oracle_get_state(const oracle_world* w, double* out) {
+    for (int ei = 0; ei < w->E; ei++) {
+        const Env* e = &w->envs[ei];
+        for (int i = 0; i < e->nb; i++) {
+            const Body* b = &e->bodies[i];
+            double* o = out + 13 * (w->body_off[ei] + i);
+            o[0] = b->x.x; o[1] = b->x.y; o[2] = b->x.z;
+            o[3] = b->q.x; o[4] = b->q.y; o[5] = b->q.z; o[6] = b->q.w;
+            o[7] = b->v.x; o[8] = b->v.y; o[9] = b->v.z;
+            o[10] = b->w.x; o[11] = b->w.y; o[12] = b->w.z;
+        }
+    }
+}
+
+void oracle_set_state(oracle_world* w, const double* in) {
+    for (int ei = 0; ei < w->E; ei++) {
+        Env* e = &w->envs[ei];
+        for (int i = 0; i < e->nb; i++) {
+            Body* b = &e->bodies[i];
+            const double* o = in + 13 * (w->body_off[ei] + i);
+            b->x = V(o[0], o[1], o[2]);
+            b->q = Q(o[3], o[4], o[5], o[6]);
+            if (b->dyn) { b->v = V(o[7], o[8], o[9]); b->w = V(o[10], o[11], o[12]); }
+        }
+    }
+}
+
+void oracle_get_targets(const oracle_world* w, double* out) {
+    for (int ei = 0; ei < w->E; ei++) {
+        const Env* e = &w->envs[ei];
+        for (int j = 0; j < e->nj; j++) out[w->joint_off[ei] + j] = e->joints[j].target;
+    }
+}
+
+unsigned oracle_env_status(const oracle_world* w, int env) { return w->envs[env].status; }
+long long oracle_env_ties(const oracle_world* w, int env) { return w->envs[env].ties; }
+
+void oracle_counters(const oracle_world* w, long long* out) {
+    for (int k = 0; k < OC_NUM; k++) out[k] = 0;
+    for (int ei = 0; ei < w->E; ei++)
+        for (int k = 0; k < OC_NUM; k++) out[k] += w->envs[ei].cnt[k];
+}
+
+int oracle_get_manifolds(const oracle_world* w, int env, int cap, int* pairs, int* npts, double* pts) {
+    const Env* e = &w->envs[env];
+    for (int m = 0; m < e->nman && m < cap; m++) {
+        const Manifold* M = &e->man[m];
+        pairs[2 * m] = M->a; pairs[2 * m + 1] = M->b; npts[m] = M->np;
+        for (int k = 0; k < 4; k++) {
+            double* o = pts + (size_t)40 * m + 10 * k;
+            if (k >= M->np) { memset(o, 0, sizeof(double) * 10); continue; }
+            const CPoint* c = &M->p[k];
+            o[0] = c->cA.x; o[1] = c->cA.y; o[2] = c->cA.z;
+            o[3] = c->cB.x; o[4] = c->cB.y; o[5] = c->cB.z;
+            o[6] = c->n.x; o[7] = c->n.y; o[8] = c->n.z; o[9] = c->d;
+        }
+    }
+    return e->nman;
+}
+
+int oracle_get_margin_ties(const oracle_world* w, int env, int cap, int* pairs) {
+    const Env* e = &w->envs[env];
+    for (int i = 0; i < e->ntie && i < cap; i++) { pairs[2 * i] = e->tiepairs[i][0]; pairs[2 * i + 1] = e->tiepairs[i][1]; }
+    return e->ntie;
+}
+
+int oracle_get_colors(const oracle_world* w, int env, int cap, int* colors) {
+    const Env* e = &w->envs[env];
+    for (int i = 0; i < e->ncons && i < cap; i++) colors[i] = e->cons[i].color;
+    return e->ncons;
+}
+
+int oracle_get_rows(const oracle_world* w, int env, int cap, double* out) {
+    const Env* e = &w->envs[env];
+    for (int r = 0; r < e->nrows && r < cap; r++) {
+        const Row* R = &e->rows[r];
+        double* o = out + 16 * r;
+        o[0] = R->a; o[1] = R->b; o[2] = R->kind;
+        o[3] = R->lin.x; o[4] = R->lin.y; o[5] = R->lin.z;
+        o[6] = R->angA.x; o[7] = R->angA.y; o[8] = R->angA.z;
+        o[9] = R->angB.x; o[10] = R->angB.y; o[11] = R->angB.z;
+        o[12] = R->k; o[13] = R->bias; o[14] = R->lambda; o[15] = R->mu;
+    }
+    return e->nrows;
+}
+
+int oracle_collide(const double* da, const double* db, double margin, double* out) {
+    Env e; memset(&e, 0, sizeof(e));
+    Body A, B;
+    body_from_desc(&A, da); body_from_desc(&B, db);
+    Shape SA = shape_of(&A), SB = shape_of(&B);
+    Cand pts[4]; int mt;
+    int n = collide(&e, &SA, &SB, margin, pts, &mt);
+    for (int k = 0; k < n; k++) {
+        double* o = out + 10 * k;
+        o[0] = pts[k].cA.x; o[1] = pts[k].cA.y; o[2] = pts[k].cA.z;
+        o[3] = pts[k].cB.x; o[4] = pts[k].cB.y; o[5] = pts[k].cB.z;
+        o[6] = pts[k].n.x; o[7] = pts[k].n.y; o[8] = pts[k].n.z; o[9] = pts[k].d;
+    }
+    return n;
+}

@@ -1,0 +1,106 @@
+/*
+ * FP64 CPU oracle of the batched rigid-body step -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg may load this library.  It shares no code, header or constant table
+ * with the CUDA path; it consumes the same seeded scene descriptors.
+ *
+ * The step is the one described in the paper's GPU-parallel simulation
+ * (Sec. "GPU Parallelized Simulation and Rendering", Appendix "Simulation and
+ * Rendering Benchmarking", Setup: simulation frequency and solver position /
+ * velocity iteration counts) with the PD joint-target drive of Appendix
+ * "Controller / Action Space".  The paper delegates the physics to an engine
+ * and states no algorithm, so each stage follows a named published method:
+ *   broadphase       brute-force AABB overlap with a contact margin
+ *   narrowphase      closest points and SAT (Ericson 2005, Real-Time Collision
+ *                    Detection, 4.4, 5.1.9) with Sutherland-Hodgman clipping
+ *   colouring        greedy graph colouring over the constraint list
+ *   solver           substepped sequential impulses with soft drives
+ *                    (Catto 2005; Catto 2011 soft constraints; Macklin et al.
+ *                    2019 "Small Steps"), Coulomb friction pyramid
+ *   integration      symplectic Euler with quaternion renormalisation
+ *
+ * Descriptor rows are doubles (converted losslessly from the float32 scene):
+ *   body  [22]: type, p0, p1, p2, mass, pos[3], quat[4] (x,y,z,w), linvel[3],
+ *               angvel[3], mu, restitution, group, mask
+ *   joint [22]: type, parent, child, parent_frame[7] (pos, quat), child_frame[7],
+ *               lower, upper, kp, kd, target0
+ *   params[11]: dt, substeps, pos_iters, vel_iters, gx, gy, gz, margin,
+ *               max_depen_vel, contact_capacity, pair_capacity
+ */
+#ifndef MS_ORACLE_H
+#define MS_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oracle_world oracle_world;
+
+enum { OR_SPHERE = 0, OR_CAPSULE = 1, OR_BOX = 2, OR_PLANE = 3 };
+enum { OR_REVOLUTE = 0, OR_PRISMATIC = 1 };
+enum { OR_ST_PAIR_OVERFLOW = 1, OR_ST_CONTACT_OVERFLOW = 2, OR_ST_COLOR_OVERFLOW = 4 };
+
+/* Counter slots returned by oracle_counters (sums over envs and steps). */
+enum {
+    OC_STEPS = 0, OC_PAIRS_TESTED, OC_PAIRS_CANDIDATE,
+    OC_NP_SS, OC_NP_SC, OC_NP_SB, OC_NP_SP, OC_NP_CC, OC_NP_CB, OC_NP_CP, OC_NP_BB, OC_NP_BP,
+    OC_CONTACT_POINTS, OC_CONSTRAINTS, OC_ROWS_PREP, OC_ROW_SOLVE_2DYN, OC_ROW_SOLVE_1DYN,
+    OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NUM
+};
+
+oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
+                            const long long* joint_off, const double* joints,
+                            const double* params);
+void oracle_destroy(oracle_world* w);
+
+/* Advance every env n_steps steps.  actions: [n_steps][n_envs][A] drive
+ * targets (NaN keeps the previous target) or NULL.  n_threads >= 1 splits the
+ * envs statically over pthreads.  Returns 0. */
+int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int n_threads);
+
+/* State of all bodies, [n_bodies][13] = pos[3], quat[4], linvel[3], angvel[3]. */
+void oracle_get_state(const oracle_world* w, double* out);
+/* Overwrite the state of all bodies (same layout); used for restart tests. */
+void oracle_set_state(oracle_world* w, const double* in);
+/* Current drive targets [n_joints]. */
+void oracle_get_targets(const oracle_world* w, double* out);
+
+unsigned oracle_env_status(const oracle_world* w, int env);
+/* Number of discrete decisions of the env (since create) whose deciding
+ * quantity was within 1e-5 of its threshold. */
+long long oracle_env_ties(const oracle_world* w, int env);
+void oracle_counters(const oracle_world* w, long long* out /* [OC_NUM] */);
+
+/* Contact manifolds of the env's last narrowphase, in pair order.
+ * pairs [cap][2] (env-local body indices a, b), npts [cap],
+ * pts [cap][4][10] = cA[3], cB[3], n[3], d.  Returns the manifold count
+ * (at most cap are written). */
+int oracle_get_manifolds(const oracle_world* w, int env, int cap, int* pairs, int* npts, double* pts);
+/* Pairs whose any candidate point had |d - margin| < 1e-5 in the last
+ * narrowphase (excluded from exact pair-set comparison).  Returns count. */
+int oracle_get_margin_ties(const oracle_world* w, int env, int cap, int* pairs);
+/* Colour of each constraint (joints, then manifolds) of the last step. */
+int oracle_get_colors(const oracle_world* w, int env, int cap, int* colors);
+/* Rows of the env's last substep in constraint-list order:
+ * [cap][16] = a, b, kind, lin[3], angA[3], angB[3], k, bias, lambda, mu. */
+int oracle_get_rows(const oracle_world* w, int env, int cap, double* rows);
+
+/* Narrowphase of one pair in isolation.  bodyA, bodyB are descriptor rows
+ * (A must be the lower shape rank, or the lower index for equal ranks).
+ * out [8][10] as in oracle_get_manifolds.  Returns the point count after
+ * the margin filter and the reduction to 4. */
+int oracle_collide(const double* bodyA, const double* bodyB, double margin, double* out);
+
+/* Greedy colouring of a constraint list given as body pairs (-1 = static);
+ * dyn[i] != 0 marks body i dynamic.  Returns the colour count or -1 on
+ * overflow of 64 colours. */
+int oracle_color(int n_cons, const int* a, const int* b, const int* dyn, int* colors);
+
+/* Body-frame diagonal inertia of a descriptor row (mass > 0). */
+void oracle_inertia(const double* body, double* out3);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
