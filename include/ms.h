@@ -1,0 +1,244 @@
+/*
+ * ms.h -- C ABI of the B300 batched rigid-body step (libmsim.so).
+ *
+ * The library advances thousands of independent manipulation environments
+ * ("envs") per call on one GPU: the GPU-parallel physics step the paper's
+ * simulator runs for every parallel env (Sec. "GPU Parallelized Simulation
+ * and Rendering"; heterogeneous envs with different object counts and DOF,
+ * Sec. "Heterogeneous GPU Simulation"), with the drive targets of its PD
+ * joint-position controller (Appendix "Controller / Action Space") and the
+ * simulation-frequency / solver-iteration knobs of its benchmark setup
+ * (Appendix "Simulation and Rendering Benchmarking", Setup).  Each call runs,
+ * per env and step: broadphase, primitive narrowphase into <= 4-point
+ * manifolds, greedy constraint colouring, then per substep constraint prep,
+ * a fixed-iteration Gauss-Seidel / TGS solve with a Coulomb friction pyramid
+ * and soft PD drives, and symplectic integration.
+ *
+ * Conventions: z-up world, SI units, quaternions (x, y, z, w), capsule axis
+ * and plane normal along local +z, joint axis along the joint frame's +x.
+ *
+ * Errors: every function returns ms_status.  Argument errors are detected
+ * synchronously and nothing is enqueued.  Conditions found on the device
+ * (capacity overflow, non-finite state) set per-env status bits that
+ * ms_sync() returns; device code never traps or asserts.  ms_last_error()
+ * returns a thread-local description of the last failure.
+ *
+ * Threading: a batch may be used from one host thread at a time.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ms_status;
+enum {
+    MS_OK = 0,
+    MS_ERR_INVALID_ARG = 1,
+    MS_ERR_OOM = 2,
+    MS_ERR_CUDA = 3,
+    MS_ERR_CONTACT_OVERFLOW = 4,
+    MS_ERR_COLOR_OVERFLOW = 5,
+    MS_ERR_NAN = 6,
+    MS_ERR_TIMEOUT = 7,
+    MS_ERR_NOT_ADMITTED = 8,
+    MS_ERR_BUSY = 9,
+    MS_ERR_PAIR_OVERFLOW = 10,
+    MS_ERR_NOT_FOUND = 11
+};
+
+/* per-env device status bits (ms_sync env_status) */
+enum {
+    MS_ENV_PAIR_OVERFLOW = 1u,      /* more broadphase pairs than pair_capacity   */
+    MS_ENV_CONTACT_OVERFLOW = 2u,   /* more contact points than contact_capacity  */
+    MS_ENV_COLOR_OVERFLOW = 4u,     /* a constraint found none of 64 colours free */
+    MS_ENV_NAN = 8u                 /* non-finite state; the env is frozen        */
+};
+
+enum { MS_SPHERE = 0, MS_CAPSULE = 1, MS_BOX = 2, MS_PLANE = 3 };
+enum { MS_REVOLUTE = 0, MS_PRISMATIC = 1 };
+
+/* Body descriptor (84 bytes, no padding).
+ *   p: sphere {r}, capsule {r, half_length}, box {hx, hy, hz}, plane unused.
+ *   mass 0 (and every plane) = static: never moves; its velocities are ignored.
+ *   Two bodies may touch iff (group_a & mask_b) && (group_b & mask_a). */
+typedef struct {
+    int32_t type;
+    float p[3];
+    float mass;
+    float pos[3];
+    float quat[4];
+    float linvel[3];
+    float angvel[3];
+    float mu;
+    float restitution;           /* accepted, not modelled (must be 0 or is ignored) */
+    uint16_t group, mask;
+} ms_body_desc;
+
+/* Joint descriptor (88 bytes).  parent = -1 attaches to the world.  Frames
+ * are (pos[3], quat[4]) in the body's local frame; the joint axis is the
+ * frame's +x.  Limits are [lower, upper] (rad or m).  The drive pulls the
+ * joint coordinate toward its target with stiffness kp and damping kd
+ * (kp = kd = 0: no drive).  target0 is the initial target. */
+typedef struct {
+    int32_t type;
+    int32_t parent, child;
+    float parent_frame[7];
+    float child_frame[7];
+    float lower, upper, kp, kd, target0;
+} ms_joint_desc;
+
+/* One env: its bodies and joints (indices are env-local). */
+typedef struct {
+    int32_t n_bodies, n_joints;
+    const ms_body_desc* bodies;
+    const ms_joint_desc* joints;
+} ms_scene_desc;
+
+/* Solver parameters shared by every env of a batch.
+ *   dt: step length; substeps: h = dt / substeps; pos_iters / vel_iters:
+ *   solver sweeps per substep; margin: contact margin (speculative contacts
+ *   are kept while d < margin); max_depen_vel: cap on the penetration
+ *   recovery speed; pair_capacity / contact_capacity: per-env limits, beyond
+ *   which pairs / manifolds are dropped in order and a status bit is set. */
+typedef struct {
+    float dt;
+    int32_t substeps, pos_iters, vel_iters;
+    float gravity[3];
+    float margin;
+    float max_depen_vel;
+    int32_t contact_capacity;
+    int32_t pair_capacity;
+} ms_sim_params;
+
+typedef struct ms_batch ms_batch;
+
+/* Borrowed device views of a batch's resident state (structure of arrays).
+ * Valid until the next ms_step / ms_step_plain / ms_set_state / ms_destroy.
+ * x, q, v, w: float4 per body (pos | quat xyzw | linvel | angvel; .w of x,
+ * v, w unused).  body_off / joint_off: int32 [n_envs + 1] CSR offsets.
+ * targets: float per joint.  status: uint32 per env. */
+typedef struct {
+    int32_t n_envs, n_bodies, n_joints, max_act;
+    void* x;
+    void* q;
+    void* v;
+    void* w;
+    const int32_t* body_off;
+    const int32_t* joint_off;
+    float* targets;
+    uint32_t* status;
+} ms_state_view;
+
+/* Create a batch of n_envs envs (each up to 64 bodies).  The descriptors are
+ * validated and copied; the caller keeps ownership of descs.  The batch owns
+ * all device memory it allocates on the current device.
+ * Errors: MS_ERR_INVALID_ARG (bad descriptor or parameter; ms_last_error
+ * names the env and field), MS_ERR_OOM, MS_ERR_CUDA. */
+ms_status ms_create_batch(const ms_scene_desc* descs, int n_envs, const ms_sim_params* p,
+                          ms_batch** out);
+
+/* Same, from flat tables: bodies[body_off[E]], joints[joint_off[E]] with
+ * body_off / joint_off int32 [n_envs + 1]. */
+ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_off,
+                               const ms_joint_desc* joints, const int32_t* joint_off,
+                               int n_envs, const ms_sim_params* p, ms_batch** out);
+
+/* Advance every env n_steps steps on `stream` (cudaStream_t; NULL = legacy
+ * default stream) with the batched path: one persistent launch pops envs
+ * from a work queue (longest first) and keeps each env's bodies, contacts
+ * and rows on chip for all n_steps; the launch sequence is captured once per
+ * (n_steps, tuning) in a CUDA graph and replayed.
+ * actions: device float [n_steps][n_envs][A] drive targets (A = the
+ * batch's max joints per env), NaN = keep the previous target; NULL = no
+ * change.  Must stay valid until the stream reaches the step.  Asynchronous:
+ * returns after enqueueing. */
+ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream);
+
+/* Same step through the plain comparison path: one block per env and one
+ * kernel launch per stage (and per solver sweep), state in global memory.
+ * Results are bit-identical to ms_step. */
+ms_status ms_step_plain(ms_batch* b, const float* actions, int n_steps, void* stream);
+
+/* Borrowed device pointers to the resident state (see ms_state_view). */
+ms_status ms_get_state(ms_batch* b, ms_state_view* out);
+
+/* Copy the state as float [n_bodies][13] = pos[3], quat[4], linvel[3],
+ * angvel[3] to dst (dst_kind 0 = host, 1 = device), ordered on `stream`.
+ * A host dst should be pinned for the copy to overlap. */
+ms_status ms_copy_state(ms_batch* b, float* dst, int dst_kind, void* stream);
+
+/* Overwrite the state of the envs whose env_mask byte is non-zero
+ * (env_mask NULL = all envs) from src float [n_bodies][13] (src_kind 0 =
+ * host, 1 = device).  Static bodies keep their pose.  Clears those envs'
+ * status bits.  Used for partial resets and checkpoint restore. */
+ms_status ms_set_state(ms_batch* b, const float* src, int src_kind, const uint8_t* env_mask,
+                       void* stream);
+
+/* Wait for the batch's last stream, then OR the per-env status bits.
+ * env_status (nullable) receives uint32 [n_envs].  Returns MS_OK, or the
+ * error of the first set bit in order pair, contact, colour, NaN. */
+ms_status ms_sync(ms_batch* b, uint32_t* env_status);
+
+/* Free the batch (synchronises its stream).  NULL is accepted. */
+ms_status ms_destroy(ms_batch* b);
+
+/* Thread-local description of the last error, "" if none. */
+const char* ms_last_error(void);
+
+/* ----------------------------------------------------------------------- */
+/* Introspection and tuning                                                */
+/* ----------------------------------------------------------------------- */
+
+/* Record the contact manifolds of every env's last step (off by default;
+ * costs one extra global write per contact).  record = 0 / 1. */
+ms_status ms_set_record_contacts(ms_batch* b, int record);
+
+/* Contact manifolds recorded at env `env`'s last step, in pair order:
+ * pairs int32 [cap][2] (env-local bodies a, b; a is the lower shape rank or
+ * index), npts int32 [cap], pts float [cap][4][10] = cA[3], cB[3], n[3], d
+ * (n points from b toward a, d = n.(cA - cB)).  Host buffers; synchronises.
+ * *count receives the number of manifolds (at most cap are written).
+ * MS_ERR_INVALID_ARG if recording is off. */
+ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t* npts,
+                          float* pts, int* count);
+
+/* Batched-path launch shape.  lanes_per_env in {4, 8, 16, 32}: envs per
+ * warp = 32 / lanes_per_env; warps_per_cta in [1, 16]; rows_in_smem: keep
+ * constraint rows in shared memory (1) or in an L2-resident global slot (0).
+ * Any choice gives bit-identical results. */
+typedef struct {
+    int32_t lanes_per_env;
+    int32_t warps_per_cta;
+    int32_t rows_in_smem;
+    int32_t ctas_per_sm;     /* output of ms_get_tuning: resident CTAs per SM */
+} ms_tuning;
+
+ms_status ms_set_tuning(ms_batch* b, const ms_tuning* t);
+ms_status ms_get_tuning(ms_batch* b, ms_tuning* t);
+
+/* Time each candidate tuning on `n_steps`-step calls (state is saved and
+ * restored around the trials), keep the fastest.  cache_path (nullable): a
+ * JSON file mapping a scene signature to its best tuning; read first, and
+ * updated after tuning.  best (nullable) receives the choice. */
+ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_path, ms_tuning* best, void* stream);
+
+/* Device bytes held by the batch (state, parameters, workspaces). */
+ms_status ms_memory_bytes(ms_batch* b, size_t* bytes);
+
+/* Estimated device bytes of a batch before creating it (for admission). */
+ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* joint_off, int n_envs,
+                            const ms_sim_params* p, size_t* bytes);
+
+/* sizeof(ms_body_desc), sizeof(ms_joint_desc), sizeof(ms_sim_params),
+ * sizeof(ms_state_view), sizeof(ms_tuning): lets bindings check layouts. */
+void ms_abi_sizes(int32_t* out5);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
