@@ -1,0 +1,343 @@
+"""Benchmark of the batched rigid-body step: env-steps/s on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config arm]
+                    [--impl ours|reference] [--n-per-call 1]
+
+A timed "step" is one call of the public entry point ms_step advancing every
+env of the configuration by --n-per-call physics steps (all stages:
+broadphase, narrowphase, colouring, prep, solve, integration).  Inputs are
+the seeded synthetic scenes of scenegen, resident on the GPU; L2 is flushed
+(256 MB write) before every timed step, outside the timed events.  Prints
+one JSON line (rank 0).  Under torchrun every rank runs its own batch of the
+configuration (weak scaling, no collective in the step).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on the host cores for the same configuration and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen  # noqa: E402
+
+METRIC = "env-steps/s on 1 B300, batched vs plain at oracle tol; served p50/p99 latency"
+WORKLOADS = {
+    "arm": "7-DoF capsule arm + 2 prismatic box fingers + cube on a plane, 4096 envs "
+           "(dt 0.01 s, 4 substeps, 8+1 iterations, PD kp 1000 kd 100, targets N(0,0.3) per step)",
+    "small": "plane + 1 box + 3 spheres, 64 envs (dt 0.01 s, 4 substeps, 8+1 iterations)",
+    "clutter": "1-32 boxes/spheres/capsules in a 5-box bin, 16384 envs (dt 0.01 s, 4 substeps, 8+1)",
+    "hand": "16-DoF capsule hand holding a cube, 4096 envs (dt 1/120 s, 8 substeps, 16+1 iterations)",
+}
+
+# FLOP weights per counted operation ("Algorithmic work")
+FLOP_WEIGHTS = {
+    "row_solve_2dyn": 61, "row_solve_1dyn": 31, "rows_prep": 40, "body_inertia": 45,
+    "body_integrate": 40, "warm_apply": 25, "pairs_tested": 10,
+    "np_ss": 20, "np_sc": 40, "np_sb": 60, "np_sp": 15, "np_cc": 120, "np_cb": 300, "np_cp": 30,
+    "np_bb": 1000, "np_bp": 150,
+}
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def algorithmic_flops_per_env_step(name, sample_envs=128, steps=5):
+    """Oracle op counters on a sample of the workload x fixed FLOP weights."""
+    import oracle
+    sc = scenegen.make_scene(name, n_envs=min(sample_envs, scenegen.CONFIG_SIZES[name]))
+    o = oracle.Oracle(sc)
+    o.step(steps, threads=os.cpu_count() or 1)
+    c = o.counters()
+    flops = sum(FLOP_WEIGHTS[k] * c[k] for k in FLOP_WEIGHTS)
+    return flops / (sc.n_envs * steps), c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_cpu_baseline(name, n_envs, steps):
+    """The oracle as it stands, on every host core, on a bounded sample."""
+    import oracle
+    sc = scenegen.make_scene(name, n_envs=n_envs)
+    o = oracle.Oracle(sc)
+    acts = sc.actions(0, steps)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o.step(steps, actions=acts, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_envs * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_envs} envs x {steps} steps of the {name} workload, FP64, {cores} threads "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle on the host cores, same metric.
+    Each timed step advances a bounded sample of the workload by one step."""
+    if rank != 0:
+        return
+    E = scenegen.CONFIG_SIZES[args.config]
+    sample_envs = min(E, 512)
+    time_cpu_baseline(args.config, min(sample_envs, 64), 1)        # warm-up (page-in, build)
+    vals = [time_cpu_baseline(args.config, sample_envs, 1)["value"] for _ in range(args.steps)]
+    v = statistics.median(vals)
+    cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * E / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded scenegen scenes)",
+            "config": {"workload": WORKLOADS[args.config], "n_envs": E, "n_per_call": 1,
+                       "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample_envs} of {E} envs x 1 step per timed step, "
+                                       f"median of {args.steps}, {cores} threads"},
+            "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--config", default="arm", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-per-call", type=int, default=1)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    from paper_2410_00425_b300 import Batch, build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    name = args.config
+    E = scenegen.CONFIG_SIZES[name]
+    sc = scenegen.make_scene(name, seed=None if rank == 0 else 1000 + rank)
+    n = args.n_per_call
+    total_calls = args.warmup + args.steps
+    acts_np = sc.actions(0, n * total_calls)
+    acts = None if acts_np is None else torch.from_numpy(acts_np).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def act(i):
+        return None if acts is None else acts[i * n:(i + 1) * n]
+
+    b = Batch(sc)
+    tuning = None
+    if not args.no_autotune:
+        tuning = b.autotune(n, cache_path=os.path.join(ROOT, "paper_2410_00425_b300", "tuning_cache.json"),
+                            stream=stream)
+    else:
+        tuning = b.tuning()
+    b.close()
+
+    def timed(plain, launches_per_call):
+        bb = Batch(sc)
+        if not plain and tuning:
+            bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup):
+                bb.step(act(i), n, stream=stream, plain=plain)
+        stream.synchronize()
+        times = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))                      # L2 flush, outside the events
+                stream.wait_stream(torch.cuda.current_stream())
+                ev[i][0].record(stream)
+                bb.step(act(args.warmup + i), n, stream=stream, plain=plain)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+        barrier(ws)
+        times = [a.elapsed_time(z) for a, z in ev]
+        code, status = bb.sync()
+        bb.close()
+        return sum(times) / 1e3, times, clk.summary(), code, launches_per_call * args.steps
+
+    t_b, times_b, clocks, code, launches = timed(False, 1)
+    t_b = reduce_max(t_b, ws)
+    value = ws * E * n * args.steps / t_b
+    plain_value = None
+    if not args.no_plain:
+        p = sc.params
+        lp = n * (3 + p["substeps"] * (3 + p["pos_iters"] + p["vel_iters"]) + 1)
+        t_p, _, _, _, _ = timed(True, lp)
+        t_p = reduce_max(t_p, ws)
+        plain_value = ws * E * n * args.steps / t_p
+
+    # e2e: host actions in (pinned), state out to pinned host, every step
+    bb = Batch(sc)
+    if tuning:
+        bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
+    h_act = None if acts_np is None else torch.from_numpy(acts_np).pin_memory()
+    d_act = None if acts is None else torch.empty_like(acts[:n])
+    h_state = torch.empty((bb.NB, 13), dtype=torch.float32).pin_memory()
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            if d_act is not None:
+                d_act.copy_(h_act[i * n:(i + 1) * n], non_blocking=True)
+            bb.step(d_act, n, stream=stream)
+            bb.state_to_host(h_state, stream=stream)
+    stream.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            j = args.warmup + i
+            if d_act is not None:
+                d_act.copy_(h_act[j * n:(j + 1) * n], non_blocking=True)
+            bb.step(d_act, n, stream=stream)
+            bb.state_to_host(h_state, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    t_e = reduce_max(e0.elapsed_time(e1) / 1e3, ws)
+    bb.close()
+    h2d = 0 if d_act is None else d_act.numel() * 4
+    d2h = h_state.numel() * 4
+
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fl, _ = algorithmic_flops_per_env_step(name)
+    kernel_s = statistics.mean(times_b) / 1e3
+    achieved = fl * E * n / kernel_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenegen scenes)",
+        "config": {"workload": WORKLOADS[name], "n_envs": E, "n_per_call": n, "path": "batched",
+                   "tuning": tuning, "l2": "flushed (256 MB write) before every timed step"},
+        "plain_value": plain_value,
+        "batched_over_plain": None if not plain_value else value / plain_value,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                                  f"{sm_max:.0f} MHz (unit counts and max clock)",
+                     "flops_per_env_step": fl},
+        "e2e": {"value": ws * E * n * args.steps / t_e, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "status": code,
+        "device": props.name,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

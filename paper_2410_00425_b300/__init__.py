@@ -1,0 +1,88 @@
+"""B300-native batched rigid-body step (sm_103a CUDA behind the C ABI of
+include/ms.h).
+
+    import torch, scenegen
+    from paper_2410_00425_b300 import Batch
+    b = Batch(scenegen.make_scene("arm"))
+    b.step(actions_cuda_tensor, n_steps=10, stream=torch.cuda.Stream())
+
+``Batch`` only marshals arguments to the library; every stage of the step
+runs in the CUDA kernels of ``libmsim.so``.  There is no CPU fallback:
+constructing a batch without the built library or without a CUDA device
+raises.
+"""
+from __future__ import annotations
+
+from . import _ffi
+from ._ffi import MSError, load  # noqa: F401
+
+
+class Batch:
+    """Owns one ms_batch (all envs of a scene resident on the current GPU)."""
+
+    def __init__(self, scene, record_contacts: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.scene = scene
+        self.E = scene.n_envs
+        self.NB = int(scene.body_off[-1])
+        self.NJ = int(scene.joint_off[-1])
+        self.A = int((scene.joint_off[1:] - scene.joint_off[:-1]).max()) if self.E else 0
+        self.h = _ffi.ms_create_batch_flat(scene.bodies, scene.body_off, scene.joints,
+                                           scene.joint_off, scene.params)
+        if record_contacts:
+            _ffi.ms_set_record_contacts(self.h, True)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _ffi.ms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, actions=None, n_steps: int = 1, stream=None, plain: bool = False):
+        """actions: CUDA float32 tensor [n_steps, E, A] (NaN keeps a target)."""
+        if actions is not None:
+            assert actions.is_cuda and actions.dtype.is_floating_point and actions.is_contiguous()
+            assert tuple(actions.shape) == (n_steps, self.E, self.A), (tuple(actions.shape), (n_steps, self.E, self.A))
+        fn = _ffi.ms_step_plain if plain else _ffi.ms_step
+        fn(self.h, actions, n_steps, stream)
+
+    def state(self, stream=None):
+        """Device copy of the state, float32 [n_bodies, 13]."""
+        import torch
+        out = torch.empty((self.NB, 13), dtype=torch.float32, device="cuda")
+        _ffi.ms_copy_state(self.h, out, 1, stream)
+        return out
+
+    def state_to_host(self, out, stream=None):
+        """Copy the state into a (pinned) host tensor [n_bodies, 13]."""
+        _ffi.ms_copy_state(self.h, out, 0, stream)
+        return out
+
+    def set_state(self, src, env_mask=None, stream=None):
+        kind = 1 if getattr(src, "is_cuda", False) else 0
+        _ffi.ms_set_state(self.h, src, kind, env_mask, stream)
+
+    def sync(self):
+        return _ffi.ms_sync(self.h)
+
+    def contacts(self, env: int, cap: int = 1024):
+        return _ffi.ms_get_contacts(self.h, env, cap)
+
+    def set_tuning(self, lanes_per_env=32, warps_per_cta=4, rows_in_smem=1):
+        _ffi.ms_set_tuning(self.h, lanes_per_env, warps_per_cta, rows_in_smem)
+
+    def tuning(self):
+        return _ffi.ms_get_tuning(self.h)
+
+    def autotune(self, n_steps=1, cache_path=None, stream=None):
+        return _ffi.ms_autotune(self.h, n_steps, cache_path, stream)
+
+    def memory_bytes(self):
+        return _ffi.ms_memory_bytes(self.h)

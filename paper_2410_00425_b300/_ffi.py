@@ -1,0 +1,251 @@
+"""ctypes binding of libmsim.so (include/ms.h): argument marshalling only.
+
+Every function keeps the C name.  Device buffers are passed as torch CUDA
+tensors (their data_ptr) and streams as torch.cuda.Stream (their raw
+handle); nothing here computes any part of the step.  Loading fails loudly
+when the library is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsim.so")
+
+MS_OK = 0
+STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_INVALID_ARG", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA",
+                4: "MS_ERR_CONTACT_OVERFLOW", 5: "MS_ERR_COLOR_OVERFLOW", 6: "MS_ERR_NAN",
+                7: "MS_ERR_TIMEOUT", 8: "MS_ERR_NOT_ADMITTED", 9: "MS_ERR_BUSY",
+                10: "MS_ERR_PAIR_OVERFLOW", 11: "MS_ERR_NOT_FOUND"}
+ENV_PAIR_OVERFLOW, ENV_CONTACT_OVERFLOW, ENV_COLOR_OVERFLOW, ENV_NAN = 1, 2, 4, 8
+
+
+class MSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ms_sim_params(C.Structure):
+    _fields_ = [("dt", C.c_float), ("substeps", C.c_int32), ("pos_iters", C.c_int32),
+                ("vel_iters", C.c_int32), ("gravity", C.c_float * 3), ("margin", C.c_float),
+                ("max_depen_vel", C.c_float), ("contact_capacity", C.c_int32),
+                ("pair_capacity", C.c_int32)]
+
+
+class ms_scene_desc(C.Structure):
+    _fields_ = [("n_bodies", C.c_int32), ("n_joints", C.c_int32),
+                ("bodies", C.c_void_p), ("joints", C.c_void_p)]
+
+
+class ms_state_view(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("n_bodies", C.c_int32), ("n_joints", C.c_int32),
+                ("max_act", C.c_int32), ("x", C.c_void_p), ("q", C.c_void_p), ("v", C.c_void_p),
+                ("w", C.c_void_p), ("body_off", C.c_void_p), ("joint_off", C.c_void_p),
+                ("targets", C.c_void_p), ("status", C.c_void_p)]
+
+
+class ms_tuning(C.Structure):
+    _fields_ = [("lanes_per_env", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("rows_in_smem", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("ms_create_batch", C.c_int, [C.c_void_p, C.c_int, C.POINTER(ms_sim_params), C.POINTER(C.c_void_p)]),
+    ("ms_create_batch_flat", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.POINTER(ms_sim_params), C.POINTER(C.c_void_p)]),
+    ("ms_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_step_plain", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_get_state", C.c_int, [C.c_void_p, C.POINTER(ms_state_view)]),
+    ("ms_copy_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("ms_sync", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("ms_destroy", C.c_int, [C.c_void_p]),
+    ("ms_last_error", C.c_char_p, []),
+    ("ms_set_record_contacts", C.c_int, [C.c_void_p, C.c_int]),
+    ("ms_get_contacts", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.POINTER(C.c_int)]),
+    ("ms_set_tuning", C.c_int, [C.c_void_p, C.POINTER(ms_tuning)]),
+    ("ms_get_tuning", C.c_int, [C.c_void_p, C.POINTER(ms_tuning)]),
+    ("ms_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_char_p, C.POINTER(ms_tuning), C.c_void_p]),
+    ("ms_memory_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("ms_estimate_bytes", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(ms_sim_params),
+                                    C.POINTER(C.c_size_t)]),
+    ("ms_abi_sizes", None, [C.c_void_p]),
+]
+
+EXPORTS = [s[0] for s in _SIGS]
+
+
+def load(path: str = LIB_PATH):
+    """Load libmsim.so; raises if it is missing (build it with
+    ``python -m paper_2410_00425_b300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libmsim.so not built at {path}; run python -m paper_2410_00425_b300.build")
+        lib = C.CDLL(path)
+        for name, res, args in _SIGS:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        sizes = (C.c_int32 * 5)()
+        lib.ms_abi_sizes(sizes)
+        expect = [84, 88, C.sizeof(ms_sim_params), C.sizeof(ms_state_view), C.sizeof(ms_tuning)]
+        if list(sizes) != expect:
+            raise ImportError(f"ABI layout mismatch: library {list(sizes)} vs binding {expect}")
+        _lib = lib
+    return _lib
+
+
+def check(code: int):
+    if code != MS_OK:
+        raise MSError(code, load().ms_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor / numpy array / None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_params(p: dict) -> ms_sim_params:
+    sp = ms_sim_params()
+    sp.dt = p["dt"]; sp.substeps = p["substeps"]; sp.pos_iters = p["pos_iters"]
+    sp.vel_iters = p["vel_iters"]
+    for i in range(3):
+        sp.gravity[i] = p["gravity"][i]
+    sp.margin = p["margin"]; sp.max_depen_vel = p["max_depen_vel"]
+    sp.contact_capacity = p["contact_capacity"]; sp.pair_capacity = p["pair_capacity"]
+    return sp
+
+
+# ---- thin wrappers with the C names -------------------------------------
+def ms_create_batch_flat(bodies: np.ndarray, body_off: np.ndarray, joints: np.ndarray,
+                         joint_off: np.ndarray, params: dict) -> int:
+    L = load()
+    bodies = np.ascontiguousarray(bodies)
+    joints = np.ascontiguousarray(joints)
+    bo = np.ascontiguousarray(body_off, np.int32)
+    jo = np.ascontiguousarray(joint_off, np.int32)
+    out = C.c_void_p()
+    sp = make_params(params)
+    check(L.ms_create_batch_flat(bodies.ctypes.data, bo.ctypes.data,
+                                 joints.ctypes.data if len(joints) else None, jo.ctypes.data,
+                                 len(bo) - 1, C.byref(sp), C.byref(out)))
+    return out.value
+
+
+def ms_create_batch(descs, n_envs: int, params: dict) -> int:
+    """descs: ctypes array of ms_scene_desc."""
+    L = load()
+    out = C.c_void_p()
+    sp = make_params(params)
+    check(L.ms_create_batch(C.cast(descs, C.c_void_p), n_envs, C.byref(sp), C.byref(out)))
+    return out.value
+
+
+def ms_step(b, actions=None, n_steps=1, stream=None):
+    return check(load().ms_step(b, _ptr(actions), n_steps, _stream(stream)))
+
+
+def ms_step_plain(b, actions=None, n_steps=1, stream=None):
+    return check(load().ms_step_plain(b, _ptr(actions), n_steps, _stream(stream)))
+
+
+def ms_get_state(b) -> ms_state_view:
+    v = ms_state_view()
+    check(load().ms_get_state(b, C.byref(v)))
+    return v
+
+
+def ms_copy_state(b, dst, dst_kind, stream=None):
+    return check(load().ms_copy_state(b, _ptr(dst), dst_kind, _stream(stream)))
+
+
+def ms_set_state(b, src, src_kind, env_mask=None, stream=None):
+    m = None if env_mask is None else np.ascontiguousarray(env_mask, np.uint8)
+    return check(load().ms_set_state(b, _ptr(src), src_kind, None if m is None else m.ctypes.data,
+                                     _stream(stream)))
+
+
+def ms_sync(b):
+    """Returns (status code, per-env status bits) without raising."""
+    v = ms_get_state(b)
+    st = np.zeros(v.n_envs, np.uint32)
+    code = load().ms_sync(b, st.ctypes.data)
+    return code, st
+
+
+def ms_destroy(b):
+    return check(load().ms_destroy(b))
+
+
+def ms_last_error() -> str:
+    return load().ms_last_error().decode()
+
+
+def ms_set_record_contacts(b, record=True):
+    return check(load().ms_set_record_contacts(b, int(record)))
+
+
+def ms_get_contacts(b, env, cap=1024):
+    pairs = np.zeros((cap, 2), np.int32)
+    npts = np.zeros(cap, np.int32)
+    pts = np.zeros((cap, 4, 10), np.float32)
+    n = C.c_int()
+    check(load().ms_get_contacts(b, env, cap, pairs.ctypes.data, npts.ctypes.data, pts.ctypes.data,
+                                 C.byref(n)))
+    m = min(n.value, cap)
+    return pairs[:m], npts[:m], pts[:m]
+
+
+def ms_set_tuning(b, lanes_per_env, warps_per_cta, rows_in_smem):
+    t = ms_tuning(lanes_per_env, warps_per_cta, rows_in_smem, 0)
+    return check(load().ms_set_tuning(b, C.byref(t)))
+
+
+def ms_get_tuning(b) -> dict:
+    t = ms_tuning()
+    check(load().ms_get_tuning(b, C.byref(t)))
+    return dict(lanes_per_env=t.lanes_per_env, warps_per_cta=t.warps_per_cta,
+                rows_in_smem=t.rows_in_smem, ctas_per_sm=t.ctas_per_sm)
+
+
+def ms_autotune(b, n_steps=1, cache_path=None, stream=None) -> dict:
+    t = ms_tuning()
+    check(load().ms_autotune(b, n_steps, cache_path.encode() if cache_path else None, C.byref(t),
+                             _stream(stream)))
+    return dict(lanes_per_env=t.lanes_per_env, warps_per_cta=t.warps_per_cta,
+                rows_in_smem=t.rows_in_smem, ctas_per_sm=t.ctas_per_sm)
+
+
+def ms_memory_bytes(b) -> int:
+    n = C.c_size_t()
+    check(load().ms_memory_bytes(b, C.byref(n)))
+    return n.value
+
+
+def ms_estimate_bytes(body_off, joint_off, params: dict) -> int:
+    bo = np.ascontiguousarray(body_off, np.int32)
+    jo = np.ascontiguousarray(joint_off, np.int32)
+    n = C.c_size_t()
+    sp = make_params(params)
+    check(load().ms_estimate_bytes(bo.ctypes.data, jo.ctypes.data, len(bo) - 1, C.byref(sp), C.byref(n)))
+    return n.value

@@ -1,0 +1,789 @@
+// Host side of the C ABI declared in include/ms.h.
+//
+// A batch keeps every env's state resident on the device as a structure of
+// arrays with CSR offsets per env (the paper's data-oriented layout of
+// objects and articulations, Sec. "Heterogeneous GPU Simulation").  ms_step
+// replays a captured CUDA graph of the batched persistent kernel;
+// ms_step_plain launches the per-stage kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/ms.h"
+#include "ms_internal.h"
+
+using namespace ms;
+
+static thread_local std::string g_err;
+
+static ms_status fail(ms_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+    } while (0)
+
+namespace {
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;      // kept alive: the exec's node handles refer to it
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t kernel = nullptr;
+    cudaKernelNodeParams kp{};
+};
+
+struct Tuning {
+    int G = 32, warps = 4, rows_smem = 1;
+};
+
+}  // namespace
+
+struct ms_batch {
+    int device = 0;
+    int E = 0, NB = 0, NJ = 0, A = 0, max_nb = 0, max_nj = 0;
+    ms_sim_params params{};
+    DevBatch D{};
+    // device allocations
+    std::vector<void*> allocs;
+    int* d_body_env = nullptr;
+    float* d_staging = nullptr;
+    uint8_t* d_mask = nullptr;
+    int* d_queue = nullptr;
+    int* d_order = nullptr;
+    char* d_rows_global = nullptr;
+    size_t rows_global_bytes = 0;
+    size_t bytes = 0;
+    bool record = false;
+    // batched path
+    Tuning tune;
+    Layout fused_layout{};
+    int fused_threads = 0, fused_grid = 0, fused_ctas_per_sm = 0;
+    size_t fused_smem = 0;
+    bool fused_ready = false;
+    std::map<long long, GraphEntry> graphs;
+    cudaStream_t last = nullptr;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::vector<int> h_body_off, h_joint_off;
+};
+
+static ms_status dmalloc(ms_batch* b, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA,
+                                      "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    b->allocs.push_back(*p);
+    b->bytes += bytes;
+    return MS_OK;
+}
+
+template <typename T>
+static ms_status upload(ms_batch* b, T** dst, const std::vector<T>& src) {
+    ms_status s = dmalloc(b, (void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (s) return s;
+    if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return MS_OK;
+}
+
+static void drop_graphs(ms_batch* b) {
+    for (auto& kv : b->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    b->graphs.clear();
+}
+
+static void free_all(ms_batch* b) {
+    drop_graphs(b);
+    for (void* p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+}
+
+static bool finite3(const float* v, int n) {
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Body-frame principal inertia of a uniform solid of the given mass.
+static void body_inertia(const ms_body_desc& d, float out[3]) {
+    double m = d.mass;
+    if (d.type == MS_SPHERE) {
+        double r = d.p[0];
+        out[0] = out[1] = out[2] = (float)(0.4 * m * r * r);
+    } else if (d.type == MS_BOX) {
+        double x = d.p[0], y = d.p[1], z = d.p[2];
+        out[0] = (float)(m * (y * y + z * z) / 3.0);
+        out[1] = (float)(m * (x * x + z * z) / 3.0);
+        out[2] = (float)(m * (x * x + y * y) / 3.0);
+    } else {  // capsule along z: cylinder of length 2l + two hemispherical caps
+        const double pi = 3.14159265358979323846;
+        double r = d.p[0], l = d.p[1];
+        double vcyl = 2.0 * pi * r * r * l, vsph = 4.0 * pi * r * r * r / 3.0;
+        double mcyl = m * vcyl / (vcyl + vsph), msph = m - mcyl;
+        // a cap's centroid lies 3r/8 past the segment end; about the capsule
+        // centre each cap contributes m_cap (2r^2/5 + l^2 + 3lr/4)
+        double ixx = mcyl * (3.0 * r * r + 4.0 * l * l) / 12.0 + msph * (0.4 * r * r + l * l + 0.75 * l * r);
+        double izz = 0.5 * mcyl * r * r + 0.4 * msph * r * r;
+        out[0] = out[1] = (float)ixx;
+        out[2] = (float)izz;
+    }
+}
+
+static ms_status validate_params(const ms_sim_params* p) {
+    if (!p) return fail(MS_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_INVALID_ARG, "dt must be > 0");
+    if (p->substeps < 1 || p->substeps > 1024) return fail(MS_ERR_INVALID_ARG, "substeps must be in [1, 1024]");
+    if (p->pos_iters < 0 || p->vel_iters < 0 || p->pos_iters > 100000 || p->vel_iters > 100000)
+        return fail(MS_ERR_INVALID_ARG, "iteration counts must be >= 0");
+    if (!finite3(p->gravity, 3)) return fail(MS_ERR_INVALID_ARG, "gravity must be finite");
+    if (!(p->margin >= 0.f) || !std::isfinite(p->margin)) return fail(MS_ERR_INVALID_ARG, "margin must be >= 0");
+    if (!(p->max_depen_vel > 0.f)) return fail(MS_ERR_INVALID_ARG, "max_depen_vel must be > 0");
+    if (p->contact_capacity < 1 || p->contact_capacity > 16384)
+        return fail(MS_ERR_INVALID_ARG, "contact_capacity must be in [1, 16384]");
+    if (p->pair_capacity < 1 || p->pair_capacity > 65535)
+        return fail(MS_ERR_INVALID_ARG, "pair_capacity must be in [1, 65535]");
+    return MS_OK;
+}
+
+static ms_status validate_env(int e, const ms_body_desc* bd, int nb, const ms_joint_desc* jd, int nj) {
+    if (nb < 1 || nb > 64) return fail(MS_ERR_INVALID_ARG, "env %d: n_bodies %d not in [1, 64]", e, nb);
+    if (nj < 0 || nj > 512) return fail(MS_ERR_INVALID_ARG, "env %d: n_joints %d not in [0, 512]", e, nj);
+    if (!bd) return fail(MS_ERR_INVALID_ARG, "env %d: bodies is NULL", e);
+    if (nj > 0 && !jd) return fail(MS_ERR_INVALID_ARG, "env %d: joints is NULL", e);
+    for (int i = 0; i < nb; i++) {
+        const ms_body_desc& d = bd[i];
+        if (d.type < MS_SPHERE || d.type > MS_PLANE) return fail(MS_ERR_INVALID_ARG, "env %d body %d: bad type %d", e, i, d.type);
+        if (!finite3(d.pos, 3) || !finite3(d.quat, 4) || !finite3(d.linvel, 3) || !finite3(d.angvel, 3) ||
+            !std::isfinite(d.mass) || !std::isfinite(d.mu))
+            return fail(MS_ERR_INVALID_ARG, "env %d body %d: non-finite field", e, i);
+        double qn = (double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] + (double)d.quat[2] * d.quat[2] +
+                    (double)d.quat[3] * d.quat[3];
+        if (qn < 1e-12) return fail(MS_ERR_INVALID_ARG, "env %d body %d: zero quaternion", e, i);
+        if (d.mass < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mass", e, i);
+        if (d.mu < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mu", e, i);
+        int need = d.type == MS_SPHERE ? 1 : (d.type == MS_CAPSULE ? 2 : (d.type == MS_BOX ? 3 : 0));
+        for (int k = 0; k < need; k++)
+            if (!(d.p[k] > 0.f) || !std::isfinite(d.p[k]))
+                return fail(MS_ERR_INVALID_ARG, "env %d body %d: shape size p[%d] must be > 0", e, i, k);
+    }
+    for (int j = 0; j < nj; j++) {
+        const ms_joint_desc& d = jd[j];
+        if (d.type != MS_REVOLUTE && d.type != MS_PRISMATIC) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: bad type", e, j);
+        if (d.parent < -1 || d.parent >= nb || d.child < 0 || d.child >= nb || d.parent == d.child)
+            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: bad parent/child %d/%d", e, j, d.parent, d.child);
+        if (!finite3(d.parent_frame, 7) || !finite3(d.child_frame, 7) || !std::isfinite(d.lower) ||
+            !std::isfinite(d.upper) || !std::isfinite(d.kp) || !std::isfinite(d.kd) || !std::isfinite(d.target0))
+            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: non-finite field", e, j);
+        if (d.lower > d.upper) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: lower > upper", e, j);
+        if (d.kp < 0.f || d.kd < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: negative gain", e, j);
+        const float* qa = d.parent_frame + 3;
+        const float* qb = d.child_frame + 3;
+        if (qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3] < 1e-12f ||
+            qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3] < 1e-12f)
+            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: zero frame quaternion", e, j);
+    }
+    return MS_OK;
+}
+
+static void normq(const float* q, float* o) {
+    double n = std::sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3]);
+    for (int k = 0; k < 4; k++) o[k] = (float)(q[k] / n);
+}
+
+static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb_of, const ms_joint_desc* const* joints_of,
+                             const int* nj_of, int E, const ms_sim_params* p, ms_batch** out) {
+    if (!out) return fail(MS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (E < 1) return fail(MS_ERR_INVALID_ARG, "n_envs must be >= 1");
+    ms_status st = validate_params(p);
+    if (st) return st;
+    for (int e = 0; e < E; e++) {
+        st = validate_env(e, bodies_of[e], nb_of[e], joints_of[e], nj_of[e]);
+        if (st) return st;
+    }
+    ms_batch* b = new ms_batch();
+    b->params = *p;
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    b->smem_optin = (size_t)optin;
+    b->E = E;
+    b->h_body_off.assign(E + 1, 0);
+    b->h_joint_off.assign(E + 1, 0);
+    for (int e = 0; e < E; e++) {
+        b->h_body_off[e + 1] = b->h_body_off[e] + nb_of[e];
+        b->h_joint_off[e + 1] = b->h_joint_off[e] + nj_of[e];
+        b->max_nb = std::max(b->max_nb, nb_of[e]);
+        b->max_nj = std::max(b->max_nj, nj_of[e]);
+    }
+    b->NB = b->h_body_off[E];
+    b->NJ = b->h_joint_off[E];
+    b->A = b->max_nj;
+    std::vector<float4> x(b->NB), q(b->NB), v(b->NB), w(b->NB), shape(b->NB), inv(b->NB);
+    std::vector<int2> meta(b->NB);
+    std::vector<unsigned long long> adj(b->NB, 0ull);
+    std::vector<int> body_env(b->NB);
+    std::vector<float4> jf(4 * (size_t)b->NJ), jp(b->NJ);
+    std::vector<int4> jm(b->NJ);
+    std::vector<float> jt(b->NJ);
+    for (int e = 0; e < E; e++) {
+        int b0 = b->h_body_off[e], j0 = b->h_joint_off[e];
+        for (int i = 0; i < nb_of[e]; i++) {
+            const ms_body_desc& d = bodies_of[e][i];
+            int k = b0 + i;
+            bool dyn = d.type != MS_PLANE && d.mass > 0.f;
+            float qq[4];
+            normq(d.quat, qq);
+            x[k] = make_float4(d.pos[0], d.pos[1], d.pos[2], 0.f);
+            q[k] = make_float4(qq[0], qq[1], qq[2], qq[3]);
+            v[k] = dyn ? make_float4(d.linvel[0], d.linvel[1], d.linvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            w[k] = dyn ? make_float4(d.angvel[0], d.angvel[1], d.angvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            shape[k] = make_float4(d.p[0], d.p[1], d.p[2], d.mu);
+            if (dyn) {
+                float I[3];
+                body_inertia(d, I);
+                inv[k] = make_float4(1.f / I[0], 1.f / I[1], 1.f / I[2], (float)(1.0 / (double)d.mass));
+            } else {
+                inv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            meta[k] = make_int2(d.type | (dyn ? 1 << 8 : 0), (int)((unsigned)d.group | ((unsigned)d.mask << 16)));
+            body_env[k] = e;
+        }
+        for (int j = 0; j < nj_of[e]; j++) {
+            const ms_joint_desc& d = joints_of[e][j];
+            int k = j0 + j;
+            float qa[4], qb[4];
+            normq(d.parent_frame + 3, qa);
+            normq(d.child_frame + 3, qb);
+            jf[4 * k] = make_float4(d.parent_frame[0], d.parent_frame[1], d.parent_frame[2], 0.f);
+            jf[4 * k + 1] = make_float4(qa[0], qa[1], qa[2], qa[3]);
+            jf[4 * k + 2] = make_float4(d.child_frame[0], d.child_frame[1], d.child_frame[2], 0.f);
+            jf[4 * k + 3] = make_float4(qb[0], qb[1], qb[2], qb[3]);
+            jp[k] = make_float4(d.lower, d.upper, d.kp, d.kd);
+            jm[k] = make_int4(d.type, d.parent, d.child, 0);
+            jt[k] = d.target0;
+            if (d.parent >= 0) {
+                adj[b0 + d.parent] |= 1ull << d.child;
+                adj[b0 + d.child] |= 1ull << d.parent;
+            }
+        }
+    }
+    DevBatch& D = b->D;
+    D.E = E; D.NB = b->NB; D.NJ = b->NJ; D.A = b->A;
+    D.P.dt = p->dt; D.P.h = p->dt / (float)p->substeps;
+    D.P.substeps = p->substeps; D.P.pos_iters = p->pos_iters; D.P.vel_iters = p->vel_iters;
+    D.P.gx = p->gravity[0]; D.P.gy = p->gravity[1]; D.P.gz = p->gravity[2];
+    D.P.margin = p->margin; D.P.vmax = p->max_depen_vel;
+    D.P.pair_cap = p->pair_capacity; D.P.contact_cap = p->contact_capacity;
+    ms_status s = MS_OK;
+    int* bo = nullptr; int* jo = nullptr;
+#define UP(dst, src) do { if ((s = upload(b, dst, src)) != MS_OK) { free_all(b); delete b; return s; } } while (0)
+    UP(&bo, b->h_body_off);
+    UP(&jo, b->h_joint_off);
+    D.body_off = bo; D.joint_off = jo;
+    UP(&D.x, x); UP(&D.q, q); UP(&D.v, v); UP(&D.w, w);
+    float4* d_shape; float4* d_inv; int2* d_meta; unsigned long long* d_adj;
+    UP(&d_shape, shape); UP(&d_inv, inv); UP(&d_meta, meta); UP(&d_adj, adj);
+    D.shape = d_shape; D.inv = d_inv; D.meta = d_meta; D.adj = d_adj;
+    float4* d_jf; float4* d_jp; int4* d_jm;
+    UP(&d_jf, jf); UP(&d_jp, jp); UP(&d_jm, jm); UP(&D.jt, jt);
+    D.jf = d_jf; D.jp = d_jp; D.jm = d_jm;
+    UP(&b->d_body_env, body_env);
+    std::vector<unsigned> zeros(E, 0u);
+    UP(&D.status, zeros);
+    // longest-first order for the batched work queue: the estimated cost is
+    // dominated by rows x sweeps (8 per joint) and the pair tests
+    std::vector<int> order(E);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<long long> cost(E);
+    for (int e = 0; e < E; e++) cost[e] = 8LL * nj_of[e] * 4 + (long long)nb_of[e] * nb_of[e] + 12LL * nb_of[e];
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    UP(&b->d_order, order);
+#undef UP
+    if ((s = dmalloc(b, (void**)&b->d_queue, 16)) != MS_OK) { free_all(b); delete b; return s; }
+    if ((s = dmalloc(b, (void**)&b->d_staging, sizeof(float) * 13 * (size_t)b->NB)) != MS_OK) { free_all(b); delete b; return s; }
+    if ((s = dmalloc(b, (void**)&b->d_mask, (size_t)E)) != MS_OK) { free_all(b); delete b; return s; }
+    D.plain_ws = nullptr;
+    D.rec_man = nullptr; D.rec_pts = nullptr; D.rec_cnt = nullptr;
+    cudaError_t ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) { free_all(b); delete b; return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(ce)); }
+    *out = b;
+    g_err.clear();
+    return MS_OK;
+}
+
+extern "C" ms_status ms_create_batch(const ms_scene_desc* descs, int n_envs, const ms_sim_params* p, ms_batch** out) {
+    if (!descs) return fail(MS_ERR_INVALID_ARG, "descs is NULL");
+    if (n_envs < 1) return fail(MS_ERR_INVALID_ARG, "n_envs must be >= 1");
+    std::vector<const ms_body_desc*> bo(n_envs);
+    std::vector<const ms_joint_desc*> jo(n_envs);
+    std::vector<int> nb(n_envs), nj(n_envs);
+    for (int e = 0; e < n_envs; e++) {
+        bo[e] = descs[e].bodies; jo[e] = descs[e].joints;
+        nb[e] = descs[e].n_bodies; nj[e] = descs[e].n_joints;
+    }
+    return create_impl(bo.data(), nb.data(), jo.data(), nj.data(), n_envs, p, out);
+}
+
+extern "C" ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_off, const ms_joint_desc* joints,
+                                          const int32_t* joint_off, int n_envs, const ms_sim_params* p, ms_batch** out) {
+    if (!bodies || !body_off || !joint_off) return fail(MS_ERR_INVALID_ARG, "NULL table");
+    if (n_envs < 1) return fail(MS_ERR_INVALID_ARG, "n_envs must be >= 1");
+    std::vector<const ms_body_desc*> bo(n_envs);
+    std::vector<const ms_joint_desc*> jo(n_envs);
+    std::vector<int> nb(n_envs), nj(n_envs);
+    if (body_off[0] != 0 || joint_off[0] != 0) return fail(MS_ERR_INVALID_ARG, "offsets must start at 0");
+    for (int e = 0; e < n_envs; e++) {
+        if (body_off[e + 1] < body_off[e] || joint_off[e + 1] < joint_off[e])
+            return fail(MS_ERR_INVALID_ARG, "offsets must be non-decreasing (env %d)", e);
+        bo[e] = bodies + body_off[e];
+        jo[e] = joints ? joints + joint_off[e] : nullptr;
+        nb[e] = body_off[e + 1] - body_off[e];
+        nj[e] = joint_off[e + 1] - joint_off[e];
+    }
+    return create_impl(bo.data(), nb.data(), jo.data(), nj.data(), n_envs, p, out);
+}
+
+// --------------------------------------------------------------- plain path
+static ms_status ensure_plain(ms_batch* b) {
+    if (b->D.plain_ws) return MS_OK;
+    const ms_sim_params& p = b->params;
+    b->D.plain_layout = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, false, true);
+    void* ws = nullptr;
+    ms_status s = dmalloc(b, &ws, (size_t)b->E * b->D.plain_layout.bytes);
+    if (s) return s;
+    b->D.plain_ws = (char*)ws;
+    return MS_OK;
+}
+
+static ms_status check_step_args(ms_batch* b, int n_steps) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (n_steps < 0 || n_steps > 1000000) return fail(MS_ERR_INVALID_ARG, "n_steps must be in [0, 1e6]");
+    return MS_OK;
+}
+
+extern "C" ms_status ms_step_plain(ms_batch* b, const float* actions, int n_steps, void* stream) {
+    ms_status s = check_step_args(b, n_steps);
+    if (s) return s;
+    if ((s = ensure_plain(b)) != MS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_plain(b->D, actions, n_steps, st);
+    CK(cudaGetLastError());
+    b->last = st;
+    return MS_OK;
+}
+
+// ------------------------------------------------------------- batched path
+static ms_status configure_fused(ms_batch* b) {
+    if (b->fused_ready) return MS_OK;
+    const ms_sim_params& p = b->params;
+    Tuning& t = b->tune;
+    int gpw = 32 / t.G;
+    bool rows_smem = t.rows_smem != 0;
+    Layout L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, rows_smem);
+    size_t smem = (size_t)L.bytes * t.warps * gpw;
+    if (smem > b->smem_optin && rows_smem) {
+        rows_smem = false;
+        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false);
+        smem = (size_t)L.bytes * t.warps * gpw;
+    }
+    if (smem > b->smem_optin)
+        return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)", smem, b->smem_optin);
+    int threads = 32 * t.warps;
+    int per_sm = 0;
+    CK(fused_occupancy(t.G, threads, smem, &per_sm));
+    if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
+    int groups_per_cta = t.warps * gpw;
+    int grid = per_sm * b->sm_count;
+    int need = (b->E + groups_per_cta - 1) / groups_per_cta;
+    if (grid > need) grid = need;
+    if (!rows_smem) {
+        size_t bytes = (size_t)grid * groups_per_cta * L.rows_bytes;
+        if (bytes > b->rows_global_bytes) {
+            void* p2 = nullptr;
+            ms_status s = dmalloc(b, &p2, bytes);
+            if (s) return s;
+            b->d_rows_global = (char*)p2;
+            b->rows_global_bytes = bytes;
+        }
+    }
+    t.rows_smem = rows_smem ? 1 : 0;
+    b->fused_layout = L;
+    b->fused_threads = threads;
+    b->fused_grid = grid;
+    b->fused_smem = smem;
+    b->fused_ctas_per_sm = per_sm;
+    b->fused_ready = true;
+    return MS_OK;
+}
+
+static FusedCfg fused_cfg(ms_batch* b) {
+    FusedCfg C;
+    C.layout = b->fused_layout;
+    C.queue = b->d_queue;
+    C.order = b->d_order;
+    C.rows_global = b->d_rows_global;
+    return C;
+}
+
+static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
+    CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
+    CK(launch_fused(b->D, actions, n_steps, fused_cfg(b), b->tune.G, b->fused_grid, b->fused_threads, b->fused_smem, st));
+    return MS_OK;
+}
+
+extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
+    ms_status s = check_step_args(b, n_steps);
+    if (s) return s;
+    if (n_steps == 0) return MS_OK;
+    if ((s = configure_fused(b)) != MS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    b->last = st;
+    if (st == nullptr) return enqueue_fused(b, actions, n_steps, st);   // the legacy stream cannot be captured
+    long long key = (long long)n_steps;
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        ms_status es = enqueue_fused(b, actions, n_steps, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (es) return es;
+        if (ce != cudaSuccess) return fail(MS_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ce));
+        GraphEntry ge;
+        CK(cudaGraphInstantiate(&ge.exec, graph, 0));
+        size_t n = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &n));
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) { ge.kernel = nd; CK(cudaGraphKernelNodeGetParams(nd, &ge.kp)); }
+        }
+        ge.graph = graph;
+        it = b->graphs.emplace(key, ge).first;
+        CK(cudaGraphLaunch(it->second.exec, st));
+        return MS_OK;
+    }
+    // the actions pointer is the only argument that changes between calls
+    GraphEntry& ge = it->second;
+    DevBatch Dv = b->D;
+    const float* act = actions;
+    int ns = n_steps;
+    FusedCfg C = fused_cfg(b);
+    void* args[] = {(void*)&Dv, (void*)&act, (void*)&ns, (void*)&C};
+    cudaKernelNodeParams kp = ge.kp;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CK(cudaGraphExecKernelNodeSetParams(ge.exec, ge.kernel, &kp));
+    CK(cudaGraphLaunch(ge.exec, st));
+    return MS_OK;
+}
+
+// -------------------------------------------------------------------- state
+extern "C" ms_status ms_get_state(ms_batch* b, ms_state_view* out) {
+    if (!b || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    out->n_envs = b->E; out->n_bodies = b->NB; out->n_joints = b->NJ; out->max_act = b->A;
+    out->x = b->D.x; out->q = b->D.q; out->v = b->D.v; out->w = b->D.w;
+    out->body_off = b->D.body_off; out->joint_off = b->D.joint_off;
+    out->targets = b->D.jt; out->status = b->D.status;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_copy_state(ms_batch* b, float* dst, int dst_kind, void* stream) {
+    if (!b || !dst) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (dst_kind != 0 && dst_kind != 1) return fail(MS_ERR_INVALID_ARG, "dst_kind must be 0 (host) or 1 (device)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dst_kind == 1) {
+        launch_pack_state(b->D, dst, st);
+    } else {
+        launch_pack_state(b->D, b->d_staging, st);
+        CK(cudaMemcpyAsync(dst, b->d_staging, sizeof(float) * 13 * (size_t)b->NB, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaGetLastError());
+    b->last = st;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_set_state(ms_batch* b, const float* src, int src_kind, const uint8_t* env_mask, void* stream) {
+    if (!b || !src) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (src_kind != 0 && src_kind != 1) return fail(MS_ERR_INVALID_ARG, "src_kind must be 0 (host) or 1 (device)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const float* dsrc = src;
+    if (src_kind == 0) {
+        CK(cudaMemcpyAsync(b->d_staging, src, sizeof(float) * 13 * (size_t)b->NB, cudaMemcpyHostToDevice, st));
+        dsrc = b->d_staging;
+    }
+    const uint8_t* dmask = nullptr;
+    if (env_mask) {
+        CK(cudaMemcpyAsync(b->d_mask, env_mask, (size_t)b->E, cudaMemcpyHostToDevice, st));
+        dmask = b->d_mask;
+    }
+    launch_unpack_state(b->D, dsrc, dmask, b->d_body_env, st);
+    CK(cudaGetLastError());
+    // the host buffers may be reused as soon as this returns
+    CK(cudaStreamSynchronize(st));
+    b->last = st;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_sync(ms_batch* b, uint32_t* env_status) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    CK(cudaStreamSynchronize(b->last));
+    CK(cudaGetLastError());
+    std::vector<uint32_t> st(b->E);
+    CK(cudaMemcpy(st.data(), b->D.status, sizeof(uint32_t) * b->E, cudaMemcpyDeviceToHost));
+    uint32_t any = 0;
+    for (uint32_t s : st) any |= s;
+    if (env_status) memcpy(env_status, st.data(), sizeof(uint32_t) * b->E);
+    if (any & MS_ENV_PAIR_OVERFLOW) return fail(MS_ERR_PAIR_OVERFLOW, "an env exceeded pair_capacity");
+    if (any & MS_ENV_CONTACT_OVERFLOW) return fail(MS_ERR_CONTACT_OVERFLOW, "an env exceeded contact_capacity");
+    if (any & MS_ENV_COLOR_OVERFLOW) return fail(MS_ERR_COLOR_OVERFLOW, "an env needed more than 64 colours");
+    if (any & MS_ENV_NAN) return fail(MS_ERR_NAN, "an env reached a non-finite state and was frozen");
+    return MS_OK;
+}
+
+extern "C" ms_status ms_destroy(ms_batch* b) {
+    if (!b) return MS_OK;
+    cudaStreamSynchronize(b->last);
+    free_all(b);
+    delete b;
+    return MS_OK;
+}
+
+extern "C" const char* ms_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------ introspection
+extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (record && !b->D.rec_man) {
+        void *m = nullptr, *p = nullptr, *c = nullptr;
+        ms_status s;
+        if ((s = dmalloc(b, &m, sizeof(int4) * (size_t)b->E * b->params.pair_capacity)) != MS_OK) return s;
+        if ((s = dmalloc(b, &p, sizeof(float) * 10 * (size_t)b->E * b->params.contact_capacity)) != MS_OK) return s;
+        if ((s = dmalloc(b, &c, sizeof(int) * (size_t)b->E)) != MS_OK) return s;
+        CK(cudaMemset(c, 0, sizeof(int) * (size_t)b->E));
+        b->D.rec_man = (int4*)m; b->D.rec_pts = (float*)p; b->D.rec_cnt = (int*)c;
+    }
+    b->record = record != 0;
+    if (!b->record) { b->D.rec_man = nullptr; b->D.rec_pts = nullptr; b->D.rec_cnt = nullptr; }
+    drop_graphs(b);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t* npts, float* pts, int* count) {
+    if (!b || !count) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->D.rec_man) return fail(MS_ERR_INVALID_ARG, "contact recording is off");
+    if (env < 0 || env >= b->E) return fail(MS_ERR_INVALID_ARG, "env %d out of range", env);
+    CK(cudaStreamSynchronize(b->last));
+    int n = 0;
+    CK(cudaMemcpy(&n, b->D.rec_cnt + env, sizeof(int), cudaMemcpyDeviceToHost));
+    *count = n;
+    int m = std::min(n, cap);
+    if (m <= 0) return MS_OK;
+    std::vector<int4> man(m);
+    CK(cudaMemcpy(man.data(), b->D.rec_man + (size_t)env * b->params.pair_capacity, sizeof(int4) * m, cudaMemcpyDeviceToHost));
+    std::vector<float> P(10 * (size_t)b->params.contact_capacity);
+    CK(cudaMemcpy(P.data(), b->D.rec_pts + (size_t)env * b->params.contact_capacity * 10, sizeof(float) * P.size(),
+                  cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; i++) {
+        if (pairs) { pairs[2 * i] = man[i].x; pairs[2 * i + 1] = man[i].y; }
+        if (npts) npts[i] = man[i].z;
+        if (pts) {
+            for (int k = 0; k < 4; k++)
+                for (int f = 0; f < 10; f++)
+                    pts[(size_t)40 * i + 10 * k + f] = k < man[i].z ? P[10 * (size_t)(man[i].w + k) + f] : 0.f;
+        }
+    }
+    return MS_OK;
+}
+
+extern "C" ms_status ms_set_tuning(ms_batch* b, const ms_tuning* t) {
+    if (!b || !t) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (t->lanes_per_env != 4 && t->lanes_per_env != 8 && t->lanes_per_env != 16 && t->lanes_per_env != 32)
+        return fail(MS_ERR_INVALID_ARG, "lanes_per_env must be 4, 8, 16 or 32");
+    if (t->warps_per_cta < 1 || t->warps_per_cta > 16) return fail(MS_ERR_INVALID_ARG, "warps_per_cta must be in [1, 16]");
+    Tuning old = b->tune;
+    b->tune.G = t->lanes_per_env;
+    b->tune.warps = t->warps_per_cta;
+    b->tune.rows_smem = t->rows_in_smem ? 1 : 0;
+    b->fused_ready = false;
+    drop_graphs(b);
+    ms_status s = configure_fused(b);
+    if (s) { b->tune = old; b->fused_ready = false; configure_fused(b); return s; }
+    return MS_OK;
+}
+
+extern "C" ms_status ms_get_tuning(ms_batch* b, ms_tuning* t) {
+    if (!b || !t) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    ms_status s = configure_fused(b);
+    if (s) return s;
+    t->lanes_per_env = b->tune.G;
+    t->warps_per_cta = b->tune.warps;
+    t->rows_in_smem = b->tune.rows_smem;
+    t->ctas_per_sm = b->fused_ctas_per_sm;
+    return MS_OK;
+}
+
+static std::string signature(ms_batch* b) {
+    std::ostringstream os;
+    const ms_sim_params& p = b->params;
+    os << "E" << b->E << "_NB" << b->NB << "_NJ" << b->NJ << "_mb" << b->max_nb << "_mj" << b->max_nj << "_pc"
+       << p.pair_capacity << "_cc" << p.contact_capacity << "_s" << p.substeps << "_i" << p.pos_iters << "_" << p.vel_iters;
+    return os.str();
+}
+
+static bool cache_lookup(const char* path, const std::string& key, ms_tuning* t) {
+    if (!path) return false;
+    std::ifstream f(path);
+    if (!f) return false;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    std::string s = ss.str();
+    std::string needle = "\"" + key + "\"";
+    size_t p = s.find(needle);
+    if (p == std::string::npos) return false;
+    int G, W, R;
+    if (sscanf(s.c_str() + p + needle.size(), " : [%d, %d, %d]", &G, &W, &R) != 3) return false;
+    t->lanes_per_env = G; t->warps_per_cta = W; t->rows_in_smem = R;
+    return true;
+}
+
+static void cache_store(const char* path, const std::string& key, const ms_tuning& t) {
+    if (!path) return;
+    std::map<std::string, std::string> entries;
+    {
+        std::ifstream f(path);
+        std::string line;
+        while (f && std::getline(f, line)) {
+            size_t a = line.find('"'), c = line.find('"', a + 1);
+            size_t lb = line.find('['), rb = line.find(']');
+            if (a == std::string::npos || c == std::string::npos || lb == std::string::npos || rb == std::string::npos) continue;
+            entries[line.substr(a + 1, c - a - 1)] = line.substr(lb, rb - lb + 1);
+        }
+    }
+    char buf[64];
+    snprintf(buf, sizeof(buf), "[%d, %d, %d]", t.lanes_per_env, t.warps_per_cta, t.rows_in_smem);
+    entries[key] = buf;
+    std::ofstream o(path);
+    o << "{\n";
+    size_t i = 0;
+    for (auto& kv : entries) {
+        o << "  \"" << kv.first << "\": " << kv.second << (++i < entries.size() ? ",\n" : "\n");
+    }
+    o << "}\n";
+}
+
+extern "C" ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_path, ms_tuning* best, void* stream) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (n_steps < 1) return fail(MS_ERR_INVALID_ARG, "n_steps must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string key = signature(b);
+    ms_tuning t{};
+    if (cache_lookup(cache_path, key, &t) && ms_set_tuning(b, &t) == MS_OK) {
+        if (best) ms_get_tuning(b, best);
+        return MS_OK;
+    }
+    // save the state so the trials leave the batch unchanged
+    float* save = nullptr;
+    float* tsave = nullptr;
+    unsigned* ssave = nullptr;
+    CK(cudaMalloc(&save, sizeof(float) * 13 * (size_t)b->NB));
+    CK(cudaMalloc(&tsave, sizeof(float) * std::max(b->NJ, 1)));
+    CK(cudaMalloc(&ssave, sizeof(unsigned) * b->E));
+    launch_pack_state(b->D, save, st);
+    CK(cudaMemcpyAsync(tsave, b->D.jt, sizeof(float) * b->NJ, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ssave, b->D.status, sizeof(unsigned) * b->E, cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    ms_tuning bt = {b->tune.G, b->tune.warps, b->tune.rows_smem, 0};
+    const int Gs[] = {32, 16, 8, 4};
+    const int Ws[] = {2, 4, 8};
+    for (int G : Gs)
+        for (int W : Ws)
+            for (int R = 1; R >= 0; R--) {
+                ms_tuning c = {G, W, R, 0};
+                if (ms_set_tuning(b, &c) != MS_OK) continue;
+                if (R == 1 && b->tune.rows_smem == 0) continue;   // rows did not fit: same as R = 0
+                ms_step(b, nullptr, n_steps, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; r++) ms_step(b, nullptr, n_steps, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms_ = 0.f;
+                cudaEventElapsedTime(&ms_, e0, e1);
+                if (ms_ < best_ms) { best_ms = ms_; bt = c; }
+                // restore before the next candidate
+                launch_unpack_state(b->D, save, nullptr, b->d_body_env, st);
+                cudaMemcpyAsync(b->D.jt, tsave, sizeof(float) * b->NJ, cudaMemcpyDeviceToDevice, st);
+            }
+    ms_set_tuning(b, &bt);
+    launch_unpack_state(b->D, save, nullptr, b->d_body_env, st);
+    cudaMemcpyAsync(b->D.jt, tsave, sizeof(float) * b->NJ, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(b->D.status, ssave, sizeof(unsigned) * b->E, cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+    cudaFree(save); cudaFree(tsave); cudaFree(ssave);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    cache_store(cache_path, key, bt);
+    if (best) ms_get_tuning(b, best);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_memory_bytes(ms_batch* b, size_t* bytes) {
+    if (!b || !bytes) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    *bytes = b->bytes;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* joint_off, int n_envs, const ms_sim_params* p,
+                                       size_t* bytes) {
+    if (!body_off || !joint_off || !p || !bytes || n_envs < 1) return fail(MS_ERR_INVALID_ARG, "bad argument");
+    size_t NB = (size_t)body_off[n_envs], NJ = (size_t)joint_off[n_envs];
+    int max_nb = 0, max_nj = 0;
+    for (int e = 0; e < n_envs; e++) {
+        max_nb = std::max(max_nb, body_off[e + 1] - body_off[e]);
+        max_nj = std::max(max_nj, joint_off[e + 1] - joint_off[e]);
+    }
+    // resident state and parameters, the staging buffer and the per-env
+    // workspace of the plain path (the batched path's is per resident slot)
+    size_t state = NB * (16 * 6 + 8 + 8 + 4 + 52) + NJ * (64 + 16 + 16 + 4) + (size_t)n_envs * 16 + 64;
+    Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, true);
+    *bytes = state + (size_t)n_envs * L.bytes;
+    return MS_OK;
+}
+
+extern "C" void ms_abi_sizes(int32_t* out5) {
+    if (!out5) return;
+    out5[0] = (int32_t)sizeof(ms_body_desc);
+    out5[1] = (int32_t)sizeof(ms_joint_desc);
+    out5[2] = (int32_t)sizeof(ms_sim_params);
+    out5[3] = (int32_t)sizeof(ms_state_view);
+    out5[4] = (int32_t)sizeof(ms_tuning);
+}

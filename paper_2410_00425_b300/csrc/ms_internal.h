@@ -1,0 +1,69 @@
+// Internal declarations shared by the host API and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "ms_math.cuh"
+
+namespace ms {
+
+// Byte offsets of one env's arrays inside a workspace slot (-1: absent).
+struct Layout {
+    int bytes;
+    int x, q, v, w, shape, inv, meta, adj;  // body copies (batched path only)
+    int jf, jp, jm, jt;                     // joint copies (batched path only)
+    int iw, aabb, pairs, man, pts, cons, colr, order, color_off, used, cnt, status;
+    int rows;                               // -1: rows live in a global slot
+    int rows_bytes;
+};
+
+Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool with_rows);
+
+// Kernel-side view of a batch (plain pointers, passed by value).
+struct DevParams {
+    float dt, h;
+    int substeps, pos_iters, vel_iters;
+    float gx, gy, gz;
+    float margin, vmax;
+    int pair_cap, contact_cap;
+};
+
+struct DevBatch {
+    int E, NB, NJ, A;
+    DevParams P;
+    const int* body_off;
+    const int* joint_off;
+    float4 *x, *q, *v, *w;
+    const float4* shape;
+    const float4* inv;
+    const int2* meta;
+    const unsigned long long* adj;
+    const float4* jf;
+    const float4* jp;
+    const int4* jm;
+    float* jt;
+    unsigned* status;
+    char* plain_ws;
+    Layout plain_layout;
+    int4* rec_man;
+    float* rec_pts;
+    int* rec_cnt;
+};
+
+struct FusedCfg {
+    Layout layout;
+    int* queue;
+    const int* order;
+    char* rows_global;
+};
+
+int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s);
+cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,
+                         int grid, int threads, size_t smem, cudaStream_t s);
+void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
+void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask, const int* body_env,
+                         cudaStream_t s);
+
+}  // namespace ms

@@ -1,0 +1,594 @@
+// Stages of the batched rigid-body step, written once over an "env view"
+// (pointers to one env's bodies, joints and workspace) and a lane group
+// (G = 4..32 lanes of one warp working on that env).  The plain path calls
+// each stage from its own kernel with the view in global memory; the
+// batched path calls all of them from one persistent kernel with the view
+// in shared memory.  The arithmetic is the same code in both, so the two
+// paths agree bit for bit.
+//
+// Per step: drive targets <- actions; broadphase; narrowphase; colouring
+// (once per step, at the step-start poses).  Per substep: gravity + world
+// inverse inertia + rows; warm start; pos_iters sweeps; integration +
+// relax bias; vel_iters relax sweeps.  The solver is substepped sequential
+// impulses (Catto 2005) in the small-steps arrangement of Macklin et al.
+// 2019, with PD drives as soft constraints (Catto 2011), a per-row Coulomb
+// pyramid and a relax pass without penetration push.
+#pragma once
+#include "ms_internal.h"
+#include "ms_narrow.cuh"
+
+namespace ms {
+
+using Params = DevParams;
+
+enum { RK_NORMAL = 0, RK_FRICTION = 1, RK_EQ = 2, RK_LIMIT = 3, RK_DRIVE = 4 };
+enum { ST_PAIR = 1u, ST_CONTACT = 2u, ST_COLOR = 4u, ST_NAN = 8u };
+enum { C_NPAIRS = 0, C_NMAN = 1, C_NPTS = 2, C_NCONS = 3, C_NCOLORS = 4, C_NUM = 8 };
+enum { MAX_COLORS = 64 };
+
+// One constraint row (96 B, six float4 for vector loads).
+//   r0 = lin, inv_k   r1 = angA, bias     r2 = angB, relax_bias
+//   r3 = I_A^-1 angA, k                   r4 = I_B^-1 angB, aux (mu | gamma)
+//   r5 = lambda, kind (int bits), partner row within the constraint, -
+struct Row {
+    float4 r0, r1, r2, r3, r4, r5;
+};
+
+struct EnvView {
+    int nb, nj;
+    float4 *x, *q, *v, *w;            // state
+    const float4* shape;              // p0, p1, p2, mu
+    const float4* inv;                // 1/Ixx, 1/Iyy, 1/Izz, 1/m (0 = static)
+    const int2* meta;                 // x: type | dyn << 8; y: group | mask << 16
+    const unsigned long long* adj;    // joint adjacency bit mask per body
+    const float4* jf;                 // 4 per joint: parent pos, parent quat, child pos, child quat
+    const float4* jp;                 // lower, upper, kp, kd
+    const int4* jm;                   // type, parent, child, -
+    float* jt;                        // drive targets
+    S3* iw;                           // world inverse inertia per body
+    float4* aabb;                     // 2 per body
+    int* pairs;                       // i | j << 16
+    int4* man;                        // a, b, npts, first point
+    float4* pts;                      // 3 per point: (aA, d), (aB, -), (n, -)
+    int4* cons;                       // a, b, row0, nrows | kind << 8 | idx << 9
+    int* colr;                        // colour per constraint
+    int* order;                       // solve order
+    int* color_off;                   // MAX_COLORS + 1
+    unsigned long long* used;         // colour masks per body
+    Row* rows;
+    int* cnt;                         // C_NUM counters
+    unsigned* status;                 // env status word
+    int4* rec_man;                    // recorded manifolds (nullable)
+    float* rec_pts;                   // recorded points [contact_cap][10]
+    int* rec_cnt;
+};
+
+struct Grp {
+    int lane, size, base;
+    unsigned mask;
+    MSD void sync() const { __syncwarp(mask); }
+    MSD unsigned ballot(bool p) const { return __ballot_sync(mask, p) >> base; }
+    MSD unsigned lt() const { return (1u << lane) - 1u; }
+    MSD int shfl(int v, int src) const { return __shfl_sync(mask, v, src, size); }
+    MSD int incl_scan(int v) const {
+        for (int d = 1; d < size; d <<= 1) {
+            int t = __shfl_up_sync(mask, v, d, size);
+            if (lane >= d) v += t;
+        }
+        return v;
+    }
+    MSD int max_all(int v) const {
+        for (int d = size >> 1; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(mask, v, d, size));
+        return v;
+    }
+    MSD bool any(bool p) const { return ballot(p) != 0u; }
+};
+
+MSD bool is_dyn(const EnvView& e, int i) { return i >= 0 && ((e.meta[i].x >> 8) & 1); }
+MSD int shape_type(const EnvView& e, int i) { return e.meta[i].x & 0xff; }
+
+// ---------------------------------------------------------------- actions
+MSD void stage_actions(EnvView& e, const Grp& g, const float* act, int A) {
+    if (act)
+        for (int j = g.lane; j < e.nj && j < A; j += g.size) {
+            float t = act[j];
+            if (!isnan(t)) e.jt[j] = t;
+        }
+    g.sync();
+}
+
+// ------------------------------------------------------------- broadphase
+MSD void aabb_of(const EnvView& e, int i, float hm, float4& lo, float4& hi) {
+    float4 s = e.shape[i];
+    int t = shape_type(e, i);
+    float3 c = xyz(e.x[i]);
+    float3 ext;
+    if (t == SH_SPHERE) {
+        ext = f3(s.x, s.x, s.x);
+    } else {
+        M3 R = qmat(e.q[i]);
+        if (t == SH_BOX) {
+            ext = f3(fabsf(R.m[0]) * s.x + fabsf(R.m[1]) * s.y + fabsf(R.m[2]) * s.z,
+                     fabsf(R.m[3]) * s.x + fabsf(R.m[4]) * s.y + fabsf(R.m[5]) * s.z,
+                     fabsf(R.m[6]) * s.x + fabsf(R.m[7]) * s.y + fabsf(R.m[8]) * s.z);
+        } else {
+            float3 ax = mcol(R, 2);
+            ext = f3(fabsf(ax.x) * s.y + s.x, fabsf(ax.y) * s.y + s.x, fabsf(ax.z) * s.y + s.x);
+        }
+    }
+    ext = ext + f3(hm, hm, hm);
+    lo = f4(c - ext, 0.f);
+    hi = f4(c + ext, 0.f);
+}
+
+// p-th pair (i < j) in lexicographic order of n items
+MSD void pair_from_index(int p, int n, int& i, int& j) {
+    float b = 2.f * n - 1.f;
+    int ii = (int)floorf((b - sqrtf(b * b - 8.f * p)) * 0.5f);
+    if (ii < 0) ii = 0;
+    if (ii > n - 2) ii = n - 2;
+    while (ii > 0 && ii * (2 * n - ii - 1) / 2 > p) ii--;
+    while (ii < n - 2 && (ii + 1) * (2 * n - ii - 2) / 2 <= p) ii++;
+    i = ii;
+    j = p - ii * (2 * n - ii - 1) / 2 + ii + 1;
+}
+
+MSD void stage_broadphase(EnvView& e, const Grp& g, const Params& P) {
+    int nb = e.nb;
+    for (int i = g.lane; i < nb; i += g.size) {
+        if (shape_type(e, i) == SH_PLANE) continue;
+        float4 lo, hi;
+        aabb_of(e, i, 0.5f * P.margin, lo, hi);
+        e.aabb[2 * i] = lo;
+        e.aabb[2 * i + 1] = hi;
+    }
+    g.sync();
+    int total = nb * (nb - 1) / 2;
+    int count = 0;
+    for (int c = 0; c < total; c += g.size) {
+        int p = c + g.lane;
+        bool pred = false;
+        int i = 0, j = 0;
+        if (p < total) {
+            pair_from_index(p, nb, i, j);
+            int2 mi = e.meta[i], mj = e.meta[j];
+            bool di = (mi.x >> 8) & 1, dj = (mj.x >> 8) & 1;
+            unsigned gi = mi.y & 0xffff, ki = (unsigned)mi.y >> 16;
+            unsigned gj = mj.y & 0xffff, kj = (unsigned)mj.y >> 16;
+            pred = (di || dj) && (gi & kj) && (gj & ki) && !((e.adj[i] >> j) & 1ull);
+            if (pred && (mi.x & 0xff) != SH_PLANE && (mj.x & 0xff) != SH_PLANE) {
+                float4 la = e.aabb[2 * i], ha = e.aabb[2 * i + 1];
+                float4 lb = e.aabb[2 * j], hb = e.aabb[2 * j + 1];
+                pred = la.x <= hb.x && lb.x <= ha.x && la.y <= hb.y && lb.y <= ha.y &&
+                       la.z <= hb.z && lb.z <= ha.z;
+            }
+        }
+        unsigned bits = g.ballot(pred);
+        if (pred) {
+            int pos = count + __popc(bits & g.lt());
+            if (pos < P.pair_cap) e.pairs[pos] = i | (j << 16);
+        }
+        count += __popc(bits);
+    }
+    if (g.lane == 0) {
+        e.cnt[C_NPAIRS] = min(count, P.pair_cap);
+        if (count > P.pair_cap) *e.status |= ST_PAIR;
+    }
+    g.sync();
+}
+
+// ------------------------------------------------------------ narrowphase
+MSD Shape shape_at(const EnvView& e, int i) {
+    Shape s;
+    s.x = xyz(e.x[i]);
+    s.R = qmat(e.q[i]);
+    s.type = shape_type(e, i);
+    float4 p = e.shape[i];
+    s.p0 = p.x; s.p1 = p.y; s.p2 = p.z;
+    return s;
+}
+
+MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
+    int npairs = e.cnt[C_NPAIRS];
+    int total = 0, nman = 0, kept_end = 0;
+    bool overflow = false;
+    for (int c = 0; c < npairs; c += g.size) {
+        int p = c + g.lane;
+        Cand pts[4];
+        int n = 0, a = 0, b = 0;
+        Shape SA, SB;
+        if (p < npairs) {
+            int pr = e.pairs[p];
+            int i = pr & 0xffff, j = pr >> 16;
+            a = i; b = j;
+            if (shape_type(e, j) < shape_type(e, i)) { a = j; b = i; }
+            SA = shape_at(e, a);
+            SB = shape_at(e, b);
+            n = collide(SA, SB, P.margin, pts);
+        }
+        int incl = g.incl_scan(n);
+        int chunk_total = g.shfl(incl, g.size - 1);
+        int start = total + incl - n;
+        bool keep = n > 0 && start + n <= P.contact_cap;
+        overflow |= (n > 0 && !keep);
+        unsigned bits = g.ballot(keep);
+        if (keep) {
+            int midx = nman + __popc(bits & g.lt());
+            e.man[midx] = make_int4(a, b, n, start);
+            float3 xa = SA.x, xb = SB.x;
+            for (int k = 0; k < n; k++) {
+                float3 aA = mtv(SA.R, pts[k].cA - xa);
+                float3 aB = mtv(SB.R, pts[k].cB - xb);
+                float4* o = e.pts + 3 * (start + k);
+                o[0] = f4(aA, pts[k].d);
+                o[1] = f4(aB, 0.f);
+                o[2] = f4(pts[k].n, 0.f);
+                if (e.rec_pts) {
+                    float* rp = e.rec_pts + 10 * (start + k);
+                    rp[0] = pts[k].cA.x; rp[1] = pts[k].cA.y; rp[2] = pts[k].cA.z;
+                    rp[3] = pts[k].cB.x; rp[4] = pts[k].cB.y; rp[5] = pts[k].cB.z;
+                    rp[6] = pts[k].n.x; rp[7] = pts[k].n.y; rp[8] = pts[k].n.z; rp[9] = pts[k].d;
+                }
+            }
+            if (e.rec_man) e.rec_man[midx] = make_int4(a, b, n, start);
+        }
+        kept_end = max(kept_end, g.max_all(keep ? start + n : 0));
+        nman += __popc(bits);
+        total += chunk_total;
+    }
+    bool ov = g.any(overflow);
+    if (g.lane == 0) {
+        e.cnt[C_NMAN] = nman;
+        e.cnt[C_NPTS] = kept_end;
+        if (ov) *e.status |= ST_CONTACT;
+        if (e.rec_cnt) *e.rec_cnt = nman;
+    }
+    g.sync();
+}
+
+// -------------------------------------------------------------- colouring
+// Constraint list = joints (index order) then manifolds (pair order).  Each
+// takes the lowest colour free on both of its dynamic bodies (static bodies
+// impose nothing); the solve order lists constraints colour by colour.
+MSD void stage_color(EnvView& e, const Grp& g) {
+    int nj = e.nj, nman = e.cnt[C_NMAN];
+    int ncons = nj + nman;
+    for (int i = g.lane; i < ncons; i += g.size) {
+        if (i < nj) {
+            int4 jm = e.jm[i];
+            e.cons[i] = make_int4(jm.y, jm.z, 8 * i, 8 | (i << 9));
+        } else {
+            int m = i - nj;
+            int4 M = e.man[m];
+            e.cons[i] = make_int4(M.x, M.y, 8 * nj + 3 * M.w, (3 * M.z) | (1 << 8) | (m << 9));
+        }
+    }
+    for (int b = g.lane; b < e.nb; b += g.size) e.used[b] = 0ull;
+    g.sync();
+    if (g.lane == 0) {
+        int ncol = 0;
+        bool overflow = false;
+        for (int i = 0; i < ncons; i++) {
+            int4 c = e.cons[i];
+            bool da = is_dyn(e, c.x), db = is_dyn(e, c.y);
+            unsigned long long m = (da ? e.used[c.x] : 0ull) | (db ? e.used[c.y] : 0ull);
+            if (m == ~0ull) { e.colr[i] = -1; overflow = true; continue; }
+            int col = __ffsll((long long)~m) - 1;
+            e.colr[i] = col;
+            if (da) e.used[c.x] |= 1ull << col;
+            if (db) e.used[c.y] |= 1ull << col;
+            if (col + 1 > ncol) ncol = col + 1;
+        }
+        for (int c = 0; c <= ncol; c++) e.color_off[c] = 0;
+        for (int i = 0; i < ncons; i++)
+            if (e.colr[i] >= 0) e.color_off[e.colr[i] + 1]++;
+        for (int c = 0; c < ncol; c++) e.color_off[c + 1] += e.color_off[c];
+        // stable scatter; used[] is free again, reuse color_off via a cursor pass
+        for (int c = 0; c < ncol; c++) {
+            int k = e.color_off[c];
+            for (int i = 0; i < ncons; i++)
+                if (e.colr[i] == c) e.order[k++] = i;
+        }
+        e.cnt[C_NCONS] = ncons;
+        e.cnt[C_NCOLORS] = ncol;
+        if (overflow) *e.status |= ST_COLOR;
+    }
+    g.sync();
+    int nrows = 8 * nj + 3 * e.cnt[C_NPTS];
+    for (int r = g.lane; r < nrows; r += g.size) e.rows[r].r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    g.sync();
+}
+
+// ------------------------------------------------------------------- prep
+struct BodyPose {
+    float3 x;
+    float4 q;
+    M3 R;
+    S3 iw;
+    float im;
+};
+
+MSD BodyPose pose_of(const EnvView& e, int i) {
+    BodyPose b;
+    if (i < 0) {
+        b.x = f3(0.f, 0.f, 0.f);
+        b.q = make_float4(0.f, 0.f, 0.f, 1.f);
+        b.R = qmat(b.q);
+        b.iw = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        b.im = 0.f;
+        return b;
+    }
+    b.x = xyz(e.x[i]);
+    b.q = e.q[i];
+    b.R = qmat(b.q);
+    b.iw = e.iw[i];
+    b.im = e.inv[i].w;
+    return b;
+}
+
+MSD float contact_bias(float d, float h, float vmax) { return d >= 0.f ? d / h : fmaxf(d / h, -vmax); }
+
+MSD void finish_row(Row& r, float3 lin, float3 angA, float3 angB, const BodyPose& A, const BodyPose& B,
+                    float bias, int kind, float aux, int partner) {
+    float3 wa = smv(A.iw, angA), wb = smv(B.iw, angB);
+    float k = (A.im + B.im) * dot(lin, lin) + dot(angA, wa) + dot(angB, wb);
+    r.r0 = f4(lin, k > 0.f ? 1.f / k : 0.f);
+    r.r1 = f4(angA, bias);
+    r.r2 = f4(angB, 0.f);
+    r.r3 = f4(wa, k);
+    r.r4 = f4(wb, aux);
+    r.r5 = make_float4(r.r5.x, __int_as_float(kind), __int_as_float(partner), 0.f);
+}
+
+MSD void point_row(Row& r, float3 e_, float3 rA, float3 rB, const BodyPose& A, const BodyPose& B, float bias,
+                   int kind, float aux, int partner) {
+    finish_row(r, e_, cross(rA, e_), cross(e_, rB), A, B, bias, kind, aux, partner);
+}
+
+MSD void ang_row(Row& r, float3 jA, float3 jB, const BodyPose& A, const BodyPose& B, float bias, int kind) {
+    finish_row(r, f3(0.f, 0.f, 0.f), jA, jB, A, B, bias, kind, 0.f, 0);
+}
+
+struct JointGeo {
+    float3 wP, wC, rP, rC, a, c;
+    float phi;
+    float4 qPw, qCw;
+};
+
+MSD JointGeo joint_geo(const EnvView& e, int j, int type, const BodyPose& P, const BodyPose& C) {
+    JointGeo g;
+    float4 f0 = e.jf[4 * j], f1 = e.jf[4 * j + 1], f2 = e.jf[4 * j + 2], f3_ = e.jf[4 * j + 3];
+    g.rP = mv(P.R, xyz(f0));
+    g.rC = mv(C.R, xyz(f2));
+    g.wP = P.x + g.rP;
+    g.wC = C.x + g.rC;
+    g.qPw = qmul(P.q, f1);
+    g.qCw = qmul(C.q, f3_);
+    g.a = qrot(g.qPw, f3(1.f, 0.f, 0.f));
+    g.c = qrot(g.qCw, f3(1.f, 0.f, 0.f));
+    if (type == 0) {
+        float4 qr = qmul(qconj(g.qPw), g.qCw);
+        g.phi = wrap_pi(2.f * atan2f(qr.x, qr.w));
+    } else {
+        g.phi = dot(g.a, g.wC - g.wP);
+    }
+    return g;
+}
+
+MSD void prep_constraint(EnvView& e, int ci, const Params& P) {
+    int4 c = e.cons[ci];
+    int kind = (c.w >> 8) & 1, idx = c.w >> 9;
+    BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
+    Row* R = e.rows + c.z;
+    float h = P.h;
+    if (kind == 1) {
+        int4 M = e.man[idx];
+        int np = M.z;
+        float mu = 0.5f * (e.shape[M.x].w + e.shape[M.y].w);
+        for (int k = 0; k < np; k++) {
+            const float4* pt = e.pts + 3 * (M.w + k);
+            float3 aA = xyz(pt[0]), aB = xyz(pt[1]), n = xyz(pt[2]);
+            float3 rA = mv(A.R, aA), rB = mv(B.R, aB);
+            float d = dot(n, (A.x + rA) - (B.x + rB));
+            int ax = basis_axis(n);
+            float3 t1 = cross(n, axis3(ax));
+            t1 = t1 * (1.f / len(t1));
+            float3 t2 = cross(n, t1);
+            point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), RK_NORMAL, mu, 0);
+            point_row(R[np + 2 * k], t1, rA, rB, A, B, 0.f, RK_FRICTION, mu, k);
+            point_row(R[np + 2 * k + 1], t2, rA, rB, A, B, 0.f, RK_FRICTION, mu, k);
+        }
+    } else {
+        int4 jm = e.jm[idx];
+        float4 jp = e.jp[idx];
+        JointGeo gj = joint_geo(e, idx, jm.x, A, B);
+        if (jm.x == 0) {
+            for (int t = 0; t < 3; t++) {
+                float3 ee = axis3(t);
+                point_row(R[t], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
+            }
+            int k = basis_axis(gj.a);
+            float3 b1 = cross(gj.a, axis3(k));
+            b1 = b1 * (1.f / len(b1));
+            float3 b2 = cross(gj.a, b1);
+            float3 axc = cross(gj.a, gj.c);
+            ang_row(R[3], -b1, b1, A, B, dot(b1, axc) / h, RK_EQ);
+            ang_row(R[4], -b2, b2, A, B, dot(b2, axc) / h, RK_EQ);
+            ang_row(R[5], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), RK_LIMIT);
+            ang_row(R[6], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), RK_LIMIT);
+            ang_row(R[7], -gj.a, gj.a, A, B, 0.f, RK_DRIVE);
+        } else {
+            int k = basis_axis(gj.a);
+            float3 b1 = cross(gj.a, axis3(k));
+            b1 = b1 * (1.f / len(b1));
+            float3 b2 = cross(gj.a, b1);
+            point_row(R[0], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
+            point_row(R[1], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
+            float4 qe = qmul(gj.qPw, qconj(gj.qCw));
+            float sg = qe.w >= 0.f ? 1.f : -1.f;
+            float3 th = f3(2.f * sg * qe.x, 2.f * sg * qe.y, 2.f * sg * qe.z);
+            for (int t = 0; t < 3; t++) {
+                float3 ee = axis3(t);
+                ang_row(R[2 + t], ee, -ee, A, B, comp(th, t) / h, RK_EQ);
+            }
+            point_row(R[5], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), RK_LIMIT, 0.f, 0);
+            point_row(R[6], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), RK_LIMIT, 0.f, 0);
+            point_row(R[7], -gj.a, gj.rP, gj.rC, A, B, 0.f, RK_DRIVE, 0.f, 0);
+        }
+        // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
+        // b = kp C / (h kp + kd), C = phi - target
+        float kp = jp.z, kd = jp.w;
+        float den = h * kp + kd;
+        Row& dr = R[7];
+        if (den > 0.f) {
+            dr.r4.w = 1.f / (h * den);
+            dr.r1.w = kp * (gj.phi - e.jt[idx]) / den;
+        } else {
+            dr.r4.w = 0.f;
+            dr.r1.w = 0.f;
+            dr.r3.w = 0.f;
+            dr.r0.w = 0.f;
+        }
+    }
+}
+
+MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
+    float h = P.h;
+    for (int i = g.lane; i < e.nb; i += g.size) {
+        if (is_dyn(e, i)) {
+            float4 v = e.v[i];
+            v.x += h * P.gx; v.y += h * P.gy; v.z += h * P.gz;
+            e.v[i] = v;
+            float4 iv = e.inv[i];
+            e.iw[i] = rdrt(qmat(e.q[i]), f3(iv.x, iv.y, iv.z));
+        } else {
+            e.iw[i] = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+    }
+    g.sync();
+    int ncons = e.cnt[C_NCONS];
+    for (int ci = g.lane; ci < ncons; ci += g.size) prep_constraint(e, ci, P);
+    g.sync();
+}
+
+// ------------------------------------------------------------------ solve
+// Rows of one constraint, in order, with the two bodies' velocities in
+// registers.  mode 0: warm start (apply lambda); 1: position iteration;
+// 2: relax iteration (drives skipped, relax bias, joint rows unbiased).
+MSD void solve_constraint(EnvView& e, int ci, int mode) {
+    int4 c = e.cons[ci];
+    int nrows = c.w & 0xff;
+    bool da = is_dyn(e, c.x), db = is_dyn(e, c.y);
+    float3 vA = f3(0.f, 0.f, 0.f), wA = vA, vB = vA, wB = vA;
+    float imA = 0.f, imB = 0.f;
+    if (da) { vA = xyz(e.v[c.x]); wA = xyz(e.w[c.x]); imA = e.inv[c.x].w; }
+    if (db) { vB = xyz(e.v[c.y]); wB = xyz(e.w[c.y]); imB = e.inv[c.y].w; }
+    Row* R = e.rows + c.z;
+    for (int r = 0; r < nrows; r++) {
+        Row& row = R[r];
+        float4 r0 = row.r0;
+        float ik = r0.w;
+        if (ik <= 0.f) continue;                     // inert row
+        float4 r5 = row.r5;
+        int kind = __float_as_int(r5.y);
+        float3 lin = xyz(r0);
+        float4 r3 = row.r3, r4 = row.r4;
+        float dl;
+        if (mode == 0) {
+            dl = r5.x;
+        } else {
+            if (mode == 2 && kind == RK_DRIVE) continue;
+            float4 r1 = row.r1, r2 = row.r2;
+            float jv = dot(lin, vA - vB) + dot(xyz(r1), wA) + dot(xyz(r2), wB);
+            float old = r5.x, nl;
+            if (kind == RK_NORMAL || kind == RK_LIMIT) {
+                float bias = mode == 2 ? r2.w : r1.w;
+                nl = fmaxf(old - (jv + bias) * ik, 0.f);
+            } else if (kind == RK_FRICTION) {
+                float lim = r4.w * R[__float_as_int(r5.z)].r5.x;
+                nl = clampf(old - jv * ik, -lim, lim);
+            } else if (kind == RK_EQ) {
+                nl = old - (jv + (mode == 2 ? 0.f : r1.w)) * ik;
+            } else {
+                float gam = r4.w;
+                nl = old - (jv + r1.w + gam * old) / (r3.w + gam);
+            }
+            row.r5.x = nl;
+            dl = nl - old;
+        }
+        vA = vA + lin * (imA * dl);
+        wA = wA + xyz(r3) * dl;
+        vB = vB - lin * (imB * dl);
+        wB = wB + xyz(r4) * dl;
+    }
+    if (da) { e.v[c.x] = f4(vA, 0.f); e.w[c.x] = f4(wA, 0.f); }
+    if (db) { e.v[c.y] = f4(vB, 0.f); e.w[c.y] = f4(wB, 0.f); }
+}
+
+MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
+    int ncol = e.cnt[C_NCOLORS];
+    for (int col = 0; col < ncol; col++) {
+        int k0 = e.color_off[col], k1 = e.color_off[col + 1];
+        for (int k = k0 + g.lane; k < k1; k += g.size) solve_constraint(e, e.order[k], mode);
+        g.sync();
+    }
+}
+
+// -------------------------------------------------------------- integrate
+MSD void relax_constraint(EnvView& e, int ci, const Params& P) {
+    int4 c = e.cons[ci];
+    int kind = (c.w >> 8) & 1, idx = c.w >> 9;
+    Row* R = e.rows + c.z;
+    float h = P.h;
+    if (kind == 1) {
+        int4 M = e.man[idx];
+        BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
+        for (int k = 0; k < M.z; k++) {
+            const float4* pt = e.pts + 3 * (M.w + k);
+            float3 rA = mv(A.R, xyz(pt[0])), rB = mv(B.R, xyz(pt[1]));
+            float d = dot(xyz(pt[2]), (A.x + rA) - (B.x + rB));
+            R[k].r2.w = fmaxf(d, 0.f) / h;
+        }
+    } else {
+        BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
+        int4 jm = e.jm[idx];
+        float4 jp = e.jp[idx];
+        JointGeo gj = joint_geo(e, idx, jm.x, A, B);
+        R[5].r2.w = fmaxf(gj.phi - jp.x, 0.f) / h;
+        R[6].r2.w = fmaxf(jp.y - gj.phi, 0.f) / h;
+    }
+}
+
+MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
+    float h = P.h;
+    for (int i = g.lane; i < e.nb; i += g.size) {
+        if (!is_dyn(e, i)) continue;
+        float4 x = e.x[i], q = e.q[i];
+        float3 v = xyz(e.v[i]), w = xyz(e.w[i]);
+        x.x += h * v.x; x.y += h * v.y; x.z += h * v.z;
+        float4 wq = qmul(make_float4(w.x, w.y, w.z, 0.f), q);
+        q = qnormalize(make_float4(q.x + 0.5f * h * wq.x, q.y + 0.5f * h * wq.y, q.z + 0.5f * h * wq.z,
+                                   q.w + 0.5f * h * wq.w));
+        e.x[i] = x;
+        e.q[i] = q;
+    }
+    g.sync();
+    int ncons = e.cnt[C_NCONS];
+    for (int ci = g.lane; ci < ncons; ci += g.size) relax_constraint(e, ci, P);
+    g.sync();
+}
+
+// end-of-step check: a non-finite state freezes the env
+MSD void stage_check(EnvView& e, const Grp& g) {
+    bool bad = false;
+    for (int i = g.lane; i < e.nb; i += g.size) {
+        float4 x = e.x[i], q = e.q[i], v = e.v[i], w = e.w[i];
+        float s = x.x + x.y + x.z + q.x + q.y + q.z + q.w + v.x + v.y + v.z + w.x + w.y + w.z;
+        bad |= !isfinite(s);
+    }
+    bool any = g.any(bad);
+    if (g.lane == 0 && any) *e.status |= ST_NAN;
+    g.sync();
+}
+
+}  // namespace ms

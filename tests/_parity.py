@@ -1,0 +1,99 @@
+"""Shared helpers of the GPU parity tests: run a scene through the CUDA path
+and through the oracle, and compare them with the step's tolerances."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import scenegen
+
+# tolerances after one step (positions m, velocities m/s, angular rad/s,
+# quaternion components); rollouts of non-chaotic envs use 10x these
+TOL_X, TOL_V, TOL_W, TOL_Q = 1e-5, 1e-4, 1e-4, 1e-5
+TIE_EPS = 1e-5
+
+
+def gpu_run(scene, n_steps, plain=False, tuning=None, stream=True, record=False, calls=1):
+    import torch
+    from paper_2410_00425_b300 import Batch
+    b = Batch(scene, record_contacts=record)
+    if tuning is not None:
+        b.set_tuning(*tuning)
+    s = torch.cuda.Stream() if stream else None
+    done = 0
+    per = n_steps // calls
+    for c in range(calls):
+        n = per if c < calls - 1 else n_steps - done
+        a = scene.actions(done, n)
+        at = None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        if s is not None:
+            s.wait_stream(torch.cuda.current_stream())
+        b.step(at, n, stream=s, plain=plain)
+        done += n
+    if s is not None:
+        torch.cuda.current_stream().wait_stream(s)
+    st = b.state(stream=None)
+    torch.cuda.synchronize()
+    code, status = b.sync()
+    return b, st.cpu().numpy().astype(np.float64), status
+
+
+def oracle_run(scene, n_steps, threads=8, perturb=0.0):
+    o = oracle.Oracle(scene)
+    if perturb:
+        st = o.state()
+        dyn = scene.bodies["mass"] > 0
+        st[dyn, 0] += perturb
+        o.set_state(st)
+    o.step(n_steps, threads=threads)
+    return o
+
+
+def env_errors(scene, a, b):
+    """Per-env max errors (x, v, w, q) between two [NB,13] states."""
+    bo = scene.body_off
+    E = scene.n_envs
+    out = np.zeros((E, 4))
+    for e in range(E):
+        s = slice(bo[e], bo[e + 1])
+        A, B = a[s], b[s]
+        out[e, 0] = np.abs(A[:, 0:3] - B[:, 0:3]).max()
+        out[e, 1] = np.abs(A[:, 7:10] - B[:, 7:10]).max()
+        out[e, 2] = np.abs(A[:, 10:13] - B[:, 10:13]).max()
+        dq = np.minimum(np.abs(A[:, 3:7] - B[:, 3:7]).max(1), np.abs(A[:, 3:7] + B[:, 3:7]).max(1))
+        out[e, 3] = dq.max()
+    return out
+
+
+def within(err, scale=1.0):
+    return ((err[:, 0] <= TOL_X * scale) & (err[:, 1] <= TOL_V * scale) &
+            (err[:, 2] <= TOL_W * scale) & (err[:, 3] <= TOL_Q * scale))
+
+
+def pair_sets_match(batch, o, scene):
+    """Compare kept contact pairs of the last step; pairs the oracle marks as
+    margin ties are excluded.  Returns the list of mismatching envs."""
+    bad = []
+    for e in range(scene.n_envs):
+        gp, gn, _ = batch.contacts(e)
+        op, on, _ = o.manifolds(e)
+        ties = {tuple(t) for t in o.margin_ties(e).tolist()}
+        ties |= {(t[1], t[0]) for t in ties}
+        G = {tuple(p) for p in gp.tolist()} - ties
+        O = {tuple(p) for p in op.tolist()} - ties
+        if G != O:
+            bad.append(e)
+    return bad
+
+
+def non_chaotic(scene, n_steps, threads=8):
+    """Envs whose two FP64 runs from positions 1e-9 m apart stay within
+    1e-6 m after n_steps."""
+    a = oracle_run(scene, n_steps, threads).state()
+    b = oracle_run(scene, n_steps, threads, perturb=1e-9).state()
+    err = env_errors(scene, a, b)
+    return err[:, 0] < 1e-6, a
+
+
+def tie_free(o, scene):
+    return np.array([o.ties(e) == 0 for e in range(scene.n_envs)])

@@ -1,0 +1,216 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: contact pair sets bit-exact except oracle margin ties; after one step
+|dx| <= 1e-5 m, |dv| <= 1e-4 m/s, |dw| <= 1e-4 rad/s, quaternion <= 1e-5;
+200-step rollouts of non-chaotic envs within 10x those bounds.  Envs with a
+tie-adjacent discrete decision in the oracle are counted and excluded from
+the strict comparison."""
+import math
+
+import numpy as np
+import pytest
+
+import scenegen
+from scenegen import validation as V
+
+from _parity import (TOL_X, env_errors, gpu_run, non_chaotic, oracle_run, pair_sets_match, tie_free,
+                     within)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_00425_b300 import build
+    build.build()
+
+
+def test_freefall_closed_form():
+    sc = V.freefall(n_envs=16)
+    _, st, status = gpu_run(sc, 37)
+    p = sc.params
+    h = p["dt"] / p["substeps"]
+    N = 37 * p["substeps"]
+    g = np.array(p["gravity"])
+    x0 = sc.bodies["pos"].astype(np.float64)
+    v0 = sc.bodies["linvel"].astype(np.float64)
+    np.testing.assert_allclose(st[:, 7:10], v0 + N * h * g, atol=1e-4)
+    np.testing.assert_allclose(st[:, 0:3], x0 + N * h * v0 + h * h * g * N * (N + 1) / 2, atol=1e-5)
+    assert not status.any()
+
+
+CASES = [("small", 64), ("arm", 64), ("clutter", 256), ("hand", 64)]
+
+
+@pytest.mark.parametrize("name,n", CASES)
+def test_one_step_parity(name, n):
+    sc = scenegen.make_scene(name, n_envs=n)
+    b, st, status = gpu_run(sc, 1, record=True)
+    o = oracle_run(sc, 1)
+    bad_pairs = pair_sets_match(b, o, sc)
+    assert not bad_pairs, f"pair sets differ in envs {bad_pairs[:10]}"
+    err = env_errors(sc, st, o.state())
+    clean = tie_free(o, sc)
+    ok = within(err)
+    assert clean.mean() >= 0.9, f"too many tie-adjacent envs: {(~clean).sum()}"
+    assert ok[clean].all(), (f"{(~ok[clean]).sum()} of {clean.sum()} envs off; worst "
+                             f"{err[clean].max(0)}")
+    for e in range(sc.n_envs):
+        assert status[e] == o.status(e)
+
+
+@pytest.mark.parametrize("name,n,steps", [("small", 64, 200), ("arm", 32, 200), ("hand", 16, 100)])
+def test_rollout_parity_non_chaotic(name, n, steps):
+    sc = scenegen.make_scene(name, n_envs=n)
+    calm, ost = non_chaotic(sc, steps)
+    o = oracle_run(sc, steps)
+    _, st, _ = gpu_run(sc, steps)
+    err = env_errors(sc, st, ost)
+    clean = calm & tie_free(o, sc)
+    print(f"{name}: {calm.sum()} of {n} envs non-chaotic, {clean.sum()} also tie-free")
+    assert clean.sum() >= 1
+    ok = within(err, 10.0)
+    assert ok[clean].all(), f"worst {err[clean].max(0)}"
+
+
+@pytest.mark.parametrize("name,n", [("arm", 48), ("clutter", 128), ("hand", 32)])
+def test_plain_path_bit_identical_to_batched(name, n):
+    sc = scenegen.make_scene(name, n_envs=n)
+    _, a, sa = gpu_run(sc, 3)
+    _, b, sb = gpu_run(sc, 3, plain=True)
+    assert np.array_equal(a, b)
+    assert np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("tuning", [(16, 4, 1), (8, 4, 1), (4, 8, 1), (32, 2, 0), (8, 8, 0)])
+def test_tuning_does_not_change_results(tuning):
+    sc = scenegen.make_scene("clutter", n_envs=96)
+    _, ref, _ = gpu_run(sc, 2)
+    _, st, _ = gpu_run(sc, 2, tuning=tuning)
+    assert np.array_equal(ref, st)
+
+
+def test_env_result_independent_of_batch_composition():
+    sc = scenegen.make_scene("arm", n_envs=40)
+    _, full, _ = gpu_run(sc, 4)
+    pick = [31, 2, 17]
+    sub = sc.subset(pick)
+    _, part, _ = gpu_run(sub, 4)
+    bo = sc.body_off
+    got = np.concatenate([full[bo[e]:bo[e + 1]] for e in pick])
+    assert np.array_equal(got, part)
+
+
+def test_graph_replay_equals_eager_and_split_calls():
+    sc = scenegen.make_scene("hand", n_envs=24)
+    _, a, _ = gpu_run(sc, 6, stream=True)
+    _, b, _ = gpu_run(sc, 6, stream=False)
+    _, c, _ = gpu_run(sc, 6, stream=True, calls=3)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
+def test_contact_overflow_sets_status_and_matches_oracle():
+    sc = scenegen.make_scene("clutter", n_envs=64)
+    sc.params["contact_capacity"] = 6
+    _, st, status = gpu_run(sc, 1)
+    o = oracle_run(sc, 1)
+    assert any(status & 2)
+    for e in range(sc.n_envs):
+        assert status[e] == o.status(e)
+    err = env_errors(sc, st, o.state())
+    clean = tie_free(o, sc)
+    assert within(err)[clean].all()
+
+
+def test_set_state_checkpoint_restore_is_deterministic():
+    from paper_2410_00425_b300 import Batch
+    sc = scenegen.make_scene("arm", n_envs=16)
+    s = torch.cuda.Stream()
+    b = Batch(sc)
+    acts = torch.from_numpy(sc.actions(0, 10)).cuda()
+    b.step(acts[:5].contiguous(), 5, stream=s)
+    torch.cuda.synchronize()
+    ckpt = b.state().cpu()
+    b.step(acts[5:].contiguous(), 5, stream=s)
+    torch.cuda.synchronize()
+    first = b.state().cpu()
+    b.set_state(ckpt.contiguous(), stream=s)
+    b.step(acts[5:].contiguous(), 5, stream=s)
+    torch.cuda.synchronize()
+    again = b.state().cpu()
+    assert torch.equal(first, again)
+
+
+def test_partial_reset_touches_only_masked_envs():
+    from paper_2410_00425_b300 import Batch
+    sc = scenegen.make_scene("small", n_envs=8)
+    b = Batch(sc)
+    s = torch.cuda.Stream()
+    init = b.state().cpu()
+    b.step(None, 20, stream=s)
+    torch.cuda.synchronize()
+    moved = b.state().cpu()
+    mask = np.zeros(8, np.uint8); mask[[1, 5]] = 1
+    b.set_state(init.contiguous(), env_mask=mask, stream=s)
+    now = b.state().cpu()
+    bo = sc.body_off
+    for e in range(8):
+        ref = init if mask[e] else moved
+        assert torch.equal(now[bo[e]:bo[e + 1]], ref[bo[e]:bo[e + 1]])
+
+
+@pytest.mark.parametrize("scene_fn,steps", [
+    (lambda: V.stack(pos_iters=256), 100),
+    (lambda: V.pendulum(kp=2.0), 100),
+    (lambda: V.slider(), 30),
+    (lambda: V.incline([math.atan(0.6)]), 100),
+    (lambda: V.limit(), 100),
+])
+def test_pin_scenes_follow_oracle(scene_fn, steps):
+    sc = scene_fn()
+    if sc.n_act:
+        acts = np.full((steps, sc.n_envs, sc.n_act), np.nan, np.float32)
+        sc.action_fn = lambda s0, n, a=acts: a[s0:s0 + n]
+        if sc.name == "pendulum":
+            sc.action_fn = lambda s0, n: np.zeros((n, 1, 1), np.float32)
+    o = oracle_run(sc, steps)
+    _, st, _ = gpu_run(sc, steps)
+    err = env_errors(sc, st, o.state())
+    assert within(err, 10.0).all(), err
+
+
+@pytest.mark.parametrize("name", ["small", "arm", "clutter", "hand"])
+def test_full_size_sampled_envs(name):
+    """Full-size batch in the benchmark's launch configuration (autotuned);
+    32 sampled envs are checked against the oracle run on those envs alone."""
+    from paper_2410_00425_b300 import Batch
+    sc = scenegen.make_scene(name)
+    b = Batch(sc, record_contacts=True)
+    s = torch.cuda.Stream()
+    b.autotune(1, stream=s)
+    a = sc.actions(0, 1)
+    b.step(None if a is None else torch.from_numpy(a).cuda(), 1, stream=s)
+    torch.cuda.synchronize()
+    st = b.state().cpu().numpy().astype(np.float64)
+    code, status = b.sync()
+    g = np.random.default_rng(7)
+    pick = sorted(g.choice(sc.n_envs, size=min(32, sc.n_envs), replace=False).tolist())
+    sub = sc.subset(pick)
+    o = oracle_run(sub, 1)
+    bo = sc.body_off
+    mine = np.concatenate([st[bo[e]:bo[e + 1]] for e in pick])
+    err = env_errors(sub, mine, o.state())
+    clean = tie_free(o, sub)
+    assert clean.mean() >= 0.8
+    assert within(err)[clean].all(), err[clean].max(0)
+    for k, e in enumerate(pick):
+        assert status[e] == o.status(k)
+        gp, _, _ = b.contacts(e)
+        op, _, _ = o.manifolds(k)
+        ties = {tuple(t) for t in o.margin_ties(k).tolist()}
+        ties |= {(t[1], t[0]) for t in ties}
+        assert {tuple(p) for p in gp.tolist()} - ties == {tuple(p) for p in op.tolist()} - ties
