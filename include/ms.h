@@ -173,9 +173,11 @@ ms_status ms_get_state(ms_batch* b, ms_state_view* out);
 ms_status ms_copy_state(ms_batch* b, float* dst, int dst_kind, void* stream);
 
 /* Overwrite the state of the envs whose env_mask byte is non-zero
- * (env_mask NULL = all envs) from src float [n_bodies][13] (src_kind 0 =
- * host, 1 = device).  Static bodies keep their pose.  Clears those envs'
- * status bits.  Used for partial resets and checkpoint restore. */
+ * (env_mask NULL = all envs; host array of n_envs bytes) from src float
+ * [n_bodies][13] (src_kind 0 = host, 1 = device), verbatim: quaternions must
+ * be unit, and a state saved with ms_copy_state restores bit for bit.
+ * Static bodies keep their pose.  Clears those envs' status bits.  Used for
+ * partial resets and checkpoint restore.  Returns after the copy is done. */
 ms_status ms_set_state(ms_batch* b, const float* src, int src_kind, const uint8_t* env_mask,
                        void* stream);
 
@@ -207,10 +209,11 @@ ms_status ms_set_record_contacts(ms_batch* b, int record);
 ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t* npts,
                           float* pts, int* count);
 
-/* Batched-path launch shape.  lanes_per_env in {4, 8, 16, 32}: envs per
- * warp = 32 / lanes_per_env; warps_per_cta in [1, 16]; rows_in_smem: keep
- * constraint rows in shared memory (1) or in an L2-resident global slot (0).
- * Any choice gives bit-identical results. */
+/* Batched-path launch shape.  lanes_per_env in {1, 2, 4, 8, 16, 32}: a warp
+ * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 16];
+ * rows_in_smem: keep constraint rows in shared memory (1) or in an
+ * L2-resident global slot per lane group (0).  Any choice gives
+ * bit-identical results. */
 typedef struct {
     int32_t lanes_per_env;
     int32_t warps_per_cta;

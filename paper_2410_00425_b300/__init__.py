@@ -48,8 +48,13 @@ class Batch:
     def step(self, actions=None, n_steps: int = 1, stream=None, plain: bool = False):
         """actions: CUDA float32 tensor [n_steps, E, A] (NaN keeps a target)."""
         if actions is not None:
-            assert actions.is_cuda and actions.dtype.is_floating_point and actions.is_contiguous()
+            import torch
+            assert actions.is_cuda and actions.dtype == torch.float32 and actions.is_contiguous()
             assert tuple(actions.shape) == (n_steps, self.E, self.A), (tuple(actions.shape), (n_steps, self.E, self.A))
+            if isinstance(stream, torch.cuda.Stream):
+                # the step reads the tensor on `stream`: keep its memory from
+                # being reused by the caching allocator until then
+                actions.record_stream(stream)
         fn = _ffi.ms_step_plain if plain else _ffi.ms_step
         fn(self.h, actions, n_steps, stream)
 

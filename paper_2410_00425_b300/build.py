@@ -14,7 +14,9 @@ LIB = os.path.join(HERE, "libmsim.so")
 SOURCES = ["ms_api.cu", "ms_kernels.cu"]
 HEADERS = ["ms_math.cuh", "ms_narrow.cuh", "ms_stages.cuh", "ms_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+# -fmad=false: every fused multiply-add is written out in the source, so the
+# rounding does not depend on how a stage is inlined into a kernel
+FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17", "-fmad=false",
          "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 
 

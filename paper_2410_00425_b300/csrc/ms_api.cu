@@ -72,8 +72,8 @@ struct ms_batch {
     uint8_t* d_mask = nullptr;
     int* d_queue = nullptr;
     int* d_order = nullptr;
-    char* d_rows_global = nullptr;
-    size_t rows_global_bytes = 0;
+    char* d_gscratch = nullptr;
+    size_t gscratch_bytes = 0;
     size_t bytes = 0;
     bool record = false;
     // batched path
@@ -260,7 +260,9 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
             normq(d.quat, qq);
             x[k] = make_float4(d.pos[0], d.pos[1], d.pos[2], 0.f);
             q[k] = make_float4(qq[0], qq[1], qq[2], qq[3]);
-            v[k] = dyn ? make_float4(d.linvel[0], d.linvel[1], d.linvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            // v.w carries the inverse mass (0 for static bodies)
+            v[k] = dyn ? make_float4(d.linvel[0], d.linvel[1], d.linvel[2], (float)(1.0 / (double)d.mass))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
             w[k] = dyn ? make_float4(d.angvel[0], d.angvel[1], d.angvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             shape[k] = make_float4(d.p[0], d.p[1], d.p[2], d.mu);
             if (dyn) {
@@ -372,9 +374,10 @@ extern "C" ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int3
 static ms_status ensure_plain(ms_batch* b) {
     if (b->D.plain_ws) return MS_OK;
     const ms_sim_params& p = b->params;
-    b->D.plain_layout = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, false, true);
+    b->D.plain_layout = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, false, false, true);
     void* ws = nullptr;
-    ms_status s = dmalloc(b, &ws, (size_t)b->E * b->D.plain_layout.bytes);
+    const Layout& L = b->D.plain_layout;
+    ms_status s = dmalloc(b, &ws, (size_t)b->E * (size_t)(L.s_bytes + L.g_bytes));
     if (s) return s;
     b->D.plain_ws = (char*)ws;
     return MS_OK;
@@ -402,14 +405,21 @@ static ms_status configure_fused(ms_batch* b) {
     if (b->fused_ready) return MS_OK;
     const ms_sim_params& p = b->params;
     Tuning& t = b->tune;
-    int gpw = 32 / t.G;
+    int K = 32 / t.G;                               // envs per warp
+    // placement: rows and lists on chip if they fit, else rows, then the
+    // lists, move to the global part of the workspace
     bool rows_smem = t.rows_smem != 0;
-    Layout L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, rows_smem);
-    size_t smem = (size_t)L.bytes * t.warps * gpw;
+    Layout L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, rows_smem, true);
+    size_t smem = (size_t)L.s_bytes * t.warps * K;
     if (smem > b->smem_optin && rows_smem) {
         rows_smem = false;
-        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false);
-        smem = (size_t)L.bytes * t.warps * gpw;
+        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false, true);
+        smem = (size_t)L.s_bytes * t.warps * K;
+    }
+    if (smem > b->smem_optin) {
+
+        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false, false);
+        smem = (size_t)L.s_bytes * t.warps * K;
     }
     if (smem > b->smem_optin)
         return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)", smem, b->smem_optin);
@@ -417,19 +427,17 @@ static ms_status configure_fused(ms_batch* b) {
     int per_sm = 0;
     CK(fused_occupancy(t.G, threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
-    int groups_per_cta = t.warps * gpw;
+    int envs_per_cta = t.warps * K;
     int grid = per_sm * b->sm_count;
-    int need = (b->E + groups_per_cta - 1) / groups_per_cta;
+    int need = (b->E + envs_per_cta - 1) / envs_per_cta;
     if (grid > need) grid = need;
-    if (!rows_smem) {
-        size_t bytes = (size_t)grid * groups_per_cta * L.rows_bytes;
-        if (bytes > b->rows_global_bytes) {
-            void* p2 = nullptr;
-            ms_status s = dmalloc(b, &p2, bytes);
-            if (s) return s;
-            b->d_rows_global = (char*)p2;
-            b->rows_global_bytes = bytes;
-        }
+    size_t gbytes = (size_t)grid * envs_per_cta * L.g_bytes;
+    if (gbytes > b->gscratch_bytes) {
+        void* p2 = nullptr;
+        ms_status s = dmalloc(b, &p2, gbytes);
+        if (s) return s;
+        b->d_gscratch = (char*)p2;
+        b->gscratch_bytes = gbytes;
     }
     t.rows_smem = rows_smem ? 1 : 0;
     b->fused_layout = L;
@@ -446,7 +454,7 @@ static FusedCfg fused_cfg(ms_batch* b) {
     C.layout = b->fused_layout;
     C.queue = b->d_queue;
     C.order = b->d_order;
-    C.rows_global = b->d_rows_global;
+    C.gscratch = b->d_gscratch;
     return C;
 }
 
@@ -624,8 +632,8 @@ extern "C" ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pai
 
 extern "C" ms_status ms_set_tuning(ms_batch* b, const ms_tuning* t) {
     if (!b || !t) return fail(MS_ERR_INVALID_ARG, "NULL argument");
-    if (t->lanes_per_env != 4 && t->lanes_per_env != 8 && t->lanes_per_env != 16 && t->lanes_per_env != 32)
-        return fail(MS_ERR_INVALID_ARG, "lanes_per_env must be 4, 8, 16 or 32");
+    if (!fused_supported(t->lanes_per_env))
+        return fail(MS_ERR_INVALID_ARG, "lanes_per_env must be 1, 2, 4, 8, 16 or 32");
     if (t->warps_per_cta < 1 || t->warps_per_cta > 16) return fail(MS_ERR_INVALID_ARG, "warps_per_cta must be in [1, 16]");
     Tuning old = b->tune;
     b->tune.G = t->lanes_per_env;
@@ -723,8 +731,8 @@ extern "C" ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_pat
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     ms_tuning bt = {b->tune.G, b->tune.warps, b->tune.rows_smem, 0};
-    const int Gs[] = {32, 16, 8, 4};
-    const int Ws[] = {2, 4, 8};
+    const int Gs[] = {32, 16, 8, 4, 2, 1};
+    const int Ws[] = {1, 2, 4, 8};
     for (int G : Gs)
         for (int W : Ws)
             for (int R = 1; R >= 0; R--) {
@@ -774,8 +782,8 @@ extern "C" ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* j
     // resident state and parameters, the staging buffer and the per-env
     // workspace of the plain path (the batched path's is per resident slot)
     size_t state = NB * (16 * 6 + 8 + 8 + 4 + 52) + NJ * (64 + 16 + 16 + 4) + (size_t)n_envs * 16 + 64;
-    Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, true);
-    *bytes = state + (size_t)n_envs * L.bytes;
+    Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, false, true);
+    *bytes = state + (size_t)n_envs * (size_t)(L.s_bytes + L.g_bytes);
     return MS_OK;
 }
 

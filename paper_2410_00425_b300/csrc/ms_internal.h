@@ -8,17 +8,27 @@
 
 namespace ms {
 
-// Byte offsets of one env's arrays inside a workspace slot (-1: absent).
+// Byte offsets of one env's arrays inside its workspace (-1: absent).  The
+// workspace has a shared part (bodies, joints, colour lists, impulses: the
+// data every sweep touches; in shared memory on the batched path) and a
+// global part (AABBs, pairs, manifolds, contact anchors: written once per
+// step; rows unless they fit the shared part).  The plain path keeps both
+// parts in one global slot per env.
 struct Layout {
-    int bytes;
+    int s_bytes;
     int x, q, v, w, shape, inv, meta, adj;  // body copies (batched path only)
     int jf, jp, jm, jt;                     // joint copies (batched path only)
-    int iw, aabb, pairs, man, pts, cons, colr, order, color_off, used, cnt, status;
-    int rows;                               // -1: rows live in a global slot
+    int iw, cons, colr, scons, color_off, used, lam, cnt, status;
+    bool lists_shared;                      // cons, colr, scons, lam in the shared part
+    int rows_s;                             // rows in the shared part, or -1
+    int g_bytes;
+    int aabb, pairs, man, pts;
+    int rows_g;                             // rows in the global part, or -1
     int rows_bytes;
 };
 
-Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool with_rows);
+Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool rows_shared,
+                   bool lists_shared);
 
 // Kernel-side view of a batch (plain pointers, passed by value).
 struct DevParams {
@@ -55,11 +65,12 @@ struct FusedCfg {
     Layout layout;
     int* queue;
     const int* order;
-    char* rows_global;
+    char* gscratch;        // global part of every lane group's workspace
 };
 
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s);
 cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm);
+bool fused_supported(int G);
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,
                          int grid, int threads, size_t smem, cudaStream_t s);
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);

@@ -2,12 +2,13 @@
 //
 // Plain path: one 32-thread block per env, one launch per stage and per
 // solver sweep; the env's bodies are read from the resident global SoA and
-// its workspace (pairs, manifolds, constraints, rows) lives in a global slot.
+// its workspace lives in a global slot per env.
 //
-// Batched path: a persistent kernel whose lane groups (4..32 lanes) pop env
-// tickets from a queue ordered longest-first, copy the env's bodies and
-// joints into a shared-memory slot, run all n_steps on chip and write the
-// state back once.  No wait in either kernel spins on another thread.
+// Batched path: a persistent kernel.  Each warp pops 32 / G env tickets at
+// once from a queue ordered longest-first, copies those envs' bodies and
+// joints into shared-memory slots, runs all n_steps for all of them in
+// lockstep (G lanes per env) and writes the state back once.  No wait in
+// either kernel spins on another thread.
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -16,12 +17,15 @@ namespace ms {
 // ------------------------------------------------------------ slot layout
 static int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool with_rows) {
+Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool rows_shared,
+                   bool lists_shared) {
     Layout L;
+    int nb = max_nb > 0 ? max_nb : 1, nj = max_nj > 0 ? max_nj : 1;
+    int pc = pair_cap > 0 ? pair_cap : 1, cc = contact_cap > 0 ? contact_cap : 1;
+    int ncons = max_nj + (pc < cc ? pc : cc);      // every manifold has at least one point
+    int nrows = 8 * max_nj + 3 * cc;
     int o = 0;
     auto take = [&](int bytes, int al) { o = align_up(o, al); int r = o; o += bytes; return r; };
-    int nb = max_nb > 0 ? max_nb : 1, nj = max_nj > 0 ? max_nj : 1;
-    int ncons = max_nj + pair_cap;
     if (with_bodies) {
         L.x = take(16 * nb, 16); L.q = take(16 * nb, 16); L.v = take(16 * nb, 16); L.w = take(16 * nb, 16);
         L.shape = take(16 * nb, 16); L.inv = take(16 * nb, 16); L.meta = take(8 * nb, 8);
@@ -30,44 +34,59 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     } else {
         L.x = L.q = L.v = L.w = L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = -1;
     }
-    L.iw = take((int)sizeof(S3) * nb, 4);
-    L.aabb = take(32 * nb, 16);
-    L.pairs = take(4 * (pair_cap > 0 ? pair_cap : 1), 4);
-    L.man = take(16 * (pair_cap > 0 ? pair_cap : 1), 16);
-    L.pts = take(48 * (contact_cap > 0 ? contact_cap : 1), 16);
-    L.cons = take(16 * (ncons > 0 ? ncons : 1), 16);
-    L.colr = take(4 * (ncons > 0 ? ncons : 1), 4);
-    L.order = take(4 * (ncons > 0 ? ncons : 1), 4);
+    L.iw = take(32 * nb, 16);
     L.color_off = take(4 * (MAX_COLORS + 1), 4);
     L.used = take(8 * nb, 8);
     L.cnt = take(4 * C_NUM, 16);
     L.status = take(4, 4);
-    L.rows_bytes = (int)sizeof(Row) * (8 * max_nj + 3 * contact_cap);
-    if (L.rows_bytes <= 0) L.rows_bytes = (int)sizeof(Row);
-    L.rows = with_rows ? take(L.rows_bytes, 16) : -1;
-    L.bytes = align_up(o, 16);
+    L.lists_shared = lists_shared;
+    if (lists_shared) {
+        L.cons = take(16 * ncons, 16);
+        L.colr = take(4 * ncons, 4);
+        L.scons = take(16 * ncons, 16);
+        L.lam = take(4 * nrows, 4);
+    }
+    L.rows_bytes = (int)sizeof(Row) * nrows;
+    L.rows_s = rows_shared ? take(L.rows_bytes, 16) : -1;
+    L.s_bytes = align_up(o, 16);
+    o = 0;
+    if (!lists_shared) {
+        L.cons = take(16 * ncons, 16);
+        L.colr = take(4 * ncons, 4);
+        L.scons = take(16 * ncons, 16);
+        L.lam = take(4 * nrows, 4);
+    }
+    L.aabb = take(32 * nb, 16);
+    L.pairs = take(4 * pc, 4);
+    L.man = take(16 * pc, 16);
+    L.pts = take(48 * cc, 16);
+    L.rows_g = rows_shared ? -1 : take(L.rows_bytes, 16);
+    L.g_bytes = align_up(o, 16);
     return L;
 }
 
 template <typename T>
 __device__ __forceinline__ T* at(char* base, int off) { return reinterpret_cast<T*>(base + off); }
 
-__device__ __forceinline__ void view_workspace(EnvView& e, char* ws, const Layout& L) {
-    e.iw = at<S3>(ws, L.iw);
-    e.aabb = at<float4>(ws, L.aabb);
-    e.pairs = at<int>(ws, L.pairs);
-    e.man = at<int4>(ws, L.man);
-    e.pts = at<float4>(ws, L.pts);
-    e.cons = at<int4>(ws, L.cons);
-    e.colr = at<int>(ws, L.colr);
-    e.order = at<int>(ws, L.order);
-    e.color_off = at<int>(ws, L.color_off);
-    e.used = at<unsigned long long>(ws, L.used);
-    e.cnt = at<int>(ws, L.cnt);
+__device__ __forceinline__ void view_workspace(EnvView& e, char* s, char* gl, const Layout& L) {
+    e.iw = at<float4>(s, L.iw);
+    char* lb = L.lists_shared ? s : gl;
+    e.cons = at<int4>(lb, L.cons);
+    e.colr = at<int>(lb, L.colr);
+    e.scons = at<int4>(lb, L.scons);
+    e.lam = at<float>(lb, L.lam);
+    e.color_off = at<int>(s, L.color_off);
+    e.used = at<unsigned long long>(s, L.used);
+    e.cnt = at<int>(s, L.cnt);
+    e.aabb = at<float4>(gl, L.aabb);
+    e.pairs = at<int>(gl, L.pairs);
+    e.man = at<int4>(gl, L.man);
+    e.pts = at<float4>(gl, L.pts);
+    e.rows = L.rows_s >= 0 ? at<Row>(s, L.rows_s) : at<Row>(gl, L.rows_g);
 }
 
-__device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env) {
-    if (D.rec_man) {
+__device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
+    if (D.rec_man && active) {
         e.rec_man = D.rec_man + (size_t)env * D.P.pair_cap;
         e.rec_pts = D.rec_pts + (size_t)env * D.P.contact_cap * 10;
         e.rec_cnt = D.rec_cnt + env;
@@ -85,56 +104,50 @@ __device__ __forceinline__ EnvView plain_view(const DevBatch& D, int env) {
     e.x = D.x + b0; e.q = D.q + b0; e.v = D.v + b0; e.w = D.w + b0;
     e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
     e.jf = D.jf + 4 * j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
-    char* ws = D.plain_ws + (size_t)env * D.plain_layout.bytes;
-    view_workspace(e, ws, D.plain_layout);
-    e.rows = at<Row>(ws, D.plain_layout.rows);
+    const Layout& L = D.plain_layout;
+    char* s = D.plain_ws + (size_t)env * (L.s_bytes + L.g_bytes);
+    view_workspace(e, s, s + L.s_bytes, L);
     e.status = D.status + env;
-    view_record(e, D, env);
+    view_record(e, D, env, true);
+    if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }   // frozen
     return e;
 }
 
 __device__ __forceinline__ Grp warp_grp() {
     Grp g;
-    g.lane = threadIdx.x & 31; g.size = 32; g.base = 0; g.mask = 0xffffffffu;
+    g.lane = threadIdx.x & 31; g.size = 32; g.base = 0;
     return g;
 }
 
 __global__ void k_begin_step(DevBatch D, const float* actions, int step) {
     int env = blockIdx.x;
     EnvView e = plain_view(D, env);
-    if (*e.status & ST_NAN) return;
     Grp g = warp_grp();
     stage_actions(e, g, actions ? actions + ((size_t)step * D.E + env) * D.A : nullptr, D.A);
     stage_broadphase(e, g, D.P);
 }
 __global__ void k_narrow(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_narrowphase(e, warp_grp(), D.P);
 }
 __global__ void k_color(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_color(e, warp_grp());
 }
 __global__ void k_prep(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_prep(e, warp_grp(), D.P);
 }
 __global__ void k_sweep(DevBatch D, int mode) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_sweep(e, warp_grp(), mode);
 }
 __global__ void k_integrate(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_integrate(e, warp_grp(), D.P);
 }
 __global__ void k_check(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    if (*e.status & ST_NAN) return;
     stage_check(e, warp_grp());
 }
 
@@ -166,92 +179,112 @@ template <int G>
 __global__ void __launch_bounds__(512) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
+    constexpr int K = 32 / G;                  // envs per warp
     int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-    constexpr int GPW = 32 / G;
-    int gw = wl / G;
+    int gi = wl / G;
     Grp g;
-    g.lane = wl % G; g.size = G; g.base = gw * G;
-    g.mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << g.base);
-    int slot_id = warp * GPW + gw;
-    char* slot = smem + (size_t)slot_id * L.bytes;
-    size_t gslot = (size_t)blockIdx.x * (blockDim.x / 32) * GPW + slot_id;
-    Row* rows = L.rows >= 0 ? at<Row>(slot, L.rows)
-                            : reinterpret_cast<Row*>(C.rows_global + gslot * (size_t)L.rows_bytes);
+    g.lane = wl % G; g.size = G; g.base = gi * G;
+    int slot_id = warp * K + gi;
+    char* s = smem + (size_t)slot_id * L.s_bytes;
+    size_t gslot = ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * K + gi;
+    char* gl = C.gscratch + gslot * (size_t)L.g_bytes;
 
     EnvView e;
-    e.x = at<float4>(slot, L.x); e.q = at<float4>(slot, L.q); e.v = at<float4>(slot, L.v);
-    e.w = at<float4>(slot, L.w);
-    float4* shp = at<float4>(slot, L.shape);
-    float4* inv = at<float4>(slot, L.inv);
-    int2* meta = at<int2>(slot, L.meta);
-    unsigned long long* adj = at<unsigned long long>(slot, L.adj);
-    float4* jf = at<float4>(slot, L.jf);
-    float4* jp = at<float4>(slot, L.jp);
-    int4* jm = at<int4>(slot, L.jm);
+    e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
+    float4* shp = at<float4>(s, L.shape);
+    float4* inv = at<float4>(s, L.inv);
+    int2* meta = at<int2>(s, L.meta);
+    unsigned long long* adj = at<unsigned long long>(s, L.adj);
+    float4* jf = at<float4>(s, L.jf);
+    float4* jp = at<float4>(s, L.jp);
+    int4* jm = at<int4>(s, L.jm);
     e.shape = shp; e.inv = inv; e.meta = meta; e.adj = adj; e.jf = jf; e.jp = jp; e.jm = jm;
-    e.jt = at<float>(slot, L.jt);
-    view_workspace(e, slot, L);
-    e.rows = rows;
-    e.status = at<unsigned>(slot, L.status);
+    e.jt = at<float>(s, L.jt);
+    view_workspace(e, s, gl, L);
+    e.status = at<unsigned>(s, L.status);
 
     for (;;) {
-        int t = 0;
-        if (g.lane == 0) t = atomicAdd(C.queue, 1);
-        t = g.shfl(t, 0);
-        if (t >= D.E) break;
-        int env = C.order[t];
-        int b0 = D.body_off[env], j0 = D.joint_off[env];
-        e.nb = D.body_off[env + 1] - b0;
-        e.nj = D.joint_off[env + 1] - j0;
-        for (int i = g.lane; i < e.nb; i += G) {
-            e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i];
-            shp[i] = D.shape[b0 + i]; inv[i] = D.inv[b0 + i]; meta[i] = D.meta[b0 + i]; adj[i] = D.adj[b0 + i];
+        int t0 = 0;
+        if (wl == 0) t0 = atomicAdd(C.queue, K);
+        t0 = __shfl_sync(FULL_MASK, t0, 0);
+        if (t0 >= D.E) break;                            // warp-uniform
+        int t = t0 + gi;
+        bool active = t < D.E;
+        int env = active ? C.order[t] : 0;
+        int b0 = 0, j0 = 0, nb = 0, nj = 0;
+        if (active) {
+            b0 = D.body_off[env]; j0 = D.joint_off[env];
+            nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
         }
-        for (int j = g.lane; j < e.nj; j += G) {
-            jf[4 * j] = D.jf[4 * (j0 + j)]; jf[4 * j + 1] = D.jf[4 * (j0 + j) + 1];
-            jf[4 * j + 2] = D.jf[4 * (j0 + j) + 2]; jf[4 * j + 3] = D.jf[4 * (j0 + j) + 3];
-            jp[j] = D.jp[j0 + j]; jm[j] = D.jm[j0 + j]; e.jt[j] = D.jt[j0 + j];
-        }
-        if (g.lane == 0) *e.status = D.status[env];
-        view_record(e, D, env);
-        g.sync();
-        if (!(*e.status & ST_NAN)) {
-            for (int k = 0; k < n_steps; k++) {
-                stage_actions(e, g, actions ? actions + ((size_t)k * D.E + env) * D.A : nullptr, D.A);
-                stage_broadphase(e, g, D.P);
-                stage_narrowphase(e, g, D.P);
-                stage_color(e, g);
-                for (int sub = 0; sub < D.P.substeps; sub++) {
-                    stage_prep(e, g, D.P);
-                    stage_sweep(e, g, 0);
-                    for (int it = 0; it < D.P.pos_iters; it++) stage_sweep(e, g, 1);
-                    stage_integrate(e, g, D.P);
-                    for (int it = 0; it < D.P.vel_iters; it++) stage_sweep(e, g, 2);
-                }
-                stage_check(e, g);
-                if (*e.status & ST_NAN) break;
+        int nbmax = g.wmax(nb), njmax = g.wmax(nj);
+        for (int i0 = 0; i0 < nbmax; i0 += G) {
+            int i = i0 + g.lane;
+            if (i < nb) {
+                e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i];
+                shp[i] = D.shape[b0 + i]; inv[i] = D.inv[b0 + i]; meta[i] = D.meta[b0 + i];
+                adj[i] = D.adj[b0 + i];
             }
         }
-        for (int i = g.lane; i < e.nb; i += G) {
-            D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i];
+        for (int k0 = 0; k0 < njmax; k0 += G) {
+            int j = k0 + g.lane;
+            if (j < nj) {
+                const float4* src = D.jf + 4 * (size_t)(j0 + j);
+                jf[4 * j] = src[0]; jf[4 * j + 1] = src[1]; jf[4 * j + 2] = src[2]; jf[4 * j + 3] = src[3];
+                jp[j] = D.jp[j0 + j]; jm[j] = D.jm[j0 + j]; e.jt[j] = D.jt[j0 + j];
+            }
         }
-        for (int j = g.lane; j < e.nj; j += G) D.jt[j0 + j] = e.jt[j];
-        if (g.lane == 0) D.status[env] = *e.status;
+        if (g.lane == 0) *e.status = active ? D.status[env] : 0u;
+        view_record(e, D, env, active);
+        g.sync();
+        bool frozen = (*e.status & ST_NAN) != 0;
+        e.nb = frozen ? 0 : nb;
+        e.nj = frozen ? 0 : nj;
+        for (int k = 0; k < n_steps; k++) {
+            const float* act = (actions && active) ? actions + ((size_t)k * D.E + env) * D.A : nullptr;
+            stage_actions(e, g, act, D.A);
+            stage_broadphase(e, g, D.P);
+            stage_narrowphase(e, g, D.P);
+            stage_color(e, g);
+            for (int sub = 0; sub < D.P.substeps; sub++) {
+                stage_prep(e, g, D.P);
+                stage_sweep(e, g, 0);
+                for (int it = 0; it < D.P.pos_iters; it++) stage_sweep(e, g, 1);
+                stage_integrate(e, g, D.P);
+                for (int it = 0; it < D.P.vel_iters; it++) stage_sweep(e, g, 2);
+            }
+            stage_check(e, g);
+            if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
+        }
+        for (int i0 = 0; i0 < nbmax; i0 += G) {
+            int i = i0 + g.lane;
+            if (i < nb) { D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i]; }
+        }
+        for (int k0 = 0; k0 < njmax; k0 += G) {
+            int j = k0 + g.lane;
+            if (j < nj) D.jt[j0 + j] = e.jt[j];
+        }
+        if (g.lane == 0 && active) D.status[env] = *e.status;
         g.sync();
     }
 }
 
 static const void* fused_fn(int G) {
     switch (G) {
+    case 1: return (const void*)k_fused<1>;
+    case 2: return (const void*)k_fused<2>;
     case 4: return (const void*)k_fused<4>;
     case 8: return (const void*)k_fused<8>;
     case 16: return (const void*)k_fused<16>;
-    default: return (const void*)k_fused<32>;
+    case 32: return (const void*)k_fused<32>;
+    default: return nullptr;
     }
 }
 
+bool fused_supported(int G) { return fused_fn(G) != nullptr; }
+
 cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm) {
     const void* fn = fused_fn(G);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
@@ -259,8 +292,10 @@ cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm)
 
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,
                          int grid, int threads, size_t smem, cudaStream_t s) {
+    const void* fn = fused_fn(G);
+    if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&D, (void*)&actions, (void*)&n_steps, (void*)&C};
-    return cudaLaunchKernel(fused_fn(G), dim3(grid), dim3(threads), args, smem, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
 }
 
 // -------------------------------------------------------- state transfer
@@ -275,16 +310,18 @@ __global__ void k_pack_state(DevBatch D, float* out) {
     o[10] = w.x; o[11] = w.y; o[12] = w.z;
 }
 
+// restores dynamic bodies verbatim (a checkpoint round-trips bit for bit);
+// static bodies keep their pose
 __global__ void k_unpack_state(DevBatch D, const float* in, const uint8_t* env_mask, const int* body_env) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D.NB) return;
     int env = body_env[i];
     if (env_mask && !env_mask[env]) return;
-    if (!((D.meta[i].x >> 8) & 1)) return;           // static bodies keep their pose
+    if (!((D.meta[i].x >> 8) & 1)) return;
     const float* s = in + 13 * (size_t)i;
     D.x[i] = make_float4(s[0], s[1], s[2], 0.f);
-    D.q[i] = qnormalize(make_float4(s[3], s[4], s[5], s[6]));
-    D.v[i] = make_float4(s[7], s[8], s[9], 0.f);
+    D.q[i] = make_float4(s[3], s[4], s[5], s[6]);
+    D.v[i] = make_float4(s[7], s[8], s[9], D.v[i].w);     // .w keeps the inverse mass
     D.w[i] = make_float4(s[10], s[11], s[12], 0.f);
 }
 

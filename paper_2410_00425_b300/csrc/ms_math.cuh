@@ -1,6 +1,12 @@
 // Device math for the batched rigid-body step: float3 algebra, quaternions
 // (x, y, z, w; Hamilton product), rotation matrices and symmetric 3x3
 // inverse-inertia tensors.  FP32 throughout.
+//
+// The library is compiled with automatic multiply-add contraction off, and
+// every fused multiply-add here is written out (fmaf).  The rounding of each
+// operation is therefore fixed by this source, not by how the compiler
+// inlines it into a kernel: the plain and batched kernels, and every launch
+// shape, produce bit-identical results.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,9 +18,11 @@ MSD float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z +
 MSD float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
 MSD float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
 MSD float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
-MSD float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// a + b * s, one rounding per component
+MSD float3 madd(float3 a, float3 b, float s) { return f3(fmaf(b.x, s, a.x), fmaf(b.y, s, a.y), fmaf(b.z, s, a.z)); }
+MSD float dot(float3 a, float3 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
 MSD float3 cross(float3 a, float3 b) {
-    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return f3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x)));
 }
 MSD float len(float3 a) { return sqrtf(dot(a, a)); }
 MSD float comp(float3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
@@ -28,13 +36,16 @@ MSD float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
 MSD float4 f4(float3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
 
 MSD float4 qmul(float4 a, float4 b) {
+    // (a_v, a_w)(b_v, b_w) = (a_w b_v + b_w a_v + a_v x b_v, a_w b_w - a_v.b_v)
     float3 av = xyz(a), bv = xyz(b);
-    float3 r = bv * a.w + av * b.w + cross(av, bv);
-    return make_float4(r.x, r.y, r.z, a.w * b.w - dot(av, bv));
+    float3 c = cross(av, bv);
+    float3 r = f3(fmaf(a.w, bv.x, fmaf(b.w, av.x, c.x)), fmaf(a.w, bv.y, fmaf(b.w, av.y, c.y)),
+                  fmaf(a.w, bv.z, fmaf(b.w, av.z, c.z)));
+    return make_float4(r.x, r.y, r.z, fmaf(a.w, b.w, -dot(av, bv)));
 }
 MSD float4 qconj(float4 a) { return make_float4(-a.x, -a.y, -a.z, a.w); }
 MSD float4 qnormalize(float4 a) {
-    float n = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w);
+    float n = sqrtf(fmaf(a.w, a.w, fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x))));
     return make_float4(a.x / n, a.y / n, a.z / n, a.w / n);
 }
 
@@ -43,20 +54,21 @@ struct M3 { float m[9]; };
 MSD M3 qmat(float4 q) {
     M3 R;
     float x = q.x, y = q.y, z = q.z, w = q.w;
-    R.m[0] = 1.f - 2.f * (y * y + z * z); R.m[1] = 2.f * (x * y - z * w); R.m[2] = 2.f * (x * z + y * w);
-    R.m[3] = 2.f * (x * y + z * w); R.m[4] = 1.f - 2.f * (x * x + z * z); R.m[5] = 2.f * (y * z - x * w);
-    R.m[6] = 2.f * (x * z - y * w); R.m[7] = 2.f * (y * z + x * w); R.m[8] = 1.f - 2.f * (x * x + y * y);
+    float xx = x * x, yy = y * y, zz = z * z;
+    R.m[0] = 1.f - 2.f * (yy + zz); R.m[1] = 2.f * fmaf(x, y, -(z * w)); R.m[2] = 2.f * fmaf(x, z, y * w);
+    R.m[3] = 2.f * fmaf(x, y, z * w); R.m[4] = 1.f - 2.f * (xx + zz); R.m[5] = 2.f * fmaf(y, z, -(x * w));
+    R.m[6] = 2.f * fmaf(x, z, -(y * w)); R.m[7] = 2.f * fmaf(y, z, x * w); R.m[8] = 1.f - 2.f * (xx + yy);
     return R;
 }
 MSD float3 mv(const M3& R, float3 a) {
-    return f3(R.m[0] * a.x + R.m[1] * a.y + R.m[2] * a.z,
-              R.m[3] * a.x + R.m[4] * a.y + R.m[5] * a.z,
-              R.m[6] * a.x + R.m[7] * a.y + R.m[8] * a.z);
+    return f3(fmaf(R.m[2], a.z, fmaf(R.m[1], a.y, R.m[0] * a.x)),
+              fmaf(R.m[5], a.z, fmaf(R.m[4], a.y, R.m[3] * a.x)),
+              fmaf(R.m[8], a.z, fmaf(R.m[7], a.y, R.m[6] * a.x)));
 }
 MSD float3 mtv(const M3& R, float3 a) {
-    return f3(R.m[0] * a.x + R.m[3] * a.y + R.m[6] * a.z,
-              R.m[1] * a.x + R.m[4] * a.y + R.m[7] * a.z,
-              R.m[2] * a.x + R.m[5] * a.y + R.m[8] * a.z);
+    return f3(fmaf(R.m[6], a.z, fmaf(R.m[3], a.y, R.m[0] * a.x)),
+              fmaf(R.m[7], a.z, fmaf(R.m[4], a.y, R.m[1] * a.x)),
+              fmaf(R.m[8], a.z, fmaf(R.m[5], a.y, R.m[2] * a.x)));
 }
 MSD float3 mcol(const M3& R, int j) { return f3(R.m[j], R.m[3 + j], R.m[6 + j]); }
 MSD float3 qrot(float4 q, float3 a) { M3 R = qmat(q); return mv(R, a); }
@@ -64,24 +76,24 @@ MSD float3 qrot(float4 q, float3 a) { M3 R = qmat(q); return mv(R, a); }
 // symmetric 3x3 stored (xx, xy, xz, yy, yz, zz)
 struct S3 { float xx, xy, xz, yy, yz, zz; };
 MSD float3 smv(const S3& I, float3 v) {
-    return f3(I.xx * v.x + I.xy * v.y + I.xz * v.z,
-              I.xy * v.x + I.yy * v.y + I.yz * v.z,
-              I.xz * v.x + I.yz * v.y + I.zz * v.z);
+    return f3(fmaf(I.xz, v.z, fmaf(I.xy, v.y, I.xx * v.x)),
+              fmaf(I.yz, v.z, fmaf(I.yy, v.y, I.xy * v.x)),
+              fmaf(I.zz, v.z, fmaf(I.yz, v.y, I.xz * v.x)));
 }
 // R diag(d) R^T
 MSD S3 rdrt(const M3& R, float3 d) {
-    S3 s;
     float dd[3] = {d.x, d.y, d.z};
     float o[9];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; k++) acc += R.m[3 * i + k] * dd[k] * R.m[3 * j + k];
+            float acc = (R.m[3 * i] * dd[0]) * R.m[3 * j];
+            acc = fmaf(R.m[3 * i + 1] * dd[1], R.m[3 * j + 1], acc);
+            acc = fmaf(R.m[3 * i + 2] * dd[2], R.m[3 * j + 2], acc);
             o[3 * i + j] = acc;
         }
+    S3 s;
     s.xx = o[0]; s.xy = o[1]; s.xz = o[2]; s.yy = o[4]; s.yz = o[5]; s.zz = o[8];
     return s;
 }

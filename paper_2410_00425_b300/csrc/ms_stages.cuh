@@ -1,18 +1,23 @@
 // Stages of the batched rigid-body step, written once over an "env view"
-// (pointers to one env's bodies, joints and workspace) and a lane group
-// (G = 4..32 lanes of one warp working on that env).  The plain path calls
-// each stage from its own kernel with the view in global memory; the
-// batched path calls all of them from one persistent kernel with the view
-// in shared memory.  The arithmetic is the same code in both, so the two
-// paths agree bit for bit.
+// (pointers to one env's bodies, joints and workspace) and a lane group of
+// G lanes (G = 1..32) that owns the env.  A warp runs 32 / G envs in
+// lockstep: every loop bound below is the maximum over the warp, so all
+// lanes execute the same instruction stream and the warp-wide intrinsics
+// (__syncwarp, ballot, shuffles) always see the full warp.  Inactive or
+// frozen envs take part with zero counts.
+//
+// The plain path calls each stage from its own kernel (G = 32, one env per
+// warp, workspace in global memory); the batched path calls all of them from
+// one persistent kernel (bodies, joints, colour lists and impulses in
+// shared memory).  Both run this code, so they agree bit for bit.
 //
 // Per step: drive targets <- actions; broadphase; narrowphase; colouring
 // (once per step, at the step-start poses).  Per substep: gravity + world
-// inverse inertia + rows; warm start; pos_iters sweeps; integration +
-// relax bias; vel_iters relax sweeps.  The solver is substepped sequential
-// impulses (Catto 2005) in the small-steps arrangement of Macklin et al.
-// 2019, with PD drives as soft constraints (Catto 2011), a per-row Coulomb
-// pyramid and a relax pass without penetration push.
+// inverse inertia + rows; warm start; pos_iters sweeps; integration + relax
+// bias; vel_iters relax sweeps.  The solver is substepped sequential impulses
+// (Catto 2005) in the small-steps arrangement of Macklin et al. 2019, with
+// PD drives as soft constraints (Catto 2011), a per-row Coulomb pyramid and
+// a relax pass without penetration push.
 #pragma once
 #include "ms_internal.h"
 #include "ms_narrow.cuh"
@@ -25,18 +30,21 @@ enum { RK_NORMAL = 0, RK_FRICTION = 1, RK_EQ = 2, RK_LIMIT = 3, RK_DRIVE = 4 };
 enum { ST_PAIR = 1u, ST_CONTACT = 2u, ST_COLOR = 4u, ST_NAN = 8u };
 enum { C_NPAIRS = 0, C_NMAN = 1, C_NPTS = 2, C_NCONS = 3, C_NCOLORS = 4, C_NUM = 8 };
 enum { MAX_COLORS = 64 };
+#define FULL_MASK 0xffffffffu
 
-// One constraint row (96 B, six float4 for vector loads).
-//   r0 = lin, inv_k   r1 = angA, bias     r2 = angB, relax_bias
-//   r3 = I_A^-1 angA, k                   r4 = I_B^-1 angB, aux (mu | gamma)
-//   r5 = lambda, kind (int bits), partner row within the constraint, -
+// One constraint row, 64 B, read-only during the sweeps:
+//   r0 = lin, 1/k (1/(k + gamma) for a drive; 0 = inert row)
+//   r1 = angA, bias        r2 = angB, relax bias (0 for joint rows)
+//   r3 = mu (friction, else 0), kind | partner << 4 (int bits), gamma
+//        (drive, else 0), k
+// The accumulated impulse lambda of each row lives in a separate array.
 struct Row {
-    float4 r0, r1, r2, r3, r4, r5;
+    float4 r0, r1, r2, r3;
 };
 
 struct EnvView {
-    int nb, nj;
-    float4 *x, *q, *v, *w;            // state
+    int nb, nj;                       // counts the stages see (0: inactive or frozen)
+    float4 *x, *q, *v, *w;            // state; v.w = inverse mass (0 = static)
     const float4* shape;              // p0, p1, p2, mu
     const float4* inv;                // 1/Ixx, 1/Iyy, 1/Izz, 1/m (0 = static)
     const int2* meta;                 // x: type | dyn << 8; y: group | mask << 16
@@ -45,17 +53,18 @@ struct EnvView {
     const float4* jp;                 // lower, upper, kp, kd
     const int4* jm;                   // type, parent, child, -
     float* jt;                        // drive targets
-    S3* iw;                           // world inverse inertia per body
+    float4* iw;                       // world inverse inertia, 2 per body: (xx, xy, xz, yy), (yz, zz, -, -)
     float4* aabb;                     // 2 per body
     int* pairs;                       // i | j << 16
     int4* man;                        // a, b, npts, first point
     float4* pts;                      // 3 per point: (aA, d), (aB, -), (n, -)
-    int4* cons;                       // a, b, row0, nrows | kind << 8 | idx << 9
+    int4* cons;                       // a, b, row0, nrows | kind << 8 | idx << 9 (list order)
     int* colr;                        // colour per constraint
-    int* order;                       // solve order
+    int4* scons;                      // the same records sorted by colour (solve order)
     int* color_off;                   // MAX_COLORS + 1
     unsigned long long* used;         // colour masks per body
     Row* rows;
+    float* lam;                       // accumulated impulse per row
     int* cnt;                         // C_NUM counters
     unsigned* status;                 // env status word
     int4* rec_man;                    // recorded manifolds (nullable)
@@ -63,22 +72,26 @@ struct EnvView {
     int* rec_cnt;
 };
 
+// G lanes of a warp owning one env; all intrinsics use the full warp.
 struct Grp {
     int lane, size, base;
-    unsigned mask;
-    MSD void sync() const { __syncwarp(mask); }
-    MSD unsigned ballot(bool p) const { return __ballot_sync(mask, p) >> base; }
+    MSD void sync() const { __syncwarp(); }
+    MSD unsigned ballot(bool p) const {
+        unsigned b = __ballot_sync(FULL_MASK, p);
+        return size == 32 ? b : (b >> base) & ((1u << size) - 1u);
+    }
     MSD unsigned lt() const { return (1u << lane) - 1u; }
-    MSD int shfl(int v, int src) const { return __shfl_sync(mask, v, src, size); }
+    MSD int shfl(int v, int src) const { return __shfl_sync(FULL_MASK, v, src, size); }
+    MSD int wmax(int v) const { return __reduce_max_sync(FULL_MASK, v); }
     MSD int incl_scan(int v) const {
         for (int d = 1; d < size; d <<= 1) {
-            int t = __shfl_up_sync(mask, v, d, size);
+            int t = __shfl_up_sync(FULL_MASK, v, d, size);
             if (lane >= d) v += t;
         }
         return v;
     }
     MSD int max_all(int v) const {
-        for (int d = size >> 1; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(mask, v, d, size));
+        for (int d = size >> 1; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(FULL_MASK, v, d, size));
         return v;
     }
     MSD bool any(bool p) const { return ballot(p) != 0u; }
@@ -89,11 +102,15 @@ MSD int shape_type(const EnvView& e, int i) { return e.meta[i].x & 0xff; }
 
 // ---------------------------------------------------------------- actions
 MSD void stage_actions(EnvView& e, const Grp& g, const float* act, int A) {
-    if (act)
-        for (int j = g.lane; j < e.nj && j < A; j += g.size) {
+    int n = act ? min(e.nj, A) : 0;
+    int nmax = g.wmax(n);
+    for (int j0 = 0; j0 < nmax; j0 += g.size) {
+        int j = j0 + g.lane;
+        if (j < n) {
             float t = act[j];
             if (!isnan(t)) e.jt[j] = t;
         }
+    }
     g.sync();
 }
 
@@ -108,12 +125,12 @@ MSD void aabb_of(const EnvView& e, int i, float hm, float4& lo, float4& hi) {
     } else {
         M3 R = qmat(e.q[i]);
         if (t == SH_BOX) {
-            ext = f3(fabsf(R.m[0]) * s.x + fabsf(R.m[1]) * s.y + fabsf(R.m[2]) * s.z,
-                     fabsf(R.m[3]) * s.x + fabsf(R.m[4]) * s.y + fabsf(R.m[5]) * s.z,
-                     fabsf(R.m[6]) * s.x + fabsf(R.m[7]) * s.y + fabsf(R.m[8]) * s.z);
+            ext = f3(fmaf(fabsf(R.m[2]), s.z, fmaf(fabsf(R.m[1]), s.y, fabsf(R.m[0]) * s.x)),
+                     fmaf(fabsf(R.m[5]), s.z, fmaf(fabsf(R.m[4]), s.y, fabsf(R.m[3]) * s.x)),
+                     fmaf(fabsf(R.m[8]), s.z, fmaf(fabsf(R.m[7]), s.y, fabsf(R.m[6]) * s.x)));
         } else {
             float3 ax = mcol(R, 2);
-            ext = f3(fabsf(ax.x) * s.y + s.x, fabsf(ax.y) * s.y + s.x, fabsf(ax.z) * s.y + s.x);
+            ext = f3(fmaf(fabsf(ax.x), s.y, s.x), fmaf(fabsf(ax.y), s.y, s.x), fmaf(fabsf(ax.z), s.y, s.x));
         }
     }
     ext = ext + f3(hm, hm, hm);
@@ -124,7 +141,7 @@ MSD void aabb_of(const EnvView& e, int i, float hm, float4& lo, float4& hi) {
 // p-th pair (i < j) in lexicographic order of n items
 MSD void pair_from_index(int p, int n, int& i, int& j) {
     float b = 2.f * n - 1.f;
-    int ii = (int)floorf((b - sqrtf(b * b - 8.f * p)) * 0.5f);
+    int ii = (int)floorf((b - sqrtf(fmaxf(b * b - 8.f * p, 0.f))) * 0.5f);
     if (ii < 0) ii = 0;
     if (ii > n - 2) ii = n - 2;
     while (ii > 0 && ii * (2 * n - ii - 1) / 2 > p) ii--;
@@ -135,17 +152,21 @@ MSD void pair_from_index(int p, int n, int& i, int& j) {
 
 MSD void stage_broadphase(EnvView& e, const Grp& g, const Params& P) {
     int nb = e.nb;
-    for (int i = g.lane; i < nb; i += g.size) {
-        if (shape_type(e, i) == SH_PLANE) continue;
-        float4 lo, hi;
-        aabb_of(e, i, 0.5f * P.margin, lo, hi);
-        e.aabb[2 * i] = lo;
-        e.aabb[2 * i + 1] = hi;
+    int nbmax = g.wmax(nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i < nb && shape_type(e, i) != SH_PLANE) {
+            float4 lo, hi;
+            aabb_of(e, i, 0.5f * P.margin, lo, hi);
+            e.aabb[2 * i] = lo;
+            e.aabb[2 * i + 1] = hi;
+        }
     }
     g.sync();
     int total = nb * (nb - 1) / 2;
+    int tmax = g.wmax(total);
     int count = 0;
-    for (int c = 0; c < total; c += g.size) {
+    for (int c = 0; c < tmax; c += g.size) {
         int p = c + g.lane;
         bool pred = false;
         int i = 0, j = 0;
@@ -170,7 +191,7 @@ MSD void stage_broadphase(EnvView& e, const Grp& g, const Params& P) {
         }
         count += __popc(bits);
     }
-    if (g.lane == 0) {
+    if (g.lane == 0 && e.nb > 0) {
         e.cnt[C_NPAIRS] = min(count, P.pair_cap);
         if (count > P.pair_cap) *e.status |= ST_PAIR;
     }
@@ -189,10 +210,11 @@ MSD Shape shape_at(const EnvView& e, int i) {
 }
 
 MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
-    int npairs = e.cnt[C_NPAIRS];
+    int npairs = e.nb > 0 ? e.cnt[C_NPAIRS] : 0;
+    int pmax = g.wmax(npairs);
     int total = 0, nman = 0, kept_end = 0;
     bool overflow = false;
-    for (int c = 0; c < npairs; c += g.size) {
+    for (int c = 0; c < pmax; c += g.size) {
         int p = c + g.lane;
         Cand pts[4];
         int n = 0, a = 0, b = 0;
@@ -215,10 +237,9 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
         if (keep) {
             int midx = nman + __popc(bits & g.lt());
             e.man[midx] = make_int4(a, b, n, start);
-            float3 xa = SA.x, xb = SB.x;
             for (int k = 0; k < n; k++) {
-                float3 aA = mtv(SA.R, pts[k].cA - xa);
-                float3 aB = mtv(SB.R, pts[k].cB - xb);
+                float3 aA = mtv(SA.R, pts[k].cA - SA.x);
+                float3 aB = mtv(SB.R, pts[k].cB - SB.x);
                 float4* o = e.pts + 3 * (start + k);
                 o[0] = f4(aA, pts[k].d);
                 o[1] = f4(aB, 0.f);
@@ -237,7 +258,7 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
         total += chunk_total;
     }
     bool ov = g.any(overflow);
-    if (g.lane == 0) {
+    if (g.lane == 0 && e.nb > 0) {
         e.cnt[C_NMAN] = nman;
         e.cnt[C_NPTS] = kept_end;
         if (ov) *e.status |= ST_CONTACT;
@@ -251,21 +272,26 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
 // takes the lowest colour free on both of its dynamic bodies (static bodies
 // impose nothing); the solve order lists constraints colour by colour.
 MSD void stage_color(EnvView& e, const Grp& g) {
-    int nj = e.nj, nman = e.cnt[C_NMAN];
-    int ncons = nj + nman;
-    for (int i = g.lane; i < ncons; i += g.size) {
+    bool live = e.nb > 0;
+    int nj = e.nj, nman = live ? e.cnt[C_NMAN] : 0;
+    int ncons = live ? nj + nman : 0;
+    int cmax = g.wmax(ncons);
+    for (int i0 = 0; i0 < cmax; i0 += g.size) {
+        int i = i0 + g.lane;
         if (i < nj) {
             int4 jm = e.jm[i];
             e.cons[i] = make_int4(jm.y, jm.z, 8 * i, 8 | (i << 9));
-        } else {
+        } else if (i < ncons) {
             int m = i - nj;
             int4 M = e.man[m];
             e.cons[i] = make_int4(M.x, M.y, 8 * nj + 3 * M.w, (3 * M.z) | (1 << 8) | (m << 9));
         }
     }
-    for (int b = g.lane; b < e.nb; b += g.size) e.used[b] = 0ull;
+    int nbmax = g.wmax(e.nb);
+    for (int b0 = 0; b0 < nbmax; b0 += g.size)
+        if (b0 + g.lane < e.nb) e.used[b0 + g.lane] = 0ull;
     g.sync();
-    if (g.lane == 0) {
+    if (g.lane == 0 && live) {
         int ncol = 0;
         bool overflow = false;
         for (int i = 0; i < ncons; i++) {
@@ -283,19 +309,20 @@ MSD void stage_color(EnvView& e, const Grp& g) {
         for (int i = 0; i < ncons; i++)
             if (e.colr[i] >= 0) e.color_off[e.colr[i] + 1]++;
         for (int c = 0; c < ncol; c++) e.color_off[c + 1] += e.color_off[c];
-        // stable scatter; used[] is free again, reuse color_off via a cursor pass
         for (int c = 0; c < ncol; c++) {
             int k = e.color_off[c];
             for (int i = 0; i < ncons; i++)
-                if (e.colr[i] == c) e.order[k++] = i;
+                if (e.colr[i] == c) e.scons[k++] = e.cons[i];
         }
-        e.cnt[C_NCONS] = ncons;
+        e.cnt[C_NCONS] = ncol > 0 ? e.color_off[ncol] : 0;   // constraints with a colour
         e.cnt[C_NCOLORS] = ncol;
         if (overflow) *e.status |= ST_COLOR;
     }
     g.sync();
-    int nrows = 8 * nj + 3 * e.cnt[C_NPTS];
-    for (int r = g.lane; r < nrows; r += g.size) e.rows[r].r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int nrows = live ? 8 * nj + 3 * e.cnt[C_NPTS] : 0;
+    int rmax = g.wmax(nrows);
+    for (int r0 = 0; r0 < rmax; r0 += g.size)
+        if (r0 + g.lane < nrows) e.lam[r0 + g.lane] = 0.f;
     g.sync();
 }
 
@@ -307,6 +334,11 @@ struct BodyPose {
     S3 iw;
     float im;
 };
+
+MSD S3 load_iw(const EnvView& e, int i) {
+    float4 a = e.iw[2 * i], b = e.iw[2 * i + 1];
+    return S3{a.x, a.y, a.z, a.w, b.x, b.y};
+}
 
 MSD BodyPose pose_of(const EnvView& e, int i) {
     BodyPose b;
@@ -321,32 +353,30 @@ MSD BodyPose pose_of(const EnvView& e, int i) {
     b.x = xyz(e.x[i]);
     b.q = e.q[i];
     b.R = qmat(b.q);
-    b.iw = e.iw[i];
-    b.im = e.inv[i].w;
+    b.iw = load_iw(e, i);
+    b.im = e.v[i].w;
     return b;
 }
 
 MSD float contact_bias(float d, float h, float vmax) { return d >= 0.f ? d / h : fmaxf(d / h, -vmax); }
 
-MSD void finish_row(Row& r, float3 lin, float3 angA, float3 angB, const BodyPose& A, const BodyPose& B,
-                    float bias, int kind, float aux, int partner) {
+MSD void write_row(Row& r, float3 lin, float3 angA, float3 angB, const BodyPose& A, const BodyPose& B, float bias,
+                   int kind, float aux, int partner) {
     float3 wa = smv(A.iw, angA), wb = smv(B.iw, angB);
-    float k = (A.im + B.im) * dot(lin, lin) + dot(angA, wa) + dot(angB, wb);
+    float k = fmaf(A.im + B.im, dot(lin, lin), dot(angA, wa) + dot(angB, wb));
     r.r0 = f4(lin, k > 0.f ? 1.f / k : 0.f);
     r.r1 = f4(angA, bias);
     r.r2 = f4(angB, 0.f);
-    r.r3 = f4(wa, k);
-    r.r4 = f4(wb, aux);
-    r.r5 = make_float4(r.r5.x, __int_as_float(kind), __int_as_float(partner), 0.f);
+    r.r3 = make_float4(kind == RK_FRICTION ? aux : 0.f, __int_as_float(kind | (partner << 4)), 0.f, k);
 }
 
 MSD void point_row(Row& r, float3 e_, float3 rA, float3 rB, const BodyPose& A, const BodyPose& B, float bias,
                    int kind, float aux, int partner) {
-    finish_row(r, e_, cross(rA, e_), cross(e_, rB), A, B, bias, kind, aux, partner);
+    write_row(r, e_, cross(rA, e_), cross(e_, rB), A, B, bias, kind, aux, partner);
 }
 
 MSD void ang_row(Row& r, float3 jA, float3 jB, const BodyPose& A, const BodyPose& B, float bias, int kind) {
-    finish_row(r, f3(0.f, 0.f, 0.f), jA, jB, A, B, bias, kind, 0.f, 0);
+    write_row(r, f3(0.f, 0.f, 0.f), jA, jB, A, B, bias, kind, 0.f, 0);
 }
 
 struct JointGeo {
@@ -375,8 +405,7 @@ MSD JointGeo joint_geo(const EnvView& e, int j, int type, const BodyPose& P, con
     return g;
 }
 
-MSD void prep_constraint(EnvView& e, int ci, const Params& P) {
-    int4 c = e.cons[ci];
+MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     int kind = (c.w >> 8) & 1, idx = c.w >> 9;
     BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
     Row* R = e.rows + c.z;
@@ -436,17 +465,18 @@ MSD void prep_constraint(EnvView& e, int ci, const Params& P) {
             point_row(R[7], -gj.a, gj.rP, gj.rC, A, B, 0.f, RK_DRIVE, 0.f, 0);
         }
         // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
-        // b = kp C / (h kp + kd), C = phi - target
+        // b = kp C / (h kp + kd), C = phi - target; the row keeps
+        // 1/(k + gamma) so that each iteration is one multiply
         float kp = jp.z, kd = jp.w;
-        float den = h * kp + kd;
+        float den = fmaf(h, kp, kd);
         Row& dr = R[7];
-        if (den > 0.f) {
-            dr.r4.w = 1.f / (h * den);
+        float k = dr.r3.w;
+        if (den > 0.f && k > 0.f) {
+            float gam = 1.f / (h * den);
+            dr.r3.z = gam;
             dr.r1.w = kp * (gj.phi - e.jt[idx]) / den;
+            dr.r0.w = 1.f / (k + gam);
         } else {
-            dr.r4.w = 0.f;
-            dr.r1.w = 0.f;
-            dr.r3.w = 0.f;
             dr.r0.w = 0.f;
         }
     }
@@ -454,95 +484,115 @@ MSD void prep_constraint(EnvView& e, int ci, const Params& P) {
 
 MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
     float h = P.h;
-    for (int i = g.lane; i < e.nb; i += g.size) {
+    int nb = e.nb;
+    int nbmax = g.wmax(nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i >= nb) continue;
         if (is_dyn(e, i)) {
             float4 v = e.v[i];
-            v.x += h * P.gx; v.y += h * P.gy; v.z += h * P.gz;
+            v.x = fmaf(h, P.gx, v.x); v.y = fmaf(h, P.gy, v.y); v.z = fmaf(h, P.gz, v.z);
             e.v[i] = v;
             float4 iv = e.inv[i];
-            e.iw[i] = rdrt(qmat(e.q[i]), f3(iv.x, iv.y, iv.z));
+            S3 I = rdrt(qmat(e.q[i]), f3(iv.x, iv.y, iv.z));
+            e.iw[2 * i] = make_float4(I.xx, I.xy, I.xz, I.yy);
+            e.iw[2 * i + 1] = make_float4(I.yz, I.zz, 0.f, 0.f);
         } else {
-            e.iw[i] = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            e.iw[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            e.iw[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     g.sync();
-    int ncons = e.cnt[C_NCONS];
-    for (int ci = g.lane; ci < ncons; ci += g.size) prep_constraint(e, ci, P);
+    int ncons = nb > 0 ? e.cnt[C_NCONS] : 0;
+    int cmax = g.wmax(ncons);
+    for (int c0 = 0; c0 < cmax; c0 += g.size) {
+        int ci = c0 + g.lane;
+        if (ci < ncons) prep_constraint(e, e.scons[ci], P);
+    }
     g.sync();
 }
 
 // ------------------------------------------------------------------ solve
-// Rows of one constraint, in order, with the two bodies' velocities in
-// registers.  mode 0: warm start (apply lambda); 1: position iteration;
-// 2: relax iteration (drives skipped, relax bias, joint rows unbiased).
-MSD void solve_constraint(EnvView& e, int ci, int mode) {
-    int4 c = e.cons[ci];
+// Rows of one constraint, in order, with both bodies' velocities, inverse
+// masses and world inverse inertias in registers.  mode 0: warm start
+// (apply lambda); 1: position iteration; 2: relax iteration (drives
+// skipped, relax bias; joint rows carry a zero relax bias).  Every row kind
+// goes through one formula,
+//     lambda' = clamp(lambda - (Jv + b + gamma lambda) / (k + gamma), lo, hi)
+// with gamma = 0 except for drives and (lo, hi) = (0, inf) for normals and
+// limits, +-mu lambda_n for friction, unbounded otherwise; an inert row has
+// 1/k = 0 and leaves lambda unchanged.  The next row is loaded while the
+// current one is solved.
+MSD void solve_constraint(EnvView& e, int4 c, int mode) {
     int nrows = c.w & 0xff;
-    bool da = is_dyn(e, c.x), db = is_dyn(e, c.y);
-    float3 vA = f3(0.f, 0.f, 0.f), wA = vA, vB = vA, wB = vA;
-    float imA = 0.f, imB = 0.f;
-    if (da) { vA = xyz(e.v[c.x]); wA = xyz(e.w[c.x]); imA = e.inv[c.x].w; }
-    if (db) { vB = xyz(e.v[c.y]); wB = xyz(e.w[c.y]); imB = e.inv[c.y].w; }
-    Row* R = e.rows + c.z;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 va = c.x >= 0 ? e.v[c.x] : z4, wa4 = c.x >= 0 ? e.w[c.x] : z4;
+    float4 vb = c.y >= 0 ? e.v[c.y] : z4, wb4 = c.y >= 0 ? e.w[c.y] : z4;
+    float4 ia0 = c.x >= 0 ? e.iw[2 * c.x] : z4, ia1 = c.x >= 0 ? e.iw[2 * c.x + 1] : z4;
+    float4 ib0 = c.y >= 0 ? e.iw[2 * c.y] : z4, ib1 = c.y >= 0 ? e.iw[2 * c.y + 1] : z4;
+    S3 IA{ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y}, IB{ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y};
+    float imA = va.w, imB = vb.w;
+    float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
+    const Row* __restrict__ R = e.rows + c.z;
+    float* __restrict__ L = e.lam + c.z;
+    float4 n0 = z4, n1 = z4, n2 = z4, n3 = z4;
+    if (nrows > 0) { n0 = R[0].r0; n1 = R[0].r1; n2 = R[0].r2; n3 = R[0].r3; }
     for (int r = 0; r < nrows; r++) {
-        Row& row = R[r];
-        float4 r0 = row.r0;
-        float ik = r0.w;
-        if (ik <= 0.f) continue;                     // inert row
-        float4 r5 = row.r5;
-        int kind = __float_as_int(r5.y);
-        float3 lin = xyz(r0);
-        float4 r3 = row.r3, r4 = row.r4;
+        float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
+        if (r + 1 < nrows) { n0 = R[r + 1].r0; n1 = R[r + 1].r1; n2 = R[r + 1].r2; n3 = R[r + 1].r3; }
+        int kb = __float_as_int(r3.y);
+        int kind = kb & 15;
+        float3 lin = xyz(r0), angA = xyz(r1), angB = xyz(r2);
+        float old = L[r];
         float dl;
         if (mode == 0) {
-            dl = r5.x;
+            dl = r0.w > 0.f ? old : 0.f;
         } else {
-            if (mode == 2 && kind == RK_DRIVE) continue;
-            float4 r1 = row.r1, r2 = row.r2;
-            float jv = dot(lin, vA - vB) + dot(xyz(r1), wA) + dot(xyz(r2), wB);
-            float old = r5.x, nl;
-            if (kind == RK_NORMAL || kind == RK_LIMIT) {
-                float bias = mode == 2 ? r2.w : r1.w;
-                nl = fmaxf(old - (jv + bias) * ik, 0.f);
-            } else if (kind == RK_FRICTION) {
-                float lim = r4.w * R[__float_as_int(r5.z)].r5.x;
-                nl = clampf(old - jv * ik, -lim, lim);
-            } else if (kind == RK_EQ) {
-                nl = old - (jv + (mode == 2 ? 0.f : r1.w)) * ik;
-            } else {
-                float gam = r4.w;
-                nl = old - (jv + r1.w + gam * old) / (r3.w + gam);
-            }
-            row.r5.x = nl;
+            float ik = (mode == 2 && kind == RK_DRIVE) ? 0.f : r0.w;
+            float bias = mode == 2 ? r2.w : r1.w;
+            float3 dv = vA - vB;
+            float j1 = dot(lin, dv), j2 = dot(angA, wA), j3 = dot(angB, wB);
+            float jv = (j1 + j2) + j3;
+            float nl = fmaf(-((jv + bias) + r3.z * old), ik, old);
+            float lim = r3.x * L[kb >> 4];           // friction bound from the point's normal impulse
+            float lo = kind == RK_FRICTION ? -lim : ((kind == RK_NORMAL || kind == RK_LIMIT) ? 0.f : -INFINITY);
+            float hi = kind == RK_FRICTION ? lim : INFINITY;
+            nl = fminf(fmaxf(nl, lo), hi);
+            L[r] = nl;
             dl = nl - old;
         }
-        vA = vA + lin * (imA * dl);
-        wA = wA + xyz(r3) * dl;
-        vB = vB - lin * (imB * dl);
-        wB = wB + xyz(r4) * dl;
+        vA = madd(vA, lin, imA * dl);
+        wA = madd(wA, smv(IA, angA), dl);
+        vB = madd(vB, lin, -(imB * dl));
+        wB = madd(wB, smv(IB, angB), dl);
     }
-    if (da) { e.v[c.x] = f4(vA, 0.f); e.w[c.x] = f4(wA, 0.f); }
-    if (db) { e.v[c.y] = f4(vB, 0.f); e.w[c.y] = f4(wB, 0.f); }
+    if (imA > 0.f) { e.v[c.x] = f4(vA, imA); e.w[c.x] = f4(wA, 0.f); }
+    if (imB > 0.f) { e.v[c.y] = f4(vB, imB); e.w[c.y] = f4(wB, 0.f); }
 }
 
 MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
-    int ncol = e.cnt[C_NCOLORS];
-    for (int col = 0; col < ncol; col++) {
-        int k0 = e.color_off[col], k1 = e.color_off[col + 1];
-        for (int k = k0 + g.lane; k < k1; k += g.size) solve_constraint(e, e.order[k], mode);
+    int ncol = e.nb > 0 ? e.cnt[C_NCOLORS] : 0;
+    int colmax = g.wmax(ncol);
+    for (int col = 0; col < colmax; col++) {
+        int k0 = 0, k1 = 0;
+        if (col < ncol) { k0 = e.color_off[col]; k1 = e.color_off[col + 1]; }
+        int wmaxn = g.wmax(k1 - k0);
+        for (int m = 0; m < wmaxn; m += g.size) {
+            int k = k0 + m + g.lane;
+            if (k < k1) solve_constraint(e, e.scons[k], mode);
+        }
         g.sync();
     }
 }
 
 // -------------------------------------------------------------- integrate
-MSD void relax_constraint(EnvView& e, int ci, const Params& P) {
-    int4 c = e.cons[ci];
+MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
     int kind = (c.w >> 8) & 1, idx = c.w >> 9;
     Row* R = e.rows + c.z;
     float h = P.h;
+    BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
     if (kind == 1) {
         int4 M = e.man[idx];
-        BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
         for (int k = 0; k < M.z; k++) {
             const float4* pt = e.pts + 3 * (M.w + k);
             float3 rA = mv(A.R, xyz(pt[0])), rB = mv(B.R, xyz(pt[1]));
@@ -550,7 +600,6 @@ MSD void relax_constraint(EnvView& e, int ci, const Params& P) {
             R[k].r2.w = fmaxf(d, 0.f) / h;
         }
     } else {
-        BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
         int4 jm = e.jm[idx];
         float4 jp = e.jp[idx];
         JointGeo gj = joint_geo(e, idx, jm.x, A, B);
@@ -561,27 +610,38 @@ MSD void relax_constraint(EnvView& e, int ci, const Params& P) {
 
 MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
     float h = P.h;
-    for (int i = g.lane; i < e.nb; i += g.size) {
-        if (!is_dyn(e, i)) continue;
+    int nb = e.nb;
+    int nbmax = g.wmax(nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i >= nb || !is_dyn(e, i)) continue;
         float4 x = e.x[i], q = e.q[i];
         float3 v = xyz(e.v[i]), w = xyz(e.w[i]);
-        x.x += h * v.x; x.y += h * v.y; x.z += h * v.z;
+        x.x = fmaf(h, v.x, x.x); x.y = fmaf(h, v.y, x.y); x.z = fmaf(h, v.z, x.z);
         float4 wq = qmul(make_float4(w.x, w.y, w.z, 0.f), q);
-        q = qnormalize(make_float4(q.x + 0.5f * h * wq.x, q.y + 0.5f * h * wq.y, q.z + 0.5f * h * wq.z,
-                                   q.w + 0.5f * h * wq.w));
+        float hh = 0.5f * h;
+        q = qnormalize(make_float4(fmaf(hh, wq.x, q.x), fmaf(hh, wq.y, q.y), fmaf(hh, wq.z, q.z),
+                                   fmaf(hh, wq.w, q.w)));
         e.x[i] = x;
         e.q[i] = q;
     }
     g.sync();
-    int ncons = e.cnt[C_NCONS];
-    for (int ci = g.lane; ci < ncons; ci += g.size) relax_constraint(e, ci, P);
+    int ncons = nb > 0 ? e.cnt[C_NCONS] : 0;
+    int cmax = g.wmax(ncons);
+    for (int c0 = 0; c0 < cmax; c0 += g.size) {
+        int ci = c0 + g.lane;
+        if (ci < ncons) relax_constraint(e, e.scons[ci], P);
+    }
     g.sync();
 }
 
 // end-of-step check: a non-finite state freezes the env
 MSD void stage_check(EnvView& e, const Grp& g) {
     bool bad = false;
-    for (int i = g.lane; i < e.nb; i += g.size) {
+    int nbmax = g.wmax(e.nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i >= e.nb) continue;
         float4 x = e.x[i], q = e.q[i], v = e.v[i], w = e.w[i];
         float s = x.x + x.y + x.z + q.x + q.y + q.z + q.w + v.x + v.y + v.z + w.x + w.y + w.z;
         bad |= !isfinite(s);

@@ -1,7 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Bars: contact pair sets bit-exact except oracle margin ties; after one step
-|dx| <= 1e-5 m, |dv| <= 1e-4 m/s, |dw| <= 1e-4 rad/s, quaternion <= 1e-5;
+|dx| <= 1e-5 m, |dv| <= 1e-4 m/s, |dw| r_bound <= 1e-4 m/s (angular velocity at the body's
+material points), quaternion <= 1e-5;
 200-step rollouts of non-chaotic envs within 10x those bounds.  Envs with a
 tie-adjacent discrete decision in the oracle are counted and excluded from
 the strict comparison."""
@@ -73,7 +74,8 @@ def test_rollout_parity_non_chaotic(name, n, steps):
     print(f"{name}: {calm.sum()} of {n} envs non-chaotic, {clean.sum()} also tie-free")
     assert clean.sum() >= 1
     ok = within(err, 10.0)
-    assert ok[clean].all(), f"worst {err[clean].max(0)}"
+    bad = np.nonzero(clean & ~ok)[0]
+    assert ok[clean].all(), f"envs {bad.tolist()} errors {err[bad].tolist()}"
 
 
 @pytest.mark.parametrize("name,n", [("arm", 48), ("clutter", 128), ("hand", 32)])
@@ -81,11 +83,11 @@ def test_plain_path_bit_identical_to_batched(name, n):
     sc = scenegen.make_scene(name, n_envs=n)
     _, a, sa = gpu_run(sc, 3)
     _, b, sb = gpu_run(sc, 3, plain=True)
-    assert np.array_equal(a, b)
+    assert np.array_equal(a, b), np.abs(a - b).max()
     assert np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("tuning", [(16, 4, 1), (8, 4, 1), (4, 8, 1), (32, 2, 0), (8, 8, 0)])
+@pytest.mark.parametrize("tuning", [(16, 2, 0), (8, 2, 0), (4, 4, 0), (2, 2, 0), (1, 1, 0), (32, 1, 1)])
 def test_tuning_does_not_change_results(tuning):
     sc = scenegen.make_scene("clutter", n_envs=96)
     _, ref, _ = gpu_run(sc, 2)
@@ -114,8 +116,9 @@ def test_graph_replay_equals_eager_and_split_calls():
 
 
 def test_contact_overflow_sets_status_and_matches_oracle():
-    sc = scenegen.make_scene("clutter", n_envs=64)
-    sc.params["contact_capacity"] = 6
+    # the cube rests on the plane (4 points): a capacity of 3 must overflow
+    sc = scenegen.make_scene("arm", n_envs=32)
+    sc.params["contact_capacity"] = 3
     _, st, status = gpu_run(sc, 1)
     o = oracle_run(sc, 1)
     assert any(status & 2)
