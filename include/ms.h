@@ -56,7 +56,8 @@ enum {
     MS_ENV_PAIR_OVERFLOW = 1u,      /* more broadphase pairs than pair_capacity   */
     MS_ENV_CONTACT_OVERFLOW = 2u,   /* more contact points than contact_capacity  */
     MS_ENV_COLOR_OVERFLOW = 4u,     /* a constraint found none of 64 colours free */
-    MS_ENV_NAN = 8u                 /* non-finite state; the env is frozen        */
+    MS_ENV_NAN = 8u,                /* non-finite state; the env is frozen        */
+    MS_ENV_INVALID = 16u            /* ms_step_noalloc: descriptors out of range; the env is skipped */
 };
 
 enum { MS_SPHERE = 0, MS_CAPSULE = 1, MS_BOX = 2, MS_PLANE = 3 };
@@ -240,6 +241,60 @@ ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* joint_off, i
 /* sizeof(ms_body_desc), sizeof(ms_joint_desc), sizeof(ms_sim_params),
  * sizeof(ms_state_view), sizeof(ms_tuning): lets bindings check layouts. */
 void ms_abi_sizes(int32_t* out5);
+
+/* ----------------------------------------------------------------------- */
+/* Stepping without any device allocation                                  */
+/* ----------------------------------------------------------------------- */
+
+/* Caller-owned device arrays of a batch (all pointers are device pointers;
+ * the library never allocates or frees them).
+ *   body_off, joint_off: int32 [n_envs + 1] CSR offsets.
+ *   bodies, joints: descriptors (the pose / velocity fields of bodies are
+ *     not read; shapes, masses, friction and filters are).
+ *   x, q, v, w: float4 [n_bodies] state, read and written in place (.w of x
+ *     and w unused; v.w receives the inverse mass).  q must hold unit
+ *     quaternions.
+ *   targets: float [n_joints] drive targets, read and written in place.
+ *   status: uint32 [n_envs] status bits (MS_ENV_*), read and written; an env
+ *     whose counts exceed the maxima below or whose joints name bodies out
+ *     of range gets MS_ENV_INVALID and is left untouched.  The offsets must
+ *     lie inside the caller's arrays.
+ *   max_bodies_per_env in [1, 64] and max_joints_per_env in [0, 512] bound
+ *   every env; actions rows are max_joints_per_env wide. */
+typedef struct {
+    int32_t n_envs, max_bodies_per_env, max_joints_per_env;
+    const int32_t* body_off;
+    const int32_t* joint_off;
+    const ms_body_desc* bodies;
+    const ms_joint_desc* joints;
+    float* x;
+    float* q;
+    float* v;
+    float* w;
+    float* targets;
+    uint32_t* status;
+} ms_noalloc_batch;
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- a process whose device memory is
+ * owned entirely by another allocator (a framework's caching allocator or a
+ * fixed arena), or a control loop that cannot afford an allocation's
+ * implicit synchronisation and latency.  It advances every env n_steps
+ * steps with the same stages and results as ms_step, on `stream`, calling no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * The kernel's workspace is a fixed 32 MiB array inside the library, held by
+ * every GPU that loads the library until the process exits.  A call whose
+ * per-CTA workspace would not fit it returns MS_ERR_INVALID_ARG (with a
+ * message from ms_last_error) and enqueues nothing.  All calls share the
+ * array: calls that overlap on the GPU (different streams or host threads)
+ * race and must be serialised by the caller.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and sets the
+ * kernels' shared-memory limit; make that first call before any stream
+ * capture.  actions as in ms_step.  Asynchronous; argument errors are
+ * synchronous. */
+ms_status ms_step_noalloc(const ms_noalloc_batch* b, const ms_sim_params* p, const float* actions,
+                          int n_steps, void* stream);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,13 @@ class ms_state_view(C.Structure):
                 ("targets", C.c_void_p), ("status", C.c_void_p)]
 
 
+class ms_noalloc_batch(C.Structure):
+    _fields_ = [("n_envs", C.c_int32), ("max_bodies_per_env", C.c_int32), ("max_joints_per_env", C.c_int32),
+                ("body_off", C.c_void_p), ("joint_off", C.c_void_p), ("bodies", C.c_void_p),
+                ("joints", C.c_void_p), ("x", C.c_void_p), ("q", C.c_void_p), ("v", C.c_void_p),
+                ("w", C.c_void_p), ("targets", C.c_void_p), ("status", C.c_void_p)]
+
+
 class ms_tuning(C.Structure):
     _fields_ = [("lanes_per_env", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("rows_in_smem", C.c_int32), ("ctas_per_sm", C.c_int32)]
@@ -78,6 +85,7 @@ _SIGS = [
     ("ms_estimate_bytes", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(ms_sim_params),
                                     C.POINTER(C.c_size_t)]),
     ("ms_abi_sizes", None, [C.c_void_p]),
+    ("ms_step_noalloc", C.c_int, [C.c_void_p, C.POINTER(ms_sim_params), C.c_void_p, C.c_int, C.c_void_p]),
 ]
 
 EXPORTS = [s[0] for s in _SIGS]
@@ -234,6 +242,11 @@ def ms_autotune(b, n_steps=1, cache_path=None, stream=None) -> dict:
                              _stream(stream)))
     return dict(lanes_per_env=t.lanes_per_env, warps_per_cta=t.warps_per_cta,
                 rows_in_smem=t.rows_in_smem, ctas_per_sm=t.ctas_per_sm)
+
+
+def ms_step_noalloc(nb: ms_noalloc_batch, params: dict, actions=None, n_steps=1, stream=None):
+    sp = make_params(params)
+    return check(load().ms_step_noalloc(C.byref(nb), C.byref(sp), _ptr(actions), n_steps, _stream(stream)))
 
 
 def ms_memory_bytes(b) -> int:

@@ -585,6 +585,8 @@ extern "C" ms_status ms_destroy(ms_batch* b) {
 
 extern "C" const char* ms_last_error(void) { return g_err.c_str(); }
 
+void ms::set_last_error(const char* msg) { g_err = msg; }
+
 // ------------------------------------------------------------ introspection
 extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
     if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");

@@ -74,6 +74,7 @@ bool fused_supported(int G);
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,
                          int grid, int threads, size_t smem, cudaStream_t s);
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
+void set_last_error(const char* msg);   // the message ms_last_error() returns on this thread
 void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask, const int* body_env,
                          cudaStream_t s);
 
