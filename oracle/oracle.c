@@ -592,10 +592,11 @@ static int clip_plane(const v3* in, int nin, v3* out, v3 dir, v3 c, double hh, E
         v3 cur = in[i];
         double fc = dot(dir, sub(cur, c)) - hh;
         tie(e, fc, 0.0);
+        /* at most 8 vertices, whatever rounding does to convexity */
         if (fc <= 0.0) {
-            if (fp > 0.0) out[nout++] = add(prev, scl(sub(cur, prev), fp / (fp - fc)));
-            out[nout++] = cur;
-        } else if (fp <= 0.0) {
+            if (fp > 0.0 && nout < 8) out[nout++] = add(prev, scl(sub(cur, prev), fp / (fp - fc)));
+            if (nout < 8) out[nout++] = cur;
+        } else if (fp <= 0.0 && nout < 8) {
             out[nout++] = add(prev, scl(sub(cur, prev), fp / (fp - fc)));
         }
         prev = cur; fp = fc;
@@ -699,6 +700,11 @@ static void np_bb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
     }
 }
 
+static int first_unused(const int* used, int n) {
+    for (int k = 0; k < n; k++) if (!used[k]) return k;
+    return 0;
+}
+
 /* reduce > 4 candidates to 4, selection order p1..p4 (positions: cB) */
 static int reduce4(Env* e, const Cand* c, int n, int* sel) {
     int used[8] = {0};
@@ -706,7 +712,7 @@ static int reduce4(Env* e, const Cand* c, int n, int* sel) {
     for (int k = 1; k < n; k++) if (c[k].d < c[i1].d) i1 = k;
     for (int k = 0; k < n; k++) if (k != i1) tie(e, c[k].d, c[i1].d);
     used[i1] = 1;
-    double best, second; int i2 = -1;
+    double best, second; int i2 = first_unused(used, n);
     best = -1.0; second = -1.0;
     for (int k = 0; k < n; k++) {
         if (used[k]) continue;
@@ -716,7 +722,7 @@ static int reduce4(Env* e, const Cand* c, int n, int* sel) {
     tie(e, best, second);
     used[i2] = 1;
     v3 e12 = sub(c[i2].cB, c[i1].cB);
-    int i3 = -1; best = -1.0; second = -1.0;
+    int i3 = first_unused(used, n); best = -1.0; second = -1.0;
     for (int k = 0; k < n; k++) {
         if (used[k]) continue;
         double s = norm(cross(e12, sub(c[k].cB, c[i1].cB)));
@@ -724,7 +730,7 @@ static int reduce4(Env* e, const Cand* c, int n, int* sel) {
     }
     tie(e, best, second);
     used[i3] = 1;
-    int i4 = -1; best = -1.0; second = -1.0;
+    int i4 = first_unused(used, n); best = -1.0; second = -1.0;
     v3 P1 = c[i1].cB, P2 = c[i2].cB, P3 = c[i3].cB;
     for (int k = 0; k < n; k++) {
         if (used[k]) continue;
