@@ -211,7 +211,7 @@ ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t
                           float* pts, int* count);
 
 /* Batched-path launch shape.  lanes_per_env in {1, 2, 4, 8, 16, 32}: a warp
- * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 16];
+ * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 8];
  * rows_in_smem: keep constraint rows in shared memory (1) or in an
  * L2-resident global slot per lane group (0).  Any choice gives
  * bit-identical results. */

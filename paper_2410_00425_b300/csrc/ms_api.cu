@@ -636,7 +636,7 @@ extern "C" ms_status ms_set_tuning(ms_batch* b, const ms_tuning* t) {
     if (!b || !t) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (!fused_supported(t->lanes_per_env))
         return fail(MS_ERR_INVALID_ARG, "lanes_per_env must be 1, 2, 4, 8, 16 or 32");
-    if (t->warps_per_cta < 1 || t->warps_per_cta > 16) return fail(MS_ERR_INVALID_ARG, "warps_per_cta must be in [1, 16]");
+    if (t->warps_per_cta < 1 || t->warps_per_cta > 8) return fail(MS_ERR_INVALID_ARG, "warps_per_cta must be in [1, 8]");
     Tuning old = b->tune;
     b->tune.G = t->lanes_per_env;
     b->tune.warps = t->warps_per_cta;

@@ -176,7 +176,7 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
 
 // ----------------------------------------------------------- batched path
 template <int G>
-__global__ void __launch_bounds__(512) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
+__global__ void __launch_bounds__(256, 2) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
     constexpr int K = 32 / G;                  // envs per warp

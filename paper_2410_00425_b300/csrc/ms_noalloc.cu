@@ -85,7 +85,7 @@ __device__ __forceinline__ float4 desc_inverse_mass(const ms_body_desc& d, bool 
 // Same stages and lockstep env loop as the batched kernel; the env's
 // parameters are derived from the caller's descriptors while loading it.
 template <int G>
-__global__ void __launch_bounds__(512) k_noalloc(NoallocArgs D, const float* actions, int n_steps, Layout L,
+__global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* actions, int n_steps, Layout L,
                                                  int* queue, char* gscratch) {
     extern __shared__ __align__(16) char smem[];
     constexpr int K = 32 / G;

@@ -514,8 +514,8 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
 
 // ------------------------------------------------------------------ solve
 // Rows of one constraint, in order, with both bodies' velocities, inverse
-// masses and world inverse inertias in registers.  mode 0: warm start
-// (apply lambda); 1: position iteration; 2: relax iteration (drives
+// masses and world inverse inertias in registers.  MODE 0: warm
+// start (apply lambda); 1: position iteration; 2: relax iteration (drives
 // skipped, relax bias; joint rows carry a zero relax bias).  Every row kind
 // goes through one formula,
 //     lambda' = clamp(lambda - (Jv + b + gamma lambda) / (k + gamma), lo, hi)
@@ -523,38 +523,50 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
 // limits, +-mu lambda_n for friction, unbounded otherwise; an inert row has
 // 1/k = 0 and leaves lambda unchanged.  The next row is loaded while the
 // current one is solved.
-MSD void solve_constraint(EnvView& e, int4 c, int mode) {
+// The pointers the sweeps touch, small enough to live in registers.
+struct SolveCtx {
+    float4* v;
+    float4* w;
+    const float4* iw;
+    const Row* rows;
+    float* lam;
+};
+
+MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.iw, e.rows, e.lam}; }
+
+template <int MODE>
+MSD void solve_constraint(const SolveCtx& x, int4 c) {
     int nrows = c.w & 0xff;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 va = c.x >= 0 ? e.v[c.x] : z4, wa4 = c.x >= 0 ? e.w[c.x] : z4;
-    float4 vb = c.y >= 0 ? e.v[c.y] : z4, wb4 = c.y >= 0 ? e.w[c.y] : z4;
-    float4 ia0 = c.x >= 0 ? e.iw[2 * c.x] : z4, ia1 = c.x >= 0 ? e.iw[2 * c.x + 1] : z4;
-    float4 ib0 = c.y >= 0 ? e.iw[2 * c.y] : z4, ib1 = c.y >= 0 ? e.iw[2 * c.y + 1] : z4;
+    float4 va = c.x >= 0 ? x.v[c.x] : z4, wa4 = c.x >= 0 ? x.w[c.x] : z4;
+    float4 vb = c.y >= 0 ? x.v[c.y] : z4, wb4 = c.y >= 0 ? x.w[c.y] : z4;
+    float4 ia0 = c.x >= 0 ? x.iw[2 * c.x] : z4, ia1 = c.x >= 0 ? x.iw[2 * c.x + 1] : z4;
+    float4 ib0 = c.y >= 0 ? x.iw[2 * c.y] : z4, ib1 = c.y >= 0 ? x.iw[2 * c.y + 1] : z4;
     S3 IA{ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y}, IB{ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y};
     float imA = va.w, imB = vb.w;
     float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
-    const Row* __restrict__ R = e.rows + c.z;
-    float* __restrict__ L = e.lam + c.z;
-    float4 n0 = z4, n1 = z4, n2 = z4, n3 = z4;
-    if (nrows > 0) { n0 = R[0].r0; n1 = R[0].r1; n2 = R[0].r2; n3 = R[0].r3; }
+    const Row* R = x.rows + c.z;
+    float* L = x.lam + c.z;
+    float4 n0 = R[0].r0, n1 = R[0].r1, n2 = R[0].r2, n3 = R[0].r3;
     for (int r = 0; r < nrows; r++) {
         float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
-        if (r + 1 < nrows) { n0 = R[r + 1].r0; n1 = R[r + 1].r1; n2 = R[r + 1].r2; n3 = R[r + 1].r3; }
+        int rn = min(r + 1, nrows - 1);                  // prefetch the next row (clamped, always valid)
+        n0 = R[rn].r0; n1 = R[rn].r1; n2 = R[rn].r2; n3 = R[rn].r3;
         int kb = __float_as_int(r3.y);
         int kind = kb & 15;
         float3 lin = xyz(r0), angA = xyz(r1), angB = xyz(r2);
         float old = L[r];
         float dl;
-        if (mode == 0) {
+        if (MODE == 0) {
             dl = r0.w > 0.f ? old : 0.f;
         } else {
-            float ik = (mode == 2 && kind == RK_DRIVE) ? 0.f : r0.w;
-            float bias = mode == 2 ? r2.w : r1.w;
+            float ik = (MODE == 2 && kind == RK_DRIVE) ? 0.f : r0.w;
+            float bias = MODE == 2 ? r2.w : r1.w;
             float3 dv = vA - vB;
             float j1 = dot(lin, dv), j2 = dot(angA, wA), j3 = dot(angB, wB);
             float jv = (j1 + j2) + j3;
             float nl = fmaf(-((jv + bias) + r3.z * old), ik, old);
-            float lim = r3.x * L[kb >> 4];           // friction bound from the point's normal impulse
+            float lim = r3.x * L[kb >> 4];                // friction bound from the point's normal impulse
             float lo = kind == RK_FRICTION ? -lim : ((kind == RK_NORMAL || kind == RK_LIMIT) ? 0.f : -INFINITY);
             float hi = kind == RK_FRICTION ? lim : INFINITY;
             nl = fminf(fmaxf(nl, lo), hi);
@@ -566,23 +578,34 @@ MSD void solve_constraint(EnvView& e, int4 c, int mode) {
         vB = madd(vB, lin, -(imB * dl));
         wB = madd(wB, smv(IB, angB), dl);
     }
-    if (imA > 0.f) { e.v[c.x] = f4(vA, imA); e.w[c.x] = f4(wA, 0.f); }
-    if (imB > 0.f) { e.v[c.y] = f4(vB, imB); e.w[c.y] = f4(wB, 0.f); }
+    if (imA > 0.f) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
+    if (imB > 0.f) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
 }
 
-MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
+template <int MODE>
+MSD void sweep_mode(EnvView& e, const Grp& g) {
+    SolveCtx x = solve_ctx(e);
+    const int4* sc = e.scons;
+    const int* off = e.color_off;
     int ncol = e.nb > 0 ? e.cnt[C_NCOLORS] : 0;
     int colmax = g.wmax(ncol);
+    int k0 = 0;
     for (int col = 0; col < colmax; col++) {
-        int k0 = 0, k1 = 0;
-        if (col < ncol) { k0 = e.color_off[col]; k1 = e.color_off[col + 1]; }
+        int k1 = col < ncol ? off[col + 1] : k0;
         int wmaxn = g.wmax(k1 - k0);
         for (int m = 0; m < wmaxn; m += g.size) {
             int k = k0 + m + g.lane;
-            if (k < k1) solve_constraint(e, e.scons[k], mode);
+            if (k < k1) solve_constraint<MODE>(x, sc[k]);
         }
         g.sync();
+        k0 = k1;
     }
+}
+
+MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
+    if (mode == 0) sweep_mode<0>(e, g);
+    else if (mode == 1) sweep_mode<1>(e, g);
+    else sweep_mode<2>(e, g);
 }
 
 // -------------------------------------------------------------- integrate

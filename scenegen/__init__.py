@@ -224,7 +224,8 @@ G_PLANE, G_ARM, G_CUBE = 1, 2, 4
 
 
 def make_arm(n_envs=4096, seed=2) -> Scene:
-    params = default_params(contact_capacity=64, pair_capacity=96)
+    # typical use is 4-12 contact points and < 20 candidate pairs per env
+    params = default_params(contact_capacity=32, pair_capacity=48)
     envs_b, envs_j = [], []
     n_act = 9
     qz = axis_angle_quat((0, 1, 0), -math.pi / 2)   # frame +x -> world +z
