@@ -191,6 +191,115 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, pools=None):
+    """Open-loop Poisson load on the step server.
+
+    Sessions own 1..1024 envs (log-uniform) of a scene type drawn uniformly
+    from {arm, clutter, hand}, live for a geometric number of requests (mean
+    50) and are replaced by fresh sessions; each request steps its session
+    once with fresh drive targets.  Returns latency percentiles (host
+    arrival -> completion) and the env-steps/s the server sustained."""
+    import queue as _q
+    from paper_2410_00425_b300.server import Server
+    g = np.random.default_rng(seed)
+    types = ["arm", "clutter", "hand"]
+    if pools is None:
+        pools = {t: scenegen.make_scene(t, n_envs=1024) for t in types}
+    act_pool = {t: (pools[t].actions(0, 8) if pools[t].n_act else None) for t in types}
+    srv = Server(budget, merge=merge)
+    g_open = np.random.default_rng(seed + 1)      # the opener thread's own generator
+
+    def new_session(g):
+        t = types[int(g.integers(0, 3))]
+        n = int(np.exp(g.uniform(0.0, np.log(1024.0))))
+        n = max(1, min(1024, n))
+        a0 = int(g.integers(0, 1024 - n + 1))
+        sc = pools[t].subset(range(a0, a0 + n))
+        sid = srv.open(sc)
+        life = int(g.geometric(1.0 / 50.0))
+        return sid, t, a0, n, life
+
+    active = []
+    for _ in range(n_sessions):
+        s_ = new_session(g)
+        if s_[0] is not None:
+            active.append(list(s_))
+    repl = _q.Queue()
+    closing = _q.Queue()
+    stop = threading.Event()
+    # replacement sessions are cut from the pools before the timed region, so
+    # the opener thread only makes the (GIL-free) library calls
+    spare = []
+    for _ in range(int(rate * duration / 40) + 64):
+        t = types[int(g_open.integers(0, 3))]
+        n = max(1, min(1024, int(np.exp(g_open.uniform(0.0, np.log(1024.0))))))
+        a0 = int(g_open.integers(0, 1024 - n + 1))
+        spare.append((t, a0, n, pools[t].subset(range(a0, a0 + n)), int(g_open.geometric(1.0 / 50.0))))
+
+    def opener():
+        k = 0
+        while not stop.is_set():
+            try:
+                sid = closing.get(timeout=0.05)
+            except _q.Empty:
+                continue
+            srv.close_session(sid)
+            if k < len(spare):
+                t, a0, n, sc, life = spare[k]
+                k += 1
+                sid2 = srv.open(sc)
+                if sid2 is not None:
+                    repl.put([sid2, t, a0, n, life])
+    th = threading.Thread(target=opener, daemon=True)
+    th.start()
+    # warm-up: one request per session (first launches, graph capture)
+    for s_ in active:
+        srv.submit(s_[0], None)
+    srv.drain()
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    nxt = t0
+    submitted = 0
+    saturated = False
+    next_check = t0 + 0.5
+    while True:
+        nxt += g.exponential(1.0 / rate)
+        if nxt - t0 > duration:
+            break
+        if nxt > next_check:
+            # open loop: stop if the server falls more than 2 s of arrivals behind
+            next_check += 0.5
+            if submitted - srv.stats()["requests_done"] > 2.0 * rate:
+                saturated = True
+                break
+        while time.perf_counter() < nxt:
+            pass
+        while not repl.empty():
+            active.append(repl.get())
+        if not active:
+            continue
+        k = int(g.integers(0, len(active)))
+        sid, t, a0, n, life = active[k]
+        ap = act_pool[t]
+        srv.submit(sid, None if ap is None else ap[submitted % 8, a0:a0 + n])
+        submitted += 1
+        active[k][4] -= 1
+        if active[k][4] <= 0:
+            closing.put(sid)
+            active.pop(k)
+    srv.drain()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    stop.set()
+    th.join()
+    srv.close()
+    return {"rate_req_s": rate, "duration_s": duration, "merge": merge, "requests": int(st["requests_done"]),
+            "launches": int(st["launches"]), "p50_ms": 1e3 * st["p50"], "p99_ms": 1e3 * st["p99"],
+            "mean_ms": 1e3 * st["mean"], "env_steps_per_s": st["env_steps"] / wall,
+            "sessions_admitted": int(st["sessions_admitted"]), "sessions_rejected": int(st["sessions_rejected"]),
+            "saturated": saturated}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +311,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving sweep only (rates x merge modes)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -212,6 +324,19 @@ def main():
     import torch
     from paper_2410_00425_b300 import Batch, build
     build.build()
+    if args.serve:
+        if rank == 0:
+            torch.cuda.set_device(local)
+            pools = {t: scenegen.make_scene(t, n_envs=1024) for t in ("arm", "clutter", "hand")}
+            runs = [serve_run(r, args.serve_seconds, m, pools=pools)
+                    for r in (2000, 5000, 10000, 20000) for m in (True, False)]
+            print(json.dumps({"metric": "served step latency (host arrival -> completion), env-steps/s",
+                              "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+                              "config": {"workload": "step server: Poisson arrivals, sessions of 1-1024 envs "
+                                                     "of arm/clutter/hand, geometric lifetime mean 50 requests, "
+                                                     "120 GB HBM budget"},
+                              "runs": runs}), flush=True)
+        return
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     name = args.config
@@ -334,6 +459,10 @@ def main():
         "status": code,
         "device": props.name,
     }
+    if not args.no_serve:
+        pools = {t: scenegen.make_scene(t, n_envs=1024) for t in ("arm", "clutter", "hand")}
+        line["served"] = {"merged": serve_run(2000, 4.0, True, pools=pools),
+                          "one_launch_per_request": serve_run(2000, 4.0, False, pools=pools)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20)
     print(json.dumps(line), flush=True)

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmsim.so")
-SOURCES = ["ms_api.cu", "ms_kernels.cu", "ms_noalloc.cu"]
+SOURCES = ["ms_api.cu", "ms_kernels.cu", "ms_noalloc.cu", "ms_server.cu"]
 HEADERS = ["ms_math.cuh", "ms_narrow.cuh", "ms_stages.cuh", "ms_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 # -fmad=false: every fused multiply-add is written out in the source, so the
@@ -23,6 +23,7 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std
 def _newest_input() -> float:
     paths = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     paths.append(os.path.join(os.path.dirname(HERE), "include", "ms.h"))
+    paths.append(os.path.join(os.path.dirname(HERE), "include", "ms_server.h"))
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 

@@ -84,16 +84,21 @@ struct ms_batch {
     bool fused_ready = false;
     std::map<long long, GraphEntry> graphs;
     cudaStream_t last = nullptr;
+    cudaStream_t setup = nullptr;     // non-blocking stream for allocation and uploads
     int sm_count = 0;
     size_t smem_optin = 0;
     std::vector<int> h_body_off, h_joint_off;
 };
 
+// Device memory comes from the device's stream-ordered pool on the batch's
+// own non-blocking stream: creating a batch (or a server session) neither
+// waits for nor stalls work running on other streams.
 static ms_status dmalloc(ms_batch* b, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, b->setup);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->setup);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA,
-                                      "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+                                      "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     b->allocs.push_back(*p);
     b->bytes += bytes;
     return MS_OK;
@@ -103,7 +108,7 @@ template <typename T>
 static ms_status upload(ms_batch* b, T** dst, const std::vector<T>& src) {
     ms_status s = dmalloc(b, (void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
     if (s) return s;
-    if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, b->setup));
     return MS_OK;
 }
 
@@ -117,8 +122,13 @@ static void drop_graphs(ms_batch* b) {
 
 static void free_all(ms_batch* b) {
     drop_graphs(b);
-    for (void* p : b->allocs) cudaFree(p);
+    for (void* p : b->allocs) cudaFreeAsync(p, b->setup);
     b->allocs.clear();
+    if (b->setup) {
+        cudaStreamSynchronize(b->setup);
+        cudaStreamDestroy(b->setup);
+        b->setup = nullptr;
+    }
 }
 
 static bool finite3(const float* v, int n) {
@@ -227,6 +237,10 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     ms_batch* b = new ms_batch();
     b->params = *p;
     cudaGetDevice(&b->device);
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->setup, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return fail(MS_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+    }
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
@@ -331,7 +345,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     if ((s = dmalloc(b, (void**)&b->d_mask, (size_t)E)) != MS_OK) { free_all(b); delete b; return s; }
     D.plain_ws = nullptr;
     D.rec_man = nullptr; D.rec_pts = nullptr; D.rec_cnt = nullptr;
-    cudaError_t ce = cudaDeviceSynchronize();
+    cudaError_t ce = cudaStreamSynchronize(b->setup);
     if (ce != cudaSuccess) { free_all(b); delete b; return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(ce)); }
     *out = b;
     g_err.clear();
@@ -587,6 +601,12 @@ extern "C" const char* ms_last_error(void) { return g_err.c_str(); }
 
 void ms::set_last_error(const char* msg) { g_err = msg; }
 
+const DevBatch& ms::batch_dev(const ::ms_batch* b) { return b->D; }
+
+void ms::batch_dims(const ::ms_batch* b, int* E, int* A, int* max_nb, int* max_nj) {
+    *E = b->E; *A = b->A; *max_nb = b->max_nb; *max_nj = b->max_nj;
+}
+
 // ------------------------------------------------------------ introspection
 extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
     if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
@@ -596,7 +616,8 @@ extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
         if ((s = dmalloc(b, &m, sizeof(int4) * (size_t)b->E * b->params.pair_capacity)) != MS_OK) return s;
         if ((s = dmalloc(b, &p, sizeof(float) * 10 * (size_t)b->E * b->params.contact_capacity)) != MS_OK) return s;
         if ((s = dmalloc(b, &c, sizeof(int) * (size_t)b->E)) != MS_OK) return s;
-        CK(cudaMemset(c, 0, sizeof(int) * (size_t)b->E));
+        CK(cudaMemsetAsync(c, 0, sizeof(int) * (size_t)b->E, b->setup));
+        CK(cudaStreamSynchronize(b->setup));
         b->D.rec_man = (int4*)m; b->D.rec_pts = (float*)p; b->D.rec_cnt = (int*)c;
     }
     b->record = record != 0;

@@ -6,6 +6,8 @@
 
 #include "ms_math.cuh"
 
+struct ms_batch;   // include/ms.h
+
 namespace ms {
 
 // Byte offsets of one env's arrays inside its workspace (-1: absent).  The
@@ -75,6 +77,10 @@ cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, c
                          int grid, int threads, size_t smem, cudaStream_t s);
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
 void set_last_error(const char* msg);   // the message ms_last_error() returns on this thread
+
+// read access to a batch's device view and sizes (for the step server)
+const DevBatch& batch_dev(const ::ms_batch* b);
+void batch_dims(const ::ms_batch* b, int* E, int* A, int* max_nb, int* max_nj);
 void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask, const int* body_env,
                          cudaStream_t s);
 

@@ -285,7 +285,14 @@ bool fused_supported(int G) { return fused_fn(G) != nullptr; }
 cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm) {
     const void* fn = fused_fn(G);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is a property of the kernel function shared by every batch
+    // (and every captured graph), so it is raised once to the device maximum
+    // rather than set to one batch's size; each launch still asks only for
+    // what its layout uses.
+    int dev = 0, optin = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }

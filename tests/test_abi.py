@@ -27,12 +27,16 @@ def declared(header):
 
 
 def test_every_declared_symbol_is_exported(lib):
+    from paper_2410_00425_b300 import server
     names = declared("ms.h")
-    assert "ms_step" in names and "ms_create_batch" in names
+    snames = declared("ms_server.h")
+    assert "ms_step" in names and "ms_create_batch" in names and "ms_server_submit" in snames
     raw = C.CDLL(_ffi.LIB_PATH)
-    for n in names:
+    for n in names + snames:
         assert hasattr(raw, n), n
     assert set(names) <= set(_ffi.EXPORTS)
+    assert set(snames) <= set(server.EXPORTS)
+    server.lib()                                  # binds every server signature
 
 
 def test_struct_layouts_match(lib):
