@@ -220,13 +220,13 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, pools=None):
+def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, pools=None, life_mean=500.0):
     """Open-loop Poisson load on the step server.
 
     Sessions own 1..1024 envs (log-uniform) of a scene type drawn uniformly
     from {arm, clutter, hand}, live for a geometric number of requests (mean
-    50) and are replaced by fresh sessions; each request steps its session
-    once with fresh drive targets.  Returns latency percentiles (host
+    life_mean, an episode) and are replaced by fresh sessions; each request
+    steps its session once with fresh drive targets.  Returns latency percentiles (host
     arrival -> completion) and the env-steps/s the server sustained."""
     import queue as _q
     from paper_2410_00425_b300.server import Server
@@ -245,7 +245,7 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
         a0 = int(g.integers(0, 1024 - n + 1))
         sc = pools[t].subset(range(a0, a0 + n))
         sid = srv.open(sc)
-        life = int(g.geometric(1.0 / 50.0))
+        life = int(g.geometric(1.0 / life_mean))
         return sid, t, a0, n, life
 
     active = []
@@ -263,7 +263,9 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
         t = types[int(g_open.integers(0, 3))]
         n = max(1, min(1024, int(np.exp(g_open.uniform(0.0, np.log(1024.0))))))
         a0 = int(g_open.integers(0, 1024 - n + 1))
-        spare.append((t, a0, n, pools[t].subset(range(a0, a0 + n)), int(g_open.geometric(1.0 / 50.0))))
+        spare.append((t, a0, n, pools[t].subset(range(a0, a0 + n)), int(g_open.geometric(1.0 / life_mean))))
+
+    open_s = []
 
     def opener():
         k = 0
@@ -276,7 +278,9 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
             if k < len(spare):
                 t, a0, n, sc, life = spare[k]
                 k += 1
+                t_open = time.perf_counter()
                 sid2 = srv.open(sc)
+                open_s.append(time.perf_counter() - t_open)
                 if sid2 is not None:
                     repl.put([sid2, t, a0, n, life])
     th = threading.Thread(target=opener, daemon=True)
@@ -289,6 +293,7 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
     t0 = time.perf_counter()
     nxt = t0
     submitted = 0
+    arrivals = no_session = 0
     saturated = False
     next_check = t0 + 0.5
     while True:
@@ -305,7 +310,9 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
             pass
         while not repl.empty():
             active.append(repl.get())
+        arrivals += 1
         if not active:
+            no_session += 1              # every session is being replaced: the arrival is lost
             continue
         k = int(g.integers(0, len(active)))
         sid, t, a0, n, life = active[k]
@@ -322,10 +329,16 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
     stop.set()
     th.join()
     srv.close()
-    return {"rate_req_s": rate, "duration_s": duration, "merge": merge, "requests": int(st["requests_done"]),
+    return {"rate_req_s": rate, "duration_s": duration, "merge": merge, "arrivals": arrivals,
+            "lost_no_session": no_session, "requests": int(st["requests_done"]),
+            "session_opens": len(open_s), "open_ms_p50": 1e3 * float(np.median(open_s)) if open_s else None,
             "launches": int(st["launches"]), "p50_ms": 1e3 * st["p50"], "p99_ms": 1e3 * st["p99"],
             "mean_ms": 1e3 * st["mean"], "env_steps_per_s": st["env_steps"] / wall,
             "sessions_admitted": int(st["sessions_admitted"]), "sessions_rejected": int(st["sessions_rejected"]),
+            "graph_captures": int(st["graph_captures"]), "launch_p50_ms": 1e3 * st["launch_p50"],
+            "launch_p99_ms": 1e3 * st["launch_p99"], "launch_max_ms": 1e3 * st["launch_max"],
+            "queue_p50_ms": 1e3 * st["queue_p50"], "queue_p99_ms": 1e3 * st["queue_p99"],
+            "stage_p99_ms": 1e3 * st["stage_p99"], "stage_max_ms": 1e3 * st["stage_max"], "life_mean": life_mean,
             "saturated": saturated}
 
 
@@ -343,6 +356,8 @@ def main():
     ap.add_argument("--tuning", default=None, help="force the launch shape G,W,R (skips the autotuner)")
     ap.add_argument("--serve", action="store_true", help="serving sweep only (rates x merge modes)")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rates", default="2000,5000,10000,20000", help="arrival rates (requests/s) of --serve")
+    ap.add_argument("--serve-life", type=float, default=500.0, help="mean session lifetime (requests) of --serve")
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -358,13 +373,14 @@ def main():
         if rank == 0:
             torch.cuda.set_device(local)
             pools = {t: scenegen.make_scene(t, n_envs=1024) for t in ("arm", "clutter", "hand")}
-            runs = [serve_run(r, args.serve_seconds, m, pools=pools)
-                    for r in (2000, 5000, 10000, 20000) for m in (True, False)]
+            rates = [int(r) for r in args.serve_rates.split(",")]
+            runs = [serve_run(r, args.serve_seconds, m, pools=pools, life_mean=args.serve_life)
+                    for r in rates for m in (True, False)]
             print(json.dumps({"metric": "served step latency (host arrival -> completion), env-steps/s",
                               "unit": "ms", "n_gpus": 1, "higher_is_better": False,
                               "config": {"workload": "step server: Poisson arrivals, sessions of 1-1024 envs "
-                                                     "of arm/clutter/hand, geometric lifetime mean 50 requests, "
-                                                     "120 GB HBM budget"},
+                                                     "of arm/clutter/hand, geometric lifetime mean %g requests, "
+                                                     "120 GB HBM budget" % args.serve_life},
                               "runs": runs}), flush=True)
         return
     dev = torch.device("cuda", local)
@@ -495,8 +511,12 @@ def main():
     }
     if not args.no_serve:
         pools = {t: scenegen.make_scene(t, n_envs=1024) for t in ("arm", "clutter", "hand")}
+        # 2k requests/s: latency at load; 10k requests/s: over capacity, the
+        # env-steps/s each mode sustains (its latencies grow with the run)
         line["served"] = {"merged": serve_run(2000, 4.0, True, pools=pools),
-                          "one_launch_per_request": serve_run(2000, 4.0, False, pools=pools)}
+                          "one_launch_per_request": serve_run(2000, 4.0, False, pools=pools),
+                          "overload_10k_merged": serve_run(10000, 3.0, True, pools=pools),
+                          "overload_10k_one_launch_per_request": serve_run(10000, 3.0, False, pools=pools)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20)
     print(json.dumps(line), flush=True)

@@ -8,11 +8,18 @@
  * opens a session owning 1..1024 envs of any scene type; the session's state
  * stays resident on the device for its whole life.  Sessions are admitted
  * against an HBM budget.  Each step request advances one session by one
- * step with fresh drive targets; a worker thread merges all pending
- * requests (at most one per session) into one launch of the batched kernel
- * over the union of their envs, and stamps every request with its host
- * arrival and completion times.  The comparison mode launches one ms_step
- * per request instead.
+ * step with fresh drive targets; a worker thread merges the pending
+ * requests (at most one per session, none of a session whose previous step
+ * is still running) into one launch of the batched kernel over the union of
+ * their envs, keeps up to max_inflight such launches running at once on
+ * their own streams, and stamps every request with its host arrival and
+ * completion times.  The comparison mode launches one ms_step per request
+ * instead (with the same number of launches in flight).
+ *
+ * ms_server_create sets the release threshold of the device's default
+ * memory pool (a per-process setting) to its maximum, so that memory freed
+ * by closed sessions is kept for the next session instead of being returned
+ * to the driver at every synchronisation.
  *
  * All functions return ms_status (include/ms.h) and are thread-safe.
  */
@@ -31,6 +38,7 @@ typedef struct {
     int32_t merge;              /* 1: merge pending requests into one launch; 0: one launch per request */
     int32_t max_requests;       /* at most this many requests per merged launch (<= 0: no limit) */
     double coalesce_us;         /* after the first pending request, wait up to this long for more */
+    int32_t max_inflight;       /* launches running at once, 1..64 (0: 4) */
 } ms_server_options;
 
 typedef struct {
@@ -50,11 +58,16 @@ typedef struct {
     size_t hbm_used, hbm_budget;
     double p50, p99, mean;      /* request latency (s) over the completed requests */
     double busy_s;              /* time the worker spent with a launch in flight */
+    uint64_t graph_captures;    /* launches that captured and instantiated a new graph */
+    double launch_p50, launch_p99, launch_max;  /* host time (s) of one launch: staging to completion */
+    double queue_p50, queue_p99;                /* request arrival to the start of its launch (s) */
+    double stage_p99, stage_max;                /* host time (s) to stage and enqueue one launch */
 } ms_server_stats;
 
 /* Create a server on the current device.  hbm_budget_bytes bounds the
  * device memory of all open sessions together.  opt may be NULL (merge,
- * no limit, no coalescing wait). */
+ * no limit, no coalescing wait, 4 launches in flight).  MS_ERR_INVALID_ARG
+ * for max_inflight outside 0..64. */
 ms_status ms_server_create(size_t hbm_budget_bytes, const ms_server_options* opt, ms_server** out);
 
 /* Open a session of n_envs envs (flat tables as ms_create_batch_flat).

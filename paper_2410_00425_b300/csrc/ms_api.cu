@@ -83,7 +83,10 @@ struct ms_batch {
     size_t fused_smem = 0;
     bool fused_ready = false;
     std::map<long long, GraphEntry> graphs;
-    cudaStream_t last = nullptr;
+    // recorded after the batch's last enqueued work, on whatever stream it
+    // went to: waiting on it never touches a stream the caller may have
+    // destroyed since
+    cudaEvent_t done = nullptr;
     cudaStream_t setup = nullptr;     // non-blocking stream for allocation and uploads
     int sm_count = 0;
     size_t smem_optin = 0;
@@ -128,6 +131,10 @@ static void free_all(ms_batch* b) {
         cudaStreamSynchronize(b->setup);
         cudaStreamDestroy(b->setup);
         b->setup = nullptr;
+    }
+    if (b->done) {
+        cudaEventDestroy(b->done);
+        b->done = nullptr;
     }
 }
 
@@ -240,6 +247,12 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     {
         cudaError_t e = cudaStreamCreateWithFlags(&b->setup, cudaStreamNonBlocking);
         if (e != cudaSuccess) { delete b; return fail(MS_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
+        e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(b->setup);
+            delete b;
+            return fail(MS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+        }
     }
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
     int optin = 0;
@@ -410,7 +423,7 @@ extern "C" ms_status ms_step_plain(ms_batch* b, const float* actions, int n_step
     cudaStream_t st = (cudaStream_t)stream;
     launch_plain(b->D, actions, n_steps, st);
     CK(cudaGetLastError());
-    b->last = st;
+    CK(cudaEventRecord(b->done, st));
     return MS_OK;
 }
 
@@ -478,13 +491,7 @@ static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, c
     return MS_OK;
 }
 
-extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
-    ms_status s = check_step_args(b, n_steps);
-    if (s) return s;
-    if (n_steps == 0) return MS_OK;
-    if ((s = configure_fused(b)) != MS_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    b->last = st;
+static ms_status step_enqueue(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
     if (st == nullptr) return enqueue_fused(b, actions, n_steps, st);   // the legacy stream cannot be captured
     long long key = (long long)n_steps;
     auto it = b->graphs.find(key);
@@ -526,6 +533,17 @@ extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, voi
     return MS_OK;
 }
 
+extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
+    ms_status s = check_step_args(b, n_steps);
+    if (s) return s;
+    if (n_steps == 0) return MS_OK;
+    if ((s = configure_fused(b)) != MS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = step_enqueue(b, actions, n_steps, st)) != MS_OK) return s;
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
+}
+
 // -------------------------------------------------------------------- state
 extern "C" ms_status ms_get_state(ms_batch* b, ms_state_view* out) {
     if (!b || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
@@ -547,7 +565,7 @@ extern "C" ms_status ms_copy_state(ms_batch* b, float* dst, int dst_kind, void* 
         CK(cudaMemcpyAsync(dst, b->d_staging, sizeof(float) * 13 * (size_t)b->NB, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaGetLastError());
-    b->last = st;
+    CK(cudaEventRecord(b->done, st));
     return MS_OK;
 }
 
@@ -568,14 +586,14 @@ extern "C" ms_status ms_set_state(ms_batch* b, const float* src, int src_kind, c
     launch_unpack_state(b->D, dsrc, dmask, b->d_body_env, st);
     CK(cudaGetLastError());
     // the host buffers may be reused as soon as this returns
+    CK(cudaEventRecord(b->done, st));
     CK(cudaStreamSynchronize(st));
-    b->last = st;
     return MS_OK;
 }
 
 extern "C" ms_status ms_sync(ms_batch* b, uint32_t* env_status) {
     if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
-    CK(cudaStreamSynchronize(b->last));
+    CK(cudaEventSynchronize(b->done));
     CK(cudaGetLastError());
     std::vector<uint32_t> st(b->E);
     CK(cudaMemcpy(st.data(), b->D.status, sizeof(uint32_t) * b->E, cudaMemcpyDeviceToHost));
@@ -591,7 +609,7 @@ extern "C" ms_status ms_sync(ms_batch* b, uint32_t* env_status) {
 
 extern "C" ms_status ms_destroy(ms_batch* b) {
     if (!b) return MS_OK;
-    cudaStreamSynchronize(b->last);
+    cudaEventSynchronize(b->done);
     free_all(b);
     delete b;
     return MS_OK;
@@ -605,6 +623,10 @@ const DevBatch& ms::batch_dev(const ::ms_batch* b) { return b->D; }
 
 void ms::batch_dims(const ::ms_batch* b, int* E, int* A, int* max_nb, int* max_nj) {
     *E = b->E; *A = b->A; *max_nb = b->max_nb; *max_nj = b->max_nj;
+}
+
+bool ms::batch_has_graph(const ::ms_batch* b, int n_steps) {
+    return b->fused_ready && b->graphs.count((long long)n_steps) != 0;
 }
 
 // ------------------------------------------------------------ introspection
@@ -630,7 +652,7 @@ extern "C" ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pai
     if (!b || !count) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (!b->D.rec_man) return fail(MS_ERR_INVALID_ARG, "contact recording is off");
     if (env < 0 || env >= b->E) return fail(MS_ERR_INVALID_ARG, "env %d out of range", env);
-    CK(cudaStreamSynchronize(b->last));
+    CK(cudaEventSynchronize(b->done));
     int n = 0;
     CK(cudaMemcpy(&n, b->D.rec_cnt + env, sizeof(int), cudaMemcpyDeviceToHost));
     *count = n;

@@ -81,6 +81,8 @@ void set_last_error(const char* msg);   // the message ms_last_error() returns o
 // read access to a batch's device view and sizes (for the step server)
 const DevBatch& batch_dev(const ::ms_batch* b);
 void batch_dims(const ::ms_batch* b, int* E, int* A, int* max_nb, int* max_nj);
+// true when ms_step(b, ., n_steps, stream) will replay a graph (no capture)
+bool batch_has_graph(const ::ms_batch* b, int n_steps);
 void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask, const int* body_env,
                          cudaStream_t s);
 

@@ -8,11 +8,15 @@
 // pairs and which reads each env's batch view from a device table, so
 // sessions of different scene types and solver parameters share a launch.
 // The launch (queue reset + kernel) is captured once per workspace layout
-// in a CUDA graph whose kernel parameters are updated per launch.  Every
-// request is stamped with its host arrival and completion times.
+// (bucketed sizes) in a CUDA graph whose kernel parameters are updated per
+// launch.  Up to max_inflight launches run at once, each on its own stream
+// (a "slot"); the worker polls their completion events, so a new launch can
+// start while earlier ones run.  Every request is stamped with its host
+// arrival and completion times.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
@@ -138,9 +142,8 @@ struct Session {
     int E = 0, A = 0, max_nb = 0, max_nj = 0;
     ms_sim_params p{};
     size_t bytes = 0;
-    float* d_act = nullptr;       // [E][A] drive targets of the request being served
-    int inflight = 0;             // queued requests not yet completed
-    bool closing = false;
+    int inflight = 0;             // queued or running requests
+    bool running = false;         // one of its requests is in a launch
 };
 
 struct Req {
@@ -166,6 +169,32 @@ struct GraphE {
     cudaKernelNodeParams kp{};
 };
 
+// One launch in flight at a time per slot: its stream and completion event,
+// the requests it serves, the device tables of a merged launch with their
+// pinned host staging, and its graphs (one per workspace layout).  The
+// worker is the only thread that touches a slot.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    int status = MS_OK;
+    int envs = 0;
+    double t0 = 0.0;
+    std::vector<std::pair<Req*, Session*>> batch;
+    DevBatch* d_batches = nullptr;
+    const float** d_acts = nullptr;
+    int2* d_work = nullptr;
+    int* d_queue = nullptr;
+    char* d_gscratch = nullptr;
+    float* d_act = nullptr;
+    DevBatch* h_batches = nullptr;
+    const float** h_acts = nullptr;
+    int2* h_work = nullptr;
+    float* h_act = nullptr;
+    size_t cap_batches = 0, cap_work = 0, cap_gscratch = 0, cap_act = 0;
+    std::map<GraphKey, GraphE> graphs;
+};
+
 ms_status sfail(ms_status code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -176,133 +205,182 @@ ms_status sfail(ms_status code, const char* fmt, ...) {
     return code;
 }
 
+// Smallest listed size >= v (v itself above the list): merged launches of
+// similar sessions share a workspace layout, hence a graph.
+int bucket(int v, std::initializer_list<int> sizes) {
+    for (int s : sizes)
+        if (v <= s) return s;
+    return v;
+}
+
 }  // namespace
 
 struct ms_server {
     size_t budget = 0, used = 0;
-    ms_server_options opt{1, 0, 0.0};
+    ms_server_options opt{1, 0, 0.0, 4};
     int device = 0, sm_count = 0, smem_optin = 0;
     std::mutex mu;
+    // Serialises the worker's stream captures with the client threads'
+    // batch creation, destruction and device-wide synchronisation, any of
+    // which may invalidate a capture in flight.  Never taken while the
+    // worker holds `mu`; a client may hold `mu` and then take it.
+    std::mutex dev_mu;
     std::condition_variable cv, done_cv;
     std::thread worker;
     bool stop = false;
     uint64_t next_session = 1, next_ticket = 1;
     std::unordered_map<uint64_t, Session*> sessions;
     std::deque<uint64_t> pending;
-    std::unordered_map<uint64_t, Req> reqs;
-    cudaStream_t stream = nullptr;
-    // device tables of a merged launch, grown on demand
-    DevBatch* d_batches = nullptr;
-    const float** d_acts = nullptr;
-    int2* d_work = nullptr;
-    int* d_queue = nullptr;
-    char* d_gscratch = nullptr;
-    size_t cap_batches = 0, cap_work = 0, cap_gscratch = 0;
-    DevBatch* h_batches = nullptr;        // pinned staging
-    const float** h_acts = nullptr;
-    int2* h_work = nullptr;
-    std::map<GraphKey, GraphE> graphs;
+    std::unordered_map<uint64_t, Req> reqs;     // element addresses stay valid across inserts
+    std::vector<Slot> slots;
+    std::vector<void*> retired_host;            // outgrown pinned staging, freed at destroy
     // statistics
     uint64_t sessions_admitted = 0, sessions_rejected = 0, requests_done = 0, launches = 0, env_steps = 0;
-    std::vector<double> lat;
-    double busy = 0.0;
+    std::atomic<uint64_t> graph_captures{0};     // counted by the worker outside `mu`
+    int running = 0;                            // slots with a launch in flight
+    double busy_since = 0.0, busy = 0.0;
+    std::vector<double> lat, launch_t, queue_t, stage_t;
 };
 
-static void free_tables(ms_server* s) {
-    cudaFree(s->d_batches); cudaFree(s->d_acts); cudaFree(s->d_work); cudaFree(s->d_queue); cudaFree(s->d_gscratch);
-    cudaFreeHost(s->h_batches); cudaFreeHost(s->h_acts); cudaFreeHost(s->h_work);
-    s->d_batches = nullptr; s->d_acts = nullptr; s->d_work = nullptr; s->d_queue = nullptr; s->d_gscratch = nullptr;
-    s->h_batches = nullptr; s->h_acts = nullptr; s->h_work = nullptr;
+// Device tables grow stream-ordered on the slot's stream (no device-wide
+// synchronisation); outgrown pinned buffers are kept until destroy.
+template <class T>
+static cudaError_t grow_dev(Slot& sl, T** p, size_t& cap, size_t need, size_t elem) {
+    if (need <= cap) return cudaSuccess;
+    size_t c = std::max(need, 2 * cap);
+    if (*p) cudaFreeAsync((void*)*p, sl.stream);
+    *p = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)p, c * elem, sl.stream);
+    if (e == cudaSuccess) cap = c;
+    else cap = 0;
+    return e;
 }
 
-static cudaError_t grow_tables(ms_server* s, size_t nb, size_t nw, size_t gbytes) {
-    cudaError_t e = cudaSuccess;
-    if (nb > s->cap_batches) {
-        size_t c = std::max(nb, 2 * s->cap_batches);
-        cudaFree(s->d_batches); cudaFree(s->d_acts); cudaFreeHost(s->h_batches); cudaFreeHost(s->h_acts);
-        if ((e = cudaMalloc(&s->d_batches, c * sizeof(DevBatch))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&s->d_acts, c * sizeof(float*))) != cudaSuccess) return e;
-        if ((e = cudaMallocHost(&s->h_batches, c * sizeof(DevBatch))) != cudaSuccess) return e;
-        if ((e = cudaMallocHost((void**)&s->h_acts, c * sizeof(float*))) != cudaSuccess) return e;
-        s->cap_batches = c;
+template <class T>
+static cudaError_t grow_host(ms_server* s, T** p, size_t old_cap, size_t new_cap, size_t elem) {
+    if (new_cap <= old_cap && *p) return cudaSuccess;
+    if (*p) s->retired_host.push_back((void*)*p);
+    *p = nullptr;
+    return cudaMallocHost((void**)p, new_cap * elem);
+}
+
+static cudaError_t grow_slot(ms_server* s, Slot& sl, size_t nb, size_t nw, size_t gbytes, size_t nact) {
+    cudaError_t e;
+    if (nb > sl.cap_batches) {
+        size_t old = sl.cap_batches;
+        if ((e = grow_dev(sl, &sl.d_batches, sl.cap_batches, nb, sizeof(DevBatch))) != cudaSuccess) return e;
+        size_t c = sl.cap_batches, c2 = old;
+        if ((e = grow_dev(sl, &sl.d_acts, c2, c, sizeof(float*))) != cudaSuccess) return e;
+        if ((e = grow_host(s, &sl.h_batches, old, c, sizeof(DevBatch))) != cudaSuccess) return e;
+        if ((e = grow_host(s, &sl.h_acts, old, c, sizeof(float*))) != cudaSuccess) return e;
     }
-    if (nw > s->cap_work) {
-        size_t c = std::max(nw, 2 * s->cap_work);
-        cudaFree(s->d_work); cudaFreeHost(s->h_work);
-        if ((e = cudaMalloc(&s->d_work, c * sizeof(int2))) != cudaSuccess) return e;
-        if ((e = cudaMallocHost(&s->h_work, c * sizeof(int2))) != cudaSuccess) return e;
-        s->cap_work = c;
+    if (nw > sl.cap_work) {
+        size_t old = sl.cap_work;
+        if ((e = grow_dev(sl, &sl.d_work, sl.cap_work, nw, sizeof(int2))) != cudaSuccess) return e;
+        if ((e = grow_host(s, &sl.h_work, old, sl.cap_work, sizeof(int2))) != cudaSuccess) return e;
     }
-    if (gbytes > s->cap_gscratch) {
-        cudaFree(s->d_gscratch);
-        if ((e = cudaMalloc(&s->d_gscratch, gbytes)) != cudaSuccess) return e;
-        s->cap_gscratch = gbytes;
+    if (nact > sl.cap_act) {
+        size_t old = sl.cap_act;
+        if ((e = grow_dev(sl, &sl.d_act, sl.cap_act, nact, sizeof(float))) != cudaSuccess) return e;
+        if ((e = grow_host(s, &sl.h_act, old, sl.cap_act, sizeof(float))) != cudaSuccess) return e;
     }
-    if (!s->d_queue && (e = cudaMalloc(&s->d_queue, 256)) != cudaSuccess) return e;
+    if ((e = grow_dev(sl, &sl.d_gscratch, sl.cap_gscratch, gbytes, 1)) != cudaSuccess) return e;
+    if (!sl.d_queue && (e = cudaMallocAsync((void**)&sl.d_queue, 256, sl.stream)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-// One merged launch over the sessions of `batch` (one request each).
-static int run_merged(ms_server* s, std::vector<std::pair<Req*, Session*>>& batch) {
+static void free_slot(ms_server* s, Slot& sl) {
+    cudaStreamSynchronize(sl.stream);
+    for (auto& kv : sl.graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    sl.graphs.clear();
+    cudaFreeAsync(sl.d_batches, sl.stream); cudaFreeAsync(sl.d_acts, sl.stream); cudaFreeAsync(sl.d_work, sl.stream);
+    cudaFreeAsync(sl.d_queue, sl.stream); cudaFreeAsync(sl.d_gscratch, sl.stream); cudaFreeAsync(sl.d_act, sl.stream);
+    cudaStreamSynchronize(sl.stream);
+    cudaFreeHost(sl.h_batches); cudaFreeHost(sl.h_acts); cudaFreeHost(sl.h_work); cudaFreeHost(sl.h_act);
+    cudaEventDestroy(sl.done);
+    cudaStreamDestroy(sl.stream);
+    (void)s;
+}
+
+// Stages and launches one merged launch over the slot's sessions (one
+// request each); does not wait for it.
+static int launch_merged(ms_server* s, Slot& sl) {
+    auto& batch = sl.batch;
     int mb = 1, mj = 0, pc = 1, cc = 1;
-    size_t nwork = 0;
+    size_t nwork = 0, nact = 0;
     for (auto& rs : batch) {
         Session* se = rs.second;
         mb = std::max(mb, se->max_nb); mj = std::max(mj, se->max_nj);
         pc = std::max(pc, se->p.pair_capacity); cc = std::max(cc, se->p.contact_capacity);
         nwork += (size_t)se->E;
+        nact += rs.first->act.size();
     }
+    mb = bucket(mb, {4, 8, 12, 16, 24, 32, 48, 64});
+    mj = bucket(mj, {0, 4, 8, 12, 16, 24, 32, 48, 64});
+    pc = bucket(pc, {8, 16, 32, 64, 128, 256, 512, 1024});
+    cc = bucket(cc, {8, 16, 32, 64, 128, 256, 512, 1024});
     const int warps = 2;
     Layout L = make_layout(mb, mj, pc, cc, true, true, true);
     if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, true);
     if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, false);
     size_t smem = (size_t)L.s_bytes * warps;
-    if (smem > (size_t)s->smem_optin) return MS_ERR_INVALID_ARG;
-    // raised to the device maximum: graphs of other layouts stay valid
-    cudaFuncSetAttribute((const void*)k_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+    if (smem > (size_t)s->smem_optin) return sfail(MS_ERR_INVALID_ARG, "merged layout needs %zu B of shared memory", smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_multi, 32 * warps, smem);
-    if (per_sm < 1) return MS_ERR_INVALID_ARG;
+    if (per_sm < 1) return sfail(MS_ERR_INVALID_ARG, "merged layout does not fit on an SM");
     // a fixed grid per layout keeps one graph per layout; warps without work exit at once
     int grid = per_sm * s->sm_count;
-    if (grow_tables(s, batch.size(), nwork, (size_t)grid * warps * L.g_bytes) != cudaSuccess) return MS_ERR_OOM;
-    size_t w = 0;
+    if (grow_slot(s, sl, batch.size(), nwork, (size_t)grid * warps * L.g_bytes, nact) != cudaSuccess)
+        return sfail(MS_ERR_OOM, "server tables: device or pinned allocation failed");
+    size_t w = 0, a = 0;
     for (size_t i = 0; i < batch.size(); i++) {
         Session* se = batch[i].second;
         Req* r = batch[i].first;
-        s->h_batches[i] = batch_dev(se->b);
-        s->h_acts[i] = nullptr;
+        sl.h_batches[i] = batch_dev(se->b);
+        sl.h_acts[i] = nullptr;
         if (!r->act.empty()) {
-            cudaMemcpyAsync(se->d_act, r->act.data(), r->act.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream);
-            s->h_acts[i] = se->d_act;
+            memcpy(sl.h_act + a, r->act.data(), r->act.size() * sizeof(float));
+            sl.h_acts[i] = sl.d_act + a;
+            a += r->act.size();
         }
-        for (int e = 0; e < se->E; e++) s->h_work[w++] = make_int2((int)i, e);
+        for (int e = 0; e < se->E; e++) sl.h_work[w++] = make_int2((int)i, e);
     }
     // heaviest envs first (the work queue is popped in order)
-    std::stable_sort(s->h_work, s->h_work + w, [&](int2 a, int2 b) {
-        return batch[a.x].second->max_nj * 8 + batch[a.x].second->max_nb > batch[b.x].second->max_nj * 8 + batch[b.x].second->max_nb;
+    std::stable_sort(sl.h_work, sl.h_work + w, [&](int2 x, int2 y) {
+        const Session* sx = batch[x.x].second;
+        const Session* sy = batch[y.x].second;
+        return sx->max_nj * 8 + sx->max_nb > sy->max_nj * 8 + sy->max_nb;
     });
-    cudaMemcpyAsync(s->d_batches, s->h_batches, batch.size() * sizeof(DevBatch), cudaMemcpyHostToDevice, s->stream);
-    cudaMemcpyAsync(s->d_acts, s->h_acts, batch.size() * sizeof(float*), cudaMemcpyHostToDevice, s->stream);
-    cudaMemcpyAsync(s->d_work, s->h_work, w * sizeof(int2), cudaMemcpyHostToDevice, s->stream);
+    if (a) cudaMemcpyAsync(sl.d_act, sl.h_act, a * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
+    cudaMemcpyAsync(sl.d_batches, sl.h_batches, batch.size() * sizeof(DevBatch), cudaMemcpyHostToDevice, sl.stream);
+    cudaMemcpyAsync(sl.d_acts, sl.h_acts, batch.size() * sizeof(float*), cudaMemcpyHostToDevice, sl.stream);
+    cudaMemcpyAsync(sl.d_work, sl.h_work, w * sizeof(int2), cudaMemcpyHostToDevice, sl.stream);
     GraphKey key{L.s_bytes, L.g_bytes, 32 * warps, grid};
-    auto it = s->graphs.find(key);
-    const DevBatch* a0 = s->d_batches;
-    const float* const* a1 = s->d_acts;
-    const int2* a2 = s->d_work;
+    auto it = sl.graphs.find(key);
+    const DevBatch* a0 = sl.d_batches;
+    const float* const* a1 = sl.d_acts;
+    const int2* a2 = sl.d_work;
     int a3 = (int)w;
     Layout a4 = L;
-    int* a5 = s->d_queue;
-    char* a6 = s->d_gscratch;
+    int* a5 = sl.d_queue;
+    char* a6 = sl.d_gscratch;
     void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4, (void*)&a5, (void*)&a6};
-    if (it == s->graphs.end()) {
+    if (it == sl.graphs.end()) {
         GraphE ge;
         cudaGraph_t g;
-        if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MS_ERR_CUDA;
-        cudaMemsetAsync(s->d_queue, 0, sizeof(int), s->stream);
-        cudaLaunchKernel((const void*)k_multi, dim3(grid), dim3(32 * warps), args, smem, s->stream);
-        if (cudaStreamEndCapture(s->stream, &g) != cudaSuccess) return MS_ERR_CUDA;
-        if (cudaGraphInstantiate(&ge.exec, g, 0) != cudaSuccess) return MS_ERR_CUDA;
+        {
+            std::lock_guard<std::mutex> dk(s->dev_mu);
+            if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return sfail(MS_ERR_CUDA, "merged launch: begin capture failed");
+            cudaMemsetAsync(sl.d_queue, 0, sizeof(int), sl.stream);
+            cudaLaunchKernel((const void*)k_multi, dim3(grid), dim3(32 * warps), args, smem, sl.stream);
+            cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
+            if (ce != cudaSuccess) return sfail(MS_ERR_CUDA, "merged launch capture: %s", cudaGetErrorString(ce));
+        }
+        if (cudaGraphInstantiate(&ge.exec, g, 0) != cudaSuccess) return sfail(MS_ERR_CUDA, "graph instantiate failed");
         size_t n = 0;
         cudaGraphGetNodes(g, nullptr, &n);
         std::vector<cudaGraphNode_t> nodes(n);
@@ -313,88 +391,151 @@ static int run_merged(ms_server* s, std::vector<std::pair<Req*, Session*>>& batc
             if (ty == cudaGraphNodeTypeKernel) { ge.kernel = nd; cudaGraphKernelNodeGetParams(nd, &ge.kp); }
         }
         ge.graph = g;
-        it = s->graphs.emplace(key, ge).first;
+        it = sl.graphs.emplace(key, ge).first;
+        s->graph_captures++;
     } else {
         cudaKernelNodeParams kp = it->second.kp;
         kp.kernelParams = args;
         kp.extra = nullptr;
-        if (cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.kernel, &kp) != cudaSuccess) return MS_ERR_CUDA;
+        if (cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.kernel, &kp) != cudaSuccess)
+            return sfail(MS_ERR_CUDA, "graph parameter update failed");
     }
-    if (cudaGraphLaunch(it->second.exec, s->stream) != cudaSuccess) return MS_ERR_CUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ERR_CUDA;
-    s->launches++;
-    s->env_steps += w;
-    for (auto& rs : batch) rs.first->launch_envs = (int)w;
+    if (cudaGraphLaunch(it->second.exec, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "graph launch failed");
+    if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "event record failed");
+    sl.envs = (int)w;
     return MS_OK;
 }
 
-static int run_single(ms_server* s, Req* r, Session* se) {
+// One request, one ms_step of its session's batch; does not wait for it.
+static int launch_single(ms_server* s, Slot& sl) {
+    Req* r = sl.batch[0].first;
+    Session* se = sl.batch[0].second;
     const float* act = nullptr;
     if (!r->act.empty()) {
-        cudaMemcpyAsync(se->d_act, r->act.data(), r->act.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream);
-        act = se->d_act;
+        if (grow_slot(s, sl, 1, 1, 0, r->act.size()) != cudaSuccess)
+            return sfail(MS_ERR_OOM, "server tables: device or pinned allocation failed");
+        memcpy(sl.h_act, r->act.data(), r->act.size() * sizeof(float));
+        cudaMemcpyAsync(sl.d_act, sl.h_act, r->act.size() * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
+        act = sl.d_act;
     }
-    int st = ms_step(se->b, act, 1, s->stream);
+    int st;
+    if (batch_has_graph(se->b, 1)) {
+        st = ms_step(se->b, act, 1, sl.stream);
+    } else {                                  // the first step of a session captures its graph
+        std::lock_guard<std::mutex> dk(s->dev_mu);
+        st = ms_step(se->b, act, 1, sl.stream);
+        s->graph_captures++;
+    }
     if (st) return st;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ERR_CUDA;
-    s->launches++;
-    s->env_steps += se->E;
-    r->launch_envs = se->E;
+    if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "event record failed");
+    sl.envs = se->E;
     return MS_OK;
+}
+
+// Completes the slot's requests (mu held).
+static void retire(ms_server* s, Slot& sl, double t) {
+    for (auto& rs : sl.batch) {
+        Req* r = rs.first;
+        r->done = true;
+        r->status = sl.status;
+        r->t_done = t;
+        r->launch_envs = sl.envs;
+        r->act.clear();
+        r->act.shrink_to_fit();
+        rs.second->inflight--;
+        rs.second->running = false;
+        s->lat.push_back(t - r->t_arrive);
+        s->queue_t.push_back(sl.t0 - r->t_arrive);
+        s->requests_done++;
+    }
+    if (sl.status == MS_OK) {
+        s->launches++;
+        s->env_steps += (uint64_t)sl.envs;
+    }
+    s->launch_t.push_back(t - sl.t0);
+    sl.batch.clear();
+    sl.busy = false;
+    if (--s->running == 0) s->busy += t - s->busy_since;
 }
 
 static void worker_loop(ms_server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->cv.wait(lk, [&] { return s->stop || !s->pending.empty(); });
-        if (s->stop && s->pending.empty()) break;
-        if (s->opt.coalesce_us > 0.0) {
-            double until = now_s() + s->opt.coalesce_us * 1e-6;
-            while (!s->stop && now_s() < until) {
+        bool progress = false;
+        // 1. retire finished launches
+        for (auto& sl : s->slots) {
+            if (!sl.busy) continue;
+            if (sl.status == MS_OK) {
+                cudaError_t q = cudaEventQuery(sl.done);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) sl.status = MS_ERR_CUDA;
+            }
+            retire(s, sl, now_s());
+            progress = true;
+        }
+        if (progress) s->done_cv.notify_all();
+        // 2. start a launch on a free slot: pending requests in arrival
+        //    order, at most one per session, none of a running session
+        Slot* free_slot = nullptr;
+        for (auto& sl : s->slots)
+            if (!sl.busy) { free_slot = &sl; break; }
+        bool wait_coalesce = false;
+        if (free_slot && !s->pending.empty() && s->opt.coalesce_us > 0.0 && !s->stop) {
+            const Req& first = s->reqs[s->pending.front()];
+            wait_coalesce = now_s() < first.t_arrive + s->opt.coalesce_us * 1e-6;
+        }
+        if (free_slot && !s->pending.empty() && !wait_coalesce) {
+            std::vector<std::pair<Req*, Session*>> batch;
+            std::deque<uint64_t> keep;
+            while (!s->pending.empty()) {
+                uint64_t t = s->pending.front();
+                s->pending.pop_front();
+                Req& r = s->reqs[t];
+                auto sit = s->sessions.find(r.session);
+                if (sit == s->sessions.end()) {
+                    r.done = true; r.status = MS_ERR_NOT_FOUND; r.t_done = now_s();
+                    progress = true;
+                    continue;
+                }
+                Session* se = sit->second;
+                bool full = (s->opt.max_requests > 0 && (int)batch.size() >= s->opt.max_requests) ||
+                            (!s->opt.merge && !batch.empty());
+                if (se->running || full) { keep.push_back(t); continue; }
+                se->running = true;
+                batch.emplace_back(&r, se);
+            }
+            s->pending = std::move(keep);
+            if (!batch.empty()) {
+                Slot& sl = *free_slot;
+                sl.batch = std::move(batch);
+                sl.busy = true;
+                sl.status = MS_OK;
+                sl.envs = 0;
+                double t0 = now_s();
+                sl.t0 = t0;
+                if (s->running++ == 0) s->busy_since = t0;
                 lk.unlock();
-                std::this_thread::yield();
+                int st = s->opt.merge ? launch_merged(s, sl) : launch_single(s, sl);
+                double t1 = now_s();
+                if (st != MS_OK)
+                    fprintf(stderr, "ms_server: launch of %zu request(s) failed (%d): %s\n", sl.batch.size(), st,
+                            ms_last_error());
                 lk.lock();
+                s->stage_t.push_back(t1 - t0);
+                sl.status = st;
+                progress = true;
             }
         }
-        // take pending requests in arrival order, at most one per session
-        std::vector<std::pair<Req*, Session*>> batch;
-        std::unordered_map<uint64_t, bool> taken;
-        std::deque<uint64_t> keep;
-        while (!s->pending.empty()) {
-            uint64_t t = s->pending.front();
-            s->pending.pop_front();
-            Req& r = s->reqs[t];
-            auto sit = s->sessions.find(r.session);
-            bool lim = s->opt.max_requests > 0 && (int)batch.size() >= s->opt.max_requests;
-            if (sit == s->sessions.end()) { r.done = true; r.status = MS_ERR_NOT_FOUND; r.t_done = now_s(); continue; }
-            if (taken.count(r.session) || lim || (!s->opt.merge && !batch.empty())) { keep.push_back(t); continue; }
-            taken[r.session] = true;
-            batch.emplace_back(&r, sit->second);
-        }
-        s->pending = std::move(keep);
-        if (batch.empty()) { s->done_cv.notify_all(); continue; }
-        lk.unlock();
-        double t0 = now_s();
-        int st = s->opt.merge ? run_merged(s, batch) : run_single(s, batch[0].first, batch[0].second);
-        double t1 = now_s();
-        if (st != MS_OK) fprintf(stderr, "ms_server: launch of %zu request(s) failed (%d): %s\n", batch.size(), st,
-                                 ms_last_error());
-        lk.lock();
-        s->busy += t1 - t0;
-        for (auto& rs : batch) {
-            Req* r = rs.first;
-            r->done = true;
-            r->status = st;
-            r->t_done = t1;
-            r->act.clear();
-            r->act.shrink_to_fit();
-            rs.second->inflight--;
-            s->lat.push_back(r->t_done - r->t_arrive);
-            s->requests_done++;
-        }
-        s->done_cv.notify_all();
+        if (progress) continue;
+        bool any_busy = s->running > 0;
+        if (s->stop && s->pending.empty() && !any_busy) break;
+        if (any_busy || wait_coalesce || !s->pending.empty())
+            s->cv.wait_for(lk, std::chrono::microseconds(20));    // poll the events in flight
+        else
+            s->cv.wait(lk, [&] { return s->stop || !s->pending.empty(); });
     }
+    s->done_cv.notify_all();
 }
 
 extern "C" double ms_server_now(void) { return now_s(); }
@@ -402,15 +543,35 @@ extern "C" double ms_server_now(void) { return now_s(); }
 extern "C" ms_status ms_server_create(size_t budget, const ms_server_options* opt, ms_server** out) {
     if (!out) return sfail(MS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    if (opt && (opt->max_inflight < 0 || opt->max_inflight > 64))
+        return sfail(MS_ERR_INVALID_ARG, "max_inflight must be 0..64");
     ms_server* s = new ms_server();
     s->budget = budget;
     if (opt) s->opt = *opt;
+    if (s->opt.max_inflight == 0) s->opt.max_inflight = 4;
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
     cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete s;
-        return sfail(MS_ERR_CUDA, "cudaStreamCreate failed");
+    // raised to the device maximum once: graphs of every layout stay valid
+    cudaFuncSetAttribute((const void*)k_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+    // sessions come and go: keep freed pool memory for the next session
+    // instead of returning it to the driver at every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    s->slots.resize((size_t)s->opt.max_inflight);
+    for (auto& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto& t : s->slots) {
+                if (t.done) cudaEventDestroy(t.done);
+                if (t.stream) cudaStreamDestroy(t.stream);
+            }
+            delete s;
+            return sfail(MS_ERR_CUDA, "stream or event creation failed");
+        }
     }
     s->worker = std::thread(worker_loop, s);
     *out = s;
@@ -425,9 +586,6 @@ extern "C" ms_status ms_server_open(ms_server* s, const ms_body_desc* bodies, co
     size_t est = 0;
     ms_status st = ms_estimate_bytes(body_off, joint_off, n_envs, p, &est);
     if (st) return st;
-    int max_nj = 0;
-    for (int e = 0; e < n_envs; e++) max_nj = std::max(max_nj, joint_off[e + 1] - joint_off[e]);
-    est += sizeof(float) * (size_t)n_envs * (size_t)std::max(max_nj, 1);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->used + est > s->budget) {
@@ -437,26 +595,20 @@ extern "C" ms_status ms_server_open(ms_server* s, const ms_body_desc* bodies, co
         s->used += est;                      // reserve while the batch is built
     }
     ms_batch* b = nullptr;
-    st = ms_create_batch_flat(bodies, body_off, joints, joint_off, n_envs, p, &b);
-    Session* se = nullptr;
-    if (st == MS_OK) {
-        se = new Session();
-        se->b = b;
-        se->p = *p;
-        batch_dims(b, &se->E, &se->A, &se->max_nb, &se->max_nj);
-        se->bytes = est;
-        if (cudaMalloc(&se->d_act, sizeof(float) * (size_t)se->E * (size_t)std::max(se->A, 1)) != cudaSuccess) {
-            ms_destroy(b);
-            delete se;
-            se = nullptr;
-            st = sfail(MS_ERR_OOM, "action buffer allocation failed");
-        }
+    {
+        std::lock_guard<std::mutex> dk(s->dev_mu);
+        st = ms_create_batch_flat(bodies, body_off, joints, joint_off, n_envs, p, &b);
     }
     std::lock_guard<std::mutex> lk(s->mu);
     if (st != MS_OK) {
         s->used -= est;
         return st;
     }
+    Session* se = new Session();
+    se->b = b;
+    se->p = *p;
+    batch_dims(b, &se->E, &se->A, &se->max_nb, &se->max_nj);
+    se->bytes = est;
     se->id = s->next_session++;
     s->sessions[se->id] = se;
     s->sessions_admitted++;
@@ -464,10 +616,11 @@ extern "C" ms_status ms_server_open(ms_server* s, const ms_body_desc* bodies, co
     return MS_OK;
 }
 
-static void destroy_session(ms_server* s, Session* se) {
+// Frees a session's device memory; the caller has removed it from the
+// session table and released its bytes from the budget.
+static void free_session(ms_server* s, Session* se) {
+    std::lock_guard<std::mutex> dk(s->dev_mu);
     ms_destroy(se->b);
-    cudaFree(se->d_act);
-    s->used -= se->bytes;
     delete se;
 }
 
@@ -479,7 +632,9 @@ extern "C" ms_status ms_server_close(ms_server* s, uint64_t session) {
     Session* se = it->second;
     s->done_cv.wait(lk, [&] { return se->inflight == 0; });
     s->sessions.erase(it);
-    destroy_session(s, se);
+    s->used -= se->bytes;
+    lk.unlock();                              // the worker keeps serving while the memory is freed
+    free_session(s, se);
     return MS_OK;
 }
 
@@ -522,7 +677,7 @@ extern "C" ms_status ms_server_drain(ms_server* s) {
     if (!s) return sfail(MS_ERR_INVALID_ARG, "NULL server");
     std::unique_lock<std::mutex> lk(s->mu);
     s->done_cv.wait(lk, [&] {
-        if (!s->pending.empty()) return false;
+        if (!s->pending.empty() || s->running > 0) return false;
         for (auto& kv : s->sessions) if (kv.second->inflight) return false;
         return true;
     });
@@ -540,6 +695,7 @@ extern "C" ms_status ms_server_copy_state(ms_server* s, uint64_t session, float*
         s->done_cv.wait(lk, [&] { return se->inflight == 0; });
         b = se->b;
     }
+    std::lock_guard<std::mutex> dk(s->dev_mu);
     ms_status st = ms_copy_state(b, dst, 0, nullptr);
     if (st) return st;
     return cudaDeviceSynchronize() == cudaSuccess ? MS_OK : sfail(MS_ERR_CUDA, "copy failed");
@@ -557,19 +713,40 @@ extern "C" ms_status ms_server_stats_get(ms_server* s, ms_server_stats* out) {
     out->env_steps = s->env_steps;
     out->hbm_used = s->used;
     out->hbm_budget = s->budget;
-    out->busy_s = s->busy;
+    out->busy_s = s->busy + (s->running > 0 ? now_s() - s->busy_since : 0.0);
+    out->graph_captures = s->graph_captures;
+    // nearest-rank percentile of a sorted sample
+    auto pct = [](const std::vector<double>& v, double q) {
+        size_t k = (size_t)std::min<double>(v.size() - 1, std::max(0.0, std::ceil(q * v.size()) - 1));
+        return v[k];
+    };
     if (!s->lat.empty()) {
         std::vector<double> v = s->lat;
         std::sort(v.begin(), v.end());
-        auto pct = [&](double q) {
-            size_t k = (size_t)std::min<double>(v.size() - 1, std::max(0.0, std::ceil(q * v.size()) - 1));
-            return v[k];
-        };
-        out->p50 = pct(0.50);
-        out->p99 = pct(0.99);
+        out->p50 = pct(v, 0.50);
+        out->p99 = pct(v, 0.99);
         double sum = 0;
         for (double x : v) sum += x;
         out->mean = sum / v.size();
+    }
+    if (!s->launch_t.empty()) {
+        std::vector<double> v = s->launch_t;
+        std::sort(v.begin(), v.end());
+        out->launch_p50 = pct(v, 0.50);
+        out->launch_p99 = pct(v, 0.99);
+        out->launch_max = v.back();
+    }
+    if (!s->queue_t.empty()) {
+        std::vector<double> v = s->queue_t;
+        std::sort(v.begin(), v.end());
+        out->queue_p50 = pct(v, 0.50);
+        out->queue_p99 = pct(v, 0.99);
+    }
+    if (!s->stage_t.empty()) {
+        std::vector<double> v = s->stage_t;
+        std::sort(v.begin(), v.end());
+        out->stage_p99 = pct(v, 0.99);
+        out->stage_max = v.back();
     }
     return MS_OK;
 }
@@ -578,8 +755,13 @@ extern "C" ms_status ms_server_reset_stats(ms_server* s) {
     if (!s) return sfail(MS_ERR_INVALID_ARG, "NULL server");
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat.clear();
+    s->launch_t.clear();
+    s->queue_t.clear();
+    s->stage_t.clear();
     s->requests_done = s->launches = s->env_steps = 0;
+    s->graph_captures = 0;
     s->busy = 0.0;
+    if (s->running > 0) s->busy_since = now_s();
     return MS_OK;
 }
 
@@ -591,15 +773,15 @@ extern "C" ms_status ms_server_destroy(ms_server* s) {
     }
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    cudaStreamSynchronize(s->stream);
-    for (auto& kv : s->sessions) destroy_session(s, kv.second);
-    s->sessions.clear();
-    for (auto& kv : s->graphs) {
-        cudaGraphExecDestroy(kv.second.exec);
-        cudaGraphDestroy(kv.second.graph);
+    // sessions first: a batch stepped by ms_step remembers the slot stream
+    // of its last step and synchronises it when destroyed
+    for (auto& kv : s->sessions) {
+        s->used -= kv.second->bytes;
+        free_session(s, kv.second);
     }
-    free_tables(s);
-    cudaStreamDestroy(s->stream);
+    s->sessions.clear();
+    for (auto& sl : s->slots) free_slot(s, sl);
+    for (void* p : s->retired_host) cudaFreeHost(p);
     delete s;
     return MS_OK;
 }

@@ -9,7 +9,8 @@ from . import _ffi
 
 
 class ms_server_options(C.Structure):
-    _fields_ = [("merge", C.c_int32), ("max_requests", C.c_int32), ("coalesce_us", C.c_double)]
+    _fields_ = [("merge", C.c_int32), ("max_requests", C.c_int32), ("coalesce_us", C.c_double),
+                ("max_inflight", C.c_int32)]
 
 
 class ms_request_result(C.Structure):
@@ -22,7 +23,10 @@ class ms_server_stats(C.Structure):
     _fields_ = [("sessions_open", C.c_uint64), ("sessions_admitted", C.c_uint64),
                 ("sessions_rejected", C.c_uint64), ("requests_done", C.c_uint64), ("launches", C.c_uint64),
                 ("env_steps", C.c_uint64), ("hbm_used", C.c_size_t), ("hbm_budget", C.c_size_t),
-                ("p50", C.c_double), ("p99", C.c_double), ("mean", C.c_double), ("busy_s", C.c_double)]
+                ("p50", C.c_double), ("p99", C.c_double), ("mean", C.c_double), ("busy_s", C.c_double),
+                ("graph_captures", C.c_uint64), ("launch_p50", C.c_double), ("launch_p99", C.c_double),
+                ("launch_max", C.c_double), ("queue_p50", C.c_double), ("queue_p99", C.c_double),
+                ("stage_p99", C.c_double), ("stage_max", C.c_double)]
 
 
 _SIGS = [
@@ -58,9 +62,10 @@ def lib():
 class Server:
     """One ms_server: sessions of resident envs, step requests, latency stats."""
 
-    def __init__(self, hbm_budget_bytes: int, merge: bool = True, max_requests: int = 0, coalesce_us: float = 0.0):
+    def __init__(self, hbm_budget_bytes: int, merge: bool = True, max_requests: int = 0, coalesce_us: float = 0.0,
+                 max_inflight: int = 0):
         L = lib()
-        o = ms_server_options(int(merge), int(max_requests), float(coalesce_us))
+        o = ms_server_options(int(merge), int(max_requests), float(coalesce_us), int(max_inflight))
         h = C.c_void_p()
         _ffi.check(L.ms_server_create(int(hbm_budget_bytes), C.byref(o), C.byref(h)))
         self.h = h.value

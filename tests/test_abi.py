@@ -112,3 +112,13 @@ def test_estimate_bytes_scales_with_envs(lib):
     sc2 = scenegen.make_scene("arm", n_envs=16)
     b = _ffi.ms_estimate_bytes(sc2.body_off, sc2.joint_off, sc2.params)
     assert 1.9 * a < b < 2.1 * a
+
+
+def test_server_rejects_bad_options(lib):
+    from paper_2410_00425_b300 import server
+    L = server.lib()
+    h = C.c_void_p()
+    o = server.ms_server_options(1, 0, 0.0, 65)
+    assert L.ms_server_create(1 << 30, C.byref(o), C.byref(h)) == 1
+    assert "max_inflight" in _ffi.ms_last_error()
+    assert L.ms_server_create(1 << 30, None, None) == 1

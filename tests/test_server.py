@@ -31,12 +31,12 @@ def _alone(scene, steps):
     return st
 
 
-@pytest.mark.parametrize("merge", [True, False])
-def test_sessions_of_mixed_types_match_stepping_alone(merge):
+@pytest.mark.parametrize("merge,inflight", [(True, 1), (True, 4), (False, 1), (False, 3)])
+def test_sessions_of_mixed_types_match_stepping_alone(merge, inflight):
     from paper_2410_00425_b300.server import Server
     scenes = [scenegen.make_scene("arm", n_envs=8), scenegen.make_scene("clutter", n_envs=16),
               scenegen.make_scene("hand", n_envs=4), scenegen.make_scene("small", n_envs=3)]
-    srv = Server(8 << 30, merge=merge)
+    srv = Server(8 << 30, merge=merge, max_inflight=inflight)
     sids = [srv.open(sc) for sc in scenes]
     assert all(s is not None for s in sids)
     steps = 4
@@ -54,6 +54,7 @@ def test_sessions_of_mixed_types_match_stepping_alone(merge):
     if merge:
         assert st["launches"] <= len(tickets)
         assert st["launches"] >= steps          # one request per session per launch
+        assert st["graph_captures"] >= 1
     else:
         assert st["launches"] == len(tickets)
     assert 0 <= st["p50"] <= st["p99"]
