@@ -444,7 +444,7 @@ def main():
     plain_value = None
     if not args.no_plain:
         p = sc.params
-        lp = n * (3 + p["substeps"] * (3 + p["pos_iters"] + p["vel_iters"]) + 1)
+        lp = n * (3 + p["substeps"] * (4 + p["pos_iters"] + p["vel_iters"]) + 1)
         t_p, _, _, _, _ = timed(True, lp)
         t_p = reduce_max(t_p, ws)
         plain_value = ws * E * n * args.steps / t_p

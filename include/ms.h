@@ -212,8 +212,11 @@ ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t
 
 /* Batched-path launch shape.  lanes_per_env in {1, 2, 4, 8, 16, 32}: a warp
  * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 8];
- * rows_in_smem: keep constraint rows in shared memory (1) or in an
- * L2-resident global slot per lane group (0).  Any choice gives
+ * rows_in_smem: 1 keeps every constraint row in shared memory when one
+ * CTA fits (else as 0); 0 keeps the joint rows in shared memory together
+ * with the rows of as many contact points per env as leave enough CTAs
+ * resident for all envs to be in flight at once, the other contact rows in
+ * an L2-resident global slot per lane group.  Any choice gives
  * bit-identical results. */
 typedef struct {
     int32_t lanes_per_env;

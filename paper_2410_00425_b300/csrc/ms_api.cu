@@ -401,7 +401,8 @@ extern "C" ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int3
 static ms_status ensure_plain(ms_batch* b) {
     if (b->D.plain_ws) return MS_OK;
     const ms_sim_params& p = b->params;
-    b->D.plain_layout = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, false, false, true);
+    b->D.plain_layout = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, false, true,
+                                    p.contact_capacity, true, false);
     void* ws = nullptr;
     const Layout& L = b->D.plain_layout;
     ms_status s = dmalloc(b, &ws, (size_t)b->E * (size_t)(L.s_bytes + L.g_bytes));
@@ -433,28 +434,47 @@ static ms_status configure_fused(ms_batch* b) {
     const ms_sim_params& p = b->params;
     Tuning& t = b->tune;
     int K = 32 / t.G;                               // envs per warp
-    // placement: rows and lists on chip if they fit, else rows, then the
-    // lists, move to the global part of the workspace
-    bool rows_smem = t.rows_smem != 0;
-    Layout L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, rows_smem, true);
-    size_t smem = (size_t)L.s_bytes * t.warps * K;
-    if (smem > b->smem_optin && rows_smem) {
-        rows_smem = false;
-        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false, true);
-        smem = (size_t)L.s_bytes * t.warps * K;
-    }
-    if (smem > b->smem_optin) {
-
-        L = make_layout(b->max_nb, b->max_nj, p.pair_capacity, p.contact_capacity, true, false, false);
-        smem = (size_t)L.s_bytes * t.warps * K;
-    }
-    if (smem > b->smem_optin)
-        return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)", smem, b->smem_optin);
+    int envs_per_cta = t.warps * K;
     int threads = 32 * t.warps;
+    int cc = p.contact_capacity;
+    auto lay = [&](bool rows_j, int pts_s, bool lists) {
+        return make_layout(b->max_nb, b->max_nj, p.pair_capacity, cc, true, rows_j, pts_s, lists, false);
+    };
+    // resident CTAs per SM of a layout (0: does not fit)
+    auto occ = [&](const Layout& Lc) {
+        size_t sm = (size_t)Lc.s_bytes * envs_per_cta;
+        if (sm > b->smem_optin) return 0;
+        int n = 0;
+        if (fused_occupancy(t.G, threads, sm, &n) != cudaSuccess) return 0;
+        return n;
+    };
+    // Placement.  rows_smem: every row on chip if one CTA fits.  Otherwise
+    // (or by choice) joint rows, lists and impulses on chip, with the rows of
+    // as many contact points as keep enough CTAs resident for every env to
+    // be in flight at once; then joint rows, then the lists, move to the
+    // global part if a CTA does not fit.
+    bool all_rows = false;
+    Layout L;
+    if (t.rows_smem && occ(L = lay(true, cc, true)) >= 1) {
+        all_rows = true;
+    } else if (int o0 = occ(L = lay(true, 0, true))) {
+        int need = (b->E + envs_per_cta - 1) / envs_per_cta;
+        int want = std::min(o0, (need + b->sm_count - 1) / b->sm_count);
+        int lo = 0, hi = cc;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (occ(lay(true, mid, true)) >= want) lo = mid;
+            else hi = mid - 1;
+        }
+        L = lay(true, lo, true);
+    } else if (occ(L = lay(false, 0, true)) < 1 && occ(L = lay(false, 0, false)) < 1) {
+        return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)",
+                    (size_t)L.s_bytes * envs_per_cta, b->smem_optin);
+    }
+    size_t smem = (size_t)L.s_bytes * envs_per_cta;
     int per_sm = 0;
     CK(fused_occupancy(t.G, threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
-    int envs_per_cta = t.warps * K;
     int grid = per_sm * b->sm_count;
     int need = (b->E + envs_per_cta - 1) / envs_per_cta;
     if (grid > need) grid = need;
@@ -466,7 +486,7 @@ static ms_status configure_fused(ms_batch* b) {
         b->d_gscratch = (char*)p2;
         b->gscratch_bytes = gbytes;
     }
-    t.rows_smem = rows_smem ? 1 : 0;
+    t.rows_smem = all_rows ? 1 : 0;
     b->fused_layout = L;
     b->fused_threads = threads;
     b->fused_grid = grid;
@@ -827,7 +847,8 @@ extern "C" ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* j
     // resident state and parameters, the staging buffer and the per-env
     // workspace of the plain path (the batched path's is per resident slot)
     size_t state = NB * (16 * 6 + 8 + 8 + 4 + 52) + NJ * (64 + 16 + 16 + 4) + (size_t)n_envs * 16 + 64;
-    Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, false, true);
+    Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, true, p->contact_capacity, true,
+                           false);
     *bytes = state + (size_t)n_envs * (size_t)(L.s_bytes + L.g_bytes);
     return MS_OK;
 }

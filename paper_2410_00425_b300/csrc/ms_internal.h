@@ -11,26 +11,35 @@ struct ms_batch;   // include/ms.h
 namespace ms {
 
 // Byte offsets of one env's arrays inside its workspace (-1: absent).  The
-// workspace has a shared part (bodies, joints, colour lists, impulses: the
-// data every sweep touches; in shared memory on the batched path) and a
-// global part (AABBs, pairs, manifolds, contact anchors: written once per
-// step; rows unless they fit the shared part).  The plain path keeps both
-// parts in one global slot per env.
+// workspace has a shared part -- the data every solver sweep touches: body
+// velocities and poses, the square root of each body's world inverse
+// inertia, the colour-ordered constraint list, impulses, joint rows and the
+// rows of the first pts_s contact points -- in shared memory on the batched
+// path, and a global part: AABBs, pairs, manifolds, contact anchors, the
+// colouring scratch and the rows of the remaining contact points, written
+// once per step or substep and read through L1/L2.  The plain path keeps
+// both parts in one global slot per env.
 struct Layout {
     int s_bytes;
-    int x, q, v, w, shape, inv, meta, adj;  // body copies (batched path only)
-    int jf, jp, jm, jt;                     // joint copies (batched path only)
-    int iw, cons, colr, scons, color_off, used, lam, cnt, status;
-    bool lists_shared;                      // cons, colr, scons, lam in the shared part
-    int rows_s;                             // rows in the shared part, or -1
+    int x, q, v, w;                          // body state copies (batched path only)
+    int sq;                                  // S = (world inverse inertia)^(1/2), 2 float4 per body
+    int scons, color_off, lam, cnt, status;  // shared part unless lists_shared is false
+    bool lists_shared;                       // scons and lam in the shared part
+    bool rows_j_shared;                      // joint rows in the shared part
+    int rows_j;                              // 8 rows per joint
+    int pts_s;                               // contact points whose rows are in the shared part
+    int rows_cs;                             // their rows (3 per point), or -1
     int g_bytes;
-    int aabb, pairs, man, pts;
-    int rows_g;                             // rows in the global part, or -1
-    int rows_bytes;
+    int aabb, pairs, man, pts, cons, colr, used;
+    int rows_cg;                             // rows of every contact point (those >= pts_s are used), or -1
+    int shape, inv, meta, adj, jf, jp, jm, jt;   // parameter copies (no-allocation path only), or -1
 };
 
-Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool rows_shared,
-                   bool lists_shared);
+// with_state: x, q, v, w copied into the shared part; with_params: body and
+// joint parameters copied into the global part.  pts_s is clamped to
+// [0, contact_cap].
+Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_state, bool rows_j_shared,
+                   int pts_s, bool lists_shared, bool with_params);
 
 // Kernel-side view of a batch (plain pointers, passed by value).
 struct DevParams {

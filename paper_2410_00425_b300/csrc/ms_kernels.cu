@@ -17,72 +17,68 @@ namespace ms {
 // ------------------------------------------------------------ slot layout
 static int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_bodies, bool rows_shared,
-                   bool lists_shared) {
+Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool with_state, bool rows_j_shared,
+                   int pts_s, bool lists_shared, bool with_params) {
     Layout L;
     int nb = max_nb > 0 ? max_nb : 1, nj = max_nj > 0 ? max_nj : 1;
     int pc = pair_cap > 0 ? pair_cap : 1, cc = contact_cap > 0 ? contact_cap : 1;
+    if (pts_s < 0) pts_s = 0;
+    if (pts_s > cc) pts_s = cc;
     int ncons = max_nj + (pc < cc ? pc : cc);      // every manifold has at least one point
     int nrows = 8 * max_nj + 3 * cc;
+    const int RB = (int)sizeof(Row);
     int o = 0;
     auto take = [&](int bytes, int al) { o = align_up(o, al); int r = o; o += bytes; return r; };
-    if (with_bodies) {
+    // shared part
+    if (with_state) {
         L.x = take(16 * nb, 16); L.q = take(16 * nb, 16); L.v = take(16 * nb, 16); L.w = take(16 * nb, 16);
-        L.shape = take(16 * nb, 16); L.inv = take(16 * nb, 16); L.meta = take(8 * nb, 8);
-        L.adj = take(8 * nb, 8);
-        L.jf = take(64 * nj, 16); L.jp = take(16 * nj, 16); L.jm = take(16 * nj, 16); L.jt = take(4 * nj, 4);
     } else {
-        L.x = L.q = L.v = L.w = L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = -1;
+        L.x = L.q = L.v = L.w = -1;
     }
-    L.iw = take(32 * nb, 16);
+    L.sq = take(32 * nb, 16);
     L.color_off = take(4 * (MAX_COLORS + 1), 4);
-    L.used = take(8 * nb, 8);
     L.cnt = take(4 * C_NUM, 16);
     L.status = take(4, 4);
     L.lists_shared = lists_shared;
     if (lists_shared) {
-        L.cons = take(16 * ncons, 16);
-        L.colr = take(4 * ncons, 4);
         L.scons = take(16 * ncons, 16);
-        L.lam = take(4 * nrows, 4);
+        L.lam = take(4 * nrows, 16);
     }
-    L.rows_bytes = (int)sizeof(Row) * nrows;
-    L.rows_s = rows_shared ? take(L.rows_bytes, 16) : -1;
+    L.rows_j_shared = rows_j_shared;
+    if (rows_j_shared) L.rows_j = take(RB * 8 * nj, 16);
+    L.pts_s = pts_s;
+    L.rows_cs = pts_s > 0 ? take(RB * 3 * pts_s, 16) : -1;
     L.s_bytes = align_up(o, 16);
+    // global part
     o = 0;
     if (!lists_shared) {
-        L.cons = take(16 * ncons, 16);
-        L.colr = take(4 * ncons, 4);
         L.scons = take(16 * ncons, 16);
-        L.lam = take(4 * nrows, 4);
+        L.lam = take(4 * nrows, 16);
     }
+    if (!rows_j_shared) L.rows_j = take(RB * 8 * nj, 16);
+    L.rows_cg = pts_s < cc ? take(RB * 3 * cc, 16) : -1;
     L.aabb = take(32 * nb, 16);
     L.pairs = take(4 * pc, 4);
     L.man = take(16 * pc, 16);
     L.pts = take(48 * cc, 16);
-    L.rows_g = rows_shared ? -1 : take(L.rows_bytes, 16);
+    L.cons = take(16 * ncons, 16);
+    L.colr = take(4 * ncons, 4);
+    L.used = take(8 * nb, 8);
+    if (with_params) {
+        L.shape = take(16 * nb, 16); L.inv = take(16 * nb, 16); L.meta = take(8 * nb, 8);
+        L.adj = take(8 * nb, 8);
+        L.jf = take(64 * nj, 16); L.jp = take(16 * nj, 16); L.jm = take(16 * nj, 16); L.jt = take(4 * nj, 4);
+    } else {
+        L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = -1;
+    }
     L.g_bytes = align_up(o, 16);
     return L;
 }
 
-template <typename T>
-__device__ __forceinline__ T* at(char* base, int off) { return reinterpret_cast<T*>(base + off); }
-
-__device__ __forceinline__ void view_workspace(EnvView& e, char* s, char* gl, const Layout& L) {
-    e.iw = at<float4>(s, L.iw);
-    char* lb = L.lists_shared ? s : gl;
-    e.cons = at<int4>(lb, L.cons);
-    e.colr = at<int>(lb, L.colr);
-    e.scons = at<int4>(lb, L.scons);
-    e.lam = at<float>(lb, L.lam);
-    e.color_off = at<int>(s, L.color_off);
-    e.used = at<unsigned long long>(s, L.used);
-    e.cnt = at<int>(s, L.cnt);
-    e.aabb = at<float4>(gl, L.aabb);
-    e.pairs = at<int>(gl, L.pairs);
-    e.man = at<int4>(gl, L.man);
-    e.pts = at<float4>(gl, L.pts);
-    e.rows = L.rows_s >= 0 ? at<Row>(s, L.rows_s) : at<Row>(gl, L.rows_g);
+// the env's parameters, read in place from the resident arrays
+__device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b0, int j0) {
+    e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
+    e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
 }
 
 __device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
@@ -102,8 +98,7 @@ __device__ __forceinline__ EnvView plain_view(const DevBatch& D, int env) {
     e.nb = D.body_off[env + 1] - b0;
     e.nj = D.joint_off[env + 1] - j0;
     e.x = D.x + b0; e.q = D.q + b0; e.v = D.v + b0; e.w = D.w + b0;
-    e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
-    e.jf = D.jf + 4 * j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
+    view_params(e, D, b0, j0);
     const Layout& L = D.plain_layout;
     char* s = D.plain_ws + (size_t)env * (L.s_bytes + L.g_bytes);
     view_workspace(e, s, s + L.s_bytes, L);
@@ -146,6 +141,10 @@ __global__ void k_integrate(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
     stage_integrate(e, warp_grp(), D.P);
 }
+__global__ void k_unscale(DevBatch D) {
+    EnvView e = plain_view(D, blockIdx.x);
+    stage_unscale(e, warp_grp());
+}
 __global__ void k_check(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
     stage_check(e, warp_grp());
@@ -167,6 +166,8 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
             k_integrate<<<grid, block, 0, s>>>(D);
             launches++;
             for (int it = 0; it < D.P.vel_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 2); launches++; }
+            k_unscale<<<grid, block, 0, s>>>(D);
+            launches++;
         }
         k_check<<<grid, block, 0, s>>>(D);
         launches++;
@@ -191,15 +192,6 @@ __global__ void __launch_bounds__(256, 2) k_fused(DevBatch D, const float* actio
 
     EnvView e;
     e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
-    float4* shp = at<float4>(s, L.shape);
-    float4* inv = at<float4>(s, L.inv);
-    int2* meta = at<int2>(s, L.meta);
-    unsigned long long* adj = at<unsigned long long>(s, L.adj);
-    float4* jf = at<float4>(s, L.jf);
-    float4* jp = at<float4>(s, L.jp);
-    int4* jm = at<int4>(s, L.jm);
-    e.shape = shp; e.inv = inv; e.meta = meta; e.adj = adj; e.jf = jf; e.jp = jp; e.jm = jm;
-    e.jt = at<float>(s, L.jt);
     view_workspace(e, s, gl, L);
     e.status = at<unsigned>(s, L.status);
 
@@ -216,22 +208,11 @@ __global__ void __launch_bounds__(256, 2) k_fused(DevBatch D, const float* actio
             b0 = D.body_off[env]; j0 = D.joint_off[env];
             nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
         }
-        int nbmax = g.wmax(nb), njmax = g.wmax(nj);
+        view_params(e, D, b0, j0);
+        int nbmax = g.wmax(nb);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
-            if (i < nb) {
-                e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i];
-                shp[i] = D.shape[b0 + i]; inv[i] = D.inv[b0 + i]; meta[i] = D.meta[b0 + i];
-                adj[i] = D.adj[b0 + i];
-            }
-        }
-        for (int k0 = 0; k0 < njmax; k0 += G) {
-            int j = k0 + g.lane;
-            if (j < nj) {
-                const float4* src = D.jf + 4 * (size_t)(j0 + j);
-                jf[4 * j] = src[0]; jf[4 * j + 1] = src[1]; jf[4 * j + 2] = src[2]; jf[4 * j + 3] = src[3];
-                jp[j] = D.jp[j0 + j]; jm[j] = D.jm[j0 + j]; e.jt[j] = D.jt[j0 + j];
-            }
+            if (i < nb) { e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i]; }
         }
         if (g.lane == 0) *e.status = active ? D.status[env] : 0u;
         view_record(e, D, env, active);
@@ -245,23 +226,13 @@ __global__ void __launch_bounds__(256, 2) k_fused(DevBatch D, const float* actio
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
             stage_color(e, g);
-            for (int sub = 0; sub < D.P.substeps; sub++) {
-                stage_prep(e, g, D.P);
-                stage_sweep(e, g, 0);
-                for (int it = 0; it < D.P.pos_iters; it++) stage_sweep(e, g, 1);
-                stage_integrate(e, g, D.P);
-                for (int it = 0; it < D.P.vel_iters; it++) stage_sweep(e, g, 2);
-            }
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P);
             stage_check(e, g);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
             if (i < nb) { D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i]; }
-        }
-        for (int k0 = 0; k0 < njmax; k0 += G) {
-            int j = k0 + g.lane;
-            if (j < nj) D.jt[j0 + j] = e.jt[j];
         }
         if (g.lane == 0 && active) D.status[env] = *e.status;
         g.sync();

@@ -100,29 +100,17 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
 
     EnvView e;
     e.x = nat<float4>(s, L.x); e.q = nat<float4>(s, L.q); e.v = nat<float4>(s, L.v); e.w = nat<float4>(s, L.w);
-    float4* shp = nat<float4>(s, L.shape);
-    float4* inv = nat<float4>(s, L.inv);
-    int2* meta = nat<int2>(s, L.meta);
-    unsigned long long* adj = nat<unsigned long long>(s, L.adj);
-    float4* jf = nat<float4>(s, L.jf);
-    float4* jp = nat<float4>(s, L.jp);
-    int4* jm = nat<int4>(s, L.jm);
+    // the parameters derived from the descriptors live in the global part
+    float4* shp = nat<float4>(gl, L.shape);
+    float4* inv = nat<float4>(gl, L.inv);
+    int2* meta = nat<int2>(gl, L.meta);
+    unsigned long long* adj = nat<unsigned long long>(gl, L.adj);
+    float4* jf = nat<float4>(gl, L.jf);
+    float4* jp = nat<float4>(gl, L.jp);
+    int4* jm = nat<int4>(gl, L.jm);
     e.shape = shp; e.inv = inv; e.meta = meta; e.adj = adj; e.jf = jf; e.jp = jp; e.jm = jm;
-    e.jt = nat<float>(s, L.jt);
-    e.iw = nat<float4>(s, L.iw);
-    char* lb = L.lists_shared ? s : gl;
-    e.cons = nat<int4>(lb, L.cons);
-    e.colr = nat<int>(lb, L.colr);
-    e.scons = nat<int4>(lb, L.scons);
-    e.lam = nat<float>(lb, L.lam);
-    e.color_off = nat<int>(s, L.color_off);
-    e.used = nat<unsigned long long>(s, L.used);
-    e.cnt = nat<int>(s, L.cnt);
-    e.aabb = nat<float4>(gl, L.aabb);
-    e.pairs = nat<int>(gl, L.pairs);
-    e.man = nat<int4>(gl, L.man);
-    e.pts = nat<float4>(gl, L.pts);
-    e.rows = L.rows_s >= 0 ? nat<Row>(s, L.rows_s) : nat<Row>(gl, L.rows_g);
+    e.jt = nat<float>(gl, L.jt);
+    view_workspace(e, s, gl, L);
     e.status = nat<unsigned>(s, L.status);
     e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
 
@@ -193,13 +181,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
             stage_color(e, g);
-            for (int sub = 0; sub < D.P.substeps; sub++) {
-                stage_prep(e, g, D.P);
-                stage_sweep(e, g, 0);
-                for (int it = 0; it < D.P.pos_iters; it++) stage_sweep(e, g, 1);
-                stage_integrate(e, g, D.P);
-                for (int it = 0; it < D.P.vel_iters; it++) stage_sweep(e, g, 2);
-            }
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P);
             stage_check(e, g);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }
@@ -289,14 +271,21 @@ extern "C" ms_status ms_step_noalloc(const ms_noalloc_batch* nb, const ms_sim_pa
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int mb = nb->max_bodies_per_env, mj = nb->max_joints_per_env;
-    Layout L = make_layout(mb, mj, p->pair_capacity, p->contact_capacity, true, true, true);
+    // every row on chip if it fits; else the contact rows, then the joint
+    // rows, then the lists and impulses move to the global part
+    int pc = p->pair_capacity, cc = p->contact_capacity;
+    Layout L = make_layout(mb, mj, pc, cc, true, true, cc, true, true);
     size_t smem = (size_t)L.s_bytes * K * warps;
     if (smem > (size_t)optin) {
-        L = make_layout(mb, mj, p->pair_capacity, p->contact_capacity, true, false, true);
+        L = make_layout(mb, mj, pc, cc, true, true, 0, true, true);
         smem = (size_t)L.s_bytes * K * warps;
     }
     if (smem > (size_t)optin) {
-        L = make_layout(mb, mj, p->pair_capacity, p->contact_capacity, true, false, false);
+        L = make_layout(mb, mj, pc, cc, true, false, 0, true, true);
+        smem = (size_t)L.s_bytes * K * warps;
+    }
+    if (smem > (size_t)optin) {
+        L = make_layout(mb, mj, pc, cc, true, false, 0, false, true);
         smem = (size_t)L.s_bytes * K * warps;
     }
     if (smem > (size_t)optin)

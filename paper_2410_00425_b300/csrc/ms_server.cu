@@ -48,34 +48,10 @@ __global__ void __launch_bounds__(256, 2) k_multi(const DevBatch* __restrict__ b
     char* s = smem + (size_t)warp * L.s_bytes;
     size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
     char* gl = gscratch + gslot * (size_t)L.g_bytes;
-    auto at = [](char* base, int off) { return base + off; };
-
     EnvView e;
-    e.x = (float4*)at(s, L.x); e.q = (float4*)at(s, L.q); e.v = (float4*)at(s, L.v); e.w = (float4*)at(s, L.w);
-    float4* shp = (float4*)at(s, L.shape);
-    float4* inv = (float4*)at(s, L.inv);
-    int2* meta = (int2*)at(s, L.meta);
-    unsigned long long* adj = (unsigned long long*)at(s, L.adj);
-    float4* jf = (float4*)at(s, L.jf);
-    float4* jp = (float4*)at(s, L.jp);
-    int4* jm = (int4*)at(s, L.jm);
-    e.shape = shp; e.inv = inv; e.meta = meta; e.adj = adj; e.jf = jf; e.jp = jp; e.jm = jm;
-    e.jt = (float*)at(s, L.jt);
-    e.iw = (float4*)at(s, L.iw);
-    char* lb = L.lists_shared ? s : gl;
-    e.cons = (int4*)at(lb, L.cons);
-    e.colr = (int*)at(lb, L.colr);
-    e.scons = (int4*)at(lb, L.scons);
-    e.lam = (float*)at(lb, L.lam);
-    e.color_off = (int*)at(s, L.color_off);
-    e.used = (unsigned long long*)at(s, L.used);
-    e.cnt = (int*)at(s, L.cnt);
-    e.aabb = (float4*)at(gl, L.aabb);
-    e.pairs = (int*)at(gl, L.pairs);
-    e.man = (int4*)at(gl, L.man);
-    e.pts = (float4*)at(gl, L.pts);
-    e.rows = L.rows_s >= 0 ? (Row*)at(s, L.rows_s) : (Row*)at(gl, L.rows_g);
-    e.status = (unsigned*)at(s, L.status);
+    e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
+    view_workspace(e, s, gl, L);
+    e.status = at<unsigned>(s, L.status);
     e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
 
     for (;;) {
@@ -88,14 +64,10 @@ __global__ void __launch_bounds__(256, 2) k_multi(const DevBatch* __restrict__ b
         int env = it.y;
         int b0 = D.body_off[env], j0 = D.joint_off[env];
         int nb = D.body_off[env + 1] - b0, nj = D.joint_off[env + 1] - j0;
+        e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
+        e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
         for (int i = wl; i < nb; i += 32) {
             e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i];
-            shp[i] = D.shape[b0 + i]; inv[i] = D.inv[b0 + i]; meta[i] = D.meta[b0 + i]; adj[i] = D.adj[b0 + i];
-        }
-        for (int j = wl; j < nj; j += 32) {
-            const float4* src = D.jf + 4 * (size_t)(j0 + j);
-            jf[4 * j] = src[0]; jf[4 * j + 1] = src[1]; jf[4 * j + 2] = src[2]; jf[4 * j + 3] = src[3];
-            jp[j] = D.jp[j0 + j]; jm[j] = D.jm[j0 + j]; e.jt[j] = D.jt[j0 + j];
         }
         if (wl == 0) *e.status = D.status[env];
         g.sync();
@@ -108,18 +80,11 @@ __global__ void __launch_bounds__(256, 2) k_multi(const DevBatch* __restrict__ b
         stage_broadphase(e, g, P);
         stage_narrowphase(e, g, P);
         stage_color(e, g);
-        for (int sub = 0; sub < P.substeps; sub++) {
-            stage_prep(e, g, P);
-            stage_sweep(e, g, 0);
-            for (int k = 0; k < P.pos_iters; k++) stage_sweep(e, g, 1);
-            stage_integrate(e, g, P);
-            for (int k = 0; k < P.vel_iters; k++) stage_sweep(e, g, 2);
-        }
+        for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P);
         stage_check(e, g);
         for (int i = wl; i < nb; i += 32) {
             D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i];
         }
-        for (int j = wl; j < nj; j += 32) D.jt[j0 + j] = e.jt[j];
         if (wl == 0) D.status[env] = *e.status;
         g.sync();
     }
@@ -323,9 +288,12 @@ static int launch_merged(ms_server* s, Slot& sl) {
     pc = bucket(pc, {8, 16, 32, 64, 128, 256, 512, 1024});
     cc = bucket(cc, {8, 16, 32, 64, 128, 256, 512, 1024});
     const int warps = 2;
-    Layout L = make_layout(mb, mj, pc, cc, true, true, true);
-    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, true);
-    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, false);
+    // every row on chip if it fits; else the contact rows, then the joint
+    // rows, then the lists and impulses move to the global part
+    Layout L = make_layout(mb, mj, pc, cc, true, true, cc, true, false);
+    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, true, 0, true, false);
+    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, 0, true, false);
+    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, 0, false, false);
     size_t smem = (size_t)L.s_bytes * warps;
     if (smem > (size_t)s->smem_optin) return sfail(MS_ERR_INVALID_ARG, "merged layout needs %zu B of shared memory", smem);
     int per_sm = 0;

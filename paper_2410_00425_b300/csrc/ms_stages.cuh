@@ -12,9 +12,10 @@
 // shared memory).  Both run this code, so they agree bit for bit.
 //
 // Per step: drive targets <- actions; broadphase; narrowphase; colouring
-// (once per step, at the step-start poses).  Per substep: gravity + world
-// inverse inertia + rows; warm start; pos_iters sweeps; integration + relax
-// bias; vel_iters relax sweeps.  The solver is substepped sequential impulses
+// (once per step, at the step-start poses).  Per substep: gravity + the
+// square root of each body's world inverse inertia + rows; warm start;
+// pos_iters sweeps; integration + relax bias; vel_iters relax sweeps;
+// angular velocities back to world space.  The solver is substepped sequential impulses
 // (Catto 2005) in the small-steps arrangement of Macklin et al. 2019, with
 // PD drives as soft constraints (Catto 2011), a per-row Coulomb pyramid and
 // a relax pass without penetration push.
@@ -32,19 +33,33 @@ enum { C_NPAIRS = 0, C_NMAN = 1, C_NPTS = 2, C_NCONS = 3, C_NCOLORS = 4, C_NUM =
 enum { MAX_COLORS = 64 };
 #define FULL_MASK 0xffffffffu
 
-// One constraint row, 64 B, read-only during the sweeps:
-//   r0 = lin, 1/k (1/(k + gamma) for a drive; 0 = inert row)
-//   r1 = angA, bias        r2 = angB, relax bias (0 for joint rows)
-//   r3 = mu (friction, else 0), kind | partner << 4 (int bits), gamma
-//        (drive, else 0), k
+// Between the prep of a substep and its end, a dynamic body's angular
+// velocity is kept as w^ = S^-1 w, S = (world inverse inertia)^(1/2) =
+// R diag(1/I)^(1/2) R^T, and every angular Jacobian a of a row as S a.  Then
+// a . w = (S a) . w^, the impulse response I^-1 a dl becomes S (S a) dl =
+// S . (change of w^) with w^ += (S a) dl, and a . I^-1 a = |S a|^2: a row
+// solve needs no matrix product.  Static bodies keep S = identity and w^ = w:
+// their velocity enters Jv, and no impulse is applied to them.
+//
+// One constraint row, 48 B, read-only during the sweeps:
+//   a = lin, 1/k (1/(k + gamma) for a drive; 0 = inert row)
+//   b = S_A angA, bias (friction rows: mu; their bias is 0)
+//   c = S_B angB, relax bias (drive row: gamma; other joint rows: 0)
+// A row's kind follows from its place in its constraint: joint rows 0-4 are
+// equalities, 5 and 6 the lower and upper limit, 7 the drive; a manifold of
+// np points has np normal rows, then a pair of friction rows per point.
 // The accumulated impulse lambda of each row lives in a separate array.
 struct Row {
-    float4 r0, r1, r2, r3;
+    float4 a, b, c;
 };
+
+// Constraint record (cons, scons): a, b, first row, place | np << 2 | idx << 8
+// with place: joint rows, or a manifold's rows in the shared or global part.
+enum { CP_JOINT = 0, CP_MAN_S = 1, CP_MAN_G = 2 };
 
 struct EnvView {
     int nb, nj;                       // counts the stages see (0: inactive or frozen)
-    float4 *x, *q, *v, *w;            // state; v.w = inverse mass (0 = static)
+    float4 *x, *q, *v, *w;            // state; v.w = inverse mass (0 = static); w holds w^ during a substep
     const float4* shape;              // p0, p1, p2, mu
     const float4* inv;                // 1/Ixx, 1/Iyy, 1/Izz, 1/m (0 = static)
     const int2* meta;                 // x: type | dyn << 8; y: group | mask << 16
@@ -53,24 +68,51 @@ struct EnvView {
     const float4* jp;                 // lower, upper, kp, kd
     const int4* jm;                   // type, parent, child, -
     float* jt;                        // drive targets
-    float4* iw;                       // world inverse inertia, 2 per body: (xx, xy, xz, yy), (yz, zz, -, -)
+    float4* sq;                       // S per body, 2 float4: (xx, xy, xz, yy), (yz, zz, -, -)
     float4* aabb;                     // 2 per body
     int* pairs;                       // i | j << 16
     int4* man;                        // a, b, npts, first point
     float4* pts;                      // 3 per point: (aA, d), (aB, -), (n, -)
-    int4* cons;                       // a, b, row0, nrows | kind << 8 | idx << 9 (list order)
+    int4* cons;                       // constraint records in list order
     int* colr;                        // colour per constraint
     int4* scons;                      // the same records sorted by colour (solve order)
     int* color_off;                   // MAX_COLORS + 1
     unsigned long long* used;         // colour masks per body
-    Row* rows;
-    float* lam;                       // accumulated impulse per row
+    Row* rows_j;                      // 8 per joint
+    Row* rows_cs;                     // 3 per contact point < pts_s
+    Row* rows_cg;                     // 3 per contact point (points >= pts_s)
+    int pts_s;
+    float* lam;                       // accumulated impulse per row: joints, then contact points
     int* cnt;                         // C_NUM counters
     unsigned* status;                 // env status word
     int4* rec_man;                    // recorded manifolds (nullable)
     float* rec_pts;                   // recorded points [contact_cap][10]
     int* rec_cnt;
 };
+
+// Workspace pointers of one env from its layout (s: shared part, gl: global part).
+template <typename T>
+MSD T* at(char* base, int off) { return reinterpret_cast<T*>(base + off); }
+
+MSD void view_workspace(EnvView& e, char* s, char* gl, const Layout& L) {
+    e.sq = at<float4>(s, L.sq);
+    char* lb = L.lists_shared ? s : gl;
+    e.scons = at<int4>(lb, L.scons);
+    e.lam = at<float>(lb, L.lam);
+    e.color_off = at<int>(s, L.color_off);
+    e.cnt = at<int>(s, L.cnt);
+    e.rows_j = at<Row>(L.rows_j_shared ? s : gl, L.rows_j);
+    e.pts_s = L.pts_s;
+    e.rows_cs = L.rows_cs >= 0 ? at<Row>(s, L.rows_cs) : nullptr;
+    e.rows_cg = L.rows_cg >= 0 ? at<Row>(gl, L.rows_cg) : nullptr;
+    e.aabb = at<float4>(gl, L.aabb);
+    e.pairs = at<int>(gl, L.pairs);
+    e.man = at<int4>(gl, L.man);
+    e.pts = at<float4>(gl, L.pts);
+    e.cons = at<int4>(gl, L.cons);
+    e.colr = at<int>(gl, L.colr);
+    e.used = at<unsigned long long>(gl, L.used);
+}
 
 // G lanes of a warp owning one env; all intrinsics use the full warp.
 struct Grp {
@@ -280,11 +322,12 @@ MSD void stage_color(EnvView& e, const Grp& g) {
         int i = i0 + g.lane;
         if (i < nj) {
             int4 jm = e.jm[i];
-            e.cons[i] = make_int4(jm.y, jm.z, 8 * i, 8 | (i << 9));
+            e.cons[i] = make_int4(jm.y, jm.z, 8 * i, CP_JOINT | (i << 8));
         } else if (i < ncons) {
             int m = i - nj;
             int4 M = e.man[m];
-            e.cons[i] = make_int4(M.x, M.y, 8 * nj + 3 * M.w, (3 * M.z) | (1 << 8) | (m << 9));
+            int place = M.w + M.z <= e.pts_s ? CP_MAN_S : CP_MAN_G;
+            e.cons[i] = make_int4(M.x, M.y, 3 * M.w, place | (M.z << 2) | (m << 8));
         }
     }
     int nbmax = g.wmax(e.nb);
@@ -331,12 +374,13 @@ struct BodyPose {
     float3 x;
     float4 q;
     M3 R;
-    S3 iw;
+    S3 S;          // (world inverse inertia)^(1/2); identity for static bodies, 0 for the world
     float im;
+    bool dyn;
 };
 
-MSD S3 load_iw(const EnvView& e, int i) {
-    float4 a = e.iw[2 * i], b = e.iw[2 * i + 1];
+MSD S3 load_sq(const EnvView& e, int i) {
+    float4 a = e.sq[2 * i], b = e.sq[2 * i + 1];
     return S3{a.x, a.y, a.z, a.w, b.x, b.y};
 }
 
@@ -346,37 +390,41 @@ MSD BodyPose pose_of(const EnvView& e, int i) {
         b.x = f3(0.f, 0.f, 0.f);
         b.q = make_float4(0.f, 0.f, 0.f, 1.f);
         b.R = qmat(b.q);
-        b.iw = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        b.S = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         b.im = 0.f;
+        b.dyn = false;
         return b;
     }
     b.x = xyz(e.x[i]);
     b.q = e.q[i];
     b.R = qmat(b.q);
-    b.iw = load_iw(e, i);
+    b.S = load_sq(e, i);
     b.im = e.v[i].w;
+    b.dyn = b.im > 0.f;
     return b;
 }
 
 MSD float contact_bias(float d, float h, float vmax) { return d >= 0.f ? d / h : fmaxf(d / h, -vmax); }
 
-MSD void write_row(Row& r, float3 lin, float3 angA, float3 angB, const BodyPose& A, const BodyPose& B, float bias,
-                   int kind, float aux, int partner) {
-    float3 wa = smv(A.iw, angA), wb = smv(B.iw, angB);
-    float k = fmaf(A.im + B.im, dot(lin, lin), dot(angA, wa) + dot(angB, wb));
-    r.r0 = f4(lin, k > 0.f ? 1.f / k : 0.f);
-    r.r1 = f4(angA, bias);
-    r.r2 = f4(angB, 0.f);
-    r.r3 = make_float4(kind == RK_FRICTION ? aux : 0.f, __int_as_float(kind | (partner << 4)), 0.f, k);
+// Writes the row and returns its effective mass k (static bodies add no
+// angular term).
+MSD float write_row(Row& r, float3 lin, float3 angA, float3 angB, const BodyPose& A, const BodyPose& B, float b,
+                    float c) {
+    float3 sa = smv(A.S, angA), sb = smv(B.S, angB);
+    float ka = A.dyn ? dot(sa, sa) : 0.f, kb = B.dyn ? dot(sb, sb) : 0.f;
+    float k = fmaf(A.im + B.im, dot(lin, lin), ka + kb);
+    r.a = f4(lin, k > 0.f ? 1.f / k : 0.f);
+    r.b = f4(sa, b);
+    r.c = f4(sb, c);
+    return k;
 }
 
-MSD void point_row(Row& r, float3 e_, float3 rA, float3 rB, const BodyPose& A, const BodyPose& B, float bias,
-                   int kind, float aux, int partner) {
-    write_row(r, e_, cross(rA, e_), cross(e_, rB), A, B, bias, kind, aux, partner);
+MSD float point_row(Row& r, float3 e_, float3 rA, float3 rB, const BodyPose& A, const BodyPose& B, float b, float c) {
+    return write_row(r, e_, cross(rA, e_), cross(e_, rB), A, B, b, c);
 }
 
-MSD void ang_row(Row& r, float3 jA, float3 jB, const BodyPose& A, const BodyPose& B, float bias, int kind) {
-    write_row(r, f3(0.f, 0.f, 0.f), jA, jB, A, B, bias, kind, 0.f, 0);
+MSD float ang_row(Row& r, float3 jA, float3 jB, const BodyPose& A, const BodyPose& B, float b, float c) {
+    return write_row(r, f3(0.f, 0.f, 0.f), jA, jB, A, B, b, c);
 }
 
 struct JointGeo {
@@ -405,12 +453,18 @@ MSD JointGeo joint_geo(const EnvView& e, int j, int type, const BodyPose& P, con
     return g;
 }
 
+MSD Row* cons_rows(const EnvView& e, int4 c) {
+    int place = c.w & 3;
+    return (place == CP_JOINT ? e.rows_j : (place == CP_MAN_S ? e.rows_cs : e.rows_cg)) + c.z;
+}
+
 MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
-    int kind = (c.w >> 8) & 1, idx = c.w >> 9;
+    bool joint = (c.w & 3) == CP_JOINT;
+    int idx = c.w >> 8;
     BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
-    Row* R = e.rows + c.z;
+    Row* R = cons_rows(e, c);
     float h = P.h;
-    if (kind == 1) {
+    if (!joint) {
         int4 M = e.man[idx];
         int np = M.z;
         float mu = 0.5f * (e.shape[M.x].w + e.shape[M.y].w);
@@ -423,62 +477,62 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
             float3 t1 = cross(n, axis3(ax));
             t1 = t1 * (1.f / len(t1));
             float3 t2 = cross(n, t1);
-            point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), RK_NORMAL, mu, 0);
-            point_row(R[np + 2 * k], t1, rA, rB, A, B, 0.f, RK_FRICTION, mu, k);
-            point_row(R[np + 2 * k + 1], t2, rA, rB, A, B, 0.f, RK_FRICTION, mu, k);
+            point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), 0.f);
+            point_row(R[np + 2 * k], t1, rA, rB, A, B, mu, 0.f);
+            point_row(R[np + 2 * k + 1], t2, rA, rB, A, B, mu, 0.f);
         }
+        return;
+    }
+    int4 jm = e.jm[idx];
+    float4 jp = e.jp[idx];
+    JointGeo gj = joint_geo(e, idx, jm.x, A, B);
+    float kd7;
+    if (jm.x == 0) {
+        for (int t = 0; t < 3; t++) {
+            float3 ee = axis3(t);
+            point_row(R[t], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, 0.f);
+        }
+        int k = basis_axis(gj.a);
+        float3 b1 = cross(gj.a, axis3(k));
+        b1 = b1 * (1.f / len(b1));
+        float3 b2 = cross(gj.a, b1);
+        float3 axc = cross(gj.a, gj.c);
+        ang_row(R[3], -b1, b1, A, B, dot(b1, axc) / h, 0.f);
+        ang_row(R[4], -b2, b2, A, B, dot(b2, axc) / h, 0.f);
+        ang_row(R[5], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
+        ang_row(R[6], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
+        kd7 = ang_row(R[7], -gj.a, gj.a, A, B, 0.f, 0.f);
     } else {
-        int4 jm = e.jm[idx];
-        float4 jp = e.jp[idx];
-        JointGeo gj = joint_geo(e, idx, jm.x, A, B);
-        if (jm.x == 0) {
-            for (int t = 0; t < 3; t++) {
-                float3 ee = axis3(t);
-                point_row(R[t], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
-            }
-            int k = basis_axis(gj.a);
-            float3 b1 = cross(gj.a, axis3(k));
-            b1 = b1 * (1.f / len(b1));
-            float3 b2 = cross(gj.a, b1);
-            float3 axc = cross(gj.a, gj.c);
-            ang_row(R[3], -b1, b1, A, B, dot(b1, axc) / h, RK_EQ);
-            ang_row(R[4], -b2, b2, A, B, dot(b2, axc) / h, RK_EQ);
-            ang_row(R[5], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), RK_LIMIT);
-            ang_row(R[6], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), RK_LIMIT);
-            ang_row(R[7], -gj.a, gj.a, A, B, 0.f, RK_DRIVE);
-        } else {
-            int k = basis_axis(gj.a);
-            float3 b1 = cross(gj.a, axis3(k));
-            b1 = b1 * (1.f / len(b1));
-            float3 b2 = cross(gj.a, b1);
-            point_row(R[0], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
-            point_row(R[1], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, RK_EQ, 0.f, 0);
-            float4 qe = qmul(gj.qPw, qconj(gj.qCw));
-            float sg = qe.w >= 0.f ? 1.f : -1.f;
-            float3 th = f3(2.f * sg * qe.x, 2.f * sg * qe.y, 2.f * sg * qe.z);
-            for (int t = 0; t < 3; t++) {
-                float3 ee = axis3(t);
-                ang_row(R[2 + t], ee, -ee, A, B, comp(th, t) / h, RK_EQ);
-            }
-            point_row(R[5], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), RK_LIMIT, 0.f, 0);
-            point_row(R[6], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), RK_LIMIT, 0.f, 0);
-            point_row(R[7], -gj.a, gj.rP, gj.rC, A, B, 0.f, RK_DRIVE, 0.f, 0);
+        int k = basis_axis(gj.a);
+        float3 b1 = cross(gj.a, axis3(k));
+        b1 = b1 * (1.f / len(b1));
+        float3 b2 = cross(gj.a, b1);
+        point_row(R[0], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, 0.f);
+        point_row(R[1], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, 0.f);
+        float4 qe = qmul(gj.qPw, qconj(gj.qCw));
+        float sg = qe.w >= 0.f ? 1.f : -1.f;
+        float3 th = f3(2.f * sg * qe.x, 2.f * sg * qe.y, 2.f * sg * qe.z);
+        for (int t = 0; t < 3; t++) {
+            float3 ee = axis3(t);
+            ang_row(R[2 + t], ee, -ee, A, B, comp(th, t) / h, 0.f);
         }
-        // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
-        // b = kp C / (h kp + kd), C = phi - target; the row keeps
-        // 1/(k + gamma) so that each iteration is one multiply
-        float kp = jp.z, kd = jp.w;
-        float den = fmaf(h, kp, kd);
-        Row& dr = R[7];
-        float k = dr.r3.w;
-        if (den > 0.f && k > 0.f) {
-            float gam = 1.f / (h * den);
-            dr.r3.z = gam;
-            dr.r1.w = kp * (gj.phi - e.jt[idx]) / den;
-            dr.r0.w = 1.f / (k + gam);
-        } else {
-            dr.r0.w = 0.f;
-        }
+        point_row(R[5], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
+        point_row(R[6], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
+        kd7 = point_row(R[7], -gj.a, gj.rP, gj.rC, A, B, 0.f, 0.f);
+    }
+    // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
+    // b = kp C / (h kp + kd), C = phi - target; the row keeps
+    // 1/(k + gamma) so that each iteration is one multiply
+    float kp = jp.z, kd = jp.w;
+    float den = fmaf(h, kp, kd);
+    Row& dr = R[7];
+    if (den > 0.f && kd7 > 0.f) {
+        float gam = 1.f / (h * den);
+        dr.c.w = gam;
+        dr.b.w = kp * (gj.phi - e.jt[idx]) / den;
+        dr.a.w = 1.f / (kd7 + gam);
+    } else {
+        dr.a.w = 0.f;
     }
 }
 
@@ -494,12 +548,16 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
             v.x = fmaf(h, P.gx, v.x); v.y = fmaf(h, P.gy, v.y); v.z = fmaf(h, P.gz, v.z);
             e.v[i] = v;
             float4 iv = e.inv[i];
-            S3 I = rdrt(qmat(e.q[i]), f3(iv.x, iv.y, iv.z));
-            e.iw[2 * i] = make_float4(I.xx, I.xy, I.xz, I.yy);
-            e.iw[2 * i + 1] = make_float4(I.yz, I.zz, 0.f, 0.f);
+            float3 sd = f3(sqrtf(iv.x), sqrtf(iv.y), sqrtf(iv.z));
+            M3 R = qmat(e.q[i]);
+            S3 S = rdrt(R, sd);
+            S3 Si = rdrt(R, f3(1.f / sd.x, 1.f / sd.y, 1.f / sd.z));
+            e.sq[2 * i] = make_float4(S.xx, S.xy, S.xz, S.yy);
+            e.sq[2 * i + 1] = make_float4(S.yz, S.zz, 0.f, 0.f);
+            e.w[i] = f4(smv(Si, xyz(e.w[i])), 0.f);
         } else {
-            e.iw[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            e.iw[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            e.sq[2 * i] = make_float4(1.f, 0.f, 0.f, 1.f);
+            e.sq[2 * i + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
         }
     }
     g.sync();
@@ -513,11 +571,11 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
 }
 
 // ------------------------------------------------------------------ solve
-// Rows of one constraint, in order, with both bodies' velocities, inverse
-// masses and world inverse inertias in registers.  MODE 0: warm
-// start (apply lambda); 1: position iteration; 2: relax iteration (drives
-// skipped, relax bias; joint rows carry a zero relax bias).  Every row kind
-// goes through one formula,
+// Rows of one constraint, in order, with both bodies' velocities and
+// inverse masses in registers.  MODE 0: warm start (apply lambda); 1:
+// position iteration; 2: relax iteration (drives skipped, relax bias; joint
+// equality rows carry a zero relax bias).  Every row kind goes through one
+// formula,
 //     lambda' = clamp(lambda - (Jv + b + gamma lambda) / (k + gamma), lo, hi)
 // with gamma = 0 except for drives and (lo, hi) = (0, inf) for normals and
 // limits, +-mu lambda_n for friction, unbounded otherwise; an inert row has
@@ -527,59 +585,64 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
 struct SolveCtx {
     float4* v;
     float4* w;
-    const float4* iw;
-    const Row* rows;
+    const Row* rj;
+    const Row* rcs;
+    const Row* rcg;
     float* lam;
+    int nj;
 };
 
-MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.iw, e.rows, e.lam}; }
+MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.rows_j, e.rows_cs, e.rows_cg, e.lam, e.nj}; }
 
 template <int MODE>
 MSD void solve_constraint(const SolveCtx& x, int4 c) {
-    int nrows = c.w & 0xff;
+    int place = c.w & 3, np = (c.w >> 2) & 7;
+    bool joint = place == CP_JOINT;
+    int nrows = joint ? 8 : 3 * np;
+    const Row* R = (joint ? x.rj : (place == CP_MAN_S ? x.rcs : x.rcg)) + c.z;
+    float* L = x.lam + (joint ? c.z : 8 * x.nj + c.z);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 va = c.x >= 0 ? x.v[c.x] : z4, wa4 = c.x >= 0 ? x.w[c.x] : z4;
     float4 vb = c.y >= 0 ? x.v[c.y] : z4, wb4 = c.y >= 0 ? x.w[c.y] : z4;
-    float4 ia0 = c.x >= 0 ? x.iw[2 * c.x] : z4, ia1 = c.x >= 0 ? x.iw[2 * c.x + 1] : z4;
-    float4 ib0 = c.y >= 0 ? x.iw[2 * c.y] : z4, ib1 = c.y >= 0 ? x.iw[2 * c.y + 1] : z4;
-    S3 IA{ia0.x, ia0.y, ia0.z, ia0.w, ia1.x, ia1.y}, IB{ib0.x, ib0.y, ib0.z, ib0.w, ib1.x, ib1.y};
     float imA = va.w, imB = vb.w;
+    // a static body's velocity enters Jv but no impulse changes it
+    bool dynA = imA > 0.f, dynB = imB > 0.f;
     float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
-    const Row* R = x.rows + c.z;
-    float* L = x.lam + c.z;
-    float4 n0 = R[0].r0, n1 = R[0].r1, n2 = R[0].r2, n3 = R[0].r3;
+    float4 n0 = R[0].a, n1 = R[0].b, n2 = R[0].c;
     for (int r = 0; r < nrows; r++) {
-        float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
+        float4 ra = n0, rb = n1, rc = n2;
         int rn = min(r + 1, nrows - 1);                  // prefetch the next row (clamped, always valid)
-        n0 = R[rn].r0; n1 = R[rn].r1; n2 = R[rn].r2; n3 = R[rn].r3;
-        int kb = __float_as_int(r3.y);
-        int kind = kb & 15;
-        float3 lin = xyz(r0), angA = xyz(r1), angB = xyz(r2);
+        n0 = R[rn].a; n1 = R[rn].b; n2 = R[rn].c;
+        float3 lin = xyz(ra), sa = xyz(rb), sb = xyz(rc);
         float old = L[r];
         float dl;
         if (MODE == 0) {
-            dl = r0.w > 0.f ? old : 0.f;
+            dl = ra.w > 0.f ? old : 0.f;
         } else {
-            float ik = (MODE == 2 && kind == RK_DRIVE) ? 0.f : r0.w;
-            float bias = MODE == 2 ? r2.w : r1.w;
+            bool fric = !joint && r >= np;
+            bool drive = joint && r == 7;
+            bool eq = joint && r < 5;
+            float ik = (MODE == 2 && drive) ? 0.f : ra.w;
+            float bias = fric ? 0.f : (MODE == 2 ? (drive ? 0.f : rc.w) : rb.w);
+            float gam = drive ? rc.w : 0.f;
             float3 dv = vA - vB;
-            float j1 = dot(lin, dv), j2 = dot(angA, wA), j3 = dot(angB, wB);
+            float j1 = dot(lin, dv), j2 = dot(sa, wA), j3 = dot(sb, wB);
             float jv = (j1 + j2) + j3;
-            float nl = fmaf(-((jv + bias) + r3.z * old), ik, old);
-            float lim = r3.x * L[kb >> 4];                // friction bound from the point's normal impulse
-            float lo = kind == RK_FRICTION ? -lim : ((kind == RK_NORMAL || kind == RK_LIMIT) ? 0.f : -INFINITY);
-            float hi = kind == RK_FRICTION ? lim : INFINITY;
+            float nl = fmaf(-((jv + bias) + gam * old), ik, old);
+            float lim = fric ? rb.w * L[(r - np) >> 1] : 0.f;   // friction bound from the point's normal impulse
+            float lo = fric ? -lim : ((eq || drive) ? -INFINITY : 0.f);
+            float hi = fric ? lim : INFINITY;
             nl = fminf(fmaxf(nl, lo), hi);
             L[r] = nl;
             dl = nl - old;
         }
         vA = madd(vA, lin, imA * dl);
-        wA = madd(wA, smv(IA, angA), dl);
+        wA = madd(wA, sa, dynA ? dl : 0.f);
         vB = madd(vB, lin, -(imB * dl));
-        wB = madd(wB, smv(IB, angB), dl);
+        wB = madd(wB, sb, dynB ? dl : 0.f);
     }
-    if (imA > 0.f) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
-    if (imB > 0.f) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
+    if (dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
+    if (dynB) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
 }
 
 template <int MODE>
@@ -610,27 +673,29 @@ MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
 
 // -------------------------------------------------------------- integrate
 MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
-    int kind = (c.w >> 8) & 1, idx = c.w >> 9;
-    Row* R = e.rows + c.z;
+    bool joint = (c.w & 3) == CP_JOINT;
+    int idx = c.w >> 8;
+    Row* R = cons_rows(e, c);
     float h = P.h;
     BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
-    if (kind == 1) {
+    if (!joint) {
         int4 M = e.man[idx];
         for (int k = 0; k < M.z; k++) {
             const float4* pt = e.pts + 3 * (M.w + k);
             float3 rA = mv(A.R, xyz(pt[0])), rB = mv(B.R, xyz(pt[1]));
             float d = dot(xyz(pt[2]), (A.x + rA) - (B.x + rB));
-            R[k].r2.w = fmaxf(d, 0.f) / h;
+            R[k].c.w = fmaxf(d, 0.f) / h;
         }
     } else {
         int4 jm = e.jm[idx];
         float4 jp = e.jp[idx];
         JointGeo gj = joint_geo(e, idx, jm.x, A, B);
-        R[5].r2.w = fmaxf(gj.phi - jp.x, 0.f) / h;
-        R[6].r2.w = fmaxf(jp.y - gj.phi, 0.f) / h;
+        R[5].c.w = fmaxf(gj.phi - jp.x, 0.f) / h;
+        R[6].c.w = fmaxf(jp.y - gj.phi, 0.f) / h;
     }
 }
 
+// symplectic Euler with w = S w^; e.w keeps w^ for the relax sweeps
 MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
     float h = P.h;
     int nb = e.nb;
@@ -639,7 +704,8 @@ MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
         int i = i0 + g.lane;
         if (i >= nb || !is_dyn(e, i)) continue;
         float4 x = e.x[i], q = e.q[i];
-        float3 v = xyz(e.v[i]), w = xyz(e.w[i]);
+        float3 v = xyz(e.v[i]);
+        float3 w = smv(load_sq(e, i), xyz(e.w[i]));
         x.x = fmaf(h, v.x, x.x); x.y = fmaf(h, v.y, x.y); x.z = fmaf(h, v.z, x.z);
         float4 wq = qmul(make_float4(w.x, w.y, w.z, 0.f), q);
         float hh = 0.5f * h;
@@ -658,6 +724,17 @@ MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
     g.sync();
 }
 
+// end of a substep: angular velocities back to world space, w = S w^
+MSD void stage_unscale(EnvView& e, const Grp& g) {
+    int nb = e.nb;
+    int nbmax = g.wmax(nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i < nb && is_dyn(e, i)) e.w[i] = f4(smv(load_sq(e, i), xyz(e.w[i])), 0.f);
+    }
+    g.sync();
+}
+
 // end-of-step check: a non-finite state freezes the env
 MSD void stage_check(EnvView& e, const Grp& g) {
     bool bad = false;
@@ -672,6 +749,17 @@ MSD void stage_check(EnvView& e, const Grp& g) {
     bool any = g.any(bad);
     if (g.lane == 0 && any) *e.status |= ST_NAN;
     g.sync();
+}
+
+// One substep: prep, warm start, position sweeps, integration, relax
+// sweeps, unscale.
+MSD void run_substep(EnvView& e, const Grp& g, const Params& P) {
+    stage_prep(e, g, P);
+    stage_sweep(e, g, 0);
+    for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1);
+    stage_integrate(e, g, P);
+    for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2);
+    stage_unscale(e, g);
 }
 
 }  // namespace ms
