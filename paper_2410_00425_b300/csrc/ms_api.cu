@@ -804,13 +804,28 @@ extern "C" ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_pat
                 ms_tuning c = {G, W, R, 0};
                 if (ms_set_tuning(b, &c) != MS_OK) continue;
                 if (R == 1 && b->tune.rows_smem == 0) continue;   // rows did not fit: same as R = 0
+                // two calls to warm up (the first captures the graph), then
+                // the best of three timings of enough calls for ~5 ms
                 ms_step(b, nullptr, n_steps, st);
                 cudaEventRecord(e0, st);
-                for (int r = 0; r < 3; r++) ms_step(b, nullptr, n_steps, st);
+                ms_step(b, nullptr, n_steps, st);
                 cudaEventRecord(e1, st);
                 if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-                float ms_ = 0.f;
-                cudaEventElapsedTime(&ms_, e0, e1);
+                float one = 0.f;
+                cudaEventElapsedTime(&one, e0, e1);
+                int reps = std::max(2, std::min(50, (int)(5.f / std::max(one, 1e-3f))));
+                float ms_ = 1e30f;
+                bool ok = true;
+                for (int trial = 0; trial < 3 && ok; trial++) {
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < reps; r++) ms_step(b, nullptr, n_steps, st);
+                    cudaEventRecord(e1, st);
+                    ok = cudaEventSynchronize(e1) == cudaSuccess;
+                    float t_ = 0.f;
+                    cudaEventElapsedTime(&t_, e0, e1);
+                    ms_ = std::min(ms_, t_ / reps);
+                }
+                if (!ok) continue;
                 if (ms_ < best_ms) { best_ms = ms_; bt = c; }
                 // restore before the next candidate
                 launch_unpack_state(b->D, save, nullptr, b->d_body_env, st);

@@ -26,11 +26,17 @@ struct Layout {
     int scons, color_off, lam, cnt, status;  // shared part unless lists_shared is false
     bool lists_shared;                       // scons and lam in the shared part
     bool rows_j_shared;                      // joint rows in the shared part
-    int rows_j;                              // 8 rows per joint
+    int rows_j;                              // 8 rows per joint, interleaved: row r of joint j at r * njs + j
+    int njs;                                 // joint row stride (max joints per env, >= 1)
     int pts_s;                               // contact points whose rows are in the shared part
     int rows_cs;                             // their rows (3 per point), or -1
+    // colouring scratch (records, colours, colour masks per body): laid over
+    // the joint and contact rows of the shared part when they are there and
+    // large enough (the rows are written after colouring), else global
+    bool color_shared;
+    int cons, colr, used;
     int g_bytes;
-    int aabb, pairs, man, pts, cons, colr, used;
+    int aabb, pairs, man, pts;
     int rows_cg;                             // rows of every contact point (those >= pts_s are used), or -1
     int shape, inv, meta, adj, jf, jp, jm, jt;   // parameter copies (no-allocation path only), or -1
 };

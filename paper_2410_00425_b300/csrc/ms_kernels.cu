@@ -25,7 +25,8 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     if (pts_s < 0) pts_s = 0;
     if (pts_s > cc) pts_s = cc;
     int ncons = max_nj + (pc < cc ? pc : cc);      // every manifold has at least one point
-    int nrows = 8 * max_nj + 3 * cc;
+    int nrows = 8 * nj + 3 * cc;
+    L.njs = nj;
     const int RB = (int)sizeof(Row);
     int o = 0;
     auto take = [&](int bytes, int al) { o = align_up(o, al); int r = o; o += bytes; return r; };
@@ -48,7 +49,9 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     if (rows_j_shared) L.rows_j = take(RB * 8 * nj, 16);
     L.pts_s = pts_s;
     L.rows_cs = pts_s > 0 ? take(RB * 3 * pts_s, 16) : -1;
-    L.s_bytes = align_up(o, 16);
+    // slots of the envs of a warp start 16 B apart modulo 128 B, so equal
+    // offsets in different slots fall in different shared-memory banks
+    L.s_bytes = align_up(o, 128) + 16;
     // global part
     o = 0;
     if (!lists_shared) {
@@ -61,9 +64,18 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     L.pairs = take(4 * pc, 4);
     L.man = take(16 * pc, 16);
     L.pts = take(48 * cc, 16);
-    L.cons = take(16 * ncons, 16);
-    L.colr = take(4 * ncons, 4);
-    L.used = take(8 * nb, 8);
+    int scratch = 16 * ncons + 4 * ncons + 8 * nb;
+    int rows_s_bytes = rows_j_shared ? RB * 8 * nj + (pts_s > 0 ? RB * 3 * pts_s : 0) : 0;
+    L.color_shared = rows_j_shared && scratch <= rows_s_bytes;
+    if (L.color_shared) {
+        L.cons = L.rows_j;
+        L.colr = L.cons + 16 * ncons;
+        L.used = align_up(L.colr + 4 * ncons, 8);
+    } else {
+        L.cons = take(16 * ncons, 16);
+        L.colr = take(4 * ncons, 4);
+        L.used = take(8 * nb, 8);
+    }
     if (with_params) {
         L.shape = take(16 * nb, 16); L.inv = take(16 * nb, 16); L.meta = take(8 * nb, 8);
         L.adj = take(8 * nb, 8);
@@ -177,7 +189,7 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
 
 // ----------------------------------------------------------- batched path
 template <int G>
-__global__ void __launch_bounds__(256, 2) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
+__global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
     constexpr int K = 32 / G;                  // envs per warp

@@ -38,7 +38,7 @@ namespace ms {
 
 // One env per warp (G = 32): envs of different sessions in a launch may
 // have different substep and iteration counts, so no two share a warp.
-__global__ void __launch_bounds__(256, 2) k_multi(const DevBatch* __restrict__ batches, const float* const* actions,
+__global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ batches, const float* const* actions,
                                                   const int2* work, int n_work, Layout L, int* queue,
                                                   char* gscratch) {
     extern __shared__ __align__(16) char smem[];

@@ -55,6 +55,9 @@ struct Row {
 
 // Constraint record (cons, scons): a, b, first row, place | np << 2 | idx << 8
 // with place: joint rows, or a manifold's rows in the shared or global part.
+// A joint's rows are interleaved with the other joints' (stride njs: the
+// lanes solving different joints of a colour read different banks); its
+// "first row" is the joint index.  A manifold's rows are contiguous.
 enum { CP_JOINT = 0, CP_MAN_S = 1, CP_MAN_G = 2 };
 
 struct EnvView {
@@ -78,7 +81,8 @@ struct EnvView {
     int4* scons;                      // the same records sorted by colour (solve order)
     int* color_off;                   // MAX_COLORS + 1
     unsigned long long* used;         // colour masks per body
-    Row* rows_j;                      // 8 per joint
+    Row* rows_j;                      // 8 per joint, row r of joint j at r * njs + j
+    int njs;                          // joint row stride; joint impulses are laid out the same way
     Row* rows_cs;                     // 3 per contact point < pts_s
     Row* rows_cg;                     // 3 per contact point (points >= pts_s)
     int pts_s;
@@ -102,6 +106,7 @@ MSD void view_workspace(EnvView& e, char* s, char* gl, const Layout& L) {
     e.color_off = at<int>(s, L.color_off);
     e.cnt = at<int>(s, L.cnt);
     e.rows_j = at<Row>(L.rows_j_shared ? s : gl, L.rows_j);
+    e.njs = L.njs;
     e.pts_s = L.pts_s;
     e.rows_cs = L.rows_cs >= 0 ? at<Row>(s, L.rows_cs) : nullptr;
     e.rows_cg = L.rows_cg >= 0 ? at<Row>(gl, L.rows_cg) : nullptr;
@@ -109,9 +114,10 @@ MSD void view_workspace(EnvView& e, char* s, char* gl, const Layout& L) {
     e.pairs = at<int>(gl, L.pairs);
     e.man = at<int4>(gl, L.man);
     e.pts = at<float4>(gl, L.pts);
-    e.cons = at<int4>(gl, L.cons);
-    e.colr = at<int>(gl, L.colr);
-    e.used = at<unsigned long long>(gl, L.used);
+    char* cb = L.color_shared ? s : gl;
+    e.cons = at<int4>(cb, L.cons);
+    e.colr = at<int>(cb, L.colr);
+    e.used = at<unsigned long long>(cb, L.used);
 }
 
 // G lanes of a warp owning one env; all intrinsics use the full warp.
@@ -312,7 +318,10 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
 // -------------------------------------------------------------- colouring
 // Constraint list = joints (index order) then manifolds (pair order).  Each
 // takes the lowest colour free on both of its dynamic bodies (static bodies
-// impose nothing); the solve order lists constraints colour by colour.
+// impose nothing); the solve order lists constraints colour by colour, in
+// list order within a colour.  The greedy pass is sequential (one lane per
+// env, shared-memory scratch); the colour-ordered copy is a parallel stable
+// scatter.
 MSD void stage_color(EnvView& e, const Grp& g) {
     bool live = e.nb > 0;
     int nj = e.nj, nman = live ? e.cnt[C_NMAN] : 0;
@@ -322,7 +331,7 @@ MSD void stage_color(EnvView& e, const Grp& g) {
         int i = i0 + g.lane;
         if (i < nj) {
             int4 jm = e.jm[i];
-            e.cons[i] = make_int4(jm.y, jm.z, 8 * i, CP_JOINT | (i << 8));
+            e.cons[i] = make_int4(jm.y, jm.z, i, CP_JOINT | (i << 8));
         } else if (i < ncons) {
             int m = i - nj;
             int4 M = e.man[m];
@@ -335,34 +344,53 @@ MSD void stage_color(EnvView& e, const Grp& g) {
         if (b0 + g.lane < e.nb) e.used[b0 + g.lane] = 0ull;
     g.sync();
     if (g.lane == 0 && live) {
+        // greedy colours; color_off counts the members of each colour
         int ncol = 0;
         bool overflow = false;
         for (int i = 0; i < ncons; i++) {
             int4 c = e.cons[i];
-            bool da = is_dyn(e, c.x), db = is_dyn(e, c.y);
+            bool da = c.x >= 0 && e.v[c.x].w > 0.f, db = c.y >= 0 && e.v[c.y].w > 0.f;
             unsigned long long m = (da ? e.used[c.x] : 0ull) | (db ? e.used[c.y] : 0ull);
             if (m == ~0ull) { e.colr[i] = -1; overflow = true; continue; }
-            int col = __ffsll((long long)~m) - 1;
+            int col = __ffsll((long long)~m) - 1;        // at most ncol: a new colour is the next one
             e.colr[i] = col;
             if (da) e.used[c.x] |= 1ull << col;
             if (db) e.used[c.y] |= 1ull << col;
-            if (col + 1 > ncol) ncol = col + 1;
+            if (col == ncol) { e.color_off[col] = 0; ncol++; }
+            e.color_off[col]++;
         }
-        for (int c = 0; c <= ncol; c++) e.color_off[c] = 0;
-        for (int i = 0; i < ncons; i++)
-            if (e.colr[i] >= 0) e.color_off[e.colr[i] + 1]++;
-        for (int c = 0; c < ncol; c++) e.color_off[c + 1] += e.color_off[c];
-        for (int c = 0; c < ncol; c++) {
-            int k = e.color_off[c];
-            for (int i = 0; i < ncons; i++)
-                if (e.colr[i] == c) e.scons[k++] = e.cons[i];
-        }
-        e.cnt[C_NCONS] = ncol > 0 ? e.color_off[ncol] : 0;   // constraints with a colour
+        int acc = 0;
+        for (int c = 0; c < ncol; c++) { int n = e.color_off[c]; e.color_off[c] = acc; acc += n; }
+        e.color_off[ncol] = acc;
+        e.cnt[C_NCONS] = acc;                          // constraints with a colour
         e.cnt[C_NCOLORS] = ncol;
         if (overflow) *e.status |= ST_COLOR;
     }
     g.sync();
-    int nrows = live ? 8 * nj + 3 * e.cnt[C_NPTS] : 0;
+    // stable scatter into colour order: color_off[c] runs from the start to
+    // the end of colour c, then is shifted back into start offsets
+    int wl = g.base + g.lane;                              // lane in the warp
+    for (int i0 = 0; i0 < cmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        int col = i < ncons ? e.colr[i] : -1;
+        unsigned key = col >= 0 ? (unsigned)col | ((unsigned)g.base << 8) : 0x80000000u | (unsigned)wl;
+        unsigned peers = __match_any_sync(FULL_MASK, key);
+        int pos = 0;
+        if (col >= 0) {
+            pos = e.color_off[col] + __popc(peers & ((1u << wl) - 1u));
+            e.scons[pos] = e.cons[i];
+        }
+        g.sync();
+        if (col >= 0 && (peers >> wl) == 1u) e.color_off[col] = pos + 1;   // the highest peer
+        g.sync();
+    }
+    if (g.lane == 0 && live) {
+        int ncol = e.cnt[C_NCOLORS];
+        for (int c = ncol; c > 0; c--) e.color_off[c] = e.color_off[c - 1];
+        e.color_off[0] = 0;
+    }
+    g.sync();
+    int nrows = live ? 8 * e.njs + 3 * e.cnt[C_NPTS] : 0;
     int rmax = g.wmax(nrows);
     for (int r0 = 0; r0 < rmax; r0 += g.size)
         if (r0 + g.lane < nrows) e.lam[r0 + g.lane] = 0.f;
@@ -483,6 +511,7 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
         }
         return;
     }
+    const int J = e.njs;                        // joint row stride
     int4 jm = e.jm[idx];
     float4 jp = e.jp[idx];
     JointGeo gj = joint_geo(e, idx, jm.x, A, B);
@@ -490,42 +519,42 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     if (jm.x == 0) {
         for (int t = 0; t < 3; t++) {
             float3 ee = axis3(t);
-            point_row(R[t], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, 0.f);
+            point_row(R[t * J], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, 0.f);
         }
         int k = basis_axis(gj.a);
         float3 b1 = cross(gj.a, axis3(k));
         b1 = b1 * (1.f / len(b1));
         float3 b2 = cross(gj.a, b1);
         float3 axc = cross(gj.a, gj.c);
-        ang_row(R[3], -b1, b1, A, B, dot(b1, axc) / h, 0.f);
-        ang_row(R[4], -b2, b2, A, B, dot(b2, axc) / h, 0.f);
-        ang_row(R[5], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
-        ang_row(R[6], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
-        kd7 = ang_row(R[7], -gj.a, gj.a, A, B, 0.f, 0.f);
+        ang_row(R[3 * J], -b1, b1, A, B, dot(b1, axc) / h, 0.f);
+        ang_row(R[4 * J], -b2, b2, A, B, dot(b2, axc) / h, 0.f);
+        ang_row(R[5 * J], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
+        ang_row(R[6 * J], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
+        kd7 = ang_row(R[7 * J], -gj.a, gj.a, A, B, 0.f, 0.f);
     } else {
         int k = basis_axis(gj.a);
         float3 b1 = cross(gj.a, axis3(k));
         b1 = b1 * (1.f / len(b1));
         float3 b2 = cross(gj.a, b1);
-        point_row(R[0], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, 0.f);
-        point_row(R[1], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, 0.f);
+        point_row(R[0 * J], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, 0.f);
+        point_row(R[1 * J], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, 0.f);
         float4 qe = qmul(gj.qPw, qconj(gj.qCw));
         float sg = qe.w >= 0.f ? 1.f : -1.f;
         float3 th = f3(2.f * sg * qe.x, 2.f * sg * qe.y, 2.f * sg * qe.z);
         for (int t = 0; t < 3; t++) {
             float3 ee = axis3(t);
-            ang_row(R[2 + t], ee, -ee, A, B, comp(th, t) / h, 0.f);
+            ang_row(R[(2 + t) * J], ee, -ee, A, B, comp(th, t) / h, 0.f);
         }
-        point_row(R[5], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
-        point_row(R[6], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
-        kd7 = point_row(R[7], -gj.a, gj.rP, gj.rC, A, B, 0.f, 0.f);
+        point_row(R[5 * J], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
+        point_row(R[6 * J], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
+        kd7 = point_row(R[7 * J], -gj.a, gj.rP, gj.rC, A, B, 0.f, 0.f);
     }
     // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
     // b = kp C / (h kp + kd), C = phi - target; the row keeps
     // 1/(k + gamma) so that each iteration is one multiply
     float kp = jp.z, kd = jp.w;
     float den = fmaf(h, kp, kd);
-    Row& dr = R[7];
+    Row& dr = R[7 * J];
     if (den > 0.f && kd7 > 0.f) {
         float gam = 1.f / (h * den);
         dr.c.w = gam;
@@ -580,7 +609,9 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
 // with gamma = 0 except for drives and (lo, hi) = (0, inf) for normals and
 // limits, +-mu lambda_n for friction, unbounded otherwise; an inert row has
 // 1/k = 0 and leaves lambda unchanged.  The next row is loaded while the
-// current one is solved.
+// current one is solved, and every term that does not depend on Jv is
+// formed before it, so the chain from one row's impulse to the next row's
+// is short.
 // The pointers the sweeps touch, small enough to live in registers.
 struct SolveCtx {
     float4* v;
@@ -589,18 +620,25 @@ struct SolveCtx {
     const Row* rcs;
     const Row* rcg;
     float* lam;
-    int nj;
+    int njs;
 };
 
-MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.rows_j, e.rows_cs, e.rows_cg, e.lam, e.nj}; }
+MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.rows_j, e.rows_cs, e.rows_cg, e.lam, e.njs}; }
 
+// Every lane of the warp runs the same number of row iterations (nrmax, the
+// warp's largest row count) through straight-line code: rows past a lane's
+// own count, and lanes without a constraint (has = false), change nothing.
+// Lanes that diverged on a trip count or a row kind would run their paths
+// one after the other.
 template <int MODE>
-MSD void solve_constraint(const SolveCtx& x, int4 c) {
+MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
     int place = c.w & 3, np = (c.w >> 2) & 7;
     bool joint = place == CP_JOINT;
-    int nrows = joint ? 8 : 3 * np;
+    int nrows = has ? (joint ? 8 : 3 * np) : 0;
     const Row* R = (joint ? x.rj : (place == CP_MAN_S ? x.rcs : x.rcg)) + c.z;
-    float* L = x.lam + (joint ? c.z : 8 * x.nj + c.z);
+    float* L = x.lam + (joint ? c.z : 8 * x.njs + c.z);
+    int st = joint ? x.njs : 1;                         // row stride
+    int last = max(nrows - 1, 0);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 va = c.x >= 0 ? x.v[c.x] : z4, wa4 = c.x >= 0 ? x.w[c.x] : z4;
     float4 vb = c.y >= 0 ? x.v[c.y] : z4, wb4 = c.y >= 0 ? x.w[c.y] : z4;
@@ -609,15 +647,20 @@ MSD void solve_constraint(const SolveCtx& x, int4 c) {
     bool dynA = imA > 0.f, dynB = imB > 0.f;
     float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
     float4 n0 = R[0].a, n1 = R[0].b, n2 = R[0].c;
-    for (int r = 0; r < nrows; r++) {
+    for (int r = 0; r < nrmax; r++) {
         float4 ra = n0, rb = n1, rc = n2;
-        int rn = min(r + 1, nrows - 1);                  // prefetch the next row (clamped, always valid)
+        int rn = min(r + 1, last) * st;                  // prefetch the next row (clamped, always valid)
         n0 = R[rn].a; n1 = R[rn].b; n2 = R[rn].c;
+        bool live = r < nrows;
+        int ri = min(r, last) * st;
         float3 lin = xyz(ra), sa = xyz(rb), sb = xyz(rc);
-        float old = L[r];
+        // off the dependency chain: the body-scaled directions and, below,
+        // everything in lambda' except Jv
+        float3 linA = lin * imA, linB = lin * (-imB);
+        float old = L[ri];
         float dl;
         if (MODE == 0) {
-            dl = ra.w > 0.f ? old : 0.f;
+            dl = (live && ra.w > 0.f) ? old : 0.f;
         } else {
             bool fric = !joint && r >= np;
             bool drive = joint && r == 7;
@@ -625,24 +668,26 @@ MSD void solve_constraint(const SolveCtx& x, int4 c) {
             float ik = (MODE == 2 && drive) ? 0.f : ra.w;
             float bias = fric ? 0.f : (MODE == 2 ? (drive ? 0.f : rc.w) : rb.w);
             float gam = drive ? rc.w : 0.f;
-            float3 dv = vA - vB;
-            float j1 = dot(lin, dv), j2 = dot(sa, wA), j3 = dot(sb, wB);
-            float jv = (j1 + j2) + j3;
-            float nl = fmaf(-((jv + bias) + gam * old), ik, old);
-            float lim = fric ? rb.w * L[(r - np) >> 1] : 0.f;   // friction bound from the point's normal impulse
+            float c1 = fmaf(-fmaf(gam, old, bias), ik, old);   // old - (bias + gamma old) / (k + gamma)
+            // friction bound from the point's normal impulse (a valid index for every row)
+            float ln = L[(fric && live) ? (r - np) >> 1 : ri];
+            float lim = rb.w * ln;
             float lo = fric ? -lim : ((eq || drive) ? -INFINITY : 0.f);
             float hi = fric ? lim : INFINITY;
+            // Jv as four independent products
+            float jv = (dot(lin, vA) + dot(sa, wA)) - (dot(lin, vB) - dot(sb, wB));
+            float nl = fmaf(-jv, ik, c1);
             nl = fminf(fmaxf(nl, lo), hi);
-            L[r] = nl;
-            dl = nl - old;
+            if (live) L[ri] = nl;
+            dl = live ? nl - old : 0.f;
         }
-        vA = madd(vA, lin, imA * dl);
+        vA = madd(vA, linA, dl);
         wA = madd(wA, sa, dynA ? dl : 0.f);
-        vB = madd(vB, lin, -(imB * dl));
+        vB = madd(vB, linB, dl);
         wB = madd(wB, sb, dynB ? dl : 0.f);
     }
-    if (dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
-    if (dynB) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
+    if (has && dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
+    if (has && dynB) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
 }
 
 template <int MODE>
@@ -653,12 +698,16 @@ MSD void sweep_mode(EnvView& e, const Grp& g) {
     int ncol = e.nb > 0 ? e.cnt[C_NCOLORS] : 0;
     int colmax = g.wmax(ncol);
     int k0 = 0;
+    const int4 none = make_int4(-1, -1, 0, CP_JOINT);    // the null constraint of an idle lane
     for (int col = 0; col < colmax; col++) {
         int k1 = col < ncol ? off[col + 1] : k0;
         int wmaxn = g.wmax(k1 - k0);
         for (int m = 0; m < wmaxn; m += g.size) {
             int k = k0 + m + g.lane;
-            if (k < k1) solve_constraint<MODE>(x, sc[k]);
+            bool has = k < k1;
+            int4 c = has ? sc[k] : none;
+            int nr = has ? ((c.w & 3) == CP_JOINT ? 8 : 3 * ((c.w >> 2) & 7)) : 0;
+            solve_constraint<MODE>(x, c, has, g.wmax(nr));
         }
         g.sync();
         k0 = k1;
@@ -690,8 +739,8 @@ MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
         int4 jm = e.jm[idx];
         float4 jp = e.jp[idx];
         JointGeo gj = joint_geo(e, idx, jm.x, A, B);
-        R[5].c.w = fmaxf(gj.phi - jp.x, 0.f) / h;
-        R[6].c.w = fmaxf(jp.y - gj.phi, 0.f) / h;
+        R[5 * e.njs].c.w = fmaxf(gj.phi - jp.x, 0.f) / h;
+        R[6 * e.njs].c.w = fmaxf(jp.y - gj.phi, 0.f) / h;
     }
 }
 

@@ -13,6 +13,10 @@ import scenegen
 # |dw| * r_bound <= TOL_V, r_bound the body's bounding radius.
 TOL_X, TOL_V, TOL_Q = 1e-5, 1e-4, 1e-5
 TIE_EPS = 1e-5
+# relative velocity noise per step of the non-chaotic probe: four float32
+# ulps.  A velocity component takes ~40 row impulses per step (4 substeps x
+# 10 sweeps), each rounded once in float32; as a random walk that is ~6 ulps.
+VEL_NOISE = 4 * 2.0**-24
 
 
 def bound_radius(bodies):
@@ -105,12 +109,11 @@ def non_chaotic(scene, n_steps, threads=8, seed=11):
     float32 path introduces.  Both must hold after n_steps:
       * two FP64 runs from positions 1e-9 m apart stay within 1e-6 m;
       * an FP64 run whose state is rounded to float32 after every step, and
-        whose velocities then take one float32 ulp of relative noise (random
-        sign, seeded), stays within the one-step bars (1e-5 m, 1e-4 m/s,
-        1e-4 m/s, 1e-5) of the plain FP64 run.  Float32 state storage,
-        amplified through the d/h and C/h position-correction biases, and
-        the float32 solve arithmetic -- at least an ulp per velocity
-        component per step -- are the perturbations actually present in the
+        whose velocities then take VEL_NOISE of relative noise (random sign,
+        seeded), stays within the one-step bars (1e-5 m, 1e-4 m/s, 1e-4 m/s,
+        1e-5) of the plain FP64 run.  Float32 state storage, amplified
+        through the d/h and C/h position-correction biases, and the float32
+        solve arithmetic are the perturbations actually present in the
         comparison; a body spinning for many radians accumulates the latter
         as orientation phase.
     Returns (mask, state of the plain FP64 run)."""
@@ -122,7 +125,7 @@ def non_chaotic(scene, n_steps, threads=8, seed=11):
     for k in range(n_steps):
         o.step(1, threads=threads)
         st = o.state().astype(np.float32).astype(np.float64)
-        st[:, 7:13] *= 1.0 + rng.choice([-1.0, 1.0], size=st[:, 7:13].shape) * 2.0**-24
+        st[:, 7:13] *= 1.0 + rng.choice([-1.0, 1.0], size=st[:, 7:13].shape) * VEL_NOISE
         o.set_state(st)
     err = env_errors(scene, base, o.state())
     calm &= within(err)
