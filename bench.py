@@ -55,7 +55,7 @@ FP32_LANES_PER_SM = 128
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 40.16e6, "kernel_sha": "c1998dd4cb8728b5", "kernel": "k_fused<8>"},
+    ("arm", "8,1,0"): {"bytes": 29.83e6, "kernel_sha": "463db8ff8e1ee8cd", "kernel": "k_fused<8>"},
 }
 KERNEL_SOURCES = ("ms_kernels.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
@@ -435,6 +435,12 @@ def main():
         b.set_tuning(G, W, R)
         tuning = b.tuning()
     elif not args.no_autotune:
+        # tune on a state of the workload (arm moving, contacts made), not on
+        # the initial poses: the trials restore this state after each candidate
+        with torch.cuda.stream(stream):
+            for i in range(min(args.warmup + 15, total_calls)):
+                b.step(act(i), n, stream=stream)
+        stream.synchronize()
         tuning = b.autotune(n, cache_path=os.path.join(ROOT, "paper_2410_00425_b300", "tuning_cache.json"),
                             stream=stream)
     else:
