@@ -88,15 +88,23 @@ def load_peaks():
         return {}
 
 
-def algorithmic_flops_per_env_step(name, sample_envs=128, steps=5):
-    """Oracle op counters on a sample of the workload x fixed FLOP weights."""
+def algorithmic_flops_per_env_step(name, warmup, steps, sample_envs=32):
+    """Oracle op counters x fixed FLOP weights, counted over the same window
+    of steps the timed region covers (after `warmup` steps) on the first
+    `sample_envs` envs of the workload (per-env seeding: the same envs)."""
     import oracle
     sc = scenegen.make_scene(name, n_envs=min(sample_envs, scenegen.CONFIG_SIZES[name]))
     o = oracle.Oracle(sc)
-    o.step(steps, threads=os.cpu_count() or 1)
-    c = o.counters()
+    th = os.cpu_count() or 1
+    if warmup:
+        o.step(warmup, threads=th)
+    c0 = o.counters()
+    n = max(1, min(steps, 200))
+    o.step(n, threads=th)
+    c1 = o.counters()
+    c = {k: c1[k] - c0[k] for k in c1}
     flops = sum(FLOP_WEIGHTS[k] * c[k] for k in FLOP_WEIGHTS)
-    return flops / (sc.n_envs * steps), c
+    return flops / (sc.n_envs * n), c
 
 
 class ClockSampler:
@@ -522,7 +530,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    fl, _ = algorithmic_flops_per_env_step(name)
+    fl, _ = algorithmic_flops_per_env_step(name, args.warmup, args.steps)
     kernel_s = statistics.mean(times_b) / 1e3
     achieved = fl * E * n / kernel_s / 1e12
     line = {
