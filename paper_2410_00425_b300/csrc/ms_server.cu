@@ -6,7 +6,8 @@
 // stages their drive targets, and runs one launch of k_multi over the union
 // of their envs: a persistent kernel whose work list names (session, env)
 // pairs and which reads each env's batch view from a device table, so
-// sessions of different scene types and solver parameters share a launch.
+// sessions of different scene types and solver parameters share a launch
+// (a warp's envs always come from one session).
 // The launch (queue reset + kernel) is captured once per workspace layout
 // (bucketed sizes) in a CUDA graph whose kernel parameters are updated per
 // launch.  Up to max_inflight launches run at once, each on its own stream
@@ -36,17 +37,23 @@
 
 namespace ms {
 
-// One env per warp (G = 32): envs of different sessions in a launch may
-// have different substep and iteration counts, so no two share a warp.
+// G lanes per env, K = 32 / G envs per warp, all of one session: the work
+// list is grouped by session and each session's envs are padded to a
+// multiple of K with inactive items (env = -1), so the envs of a warp share
+// their parameters (substeps, iterations) and the lockstep loops stay
+// warp-uniform, as in the batched kernel.
+template <int G>
 __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ batches, const float* const* actions,
                                                   const int2* work, int n_work, Layout L, int* queue,
                                                   char* gscratch) {
     extern __shared__ __align__(16) char smem[];
+    constexpr int K = 32 / G;
     int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+    int gi = wl / G;
     Grp g;
-    g.lane = wl; g.size = 32; g.base = 0;
-    char* s = smem + (size_t)warp * L.s_bytes;
-    size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    g.lane = wl % G; g.size = G; g.base = gi * G;
+    char* s = smem + (size_t)(warp * K + gi) * L.s_bytes;
+    size_t gslot = ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * K + gi;
     char* gl = gscratch + gslot * (size_t)L.g_bytes;
     EnvView e;
     e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
@@ -55,40 +62,50 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
     e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
 
     for (;;) {
-        int t = 0;
-        if (wl == 0) t = atomicAdd(queue, 1);
-        t = __shfl_sync(FULL_MASK, t, 0);
-        if (t >= n_work) break;
-        int2 it = work[t];
-        const DevBatch& D = batches[it.x];
+        int t0 = 0;
+        if (wl == 0) t0 = atomicAdd(queue, K);
+        t0 = __shfl_sync(FULL_MASK, t0, 0);
+        if (t0 >= n_work) break;                              // warp-uniform; n_work is a multiple of K
+        int2 it = work[t0 + gi];
+        const DevBatch& D = batches[it.x];                    // one session per warp
         int env = it.y;
-        int b0 = D.body_off[env], j0 = D.joint_off[env];
-        int nb = D.body_off[env + 1] - b0, nj = D.joint_off[env + 1] - j0;
+        bool active = env >= 0;
+        int b0 = 0, j0 = 0, nb = 0, nj = 0;
+        if (active) {
+            b0 = D.body_off[env]; j0 = D.joint_off[env];
+            nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
+        }
         e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
         e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
-        for (int i = wl; i < nb; i += 32) {
-            e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i];
+        int nbmax = g.wmax(nb);
+        for (int i0 = 0; i0 < nbmax; i0 += G) {
+            int i = i0 + g.lane;
+            if (i < nb) { e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i]; }
         }
-        if (wl == 0) *e.status = D.status[env];
+        if (g.lane == 0) *e.status = active ? D.status[env] : 0u;
         g.sync();
         bool frozen = (*e.status & ST_NAN) != 0;
         e.nb = frozen ? 0 : nb;
         e.nj = frozen ? 0 : nj;
         DevParams P = D.P;
-        const float* act = actions[it.x] ? actions[it.x] + (size_t)env * D.A : nullptr;
+        const float* act = (active && actions[it.x]) ? actions[it.x] + (size_t)env * D.A : nullptr;
         stage_actions(e, g, act, D.A);
         stage_broadphase(e, g, P);
         stage_narrowphase(e, g, P);
         stage_color(e, g);
         for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P);
         stage_check(e, g);
-        for (int i = wl; i < nb; i += 32) {
-            D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i];
+        for (int i0 = 0; i0 < nbmax; i0 += G) {
+            int i = i0 + g.lane;
+            if (i < nb) { D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i]; }
         }
-        if (wl == 0) D.status[env] = *e.status;
+        if (g.lane == 0 && active) D.status[env] = *e.status;
         g.sync();
     }
 }
+
+constexpr int MULTI_G = 8;                      // lanes per env of merged launches
+constexpr int MULTI_K = 32 / MULTI_G;           // envs per warp
 
 }  // namespace ms
 
@@ -275,33 +292,60 @@ static void free_slot(ms_server* s, Slot& sl) {
 static int launch_merged(ms_server* s, Slot& sl) {
     auto& batch = sl.batch;
     int mb = 1, mj = 0, pc = 1, cc = 1;
-    size_t nwork = 0, nact = 0;
+    size_t nact = 0, nenv = 0;
     for (auto& rs : batch) {
         Session* se = rs.second;
         mb = std::max(mb, se->max_nb); mj = std::max(mj, se->max_nj);
         pc = std::max(pc, se->p.pair_capacity); cc = std::max(cc, se->p.contact_capacity);
-        nwork += (size_t)se->E;
         nact += rs.first->act.size();
+        nenv += (size_t)se->E;
     }
     mb = bucket(mb, {4, 8, 12, 16, 24, 32, 48, 64});
     mj = bucket(mj, {0, 4, 8, 12, 16, 24, 32, 48, 64});
     pc = bucket(pc, {8, 16, 32, 64, 128, 256, 512, 1024});
     cc = bucket(cc, {8, 16, 32, 64, 128, 256, 512, 1024});
-    const int warps = 2;
-    // every row on chip if it fits; else the contact rows, then the joint
-    // rows, then the lists and impulses move to the global part
-    Layout L = make_layout(mb, mj, pc, cc, true, true, cc, true, false);
-    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, true, 0, true, false);
-    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, 0, true, false);
-    if ((size_t)L.s_bytes * warps > (size_t)s->smem_optin) L = make_layout(mb, mj, pc, cc, true, false, 0, false, false);
-    size_t smem = (size_t)L.s_bytes * warps;
+    const int warps = 1;
+    const int envs_per_cta = warps * MULTI_K;
+    // contact rows on chip for as many points as leave 4 CTAs per SM (16
+    // envs); every row on chip if that fits, else the joint rows, then the
+    // lists and impulses move to the global part
+    auto occ = [&](const Layout& Lc) {
+        size_t sm = (size_t)Lc.s_bytes * envs_per_cta;
+        if (sm > (size_t)s->smem_optin) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k_multi<MULTI_G>, 32 * warps, sm) != cudaSuccess)
+            return 0;
+        return n;
+    };
+    Layout L{};
+    bool found = false;
+    for (int ps : {cc, 32, 16, 8, 0}) {
+        if (ps > cc) continue;
+        Layout c = make_layout(mb, mj, pc, cc, true, true, ps, true, false);
+        if (occ(c) >= 4 || (ps == 0 && occ(c) >= 1)) { L = c; found = true; break; }
+    }
+    if (!found) {
+        L = make_layout(mb, mj, pc, cc, true, false, 0, true, false);
+        if (occ(L) < 1) L = make_layout(mb, mj, pc, cc, true, false, 0, false, false);
+    }
+    size_t smem = (size_t)L.s_bytes * envs_per_cta;
     if (smem > (size_t)s->smem_optin) return sfail(MS_ERR_INVALID_ARG, "merged layout needs %zu B of shared memory", smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_multi, 32 * warps, smem);
+    int per_sm = occ(L);
     if (per_sm < 1) return sfail(MS_ERR_INVALID_ARG, "merged layout does not fit on an SM");
     // a fixed grid per layout keeps one graph per layout; warps without work exit at once
     int grid = per_sm * s->sm_count;
-    if (grow_slot(s, sl, batch.size(), nwork, (size_t)grid * warps * L.g_bytes, nact) != cudaSuccess)
+    // the work list: sessions heaviest first, each session's envs padded to a
+    // multiple of MULTI_K with inactive items
+    std::vector<int> order(batch.size());
+    for (size_t i = 0; i < batch.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const Session* sx = batch[x].second;
+        const Session* sy = batch[y].second;
+        return sx->max_nj * 8 + sx->max_nb > sy->max_nj * 8 + sy->max_nb;
+    });
+    size_t npad = 0;
+    for (auto& rs : batch) npad += (size_t)((rs.second->E + MULTI_K - 1) / MULTI_K * MULTI_K);
+    if (grow_slot(s, sl, batch.size(), npad, (size_t)grid * envs_per_cta * L.g_bytes, nact) != cudaSuccess)
         return sfail(MS_ERR_OOM, "server tables: device or pinned allocation failed");
     size_t w = 0, a = 0;
     for (size_t i = 0; i < batch.size(); i++) {
@@ -314,14 +358,12 @@ static int launch_merged(ms_server* s, Slot& sl) {
             sl.h_acts[i] = sl.d_act + a;
             a += r->act.size();
         }
-        for (int e = 0; e < se->E; e++) sl.h_work[w++] = make_int2((int)i, e);
     }
-    // heaviest envs first (the work queue is popped in order)
-    std::stable_sort(sl.h_work, sl.h_work + w, [&](int2 x, int2 y) {
-        const Session* sx = batch[x.x].second;
-        const Session* sy = batch[y.x].second;
-        return sx->max_nj * 8 + sx->max_nb > sy->max_nj * 8 + sy->max_nb;
-    });
+    for (int i : order) {
+        int E = batch[i].second->E;
+        int Ep = (E + MULTI_K - 1) / MULTI_K * MULTI_K;
+        for (int e = 0; e < Ep; e++) sl.h_work[w++] = make_int2(i, e < E ? e : -1);
+    }
     if (a) cudaMemcpyAsync(sl.d_act, sl.h_act, a * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
     cudaMemcpyAsync(sl.d_batches, sl.h_batches, batch.size() * sizeof(DevBatch), cudaMemcpyHostToDevice, sl.stream);
     cudaMemcpyAsync(sl.d_acts, sl.h_acts, batch.size() * sizeof(float*), cudaMemcpyHostToDevice, sl.stream);
@@ -344,7 +386,7 @@ static int launch_merged(ms_server* s, Slot& sl) {
             if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return sfail(MS_ERR_CUDA, "merged launch: begin capture failed");
             cudaMemsetAsync(sl.d_queue, 0, sizeof(int), sl.stream);
-            cudaLaunchKernel((const void*)k_multi, dim3(grid), dim3(32 * warps), args, smem, sl.stream);
+            cudaLaunchKernel((const void*)k_multi<MULTI_G>, dim3(grid), dim3(32 * warps), args, smem, sl.stream);
             cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
             if (ce != cudaSuccess) return sfail(MS_ERR_CUDA, "merged launch capture: %s", cudaGetErrorString(ce));
         }
@@ -370,7 +412,7 @@ static int launch_merged(ms_server* s, Slot& sl) {
     }
     if (cudaGraphLaunch(it->second.exec, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "graph launch failed");
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "event record failed");
-    sl.envs = (int)w;
+    sl.envs = (int)nenv;                    // padding items are not env-steps
     return MS_OK;
 }
 
@@ -521,7 +563,7 @@ extern "C" ms_status ms_server_create(size_t budget, const ms_server_options* op
     cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
     cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     // raised to the device maximum once: graphs of every layout stay valid
-    cudaFuncSetAttribute((const void*)k_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+    cudaFuncSetAttribute((const void*)k_multi<MULTI_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
     // sessions come and go: keep freed pool memory for the next session
     // instead of returning it to the driver at every synchronisation
     cudaMemPool_t pool;
