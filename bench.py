@@ -219,7 +219,7 @@ def barrier(ws):
         dist.barrier()
 
 
-def time_cpu_baseline(name, n_envs, steps):
+def time_cpu_baseline(name, n_envs, steps, one_core=False):
     """The oracle as it stands, on every host core, on a bounded sample."""
     import oracle
     sc = scenegen.make_scene(name, n_envs=n_envs)
@@ -229,9 +229,19 @@ def time_cpu_baseline(name, n_envs, steps):
     t0 = time.perf_counter()
     o.step(steps, actions=acts, threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": n_envs * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_envs} envs x {steps} steps of the {name} workload, FP64, {cores} threads "
-                      f"({dt:.1f} s)"}
+    out = {"value": n_envs * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n_envs} envs x {steps} steps of the {name} workload, FP64, {cores} threads "
+                     f"({dt:.1f} s)"}
+    if one_core:
+        # the same oracle on one core, on a sixteenth of the sample
+        n1 = max(1, n_envs // 16)
+        o1 = oracle.Oracle(sc.subset(range(n1)))
+        t0 = time.perf_counter()
+        o1.step(steps, actions=acts[:, :n1], threads=1)
+        d1 = time.perf_counter() - t0
+        out["value_1core"] = n1 * steps / d1
+        out["sample_1core"] = f"{n1} envs x {steps} steps, 1 thread ({d1:.1f} s)"
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -562,7 +572,7 @@ def main():
                           "overload_10k_merged": serve_run(10000, 3.0, True, pools=pools),
                           "overload_10k_one_launch_per_request": serve_run(10000, 3.0, False, pools=pools)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20)
+        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20, one_core=True)
     print(json.dumps(line), flush=True)
 
 
