@@ -119,7 +119,9 @@ def joint_rows(joints) -> np.ndarray:
 def param_row(p) -> np.ndarray:
     g = p["gravity"]
     return np.array([p["dt"], p["substeps"], p["pos_iters"], p["vel_iters"], g[0], g[1], g[2],
-                     p["margin"], p["max_depen_vel"], p["contact_capacity"], p["pair_capacity"]],
+                     p["margin"], p["max_depen_vel"], p["contact_capacity"], p["pair_capacity"],
+                     p.get("linear_damping", 0.0), p.get("angular_damping", 0.0),
+                     p.get("bounce_threshold", 1.0), p.get("warm_start", 0)],
                     np.float64)
 
 

@@ -91,7 +91,7 @@ static int basis_axis(v3 a) {
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int type; double p[3]; double mass; int dyn;
-    double inv_mass; double inv_I[3]; double mu; unsigned group, mask;
+    double inv_mass; double inv_I[3]; double mu, rest; unsigned group, mask;
     v3 x; qt q; v3 v; v3 w;
     m3 invIw;                         /* world inverse inertia, per substep */
 } Body;
@@ -102,7 +102,15 @@ typedef struct {
     double lower, upper, kp, kd, target;
 } Joint;
 
-typedef struct { v3 cA, cB, n; double d; v3 aA, aB; } CPoint;
+typedef struct {
+    v3 cA, cB, n; double d; v3 aA, aB;
+    double vn0;                       /* normal relative velocity at step start (restitution) */
+    double lmax;                      /* largest normal impulse at the end of a substep */
+} CPoint;
+
+/* a contact point of the previous step, for warm starting across steps:
+ * its normal impulse and its friction impulse as a world vector */
+typedef struct { int a, b; v3 aA; double ln; v3 ft; } PrevPoint;
 typedef struct { int a, b, np; CPoint p[4]; } Manifold;
 
 enum { RK_NORMAL = 0, RK_FRICTION = 1, RK_EQ = 2, RK_LIMIT = 3, RK_DRIVE = 4 };
@@ -127,6 +135,7 @@ typedef struct {
     int ntie; int (*tiepairs)[2];
     int ncons; Constraint* cons; int* order; int ncolors;
     int nrows; Row* rows;
+    int nprev; PrevPoint* prev;       /* contact points of the previous step (warm start) */
     unsigned status; long long ties;
     long long cnt[OC_NUM];
 } Env;
@@ -135,6 +144,7 @@ struct oracle_world {
     int E; Env* envs;
     double dt; int substeps, pos_iters, vel_iters; v3 g; double margin, vmax;
     int contact_cap, pair_cap;
+    double lin_damp, ang_damp, bounce; int warm;
     int nb_total, nj_total;
     long long* body_off; long long* joint_off;
 };
@@ -191,6 +201,7 @@ static void body_from_desc(Body* b, const double* d) {
     b->x = V(d[5], d[6], d[7]);
     b->q = qnormalize(Q(d[8], d[9], d[10], d[11]));
     b->mu = d[18];
+    b->rest = d[19];
     b->group = (unsigned)d[20]; b->mask = (unsigned)d[21];
     if (b->dyn) {
         double I[3];
@@ -801,6 +812,11 @@ static void narrowphase(const oracle_world* w, Env* e) {
             c->cA = pts[k].cA; c->cB = pts[k].cB; c->n = pts[k].n; c->d = pts[k].d;
             c->aA = mtv(&RA, sub(c->cA, BA->x));   /* body-local anchors */
             c->aB = mtv(&RB, sub(c->cB, BB->x));
+            /* approach speed along n at the step-start velocities */
+            v3 uA = add(BA->v, cross(BA->w, sub(c->cA, BA->x)));
+            v3 uB = add(BB->v, cross(BB->w, sub(c->cB, BB->x)));
+            c->vn0 = dot(c->n, sub(uA, uB));
+            c->lmax = 0.0;
         }
         total += np;
     }
@@ -1160,24 +1176,119 @@ static void integrate(Env* e, double h) {
     }
 }
 
+/* Warm start across steps (optional): a contact point takes the impulses of
+ * the first point of the previous step on the same body pair whose body-A
+ * anchor lies within WARM_RADIUS of its own (the matching of a persistent
+ * contact manifold); joint rows keep their impulses. */
+static const double WARM_RADIUS = 0.002;   /* m */
+
+static void warm_from_cache(Env* e) {
+    for (int m = 0; m < e->nman; m++) {
+        Manifold* M = &e->man[m];
+        Constraint* c = &e->cons[e->nj + m];
+        Row* R = &e->rows[c->row0];
+        for (int k = 0; k < M->np; k++) {
+            for (int q = 0; q < e->nprev; q++) {
+                const PrevPoint* P = &e->prev[q];
+                if (P->a != M->a || P->b != M->b) continue;
+                double dist = norm(sub(M->p[k].aA, P->aA));
+                tie(e, dist, WARM_RADIUS);
+                if (dist < WARM_RADIUS) {
+                    /* the friction impulse, projected onto this point's tangents */
+                    v3 t1, t2;
+                    tangents(M->p[k].n, &t1, &t2);
+                    R[k].lambda = P->ln;
+                    R[M->np + 2 * k].lambda = dot(P->ft, t1);
+                    R[M->np + 2 * k + 1].lambda = dot(P->ft, t2);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+static void store_cache(Env* e) {
+    int n = 0;
+    for (int m = 0; m < e->nman; m++) {
+        const Manifold* M = &e->man[m];
+        const Row* R = &e->rows[e->cons[e->nj + m].row0];
+        for (int k = 0; k < M->np; k++) {
+            PrevPoint* P = &e->prev[n++];
+            const Row* f1 = &R[M->np + 2 * k];
+            const Row* f2 = &R[M->np + 2 * k + 1];
+            P->a = M->a; P->b = M->b; P->aA = M->p[k].aA;
+            P->ln = R[k].lambda;
+            P->ft = add(scl(f1->lin, f1->lambda), scl(f2->lin, f2->lambda));
+        }
+    }
+    e->nprev = n;
+}
+
+/* Restitution (after the last substep; the rule of Box2D v3's solver): a
+ * contact point whose step-start approach speed exceeds the bounce threshold
+ * and that carried a normal impulse gets the normal impulse that makes its
+ * normal relative velocity -e times that approach speed, accumulated impulse
+ * kept >= 0.  e = average of the two bodies' restitution. */
+static void restitution(const oracle_world* w, Env* e) {
+    for (int o = 0; o < e->ncons; o++) {
+        int ci = e->order[o];
+        if (ci < 0) break;
+        Constraint* c = &e->cons[ci];
+        if (c->kind != 1) continue;
+        Manifold* M = &e->man[c->idx];
+        double ra = M->a >= 0 ? e->bodies[M->a].rest : 0.0, rb = M->b >= 0 ? e->bodies[M->b].rest : 0.0;
+        double er = 0.5 * (ra + rb);
+        for (int k = 0; k < M->np; k++) {
+            CPoint* p = &M->p[k];
+            Row* r = &e->rows[c->row0 + k];
+            if (er <= 0.0 || p->vn0 > -w->bounce || p->lmax <= 0.0 || r->k <= 0.0) continue;
+            double vn = row_jv(e, r);
+            double old = r->lambda;
+            double nl = fmax(old - (vn + er * p->vn0) / r->k, 0.0);
+            r->lambda = nl;
+            apply_impulse(e, r, nl - old);
+        }
+    }
+}
+
 static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
     /* drive targets: NaN keeps the previous target */
     if (act) for (int j = 0; j < e->nj && j < A; j++) if (!isnan(act[j])) e->joints[j].target = act[j];
     broadphase(w, e);
     narrowphase(w, e);
     build_constraints(e);
+    /* impulses start at zero, or (warm start) from the previous step */
+    int nj8 = 8 * e->nj;
+    double jl[nj8 > 0 ? nj8 : 1];
+    if (w->warm) for (int r = 0; r < nj8; r++) jl[r] = e->rows[r].lambda;
     for (int r = 0; r < e->nrows; r++) memset(&e->rows[r], 0, sizeof(Row));
+    if (w->warm) {
+        for (int r = 0; r < nj8; r++) e->rows[r].lambda = jl[r];
+        warm_from_cache(e);
+    }
     double h = w->dt / w->substeps;
+    double al = 1.0 / (1.0 + h * w->lin_damp), aw = 1.0 / (1.0 + h * w->ang_damp);
     for (int s = 0; s < w->substeps; s++) {
+        /* velocity damping (implicit, Box2D v3) and gravity */
         for (int i = 0; i < e->nb; i++)
-            if (e->bodies[i].dyn) e->bodies[i].v = add(e->bodies[i].v, scl(w->g, h));
+            if (e->bodies[i].dyn) {
+                e->bodies[i].v = add(scl(e->bodies[i].v, al), scl(w->g, h));
+                e->bodies[i].w = scl(e->bodies[i].w, aw);
+            }
         prep(w, e, h);
         warm_start(e);
         for (int it = 0; it < w->pos_iters; it++) sweep(e, 0);
         integrate(e, h);
         relax_bias(e, h);
         for (int it = 0; it < w->vel_iters; it++) sweep(e, 1);
+        for (int m = 0; m < e->nman; m++) {
+            Manifold* M = &e->man[m];
+            const Row* R = &e->rows[e->cons[e->nj + m].row0];
+            for (int k = 0; k < M->np; k++) M->p[k].lmax = fmax(M->p[k].lmax, R[k].lambda);
+        }
     }
+    restitution(w, e);
+    if (w->warm) store_cache(e);
     e->cnt[OC_STEPS]++;
 }
 
@@ -1192,6 +1303,7 @@ oracle_world* oracle_create(int n_envs, const long long* body_off, const double*
     w->vel_iters = (int)params[3]; w->g = V(params[4], params[5], params[6]);
     w->margin = params[7]; w->vmax = params[8];
     w->contact_cap = (int)params[9]; w->pair_cap = (int)params[10];
+    w->lin_damp = params[11]; w->ang_damp = params[12]; w->bounce = params[13]; w->warm = (int)params[14];
     w->nb_total = (int)body_off[n_envs]; w->nj_total = (int)joint_off[n_envs];
     w->body_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
     w->joint_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
@@ -1223,6 +1335,7 @@ oracle_world* oracle_create(int n_envs, const long long* body_off, const double*
         e->order = (int*)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
         int nr = 8 * e->nj + 3 * w->contact_cap;
         e->rows = (Row*)calloc((size_t)(nr > 0 ? nr : 1), sizeof(Row));
+        e->prev = (PrevPoint*)calloc((size_t)(w->contact_cap > 0 ? w->contact_cap : 1), sizeof(PrevPoint));
     }
     return w;
 }
@@ -1232,7 +1345,7 @@ void oracle_destroy(oracle_world* w) {
     for (int i = 0; i < w->E; i++) {
         Env* e = &w->envs[i];
         free(e->bodies); free(e->joints); free(e->pairs); free(e->tiepairs); free(e->man);
-        free(e->cons); free(e->order); free(e->rows);
+        free(e->cons); free(e->order); free(e->rows); free(e->prev);
     }
     free(w->envs); free(w->body_off); free(w->joint_off); free(w);
 }
@@ -1291,6 +1404,9 @@ void oracle_set_state(oracle_world* w, const double* in) {
             b->q = Q(o[3], o[4], o[5], o[6]);
             if (b->dyn) { b->v = V(o[7], o[8], o[9]); b->w = V(o[10], o[11], o[12]); }
         }
+        /* a set state starts without warm-start memory */
+        e->nprev = 0;
+        for (int r = 0; r < 8 * e->nj; r++) e->rows[r].lambda = 0.0;
     }
 }
 

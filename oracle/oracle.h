@@ -25,8 +25,22 @@
  *               angvel[3], mu, restitution, group, mask
  *   joint [22]: type, parent, child, parent_frame[7] (pos, quat), child_frame[7],
  *               lower, upper, kp, kd, target0
- *   params[11]: dt, substeps, pos_iters, vel_iters, gx, gy, gz, margin,
- *               max_depen_vel, contact_capacity, pair_capacity
+ *   params[15]: dt, substeps, pos_iters, vel_iters, gx, gy, gz, margin,
+ *               max_depen_vel, contact_capacity, pair_capacity,
+ *               linear_damping, angular_damping, bounce_threshold, warm_start
+ *
+ * Optional solver variants (all off in the default parameters):
+ *   damping          per substep v <- v / (1 + h c_lin) + h g,
+ *                    w <- w / (1 + h c_ang) (implicit damping, Box2D v3)
+ *   restitution      after the last substep, per contact point whose
+ *                    step-start approach speed exceeds bounce_threshold and
+ *                    that carried a normal impulse: the normal impulse that
+ *                    makes the normal velocity -e times the approach speed
+ *                    (Box2D v3 solver), e = mean of the two restitutions
+ *   warm start       impulses carried across steps: joint rows keep theirs;
+ *                    a contact point takes those of the first previous-step
+ *                    point of the same body pair whose body-A anchor is
+ *                    within 2 mm (persistent contact manifold matching)
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H

@@ -47,7 +47,8 @@ ALL_GROUPS = 0xFFFF
 def default_params(**kw) -> Dict:
     p = dict(dt=0.01, substeps=4, pos_iters=8, vel_iters=1,
              gravity=(0.0, 0.0, -9.81), margin=0.01, max_depen_vel=1.0,
-             contact_capacity=64, pair_capacity=128)
+             contact_capacity=64, pair_capacity=128,
+             linear_damping=0.0, angular_damping=0.0, bounce_threshold=1.0, warm_start=0)
     p.update(kw)
     return p
 
@@ -129,7 +130,7 @@ def axis_angle_quat(axis, angle) -> np.ndarray:
 
 
 def body(type_, p, mass, pos, quat=(0, 0, 0, 1), linvel=(0, 0, 0), angvel=(0, 0, 0),
-         mu=0.5, group=1, mask=ALL_GROUPS) -> np.ndarray:
+         mu=0.5, group=1, mask=ALL_GROUPS, restitution=0.0) -> np.ndarray:
     b = np.zeros((), BODY_DTYPE)
     b["type"] = type_
     b["p"] = p
@@ -139,7 +140,7 @@ def body(type_, p, mass, pos, quat=(0, 0, 0, 1), linvel=(0, 0, 0), angvel=(0, 0,
     b["linvel"] = linvel
     b["angvel"] = angvel
     b["mu"] = mu
-    b["restitution"] = 0.0
+    b["restitution"] = restitution
     b["group"] = group
     b["mask"] = mask
     return b

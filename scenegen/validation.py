@@ -129,6 +129,16 @@ def resting_box(tilt=(0.0, 0.0), mu=0.0, h=(0.03, 0.02, 0.025), mass=0.3, seed=0
     return pack("resting_box", [bl], [[]], default_params(**pk), 0, seed)
 
 
+def bouncing_ball(e=0.5, z0=0.5, vz0=0.0, r=0.02, m=0.05, n_envs=1, **pk):
+    """A sphere above the plane, frictionless, both with restitution e."""
+    envs_b = []
+    for k in range(n_envs):
+        envs_b.append([body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), mu=0.0, group=1, restitution=e),
+                       body(SPHERE, (r, 0, 0), m, (0.1 * k, 0, z0), linvel=(0.0, 0.0, vz0), mu=0.0, group=2,
+                            restitution=e)])
+    return pack("bouncing_ball", envs_b, [[] for _ in range(n_envs)], default_params(**pk), 0, 0)
+
+
 def _rot(q):
     x, y, z, w = q
     return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
