@@ -1176,33 +1176,28 @@ static void integrate(Env* e, double h) {
     }
 }
 
-/* Warm start across steps (optional): a contact point takes the impulses of
- * the first point of the previous step on the same body pair whose body-A
- * anchor lies within WARM_RADIUS of its own (the matching of a persistent
- * contact manifold); joint rows keep their impulses. */
-static const double WARM_RADIUS = 0.002;   /* m */
-
+/* Warm start across steps (optional): joint rows keep their impulses; the
+ * k-th point of a manifold takes the impulses of the k-th point of the
+ * previous step's manifold of the same body pair (the manifold's point order
+ * is that of the reduction; no distance test, so no new discrete decision),
+ * the friction impulse kept as a world vector and projected onto the new
+ * point's tangents. */
 static void warm_from_cache(Env* e) {
     for (int m = 0; m < e->nman; m++) {
         Manifold* M = &e->man[m];
         Constraint* c = &e->cons[e->nj + m];
         Row* R = &e->rows[c->row0];
-        for (int k = 0; k < M->np; k++) {
-            for (int q = 0; q < e->nprev; q++) {
-                const PrevPoint* P = &e->prev[q];
-                if (P->a != M->a || P->b != M->b) continue;
-                double dist = norm(sub(M->p[k].aA, P->aA));
-                tie(e, dist, WARM_RADIUS);
-                if (dist < WARM_RADIUS) {
-                    /* the friction impulse, projected onto this point's tangents */
-                    v3 t1, t2;
-                    tangents(M->p[k].n, &t1, &t2);
-                    R[k].lambda = P->ln;
-                    R[M->np + 2 * k].lambda = dot(P->ft, t1);
-                    R[M->np + 2 * k + 1].lambda = dot(P->ft, t2);
-                    break;
-                }
-            }
+        /* the previous step's points of this pair, in order */
+        int k = 0;
+        for (int q = 0; q < e->nprev && k < M->np; q++) {
+            const PrevPoint* P = &e->prev[q];
+            if (P->a != M->a || P->b != M->b) continue;
+            v3 t1, t2;
+            tangents(M->p[k].n, &t1, &t2);
+            R[k].lambda = P->ln;
+            R[M->np + 2 * k].lambda = dot(P->ft, t1);
+            R[M->np + 2 * k + 1].lambda = dot(P->ft, t2);
+            k++;
         }
     }
 }

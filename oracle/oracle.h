@@ -38,9 +38,9 @@
  *                    makes the normal velocity -e times the approach speed
  *                    (Box2D v3 solver), e = mean of the two restitutions
  *   warm start       impulses carried across steps: joint rows keep theirs;
- *                    a contact point takes those of the first previous-step
- *                    point of the same body pair whose body-A anchor is
- *                    within 2 mm (persistent contact manifold matching)
+ *                    the k-th point of a manifold takes those of the k-th
+ *                    point of the previous step's manifold of the same body
+ *                    pair (friction as a world vector, projected)
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H
