@@ -76,7 +76,7 @@ typedef struct {
     float linvel[3];
     float angvel[3];
     float mu;
-    float restitution;           /* accepted, not modelled (must be 0 or is ignored) */
+    float restitution;           /* [0, 1]; a contact uses the mean of its two bodies' */
     uint16_t group, mask;
 } ms_body_desc;
 
@@ -105,7 +105,18 @@ typedef struct {
  *   solver sweeps per substep; margin: contact margin (speculative contacts
  *   are kept while d < margin); max_depen_vel: cap on the penetration
  *   recovery speed; pair_capacity / contact_capacity: per-env limits, beyond
- *   which pairs / manifolds are dropped in order and a status bit is set. */
+ *   which pairs / manifolds are dropped in order and a status bit is set.
+ * Optional solver variants (0 = off; all off gives the base method):
+ *   linear_damping, angular_damping (1/s): implicit velocity damping each
+ *   substep, v <- v / (1 + h c) (+ h g), w <- w / (1 + h c) (Box2D v3);
+ *   bounce_threshold (m/s): after the last substep, a contact point whose
+ *   step-start approach speed exceeds it and that carried a normal impulse
+ *   leaves with normal velocity -e x that speed (e = mean restitution);
+ *   warm_start: 1 carries impulses across steps -- joint rows keep theirs,
+ *   the k-th point of a manifold takes the normal and (world-vector)
+ *   friction impulses of the k-th point of the previous step's manifold of
+ *   the same body pair.  ms_set_state clears this memory for the envs it
+ *   sets. */
 typedef struct {
     float dt;
     int32_t substeps, pos_iters, vel_iters;
@@ -114,6 +125,9 @@ typedef struct {
     float max_depen_vel;
     int32_t contact_capacity;
     int32_t pair_capacity;
+    float linear_damping, angular_damping;
+    float bounce_threshold;
+    int32_t warm_start;
 } ms_sim_params;
 
 typedef struct ms_batch ms_batch;

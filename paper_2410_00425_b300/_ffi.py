@@ -33,7 +33,8 @@ class ms_sim_params(C.Structure):
     _fields_ = [("dt", C.c_float), ("substeps", C.c_int32), ("pos_iters", C.c_int32),
                 ("vel_iters", C.c_int32), ("gravity", C.c_float * 3), ("margin", C.c_float),
                 ("max_depen_vel", C.c_float), ("contact_capacity", C.c_int32),
-                ("pair_capacity", C.c_int32)]
+                ("pair_capacity", C.c_int32), ("linear_damping", C.c_float), ("angular_damping", C.c_float),
+                ("bounce_threshold", C.c_float), ("warm_start", C.c_int32)]
 
 
 class ms_scene_desc(C.Structure):
@@ -141,6 +142,8 @@ def make_params(p: dict) -> ms_sim_params:
         sp.gravity[i] = p["gravity"][i]
     sp.margin = p["margin"]; sp.max_depen_vel = p["max_depen_vel"]
     sp.contact_capacity = p["contact_capacity"]; sp.pair_capacity = p["pair_capacity"]
+    sp.linear_damping = p.get("linear_damping", 0.0); sp.angular_damping = p.get("angular_damping", 0.0)
+    sp.bounce_threshold = p.get("bounce_threshold", 1.0); sp.warm_start = int(p.get("warm_start", 0))
     return sp
 
 

@@ -182,6 +182,12 @@ static ms_status validate_params(const ms_sim_params* p) {
         return fail(MS_ERR_INVALID_ARG, "contact_capacity must be in [1, 16384]");
     if (p->pair_capacity < 1 || p->pair_capacity > 65535)
         return fail(MS_ERR_INVALID_ARG, "pair_capacity must be in [1, 65535]");
+    if (!(p->linear_damping >= 0.f) || !std::isfinite(p->linear_damping) || !(p->angular_damping >= 0.f) ||
+        !std::isfinite(p->angular_damping))
+        return fail(MS_ERR_INVALID_ARG, "damping must be finite and >= 0");
+    if (!(p->bounce_threshold >= 0.f) || !std::isfinite(p->bounce_threshold))
+        return fail(MS_ERR_INVALID_ARG, "bounce_threshold must be finite and >= 0");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(MS_ERR_INVALID_ARG, "warm_start must be 0 or 1");
     return MS_OK;
 }
 
@@ -201,6 +207,8 @@ static ms_status validate_env(int e, const ms_body_desc* bd, int nb, const ms_jo
         if (qn < 1e-12) return fail(MS_ERR_INVALID_ARG, "env %d body %d: zero quaternion", e, i);
         if (d.mass < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mass", e, i);
         if (d.mu < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mu", e, i);
+        if (!(d.restitution >= 0.f && d.restitution <= 1.f))
+            return fail(MS_ERR_INVALID_ARG, "env %d body %d: restitution not in [0, 1]", e, i);
         int need = d.type == MS_SPHERE ? 1 : (d.type == MS_CAPSULE ? 2 : (d.type == MS_BOX ? 3 : 0));
         for (int k = 0; k < need; k++)
             if (!(d.p[k] > 0.f) || !std::isfinite(d.p[k]))
@@ -271,6 +279,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     b->NJ = b->h_joint_off[E];
     b->A = b->max_nj;
     std::vector<float4> x(b->NB), q(b->NB), v(b->NB), w(b->NB), shape(b->NB), inv(b->NB);
+    std::vector<float> rest(b->NB);
     std::vector<int2> meta(b->NB);
     std::vector<unsigned long long> adj(b->NB, 0ull);
     std::vector<int> body_env(b->NB);
@@ -292,6 +301,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
                        : make_float4(0.f, 0.f, 0.f, 0.f);
             w[k] = dyn ? make_float4(d.angvel[0], d.angvel[1], d.angvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             shape[k] = make_float4(d.p[0], d.p[1], d.p[2], d.mu);
+            rest[k] = d.restitution;
             if (dyn) {
                 float I[3];
                 body_inertia(d, I);
@@ -328,6 +338,12 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     D.P.gx = p->gravity[0]; D.P.gy = p->gravity[1]; D.P.gz = p->gravity[2];
     D.P.margin = p->margin; D.P.vmax = p->max_depen_vel;
     D.P.pair_cap = p->pair_capacity; D.P.contact_cap = p->contact_capacity;
+    D.P.adl = (float)(1.0 / (1.0 + (double)D.P.h * p->linear_damping));
+    D.P.adw = (float)(1.0 / (1.0 + (double)D.P.h * p->angular_damping));
+    D.P.bounce = p->bounce_threshold;
+    D.P.warm = p->warm_start;
+    D.P.restit = 0;
+    for (float r : rest) D.P.restit |= r > 0.f;
     ms_status s = MS_OK;
     int* bo = nullptr; int* jo = nullptr;
 #define UP(dst, src) do { if ((s = upload(b, dst, src)) != MS_OK) { free_all(b); delete b; return s; } } while (0)
@@ -341,6 +357,18 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     float4* d_jf; float4* d_jp; int4* d_jm;
     UP(&d_jf, jf); UP(&d_jp, jp); UP(&d_jm, jm); UP(&D.jt, jt);
     D.jf = d_jf; D.jp = d_jp; D.jm = d_jm;
+    float* d_rest;
+    UP(&d_rest, rest);
+    D.rest = d_rest;
+    D.wc = nullptr; D.wc_n = nullptr; D.wjl = nullptr;
+    if (p->warm_start) {
+        // warm-start memory: 2 float4 per (env, contact point), a count per
+        // env, 8 impulses per joint; empty at creation
+        std::vector<float4> wc(2 * (size_t)E * (size_t)p->contact_capacity, make_float4(0.f, 0.f, 0.f, 0.f));
+        std::vector<int> wn(E, 0);
+        std::vector<float> wj(8 * (size_t)std::max(b->NJ, 1), 0.f);
+        UP(&D.wc, wc); UP(&D.wc_n, wn); UP(&D.wjl, wj);
+    }
     UP(&b->d_body_env, body_env);
     std::vector<unsigned> zeros(E, 0u);
     UP(&D.status, zeros);
@@ -861,7 +889,8 @@ extern "C" ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* j
     }
     // resident state and parameters, the staging buffer and the per-env
     // workspace of the plain path (the batched path's is per resident slot)
-    size_t state = NB * (16 * 6 + 8 + 8 + 4 + 52) + NJ * (64 + 16 + 16 + 4) + (size_t)n_envs * 16 + 64;
+    size_t state = NB * (16 * 6 + 8 + 8 + 4 + 52 + 4) + NJ * (64 + 16 + 16 + 4) + (size_t)n_envs * 16 + 64;
+    if (p->warm_start) state += (size_t)n_envs * (32 * (size_t)p->contact_capacity + 4) + 32 * NJ;
     Layout L = make_layout(max_nb, max_nj, p->pair_capacity, p->contact_capacity, false, true, p->contact_capacity, true,
                            false);
     *bytes = state + (size_t)n_envs * (size_t)(L.s_bytes + L.g_bytes);

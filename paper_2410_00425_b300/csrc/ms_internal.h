@@ -38,7 +38,7 @@ struct Layout {
     int g_bytes;
     int aabb, pairs, man, pts;
     int rows_cg;                             // rows of every contact point (those >= pts_s are used), or -1
-    int shape, inv, meta, adj, jf, jp, jm, jt;   // parameter copies (no-allocation path only), or -1
+    int shape, inv, meta, adj, jf, jp, jm, jt, rest;   // parameter copies (no-allocation path only), or -1
 };
 
 // with_state: x, q, v, w copied into the shared part; with_params: body and
@@ -54,6 +54,10 @@ struct DevParams {
     float gx, gy, gz;
     float margin, vmax;
     int pair_cap, contact_cap;
+    float adl, adw;            // velocity damping factors per substep, 1 / (1 + h c)
+    float bounce;              // restitution threshold (approach speed, m/s)
+    int warm;                  // impulses carried across steps
+    int restit;                // some body of the batch has restitution > 0
 };
 
 struct DevBatch {
@@ -70,6 +74,10 @@ struct DevBatch {
     const float4* jp;
     const int4* jm;
     float* jt;
+    const float* rest;                 // restitution per body
+    float4* wc;                        // warm start: 2 per (env, contact point): (a | b << 16, aA), (ln, friction)
+    int* wc_n;                         //   contact points cached per env
+    float* wjl;                        //   8 impulses per joint
     unsigned* status;
     char* plain_ws;
     Layout plain_layout;

@@ -80,17 +80,24 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
         L.shape = take(16 * nb, 16); L.inv = take(16 * nb, 16); L.meta = take(8 * nb, 8);
         L.adj = take(8 * nb, 8);
         L.jf = take(64 * nj, 16); L.jp = take(16 * nj, 16); L.jm = take(16 * nj, 16); L.jt = take(4 * nj, 4);
+        L.rest = take(4 * nb, 4);
     } else {
-        L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = -1;
+        L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = L.rest = -1;
     }
     L.g_bytes = align_up(o, 16);
     return L;
 }
 
-// the env's parameters, read in place from the resident arrays
-__device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b0, int j0) {
+// the env's parameters and warm-start memory, read in place from the
+// resident arrays (an idle lane group has no warm-start memory)
+__device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b0, int j0, int env, bool active) {
     e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
     e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
+    e.rest = D.rest + b0;
+    bool w = active && D.wc;
+    e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
+    e.wc_n = w ? D.wc_n + env : nullptr;
+    e.wjl = w ? D.wjl + 8 * (size_t)j0 : nullptr;
 }
 
 __device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
@@ -110,7 +117,7 @@ __device__ __forceinline__ EnvView plain_view(const DevBatch& D, int env) {
     e.nb = D.body_off[env + 1] - b0;
     e.nj = D.joint_off[env + 1] - j0;
     e.x = D.x + b0; e.q = D.q + b0; e.v = D.v + b0; e.w = D.w + b0;
-    view_params(e, D, b0, j0);
+    view_params(e, D, b0, j0, env, true);
     const Layout& L = D.plain_layout;
     char* s = D.plain_ws + (size_t)env * (L.s_bytes + L.g_bytes);
     view_workspace(e, s, s + L.s_bytes, L);
@@ -139,7 +146,7 @@ __global__ void k_narrow(DevBatch D) {
 }
 __global__ void k_color(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    stage_color(e, warp_grp());
+    begin_step_solve(e, warp_grp(), D.P);
 }
 __global__ void k_prep(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
@@ -153,13 +160,22 @@ __global__ void k_integrate(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
     stage_integrate(e, warp_grp(), D.P);
 }
-__global__ void k_unscale(DevBatch D) {
+// the end of a substep: the contact impulse record, restitution after the
+// last substep, angular velocities back to world space
+__global__ void k_end_substep(DevBatch D, int last) {
     EnvView e = plain_view(D, blockIdx.x);
-    stage_unscale(e, warp_grp());
+    Grp g = warp_grp();
+    if (D.P.restit) {
+        stage_track_impulse(e, g);
+        if (last) stage_restitution(e, g, D.P);
+    }
+    stage_unscale(e, g);
 }
 __global__ void k_check(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);
-    stage_check(e, warp_grp());
+    Grp g = warp_grp();
+    end_step_solve(e, g, D.P);
+    stage_check(e, g);
 }
 
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s) {
@@ -178,7 +194,7 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
             k_integrate<<<grid, block, 0, s>>>(D);
             launches++;
             for (int it = 0; it < D.P.vel_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 2); launches++; }
-            k_unscale<<<grid, block, 0, s>>>(D);
+            k_end_substep<<<grid, block, 0, s>>>(D, sub == D.P.substeps - 1);
             launches++;
         }
         k_check<<<grid, block, 0, s>>>(D);
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             b0 = D.body_off[env]; j0 = D.joint_off[env];
             nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
         }
-        view_params(e, D, b0, j0);
+        view_params(e, D, b0, j0, env, active);
         int nbmax = g.wmax(nb);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
@@ -237,8 +253,9 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             stage_actions(e, g, act, D.A);
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
-            stage_color(e, g);
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P);
+            begin_step_solve(e, g, D.P);
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
+            end_step_solve(e, g, D.P);
             stage_check(e, g);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }
@@ -315,11 +332,16 @@ __global__ void k_unpack_state(DevBatch D, const float* in, const uint8_t* env_m
     D.w[i] = make_float4(s[10], s[11], s[12], 0.f);
 }
 
+// a set state starts with a clear status and no warm-start memory
 __global__ void k_clear_status(DevBatch D, const uint8_t* env_mask) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= D.E) return;
     if (env_mask && !env_mask[e]) return;
     D.status[e] = 0u;
+    if (D.wc_n) {
+        D.wc_n[e] = 0;
+        for (int k = 8 * D.joint_off[e]; k < 8 * D.joint_off[e + 1]; k++) D.wjl[k] = 0.f;
+    }
 }
 
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s) {

@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
     int4* jm = nat<int4>(gl, L.jm);
     e.shape = shp; e.inv = inv; e.meta = meta; e.adj = adj; e.jf = jf; e.jp = jp; e.jm = jm;
     e.jt = nat<float>(gl, L.jt);
+    float* rst = nat<float>(gl, L.rest);
+    e.rest = rst;
+    e.wc = nullptr; e.wc_n = nullptr; e.wjl = nullptr;       // no warm-start memory on this path
     view_workspace(e, s, gl, L);
     e.status = nat<unsigned>(s, L.status);
     e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
                 e.v[i] = make_float4(vv.x, vv.y, vv.z, iv.w);
                 e.w[i] = D.w[b0 + i];
                 shp[i] = make_float4(d.p[0], d.p[1], d.p[2], d.mu);
+                rst[i] = d.restitution;
                 inv[i] = iv;
                 meta[i] = make_int2(d.type | (dyn ? 1 << 8 : 0), (int)((unsigned)d.group | ((unsigned)d.mask << 16)));
                 unsigned long long m = 0ull;
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
             stage_color(e, g);
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P);
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
             stage_check(e, g);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }
@@ -255,8 +259,10 @@ extern "C" ms_status ms_step_noalloc(const ms_noalloc_batch* nb, const ms_sim_pa
     if (n_steps < 0 || n_steps > 1000000) return nfail(MS_ERR_INVALID_ARG, "n_steps must be in [0, 1e6]");
     if (!(p->dt > 0.f) || p->substeps < 1 || p->substeps > 1024 || p->pos_iters < 0 || p->vel_iters < 0 ||
         !(p->margin >= 0.f) || !(p->max_depen_vel > 0.f) || p->contact_capacity < 1 || p->contact_capacity > 16384 ||
-        p->pair_capacity < 1 || p->pair_capacity > 65535)
+        p->pair_capacity < 1 || p->pair_capacity > 65535 || !(p->linear_damping >= 0.f) ||
+        !(p->angular_damping >= 0.f) || !(p->bounce_threshold >= 0.f))
         return nfail(MS_ERR_INVALID_ARG, "invalid ms_sim_params");
+    if (p->warm_start) return nfail(MS_ERR_INVALID_ARG, "warm_start needs the memory of a batch (ms_create_batch)");
     if (n_steps == 0) return MS_OK;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -313,6 +319,11 @@ extern "C" ms_status ms_step_noalloc(const ms_noalloc_batch* nb, const ms_sim_pa
     D.P.gx = p->gravity[0]; D.P.gy = p->gravity[1]; D.P.gz = p->gravity[2];
     D.P.margin = p->margin; D.P.vmax = p->max_depen_vel;
     D.P.pair_cap = p->pair_capacity; D.P.contact_cap = p->contact_capacity;
+    D.P.adl = (float)(1.0 / (1.0 + (double)D.P.h * p->linear_damping));
+    D.P.adw = (float)(1.0 / (1.0 + (double)D.P.h * p->angular_damping));
+    D.P.bounce = p->bounce_threshold;
+    D.P.warm = 0;
+    D.P.restit = 1;                          // the descriptors live on the device: always check
     D.body_off = nb->body_off; D.joint_off = nb->joint_off;
     D.bodies = nb->bodies; D.joints = nb->joints;
     D.x = (float4*)nb->x; D.q = (float4*)nb->q; D.v = (float4*)nb->v; D.w = (float4*)nb->w;

@@ -77,6 +77,11 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
         }
         e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
         e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
+        e.rest = D.rest + b0;
+        bool wm = active && D.wc;
+        e.wc = wm ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
+        e.wc_n = wm ? D.wc_n + env : nullptr;
+        e.wjl = wm ? D.wjl + 8 * (size_t)j0 : nullptr;
         int nbmax = g.wmax(nb);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
@@ -92,8 +97,9 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
         stage_actions(e, g, act, D.A);
         stage_broadphase(e, g, P);
         stage_narrowphase(e, g, P);
-        stage_color(e, g);
-        for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P);
+        begin_step_solve(e, g, P);
+        for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P, sub == P.substeps - 1);
+        end_step_solve(e, g, P);
         stage_check(e, g);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;

@@ -71,11 +71,15 @@ struct EnvView {
     const float4* jp;                 // lower, upper, kp, kd
     const int4* jm;                   // type, parent, child, -
     float* jt;                        // drive targets
+    const float* rest;                // restitution per body
+    float4* wc;                       // warm-start memory of the env (null: off): 2 per contact point
+    int* wc_n;                        //   its count
+    float* wjl;                       //   8 impulses per joint
     float4* sq;                       // S per body, 2 float4: (xx, xy, xz, yy), (yz, zz, -, -)
     float4* aabb;                     // 2 per body
     int* pairs;                       // i | j << 16
     int4* man;                        // a, b, npts, first point
-    float4* pts;                      // 3 per point: (aA, d), (aB, -), (n, -)
+    float4* pts;                      // 3 per point: (aA, d), (aB, step-start approach speed), (n, max normal impulse)
     int4* cons;                       // constraint records in list order
     int* colr;                        // colour per constraint
     int4* scons;                      // the same records sorted by colour (solve order)
@@ -285,12 +289,15 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
         if (keep) {
             int midx = nman + __popc(bits & g.lt());
             e.man[midx] = make_int4(a, b, n, start);
+            float3 vA = xyz(e.v[a]), wA = xyz(e.w[a]), vB = xyz(e.v[b]), wB = xyz(e.w[b]);
             for (int k = 0; k < n; k++) {
                 float3 aA = mtv(SA.R, pts[k].cA - SA.x);
                 float3 aB = mtv(SB.R, pts[k].cB - SB.x);
+                // approach speed along n at the step-start velocities (restitution)
+                float3 uA = vA + cross(wA, pts[k].cA - SA.x), uB = vB + cross(wB, pts[k].cB - SB.x);
                 float4* o = e.pts + 3 * (start + k);
                 o[0] = f4(aA, pts[k].d);
-                o[1] = f4(aB, 0.f);
+                o[1] = f4(aB, dot(pts[k].n, uA - uB));
                 o[2] = f4(pts[k].n, 0.f);
                 if (e.rec_pts) {
                     float* rp = e.rec_pts + 10 * (start + k);
@@ -481,6 +488,14 @@ MSD JointGeo joint_geo(const EnvView& e, int j, int type, const BodyPose& P, con
     return g;
 }
 
+// contact tangent basis: t1 = normalize(n x e_k), k = basis_axis(n), t2 = n x t1
+MSD void tangents(float3 n, float3& t1, float3& t2) {
+    int ax = basis_axis(n);
+    t1 = cross(n, axis3(ax));
+    t1 = t1 * (1.f / len(t1));
+    t2 = cross(n, t1);
+}
+
 MSD Row* cons_rows(const EnvView& e, int4 c) {
     int place = c.w & 3;
     return (place == CP_JOINT ? e.rows_j : (place == CP_MAN_S ? e.rows_cs : e.rows_cg)) + c.z;
@@ -501,10 +516,8 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
             float3 aA = xyz(pt[0]), aB = xyz(pt[1]), n = xyz(pt[2]);
             float3 rA = mv(A.R, aA), rB = mv(B.R, aB);
             float d = dot(n, (A.x + rA) - (B.x + rB));
-            int ax = basis_axis(n);
-            float3 t1 = cross(n, axis3(ax));
-            t1 = t1 * (1.f / len(t1));
-            float3 t2 = cross(n, t1);
+            float3 t1, t2;
+            tangents(n, t1, t2);
             point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), 0.f);
             point_row(R[np + 2 * k], t1, rA, rB, A, B, mu, 0.f);
             point_row(R[np + 2 * k + 1], t2, rA, rB, A, B, mu, 0.f);
@@ -573,8 +586,9 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
         int i = i0 + g.lane;
         if (i >= nb) continue;
         if (is_dyn(e, i)) {
+            // implicit damping (factor 1 / (1 + h c); exactly 1 without) and gravity
             float4 v = e.v[i];
-            v.x = fmaf(h, P.gx, v.x); v.y = fmaf(h, P.gy, v.y); v.z = fmaf(h, P.gz, v.z);
+            v.x = fmaf(h, P.gx, v.x * P.adl); v.y = fmaf(h, P.gy, v.y * P.adl); v.z = fmaf(h, P.gz, v.z * P.adl);
             e.v[i] = v;
             float4 iv = e.inv[i];
             float3 sd = f3(sqrtf(iv.x), sqrtf(iv.y), sqrtf(iv.z));
@@ -583,7 +597,7 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
             S3 Si = rdrt(R, f3(1.f / sd.x, 1.f / sd.y, 1.f / sd.z));
             e.sq[2 * i] = make_float4(S.xx, S.xy, S.xz, S.yy);
             e.sq[2 * i + 1] = make_float4(S.yz, S.zz, 0.f, 0.f);
-            e.w[i] = f4(smv(Si, xyz(e.w[i])), 0.f);
+            e.w[i] = f4(smv(Si, xyz(e.w[i]) * P.adw), 0.f);
         } else {
             e.sq[2 * i] = make_float4(1.f, 0.f, 0.f, 1.f);
             e.sq[2 * i + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
@@ -800,15 +814,176 @@ MSD void stage_check(EnvView& e, const Grp& g) {
     g.sync();
 }
 
+// ------------------------------------------------- optional solver variants
+// Warm start across steps (P.warm): joint rows keep their impulses; the k-th
+// point of a manifold takes the normal impulse and the friction impulse (a
+// world vector, projected onto its tangents) of the k-th point of the
+// previous step's manifold of the same body pair.
+MSD Row* man_rows(const EnvView& e, int4 M) {
+    return (M.w + M.z <= e.pts_s ? e.rows_cs : e.rows_cg) + 3 * M.w;
+}
+
+// Every lane of the warp runs these stages (their loops end in warp-wide
+// operations); a lane group without warm-start memory (an idle slot) takes
+// part with zero counts.
+MSD void stage_warm_init(EnvView& e, const Grp& g) {
+    bool on = e.wc != nullptr && e.nb > 0;
+    int nj = on ? e.nj : 0, nman = on ? e.cnt[C_NMAN] : 0;
+    int n8 = 8 * nj, m8 = g.wmax(n8);
+    for (int i0 = 0; i0 < m8; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i < n8) e.lam[(i & 7) * e.njs + (i >> 3)] = e.wjl[i];
+    }
+    int nold = on ? *e.wc_n : 0;
+    float* Lc = e.lam + 8 * e.njs;
+    int mmax = g.wmax(nman);
+    for (int m0 = 0; m0 < mmax; m0 += g.size) {
+        int m = m0 + g.lane;
+        if (m >= nman) continue;
+        int4 M = e.man[m];
+        int key = M.x | (M.y << 16);
+        int k = 0;
+        for (int q = 0; q < nold && k < M.z; q++) {
+            float4 c0 = e.wc[2 * q];
+            if (__float_as_int(c0.w) != key) continue;
+            float4 c1 = e.wc[2 * q + 1];
+            float3 t1, t2;
+            tangents(xyz(e.pts[3 * (M.w + k) + 2]), t1, t2);
+            float3 ft = f3(c1.y, c1.z, c1.w);
+            Lc[3 * M.w + k] = c1.x;
+            Lc[3 * M.w + M.z + 2 * k] = dot(ft, t1);
+            Lc[3 * M.w + M.z + 2 * k + 1] = dot(ft, t2);
+            k++;
+        }
+    }
+    g.sync();
+}
+
+MSD void stage_store_warm(EnvView& e, const Grp& g) {
+    bool on = e.wc != nullptr && e.nb > 0;
+    int nj = on ? e.nj : 0, nman = on ? e.cnt[C_NMAN] : 0;
+    int n8 = 8 * nj, m8 = g.wmax(n8);
+    for (int i0 = 0; i0 < m8; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i < n8) e.wjl[i] = e.lam[(i & 7) * e.njs + (i >> 3)];
+    }
+    const float* Lc = e.lam + 8 * e.njs;
+    int mmax = g.wmax(nman);
+    for (int m0 = 0; m0 < mmax; m0 += g.size) {
+        int m = m0 + g.lane;
+        if (m >= nman) continue;
+        int4 M = e.man[m];
+        const Row* R = man_rows(e, M);
+        int key = M.x | (M.y << 16);
+        for (int k = 0; k < M.z; k++) {
+            int pnt = M.w + k;
+            float3 t1 = xyz(R[M.z + 2 * k].a), t2 = xyz(R[M.z + 2 * k + 1].a);
+            float3 ft = t1 * Lc[3 * M.w + M.z + 2 * k] + t2 * Lc[3 * M.w + M.z + 2 * k + 1];
+            e.wc[2 * pnt] = make_float4(e.pts[3 * pnt].x, e.pts[3 * pnt].y, e.pts[3 * pnt].z, __int_as_float(key));
+            e.wc[2 * pnt + 1] = make_float4(Lc[3 * M.w + k], ft.x, ft.y, ft.z);
+        }
+    }
+    if (g.lane == 0 && on) *e.wc_n = e.cnt[C_NPTS];   // idle and frozen envs keep theirs
+    g.sync();
+}
+
+// the largest normal impulse of each contact point at a substep's end
+MSD void stage_track_impulse(EnvView& e, const Grp& g) {
+    int nman = e.nb > 0 ? e.cnt[C_NMAN] : 0;
+    const float* Lc = e.lam + 8 * e.njs;
+    int mmax = g.wmax(nman);
+    for (int m0 = 0; m0 < mmax; m0 += g.size) {
+        int m = m0 + g.lane;
+        if (m >= nman) continue;
+        int4 M = e.man[m];
+        for (int k = 0; k < M.z; k++) {
+            float4& o = e.pts[3 * (M.w + k) + 2];
+            o.w = fmaxf(o.w, Lc[3 * M.w + k]);
+        }
+    }
+    g.sync();
+}
+
+// Restitution, after the last substep (in w^ space): in colour order, a
+// contact point whose step-start approach speed exceeds P.bounce and that
+// carried a normal impulse gets the normal impulse that makes its normal
+// velocity -e times that speed, the accumulated impulse kept >= 0.
+MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
+    const int4* sc = e.scons;
+    const int* off = e.color_off;
+    int ncol = e.nb > 0 ? e.cnt[C_NCOLORS] : 0;
+    int colmax = g.wmax(ncol);
+    const float* Lc0 = e.lam + 8 * e.njs;
+    int k0 = 0;
+    for (int col = 0; col < colmax; col++) {
+        int k1 = col < ncol ? off[col + 1] : k0;
+        int wmaxn = g.wmax(k1 - k0);
+        for (int mm = 0; mm < wmaxn; mm += g.size) {
+            int ci = k0 + mm + g.lane;
+            if (ci >= k1) continue;
+            int4 c = sc[ci];
+            if ((c.w & 3) == CP_JOINT) continue;
+            int np = (c.w >> 2) & 7;
+            int4 M = e.man[c.w >> 8];
+            float er = 0.5f * ((M.x >= 0 ? e.rest[M.x] : 0.f) + (M.y >= 0 ? e.rest[M.y] : 0.f));
+            if (!(er > 0.f)) continue;
+            const Row* R = cons_rows(e, c);
+            float* L = const_cast<float*>(Lc0) + c.z;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 va = c.x >= 0 ? e.v[c.x] : z4, wa4 = c.x >= 0 ? e.w[c.x] : z4;
+            float4 vb = c.y >= 0 ? e.v[c.y] : z4, wb4 = c.y >= 0 ? e.w[c.y] : z4;
+            float imA = va.w, imB = vb.w;
+            bool dynA = imA > 0.f, dynB = imB > 0.f;
+            float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
+            for (int k = 0; k < np; k++) {
+                float4 pe = e.pts[3 * (M.w + k) + 1], pm = e.pts[3 * (M.w + k) + 2];
+                float vn0 = pe.w, lmax = pm.w;
+                float4 ra = R[k].a, rb = R[k].b, rc = R[k].c;
+                if (vn0 > -P.bounce || !(lmax > 0.f) || !(ra.w > 0.f)) continue;
+                float3 lin = xyz(ra), sa = xyz(rb), sb = xyz(rc);
+                float vn = (dot(lin, vA) + dot(sa, wA)) - (dot(lin, vB) - dot(sb, wB));
+                float old = L[k];
+                float nl = fmaxf(fmaf(-fmaf(er, vn0, vn), ra.w, old), 0.f);
+                L[k] = nl;
+                float dl = nl - old;
+                vA = madd(vA, lin * imA, dl);
+                wA = madd(wA, sa, dynA ? dl : 0.f);
+                vB = madd(vB, lin * (-imB), dl);
+                wB = madd(wB, sb, dynB ? dl : 0.f);
+            }
+            if (dynA) { e.v[c.x] = f4(vA, imA); e.w[c.x] = f4(wA, 0.f); }
+            if (dynB) { e.v[c.y] = f4(vB, imB); e.w[c.y] = f4(wB, 0.f); }
+        }
+        g.sync();
+        k0 = k1;
+    }
+}
+
 // One substep: prep, warm start, position sweeps, integration, relax
-// sweeps, unscale.
-MSD void run_substep(EnvView& e, const Grp& g, const Params& P) {
+// sweeps, the contact impulse record and (last substep) restitution, unscale.
+MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
     stage_prep(e, g, P);
     stage_sweep(e, g, 0);
     for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1);
     stage_integrate(e, g, P);
     for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2);
+    if (P.restit) {
+        stage_track_impulse(e, g);
+        if (last) stage_restitution(e, g, P);
+    }
     stage_unscale(e, g);
+}
+
+// Colouring of one step, then the warm-start impulses.  P is the same for
+// every lane of a warp, so the branches are warp-uniform.
+MSD void begin_step_solve(EnvView& e, const Grp& g, const Params& P) {
+    stage_color(e, g);
+    if (P.warm) stage_warm_init(e, g);
+}
+
+// The end of a step: the warm-start memory.
+MSD void end_step_solve(EnvView& e, const Grp& g, const Params& P) {
+    if (P.warm) stage_store_warm(e, g);
 }
 
 }  // namespace ms

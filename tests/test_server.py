@@ -34,8 +34,12 @@ def _alone(scene, steps):
 @pytest.mark.parametrize("merge,inflight", [(True, 1), (True, 4), (False, 1), (False, 3)])
 def test_sessions_of_mixed_types_match_stepping_alone(merge, inflight):
     from paper_2410_00425_b300.server import Server
+    warm = scenegen.make_scene("arm", n_envs=6)         # a session with the solver variants on
+    warm.params = dict(warm.params, linear_damping=0.5, angular_damping=0.3, bounce_threshold=0.5, warm_start=1)
+    warm.bodies = warm.bodies.copy()
+    warm.bodies["restitution"] = 0.4
     scenes = [scenegen.make_scene("arm", n_envs=8), scenegen.make_scene("clutter", n_envs=16),
-              scenegen.make_scene("hand", n_envs=4), scenegen.make_scene("small", n_envs=3)]
+              scenegen.make_scene("hand", n_envs=4), scenegen.make_scene("small", n_envs=3), warm]
     srv = Server(8 << 30, merge=merge, max_inflight=inflight)
     sids = [srv.open(sc) for sc in scenes]
     assert all(s is not None for s in sids)
