@@ -3,8 +3,8 @@ restitution and warm starting across steps (all off by default).
 
 Damping is checked against the closed form of its recurrence, restitution
 against the velocity it must leave after an impact, warm starting against
-the equilibrium impulse of a resting box and against the stacking it
-improves.  The default parameters must leave every result unchanged.
+the equilibrium impulse of a resting box and against the rest it brings,
+at one position iteration, to a box on the plane and a hanging chain.  The default parameters must leave every result unchanged.
 """
 import math
 
@@ -145,9 +145,9 @@ def test_warm_start_brings_a_hanging_chain_to_rest():
     assert res[0] > 1e-5, res
 
 
-def test_warm_start_matching_by_anchor():
-    """A point takes the previous step's impulses only on the same pair and
-    within the matching radius: a set state clears the memory."""
+def test_set_state_clears_the_warm_memory():
+    """After a set state the next step starts cold: its impulses equal those
+    of a fresh world set to the same state, and differ from the warm ones."""
     sc = V.stack(n_boxes=1, pos_iters=2, warm_start=1)
     o = oracle.Oracle(sc)
     o.step(50)
