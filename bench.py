@@ -41,7 +41,7 @@ WORKLOADS = {
     "hand": "16-DoF capsule hand holding a cube, 4096 envs (dt 1/120 s, 8 substeps, 16+1 iterations)",
 }
 
-# FLOP weights per counted operation ("Algorithmic work")
+# FLOP weights per counted operation of the oracle (the step's algorithmic work model)
 FLOP_WEIGHTS = {
     "row_solve_2dyn": 61, "row_solve_1dyn": 31, "rows_prep": 40, "body_inertia": 45,
     "body_integrate": 40, "warm_apply": 25, "pairs_tested": 10,
@@ -50,12 +50,25 @@ FLOP_WEIGHTS = {
 }
 FP32_LANES_PER_SM = 128
 
+# --variants: the optional solver variants on (damping, restitution, warm start)
+VARIANT_PARAMS = dict(linear_damping=0.5, angular_damping=0.3, bounce_threshold=0.5, warm_start=1)
+VARIANT_RESTITUTION = 0.4
+
+
+def make_workload(name, variants=False, **kw):
+    sc = scenegen.make_scene(name, **kw)
+    if variants:
+        sc.params = dict(sc.params, **VARIANT_PARAMS)
+        sc.bodies = sc.bodies.copy()
+        sc.bodies["restitution"] = VARIANT_RESTITUTION
+    return sc
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # dominant kernel, from one ncu capture of the bench command (profiles/), keyed
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 29.83e6, "kernel_sha": "463db8ff8e1ee8cd", "kernel": "k_fused<8>"},
+    ("arm", "8,1,0"): {"bytes": 30.16e6, "kernel_sha": "95f4f474d2795775", "kernel": "k_fused<8>"},
 }
 KERNEL_SOURCES = ("ms_kernels.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
@@ -71,7 +84,9 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(name, tuning):
+def ncu_traffic(name, tuning, variants=False):
+    if variants:
+        return None
     key = (name, None if not tuning else "%d,%d,%d" % (tuning["lanes_per_env"], tuning["warps_per_cta"],
                                                        tuning["rows_in_smem"]))
     rec = NCU_TRAFFIC.get(key)
@@ -88,12 +103,12 @@ def load_peaks():
         return {}
 
 
-def algorithmic_flops_per_env_step(name, warmup, steps, sample_envs=32):
+def algorithmic_flops_per_env_step(name, warmup, steps, sample_envs=32, variants=False):
     """Oracle op counters x fixed FLOP weights, counted over the same window
     of steps the timed region covers (after `warmup` steps) on the first
     `sample_envs` envs of the workload (per-env seeding: the same envs)."""
     import oracle
-    sc = scenegen.make_scene(name, n_envs=min(sample_envs, scenegen.CONFIG_SIZES[name]))
+    sc = make_workload(name, variants, n_envs=min(sample_envs, scenegen.CONFIG_SIZES[name]))
     o = oracle.Oracle(sc)
     th = os.cpu_count() or 1
     if warmup:
@@ -219,10 +234,10 @@ def barrier(ws):
         dist.barrier()
 
 
-def time_cpu_baseline(name, n_envs, steps, one_core=False):
+def time_cpu_baseline(name, n_envs, steps, one_core=False, variants=False):
     """The oracle as it stands, on every host core, on a bounded sample."""
     import oracle
-    sc = scenegen.make_scene(name, n_envs=n_envs)
+    sc = make_workload(name, variants, n_envs=n_envs)
     o = oracle.Oracle(sc)
     acts = sc.actions(0, steps)
     cores = os.cpu_count() or 1
@@ -252,7 +267,8 @@ def run_reference(args, ws, rank):
     E = scenegen.CONFIG_SIZES[args.config]
     sample_envs = min(E, 512)
     time_cpu_baseline(args.config, min(sample_envs, 64), 1)        # warm-up (page-in, build)
-    vals = [time_cpu_baseline(args.config, sample_envs, 1)["value"] for _ in range(args.steps)]
+    vals = [time_cpu_baseline(args.config, sample_envs, 1, variants=args.variants)["value"]
+            for _ in range(args.steps)]
     v = statistics.median(vals)
     cores = os.cpu_count() or 1
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": ws,
@@ -260,7 +276,9 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded scenegen scenes)",
             "config": {"workload": WORKLOADS[args.config], "n_envs": E, "n_per_call": 1,
-                       "l2": "not applicable (CPU)"},
+                       "l2": "not applicable (CPU)",
+                       "variants": (dict(VARIANT_PARAMS, restitution=VARIANT_RESTITUTION) if args.variants
+                                    else None)},
             "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{sample_envs} of {E} envs x 1 step per timed step, "
                                        f"median of {args.steps}, {cores} threads"},
@@ -407,6 +425,8 @@ def main():
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000", help="arrival rates (requests/s) of --serve")
     ap.add_argument("--serve-life", type=float, default=500.0, help="mean session lifetime (requests) of --serve")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--variants", action="store_true",
+                    help="velocity damping, restitution and warm starting across steps on")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -435,7 +455,7 @@ def main():
     torch.cuda.set_device(dev)
     name = args.config
     E = scenegen.CONFIG_SIZES[name]
-    sc = scenegen.make_scene(name, seed=None if rank == 0 else 1000 + rank)
+    sc = make_workload(name, args.variants, seed=None if rank == 0 else 1000 + rank)
     n = args.n_per_call
     total_calls = args.warmup + args.steps
     acts_np = sc.actions(0, n * total_calls)
@@ -540,7 +560,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    fl, _ = algorithmic_flops_per_env_step(name, args.warmup, args.steps)
+    fl, _ = algorithmic_flops_per_env_step(name, args.warmup, args.steps, variants=args.variants)
     kernel_s = statistics.mean(times_b) / 1e3
     achieved = fl * E * n / kernel_s / 1e12
     line = {
@@ -548,11 +568,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenegen scenes)",
         "config": {"workload": WORKLOADS[name], "n_envs": E, "n_per_call": n, "path": "batched",
-                   "tuning": tuning, "l2": "flushed (256 MB write) before every timed step"},
+                   "tuning": tuning, "l2": "flushed (256 MB write) before every timed step",
+                   "variants": (dict(VARIANT_PARAMS, restitution=VARIANT_RESTITUTION) if args.variants else None)},
         "plain_value": plain_value,
         "batched_over_plain": None if not plain_value else value / plain_value,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": ncu_traffic(name, tuning),
+                     "frac": achieved / peak_tflops, "traffic": ncu_traffic(name, tuning, args.variants),
                      "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x "
                                   f"{sm_max:.0f} MHz (unit counts and max clock)",
                      "flops_per_env_step": fl},
@@ -572,7 +593,7 @@ def main():
                           "overload_10k_merged": serve_run(10000, 3.0, True, pools=pools),
                           "overload_10k_one_launch_per_request": serve_run(10000, 3.0, False, pools=pools)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20, one_core=True)
+        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20, one_core=True, variants=args.variants)
     print(json.dumps(line), flush=True)
 
 
