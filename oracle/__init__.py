@@ -54,6 +54,7 @@ def lib():
         L.oracle_get_state.argtypes = [P, dp]
         L.oracle_set_state.argtypes = [P, dp]
         L.oracle_get_targets.argtypes = [P, dp]
+        L.oracle_set_targets.argtypes = [P, dp]
         L.oracle_env_status.restype = C.c_uint
         L.oracle_env_status.argtypes = [P, C.c_int]
         L.oracle_env_ties.restype = C.c_longlong
@@ -66,6 +67,11 @@ def lib():
         L.oracle_collide.argtypes = [dp, dp, C.c_double, dp]
         L.oracle_color.argtypes = [C.c_int, ip, ip, ip, ip]
         L.oracle_inertia.argtypes = [dp, dp]
+        up = C.POINTER(C.c_ubyte)
+        L.oracle_set_task.argtypes = [P, ip, dp, C.c_int, dp, dp]
+        L.oracle_task_reset.argtypes = [P, up]
+        L.oracle_step_task.argtypes = [P, dp, C.c_int, C.c_int, C.c_int, dp, up]
+        L.oracle_task_observe.argtypes = [P, dp, up]
         _lib = L
     return _lib
 
@@ -80,6 +86,10 @@ def _ip(a):
 
 def _lp(a):
     return a.ctypes.data_as(C.POINTER(C.c_longlong))
+
+
+def _up(a):
+    return a.ctypes.data_as(C.POINTER(C.c_ubyte))
 
 
 def body_rows(bodies) -> np.ndarray:
@@ -163,6 +173,46 @@ class Oracle:
             lib().oracle_step(self.h, None, 0, n_steps, threads)
         self.steps_done += n_steps
 
+    # ------------------------------------------------------------ pick task
+    def set_task(self, task):
+        """task: dict with grip_joint, finger_a, finger_b, cube, table,
+        grasp_tol, touch_tol, delta_lo[A], delta_hi[A] (scenegen.pick_task)."""
+        idx = np.array([task["grip_joint"], task["finger_a"], task["finger_b"], task["cube"], task["table"]],
+                       np.int32)
+        tol = np.array([task["grasp_tol"], task["touch_tol"]], np.float64)
+        lo = np.ascontiguousarray(task["delta_lo"], np.float64)
+        hi = np.ascontiguousarray(task["delta_hi"], np.float64)
+        assert len(lo) == len(hi) == self.A
+        if lib().oracle_set_task(self.h, _ip(idx), _dp(tol), self.A, _dp(lo), _dp(hi)) != 0:
+            raise ValueError("task indices out of range or of the wrong body type")
+        self.D = 10 + 2 * self.A
+
+    def task_reset(self, mask=None):
+        m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+        lib().oracle_task_reset(self.h, None if m is None else _up(m))
+
+    def step_task(self, n_steps=1, actions=None, threads=1):
+        """Advance n_steps with the task's controller; returns the records
+        [n_steps][E][D] and the tie masks [n_steps][E]."""
+        if actions is None:
+            actions = self.scene.actions(self.steps_done, n_steps)
+        a = np.ascontiguousarray(actions, np.float64)
+        assert a.shape == (n_steps, self.E, self.A), a.shape
+        out = np.zeros((n_steps, self.E, self.D), np.float64)
+        ties = np.zeros((n_steps, self.E), np.uint8)
+        if lib().oracle_step_task(self.h, _dp(a), self.A, n_steps, threads, _dp(out), _up(ties)) != 0:
+            raise RuntimeError("no task set")
+        self.steps_done += n_steps
+        return out, ties
+
+    def observe(self):
+        """The task record of every env at the current state: [E][D], ties [E]."""
+        out = np.zeros((self.E, self.D), np.float64)
+        ties = np.zeros(self.E, np.uint8)
+        if lib().oracle_task_observe(self.h, _dp(out), _up(ties)) != 0:
+            raise RuntimeError("no task set")
+        return out, ties
+
     def state(self) -> np.ndarray:
         out = np.zeros((self.nb, 13), np.float64)
         lib().oracle_get_state(self.h, _dp(out))
@@ -176,6 +226,11 @@ class Oracle:
         out = np.zeros(max(self.nj, 1), np.float64)
         lib().oracle_get_targets(self.h, _dp(out))
         return out[:self.nj]
+
+    def set_targets(self, t):
+        t = np.ascontiguousarray(t, np.float64)
+        assert t.shape == (self.nj,)
+        lib().oracle_set_targets(self.h, _dp(t))
 
     def status(self, env) -> int:
         return int(lib().oracle_env_status(self.h, env))

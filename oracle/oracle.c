@@ -136,6 +136,7 @@ typedef struct {
     int ncons; Constraint* cons; int* order; int ncolors;
     int nrows; Row* rows;
     int nprev; PrevPoint* prev;       /* contact points of the previous step (warm start) */
+    double* qR;                       /* pick task: joint coordinates at the last reset */
     unsigned status; long long ties;
     long long cnt[OC_NUM];
 } Env;
@@ -145,6 +146,10 @@ struct oracle_world {
     double dt; int substeps, pos_iters, vel_iters; v3 g; double margin, vmax;
     int contact_cap, pair_cap;
     double lin_damp, ang_damp, bounce; int warm;
+    /* pick task (off unless set): gripper joint, fingers, object, table */
+    int task_on, t_grip, t_fa, t_fb, t_cube, t_table, t_A;
+    double t_grasp_tol, t_touch_tol;
+    double* t_half;                   /* [t_A] (h - l) / 2 of the delta controller */
     int nb_total, nj_total;
     long long* body_off; long long* joint_off;
 };
@@ -1248,7 +1253,18 @@ static void restitution(const oracle_world* w, Env* e) {
 
 static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
     /* drive targets: NaN keeps the previous target */
-    if (act) for (int j = 0; j < e->nj && j < A; j++) if (!isnan(act[j])) e->joints[j].target = act[j];
+    if (act)
+        for (int j = 0; j < e->nj && j < A; j++) {
+            if (isnan(act[j])) continue;
+            if (w->task_on) {
+                /* delta joint-position controller: clip the normalised action
+                 * to [-1, 1], unnormalise by (h - l) / 2, add to the target */
+                double a = fmin(fmax(act[j], -1.0), 1.0);
+                e->joints[j].target += a * (j < w->t_A ? w->t_half[j] : 0.0);
+            } else {
+                e->joints[j].target = act[j];
+            }
+        }
     broadphase(w, e);
     narrowphase(w, e);
     build_constraints(e);
@@ -1285,6 +1301,101 @@ static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
     restitution(w, e);
     if (w->warm) store_cache(e);
     e->cnt[OC_STEPS]++;
+}
+
+
+/* ------------------------------------------------------------------------- */
+/* pick task (Appendix "Vision-Based Sim2Real": Controller / Action Space,    */
+/* Observation Space, Reward)                                                 */
+/* ------------------------------------------------------------------------- */
+/* joint coordinate: revolute angle or prismatic displacement (as the limits) */
+static double joint_coord(const Env* e, int j) {
+    const Joint* jt = &e->joints[j];
+    BodyView P = view(e, jt->parent), C = view(e, jt->child);
+    return joint_geo(jt, &P, &C).phi;
+}
+
+/* signed distance from body i to the table plane (its local +z through its
+ * origin): the lowest point of the body along the plane normal */
+static double plane_gap(const Env* e, int i, int table) {
+    const Body* T = &e->bodies[table];
+    const Body* B = &e->bodies[i];
+    v3 n = qrot(T->q, V(0, 0, 1));
+    double off = dot(n, sub(B->x, T->x));
+    if (B->type == OR_SPHERE) return off - B->p[0];
+    if (B->type == OR_CAPSULE) return off - fabs(dot(n, qrot(B->q, V(0, 0, 1)))) * B->p[1] - B->p[0];
+    if (B->type == OR_BOX) {
+        double s = 0.0;
+        s += fabs(dot(n, qrot(B->q, V(1, 0, 0)))) * B->p[0];
+        s += fabs(dot(n, qrot(B->q, V(0, 1, 0)))) * B->p[1];
+        s += fabs(dot(n, qrot(B->q, V(0, 0, 1)))) * B->p[2];
+        return off - s;
+    }
+    return off;
+}
+
+/* the reward's distance term: r_dist = 1 - tanh(z * distance) */
+static double r_dist(double dist, double z) { return 1.0 - tanh(z * dist); }
+
+/* One record of D = 10 + 2A values for the env's current state:
+ *   reward, grasped, tcp_close, touch_table, x_tcp[3], x_cube[3],
+ *   q[A] (joint coordinates; 0 past the env's joints), target[A].
+ * tcp = midpoint of the two fingers' centres, g = finger b - finger a,
+ * c = the cube's side (2 x its first half-extent), up = +z:
+ *   r = r_dist(|tcp - x_cube|, 15) + (1 - up . g/|g|)
+ *       + 2 [|tcp - x_cube| <= c/2] r_dist(| |g| - c |, 40)
+ *       + [grasped] (1 + 3 r_dist(|q - q_reset|, 4/pi)) - 2 [touch_table]
+ * grasped: the gripper joint is more than grasp_tol from its target (the
+ * object blocks it); touch_table: a finger within touch_tol of the table.
+ * Returns a mask of decisions within 1e-5 of their threshold (1 grasped,
+ * 2 tcp_close, 4 touch_table). */
+static unsigned task_record(const oracle_world* w, const Env* e, double* out) {
+    int A = w->t_A;
+    unsigned ties = 0;
+    const Body* fa = &e->bodies[w->t_fa];
+    const Body* fb = &e->bodies[w->t_fb];
+    const Body* cu = &e->bodies[w->t_cube];
+    v3 tcp = scl(add(fa->x, fb->x), 0.5);
+    v3 g = sub(fb->x, fa->x);
+    double gl = norm(g);
+    double c = 2.0 * cu->p[0];
+    double dtc = norm(sub(tcp, cu->x));
+    double r = r_dist(dtc, 15.0);
+    r += gl > 0.0 ? 1.0 - g.z / gl : 1.0;
+    int close = dtc <= 0.5 * c;
+    if (fabs(dtc - 0.5 * c) < TIE_EPS) ties |= 2u;
+    if (close) r += 2.0 * r_dist(fabs(gl - c), 40.0);
+    double qd2 = 0.0;
+    for (int j = 0; j < A; j++) {
+        double q = j < e->nj ? joint_coord(e, j) : 0.0;
+        out[10 + j] = q;
+        out[10 + A + j] = j < e->nj ? e->joints[j].target : 0.0;
+        if (j < e->nj) qd2 += (q - e->qR[j]) * (q - e->qR[j]);
+    }
+    int grasped = 0;
+    if (w->t_grip >= 0 && w->t_grip < e->nj) {
+        double dq = fabs(out[10 + w->t_grip] - e->joints[w->t_grip].target);
+        grasped = dq > w->t_grasp_tol;
+        if (fabs(dq - w->t_grasp_tol) < TIE_EPS) ties |= 1u;
+    }
+    if (grasped) r += 1.0 + 3.0 * r_dist(sqrt(qd2), 4.0 / M_PI);
+    double ga = plane_gap(e, w->t_fa, w->t_table), gb = plane_gap(e, w->t_fb, w->t_table);
+    int touch = ga <= w->t_touch_tol || gb <= w->t_touch_tol;
+    if (fabs(ga - w->t_touch_tol) < TIE_EPS || fabs(gb - w->t_touch_tol) < TIE_EPS) ties |= 4u;
+    if (touch) r -= 2.0;
+    out[0] = r; out[1] = grasped; out[2] = close; out[3] = touch;
+    out[4] = tcp.x; out[5] = tcp.y; out[6] = tcp.z;
+    out[7] = cu->x.x; out[8] = cu->x.y; out[9] = cu->x.z;
+    return ties;
+}
+
+/* reset of the controller (after an env reset): target = q = q_reset */
+static void task_reset_env(Env* e) {
+    for (int j = 0; j < e->nj; j++) {
+        double q = joint_coord(e, j);
+        e->joints[j].target = q;
+        e->qR[j] = q;
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1340,29 +1451,40 @@ void oracle_destroy(oracle_world* w) {
     for (int i = 0; i < w->E; i++) {
         Env* e = &w->envs[i];
         free(e->bodies); free(e->joints); free(e->pairs); free(e->tiepairs); free(e->man);
-        free(e->cons); free(e->order); free(e->rows); free(e->prev);
+        free(e->cons); free(e->order); free(e->rows); free(e->prev); free(e->qR);
     }
-    free(w->envs); free(w->body_off); free(w->joint_off); free(w);
+    free(w->envs); free(w->body_off); free(w->joint_off); free(w->t_half); free(w);
 }
 
-typedef struct { oracle_world* w; const double* act; int A, n_steps, e0, e1; } Job;
+typedef struct {
+    oracle_world* w; const double* act; int A, n_steps, e0, e1;
+    double* out; unsigned char* ties;   /* task records [n_steps][E][D] and tie masks, or NULL */
+} Job;
 
 static void* run_job(void* p) {
     Job* j = (Job*)p;
+    oracle_world* w = j->w;
+    int D = 10 + 2 * w->t_A;
     for (int k = 0; k < j->n_steps; k++)
-        for (int ei = j->e0; ei < j->e1; ei++)
-            env_step(j->w, &j->w->envs[ei],
-                     j->act ? j->act + ((size_t)k * j->w->E + ei) * j->A : NULL, j->A);
+        for (int ei = j->e0; ei < j->e1; ei++) {
+            env_step(w, &w->envs[ei], j->act ? j->act + ((size_t)k * w->E + ei) * j->A : NULL, j->A);
+            if (j->out) {
+                unsigned t = task_record(w, &w->envs[ei], j->out + ((size_t)k * w->E + ei) * D);
+                if (j->ties) j->ties[(size_t)k * w->E + ei] = (unsigned char)t;
+            }
+        }
     return NULL;
 }
 
-int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int n_threads) {
+static int step_jobs(oracle_world* w, const double* actions, int A, int n_steps, int n_threads, double* out,
+                     unsigned char* ties) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > w->E) n_threads = w->E > 0 ? w->E : 1;
     Job* jobs = (Job*)calloc((size_t)n_threads, sizeof(Job));
     pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
     for (int t = 0; t < n_threads; t++) {
         jobs[t].w = w; jobs[t].act = actions; jobs[t].A = A; jobs[t].n_steps = n_steps;
+        jobs[t].out = out; jobs[t].ties = ties;
         jobs[t].e0 = (int)((long long)w->E * t / n_threads);
         jobs[t].e1 = (int)((long long)w->E * (t + 1) / n_threads);
     }
@@ -1372,6 +1494,56 @@ int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int 
         for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
     }
     free(jobs); free(th);
+    return 0;
+}
+
+int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int n_threads) {
+    return step_jobs(w, actions, A, n_steps, n_threads, NULL, NULL);
+}
+
+int oracle_step_task(oracle_world* w, const double* actions, int A, int n_steps, int n_threads, double* out,
+                     unsigned char* ties) {
+    if (!w->task_on) return -1;
+    return step_jobs(w, actions, A, n_steps, n_threads, out, ties);
+}
+
+int oracle_set_task(oracle_world* w, const int* idx, const double* tol, int A, const double* lo, const double* hi) {
+    for (int ei = 0; ei < w->E; ei++) {
+        const Env* e = &w->envs[ei];
+        int bodies[4] = {idx[1], idx[2], idx[3], idx[4]};
+        for (int k = 0; k < 4; k++) if (bodies[k] < 0 || bodies[k] >= e->nb) return -1;
+        if (idx[0] >= e->nj) return -1;
+        if (e->bodies[idx[3]].type != OR_BOX || e->bodies[idx[4]].type != OR_PLANE) return -1;
+    }
+    w->task_on = 1;
+    w->t_grip = idx[0]; w->t_fa = idx[1]; w->t_fb = idx[2]; w->t_cube = idx[3]; w->t_table = idx[4];
+    w->t_grasp_tol = tol[0]; w->t_touch_tol = tol[1];
+    w->t_A = A;
+    free(w->t_half);
+    w->t_half = (double*)calloc((size_t)(A > 0 ? A : 1), sizeof(double));
+    for (int j = 0; j < A; j++) w->t_half[j] = 0.5 * (hi[j] - lo[j]);
+    for (int ei = 0; ei < w->E; ei++) {
+        Env* e = &w->envs[ei];
+        free(e->qR);
+        e->qR = (double*)calloc((size_t)(e->nj > 0 ? e->nj : 1), sizeof(double));
+        task_reset_env(e);
+    }
+    return 0;
+}
+
+void oracle_task_reset(oracle_world* w, const unsigned char* mask) {
+    if (!w->task_on) return;
+    for (int ei = 0; ei < w->E; ei++)
+        if (!mask || mask[ei]) task_reset_env(&w->envs[ei]);
+}
+
+int oracle_task_observe(const oracle_world* w, double* out, unsigned char* ties) {
+    if (!w->task_on) return -1;
+    int D = 10 + 2 * w->t_A;
+    for (int ei = 0; ei < w->E; ei++) {
+        unsigned t = task_record(w, &w->envs[ei], out + (size_t)ei * D);
+        if (ties) ties[ei] = (unsigned char)t;
+    }
     return 0;
 }
 
@@ -1409,6 +1581,13 @@ void oracle_get_targets(const oracle_world* w, double* out) {
     for (int ei = 0; ei < w->E; ei++) {
         const Env* e = &w->envs[ei];
         for (int j = 0; j < e->nj; j++) out[w->joint_off[ei] + j] = e->joints[j].target;
+    }
+}
+
+void oracle_set_targets(oracle_world* w, const double* in) {
+    for (int ei = 0; ei < w->E; ei++) {
+        Env* e = &w->envs[ei];
+        for (int j = 0; j < e->nj; j++) e->joints[j].target = in[w->joint_off[ei] + j];
     }
 }
 

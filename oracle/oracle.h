@@ -79,6 +79,8 @@ void oracle_get_state(const oracle_world* w, double* out);
 void oracle_set_state(oracle_world* w, const double* in);
 /* Current drive targets [n_joints]. */
 void oracle_get_targets(const oracle_world* w, double* out);
+/* Overwrite the drive targets [n_joints]. */
+void oracle_set_targets(oracle_world* w, const double* in);
 
 unsigned oracle_env_status(const oracle_world* w, int env);
 /* Number of discrete decisions of the env (since create) whose deciding
@@ -113,6 +115,29 @@ int oracle_color(int n_cons, const int* a, const int* b, const int* dyn, int* co
 
 /* Body-frame diagonal inertia of a descriptor row (mass > 0). */
 void oracle_inertia(const double* body, double* out3);
+
+/* Pick task of the paper's sim2real appendix (Controller / Action Space,
+ * Observation Space, Reward).  idx = {gripper joint (-1 = none), finger a,
+ * finger b, cube (a box), table (a plane)}, env-local and the same in every
+ * env; tol = {grasp_tol, touch_tol}; lo, hi [A] the delta controller's bounds
+ * per joint slot.  Once set, an action a is a normalised delta: the target
+ * moves by clip(a, -1, 1) (h - l) / 2 (NaN: no change).  Setting the task
+ * resets the controller of every env (target = q = q_reset).  Returns -1
+ * (nothing changed) when an index is out of range or of the wrong type. */
+int oracle_set_task(oracle_world* w, const int* idx, const double* tol, int A, const double* lo,
+                    const double* hi);
+/* Controller reset of the envs with mask[e] != 0 (all if mask is NULL):
+ * target = q = q_reset from the current state. */
+void oracle_task_reset(oracle_world* w, const unsigned char* mask);
+/* oracle_step plus one task record per step and env: out [n_steps][E][D],
+ * D = 10 + 2A = reward, grasped, tcp_close, touch_table, x_tcp[3],
+ * x_cube[3], q[A], target[A]; ties [n_steps][E] (nullable) = decisions
+ * within 1e-5 of their threshold (1 grasped, 2 tcp_close, 4 touch_table).
+ * Returns -1 when no task is set. */
+int oracle_step_task(oracle_world* w, const double* actions, int A, int n_steps, int n_threads, double* out,
+                     unsigned char* ties);
+/* The record of every env at the current state: out [E][D], ties [E]. */
+int oracle_task_observe(const oracle_world* w, double* out, unsigned char* ties);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,7 @@ class Scene:
     n_act: int                  # A: action slots per env per step (0 = none)
     seed: int
     action_fn: Optional[Callable[[int, int], np.ndarray]] = None
+    task: Optional[Dict] = None  # pick task (pick_task); actions are then normalised deltas
 
     @property
     def n_envs(self) -> int:
@@ -97,7 +98,7 @@ class Scene:
                      np.asarray(bo, np.int32),
                      np.concatenate(jl) if jl else np.zeros(0, JOINT_DTYPE),
                      np.asarray(jo, np.int32), dict(self.params), self.n_act,
-                     self.seed, fn if self.action_fn else None)
+                     self.seed, fn if self.action_fn else None, self.task)
 
 
 def rng(seed: int, env: int, stream: int) -> np.random.Generator:
@@ -384,14 +385,53 @@ def make_hand(n_envs=4096, seed=4, kp=10.0, kd=0.3) -> Scene:
     return pack("hand", envs_b, envs_j, params, n_act, seed, actions)
 
 
+# ----------------------------------------------------------------------------
+# Config "pick": the arm envs driven by the pick task of the paper's sim2real
+# appendix -- a target delta joint-position controller with normalised
+# actions, proprioception, an is-grasped flag and the dense reward.
+# ----------------------------------------------------------------------------
+def pick_task(n_act=9) -> Dict:
+    """Task descriptor of the arm envs (env-local indices: plane 0, fingers
+    9 and 10, cube 11; joints 0-6 revolute, 7-8 the prismatic fingers).
+    Delta bounds: +-0.05 rad per step for the revolute joints (the paper's
+    Koch values), +-0.005 m for the fingers; grasp_tol 0.005 m on finger
+    joint 7 (the paper's 0.02 is in radians for a revolute gripper); a
+    finger within 1 mm of the table touches it.  float32 values, as the GPU
+    path stores them."""
+    lo = np.array([-0.05] * 7 + [-0.005] * 2, np.float32)
+    return dict(grip_joint=7, finger_a=9, finger_b=10, cube=11, table=0,
+                grasp_tol=float(np.float32(0.005)), touch_tol=float(np.float32(0.001)),
+                delta_lo=lo[:n_act], delta_hi=-lo[:n_act])
+
+
+def make_pick(n_envs=4096, seed=6, nan_frac=0.02, scale=0.7) -> Scene:
+    sc = make_arm(n_envs=n_envs, seed=seed)
+    A = sc.n_act
+
+    def actions(step0, n):
+        # normalised deltas ~ N(0, scale) (some beyond +-1: clipped by the
+        # controller), nan_frac of the slots NaN (no change)
+        out = np.empty((n, n_envs, A), np.float32)
+        for k in range(n):
+            g = step_rng(seed, step0 + k, 2)
+            out[k] = g.standard_normal((n_envs, A)) * scale
+            out[k][g.random((n_envs, A)) < nan_frac] = np.nan
+        return out
+    sc.name = "pick"
+    sc.action_fn = actions
+    sc.task = pick_task(A)
+    return sc
+
+
 CONFIGS = {
     "small": make_small,
     "arm": make_arm,
     "clutter": make_clutter,
     "hand": make_hand,
+    "pick": make_pick,
 }
 
-CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096}
+CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096, "pick": 4096}
 
 
 def make_scene(name: str, n_envs: Optional[int] = None, seed: Optional[int] = None, **kw) -> Scene:

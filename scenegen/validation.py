@@ -151,3 +151,30 @@ def _qmul(a, b):
     bv, bw = np.asarray(b[:3]), b[3]
     v = aw * bv + bw * av + np.cross(av, bv)
     return np.array([v[0], v[1], v[2], aw * bw - av @ bv])
+
+
+def grasp_probe(n_envs=1, **pk):
+    """Probe of the pick task's observations and reward (no stepping needed):
+    table plane (0); cube of side 0.04 (1) at (0.4, 0, 0.5); two box fingers
+    (2, 3; half-extents 0.01, 0.01, 0.03) on prismatic joints along world +y
+    through (0.4, 0, 0.5), at y = -0.02 and +0.02 (their joint coordinates);
+    a capsule link (4) on a revolute joint about world +y at (0, 0, 1), angle
+    0.  Joints: 0 revolute, 1 finger a (the gripper joint), 2 finger b."""
+    qy = axis_angle_quat((0, 0, 1), math.pi / 2)      # frame +x -> world +y
+    fh = (0.01, 0.01, 0.03)
+    envs_b, envs_j = [], []
+    for _ in range(n_envs):
+        envs_b.append([body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), group=1),
+                       body(BOX, (0.02, 0.02, 0.02), 0.05, (0.4, 0.0, 0.5), group=2),
+                       body(BOX, fh, 0.05, (0.4, -0.02, 0.5), group=4, mask=1),
+                       body(BOX, fh, 0.05, (0.4, 0.02, 0.5), group=4, mask=1),
+                       body(CAPSULE, (0.02, 0.1, 0), 1.0, (0.0, 0.0, 1.0), group=8, mask=0)])
+        envs_j.append([joint(REVOLUTE, -1, 4, (0, 0, 1.0, *qy), (0, 0, 0, *qy), -3.0, 3.0, 0, 0, 0),
+                       joint(PRISMATIC, -1, 2, (0.4, 0, 0.5, *qy), (0, 0, 0, *qy), -0.05, 0.05, 0, 0, 0),
+                       joint(PRISMATIC, -1, 3, (0.4, 0, 0.5, *qy), (0, 0, 0, *qy), -0.05, 0.05, 0, 0, 0)])
+    sc = pack("grasp_probe", envs_b, envs_j, default_params(**pk), 3, 0)
+    lo = np.array([-0.05, -0.005, -0.005], np.float32)
+    sc.task = dict(grip_joint=1, finger_a=2, finger_b=3, cube=1, table=0,
+                   grasp_tol=float(np.float32(0.005)), touch_tol=float(np.float32(0.001)),
+                   delta_lo=lo, delta_hi=-lo)
+    return sc
