@@ -170,8 +170,9 @@ ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_o
  * (n_steps, tuning) in a CUDA graph and replayed.
  * actions: device float [n_steps][n_envs][A] drive targets (A = the
  * batch's max joints per env), NaN = keep the previous target; NULL = no
- * change.  Must stay valid until the stream reaches the step.  Asynchronous:
- * returns after enqueueing. */
+ * change (with a task set, normalised deltas: see ms_set_task).  Must stay
+ * valid until the stream reaches the step.  Asynchronous: returns after
+ * enqueueing. */
 ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream);
 
 /* Same step through the plain comparison path: one block per env and one
@@ -206,6 +207,73 @@ ms_status ms_destroy(ms_batch* b);
 
 /* Thread-local description of the last error, "" if none. */
 const char* ms_last_error(void);
+
+/* ----------------------------------------------------------------------- */
+/* Pick task: controller, observations, reward                              */
+/* ----------------------------------------------------------------------- */
+
+/* The pick task of the paper's sim2real appendix (Controller / Action Space,
+ * Observation Space, Reward), run inside the step's kernels.  Indices are
+ * env-local and must be valid in every env of the batch:
+ *   grip_joint: the gripper joint (-1: none, never grasped); finger_a,
+ *   finger_b: the two finger bodies (tcp = midpoint of their centres, g =
+ *   finger_b - finger_a); cube: a box body (side c = 2 x its first
+ *   half-extent); table: a plane body.
+ *   grasp_tol: grasped = the gripper joint is more than grasp_tol (rad or m)
+ *   from its target, i.e. something blocks it.  touch_tol (m): a finger
+ *   whose lowest point is within touch_tol of the table touches it.
+ *   n_joints must equal the batch's A (max joints per env); delta_lo,
+ *   delta_hi: host float [A], the delta controller's bounds per joint slot.
+ * With a task set, an action is a normalised delta: the joint's target
+ * moves by clip(a, -1, 1) (h - l) / 2 each step (NaN: no change). */
+typedef struct {
+    int32_t grip_joint;
+    int32_t finger_a, finger_b;
+    int32_t cube;
+    int32_t table;
+    float grasp_tol;
+    float touch_tol;
+    int32_t n_joints;
+    const float* delta_lo;
+    const float* delta_hi;
+} ms_task_desc;
+
+/* Set (t != NULL) or remove (t == NULL) the batch's task.  Setting it resets
+ * the controller of every env (ms_task_reset) on `stream`.  The descriptor
+ * is copied.  Errors (synchronous, nothing changed): MS_ERR_INVALID_ARG for
+ * an index out of range in some env, a cube that is not a box, a table that
+ * is not a plane, n_joints != A, a negative or non-finite tolerance or
+ * bound. */
+ms_status ms_set_task(ms_batch* b, const ms_task_desc* t, void* stream);
+
+/* Controller reset of the envs whose env_mask byte is non-zero (NULL = all;
+ * host array of n_envs bytes): each joint's target and its reset coordinate
+ * q_reset (used by the reward) become its current coordinate.  A partial
+ * reset is ms_set_state(mask) followed by ms_task_reset(mask).
+ * MS_ERR_INVALID_ARG without a task.  Returns after the mask is copied. */
+ms_status ms_task_reset(ms_batch* b, const uint8_t* env_mask, void* stream);
+
+/* Length of one task record: 10 + 2 A floats =
+ *   reward, grasped (0/1), tcp_close (0/1), touch_table (0/1), x_tcp[3],
+ *   x_cube[3], q[A] (joint coordinates, 0 past the env's joints),
+ *   target[A].  reward = r_dist(|tcp - x_cube|, 15) + (1 - g.z / |g|)
+ *   + 2 tcp_close r_dist(| |g| - c |, 40) + grasped (1 + 3 r_dist(
+ *   |q - q_reset|, 4 / pi)) - 2 touch_table, r_dist(d, z) = 1 - tanh(z d),
+ *   tcp_close = |tcp - x_cube| <= c / 2.  An env frozen by a non-finite
+ *   state writes NaN. */
+int ms_task_record_len(const ms_batch* b);
+
+/* The record of every env at the current state into out (device float
+ * [n_envs][ms_task_record_len]), on `stream`.  MS_ERR_INVALID_ARG without a
+ * task. */
+ms_status ms_task_observe(ms_batch* b, float* out, void* stream);
+
+/* ms_step (flags 0) or ms_step_plain (flags MS_STEP_PLAIN) that also writes
+ * one task record per step and env into out (device float
+ * [n_steps][n_envs][ms_task_record_len], nullable; non-NULL needs a task).
+ * out must stay valid until the stream reaches the step. */
+enum { MS_STEP_PLAIN = 1 };
+ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, float* out, int flags, void* stream);
 
 /* ----------------------------------------------------------------------- */
 /* Introspection and tuning                                                */

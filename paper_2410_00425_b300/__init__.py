@@ -45,18 +45,44 @@ class Batch:
         except Exception:
             pass
 
-    def step(self, actions=None, n_steps: int = 1, stream=None, plain: bool = False):
-        """actions: CUDA float32 tensor [n_steps, E, A] (NaN keeps a target)."""
-        if actions is not None:
-            import torch
-            assert actions.is_cuda and actions.dtype == torch.float32 and actions.is_contiguous()
-            assert tuple(actions.shape) == (n_steps, self.E, self.A), (tuple(actions.shape), (n_steps, self.E, self.A))
+    def step(self, actions=None, n_steps: int = 1, stream=None, plain: bool = False, out=None):
+        """actions: CUDA float32 tensor [n_steps, E, A] (NaN keeps a target;
+        normalised deltas once a task is set).  out: CUDA float32 tensor
+        [n_steps, E, record_len] receiving the task records, or None."""
+        import torch
+        for t, shape in ((actions, (n_steps, self.E, self.A)), (out, (n_steps, self.E, self.record_len()))):
+            if t is None:
+                continue
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+            assert tuple(t.shape) == shape, (tuple(t.shape), shape)
             if isinstance(stream, torch.cuda.Stream):
-                # the step reads the tensor on `stream`: keep its memory from
+                # the step uses the tensor on `stream`: keep its memory from
                 # being reused by the caching allocator until then
-                actions.record_stream(stream)
-        fn = _ffi.ms_step_plain if plain else _ffi.ms_step
-        fn(self.h, actions, n_steps, stream)
+                t.record_stream(stream)
+        if out is None:
+            fn = _ffi.ms_step_plain if plain else _ffi.ms_step
+            fn(self.h, actions, n_steps, stream)
+        else:
+            _ffi.ms_step_ex(self.h, actions, n_steps, out, _ffi.MS_STEP_PLAIN if plain else 0, stream)
+
+    # ---------------------------------------------------------- pick task
+    def set_task(self, task, stream=None):
+        """Set (dict, see scenegen.pick_task) or remove (None) the pick task;
+        setting it resets every env's controller."""
+        _ffi.ms_set_task(self.h, task, stream)
+
+    def task_reset(self, env_mask=None, stream=None):
+        _ffi.ms_task_reset(self.h, env_mask, stream)
+
+    def record_len(self) -> int:
+        return _ffi.ms_task_record_len(self.h)
+
+    def observe(self, stream=None):
+        """Task records of every env at the current state, [E, record_len]."""
+        import torch
+        out = torch.empty((self.E, self.record_len()), dtype=torch.float32, device="cuda")
+        _ffi.ms_task_observe(self.h, out, stream)
+        return out
 
     def state(self, stream=None):
         """Device copy of the state, float32 [n_bodies, 13]."""

@@ -56,6 +56,15 @@ class ms_noalloc_batch(C.Structure):
                 ("w", C.c_void_p), ("targets", C.c_void_p), ("status", C.c_void_p)]
 
 
+class ms_task_desc(C.Structure):
+    _fields_ = [("grip_joint", C.c_int32), ("finger_a", C.c_int32), ("finger_b", C.c_int32),
+                ("cube", C.c_int32), ("table", C.c_int32), ("grasp_tol", C.c_float), ("touch_tol", C.c_float),
+                ("n_joints", C.c_int32), ("delta_lo", C.c_void_p), ("delta_hi", C.c_void_p)]
+
+
+MS_STEP_PLAIN = 1
+
+
 class ms_tuning(C.Structure):
     _fields_ = [("lanes_per_env", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("rows_in_smem", C.c_int32), ("ctas_per_sm", C.c_int32)]
@@ -87,6 +96,11 @@ _SIGS = [
                                     C.POINTER(C.c_size_t)]),
     ("ms_abi_sizes", None, [C.c_void_p]),
     ("ms_step_noalloc", C.c_int, [C.c_void_p, C.POINTER(ms_sim_params), C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_set_task", C.c_int, [C.c_void_p, C.POINTER(ms_task_desc), C.c_void_p]),
+    ("ms_task_reset", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ms_task_record_len", C.c_int, [C.c_void_p]),
+    ("ms_task_observe", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ms_step_ex", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
 ]
 
 EXPORTS = [s[0] for s in _SIGS]
@@ -178,6 +192,37 @@ def ms_step(b, actions=None, n_steps=1, stream=None):
 
 def ms_step_plain(b, actions=None, n_steps=1, stream=None):
     return check(load().ms_step_plain(b, _ptr(actions), n_steps, _stream(stream)))
+
+
+def ms_step_ex(b, actions=None, n_steps=1, out=None, flags=0, stream=None):
+    return check(load().ms_step_ex(b, _ptr(actions), n_steps, _ptr(out), flags, _stream(stream)))
+
+
+def ms_set_task(b, task, stream=None):
+    """task: dict (grip_joint, finger_a, finger_b, cube, table, grasp_tol,
+    touch_tol, delta_lo[A], delta_hi[A]) or None to remove it."""
+    L = load()
+    if task is None:
+        return check(L.ms_set_task(b, None, _stream(stream)))
+    lo = np.ascontiguousarray(task["delta_lo"], np.float32)
+    hi = np.ascontiguousarray(task["delta_hi"], np.float32)
+    t = ms_task_desc(int(task["grip_joint"]), int(task["finger_a"]), int(task["finger_b"]), int(task["cube"]),
+                     int(task["table"]), float(task["grasp_tol"]), float(task["touch_tol"]), len(lo),
+                     lo.ctypes.data, hi.ctypes.data)
+    return check(L.ms_set_task(b, C.byref(t), _stream(stream)))
+
+
+def ms_task_reset(b, env_mask=None, stream=None):
+    m = None if env_mask is None else np.ascontiguousarray(env_mask, np.uint8)
+    return check(load().ms_task_reset(b, None if m is None else m.ctypes.data, _stream(stream)))
+
+
+def ms_task_record_len(b) -> int:
+    return int(load().ms_task_record_len(b))
+
+
+def ms_task_observe(b, out, stream=None):
+    return check(load().ms_task_observe(b, _ptr(out), _stream(stream)))
 
 
 def ms_get_state(b) -> ms_state_view:

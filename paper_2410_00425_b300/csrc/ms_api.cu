@@ -91,6 +91,11 @@ struct ms_batch {
     int sm_count = 0;
     size_t smem_optin = 0;
     std::vector<int> h_body_off, h_joint_off;
+    std::vector<uint8_t> h_type;      // shape type per body
+    // pick task
+    float* d_task_half = nullptr;     // [A]
+    float* d_task_qR = nullptr;       // [NJ]
+    std::vector<float> h_task_half;
 };
 
 // Device memory comes from the device's stream-ordered pool on the batch's
@@ -286,6 +291,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     std::vector<float4> jf(4 * (size_t)b->NJ), jp(b->NJ);
     std::vector<int4> jm(b->NJ);
     std::vector<float> jt(b->NJ);
+    b->h_type.assign(b->NB, 0);
     for (int e = 0; e < E; e++) {
         int b0 = b->h_body_off[e], j0 = b->h_joint_off[e];
         for (int i = 0; i < nb_of[e]; i++) {
@@ -311,6 +317,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
             }
             meta[k] = make_int2(d.type | (dyn ? 1 << 8 : 0), (int)((unsigned)d.group | ((unsigned)d.mask << 16)));
             body_env[k] = e;
+            b->h_type[k] = (uint8_t)d.type;
         }
         for (int j = 0; j < nj_of[e]; j++) {
             const ms_joint_desc& d = joints_of[e][j];
@@ -446,14 +453,7 @@ static ms_status check_step_args(ms_batch* b, int n_steps) {
 }
 
 extern "C" ms_status ms_step_plain(ms_batch* b, const float* actions, int n_steps, void* stream) {
-    ms_status s = check_step_args(b, n_steps);
-    if (s) return s;
-    if ((s = ensure_plain(b)) != MS_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    launch_plain(b->D, actions, n_steps, st);
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(b->done, st));
-    return MS_OK;
+    return ms_step_ex(b, actions, n_steps, nullptr, MS_STEP_PLAIN, stream);
 }
 
 // ------------------------------------------------------------- batched path
@@ -533,20 +533,28 @@ static FusedCfg fused_cfg(ms_batch* b) {
     return C;
 }
 
-static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
+// the batch's device view with this call's record buffer
+static DevBatch call_view(const ms_batch* b, float* out) {
+    DevBatch D = b->D;
+    D.T.out = out;
+    return D;
+}
+
+static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, float* out, cudaStream_t st) {
     CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
-    CK(launch_fused(b->D, actions, n_steps, fused_cfg(b), b->tune.G, b->fused_grid, b->fused_threads, b->fused_smem, st));
+    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_grid, b->fused_threads,
+                    b->fused_smem, st));
     return MS_OK;
 }
 
-static ms_status step_enqueue(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
-    if (st == nullptr) return enqueue_fused(b, actions, n_steps, st);   // the legacy stream cannot be captured
+static ms_status step_enqueue(ms_batch* b, const float* actions, int n_steps, float* out, cudaStream_t st) {
+    if (st == nullptr) return enqueue_fused(b, actions, n_steps, out, st);   // the legacy stream cannot be captured
     long long key = (long long)n_steps;
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        ms_status es = enqueue_fused(b, actions, n_steps, st);
+        ms_status es = enqueue_fused(b, actions, n_steps, out, st);
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (es) return es;
         if (ce != cudaSuccess) return fail(MS_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ce));
@@ -566,9 +574,9 @@ static ms_status step_enqueue(ms_batch* b, const float* actions, int n_steps, cu
         CK(cudaGraphLaunch(it->second.exec, st));
         return MS_OK;
     }
-    // the actions pointer is the only argument that changes between calls
+    // the actions and record pointers are the arguments that change between calls
     GraphEntry& ge = it->second;
-    DevBatch Dv = b->D;
+    DevBatch Dv = call_view(b, out);
     const float* act = actions;
     int ns = n_steps;
     FusedCfg C = fused_cfg(b);
@@ -581,13 +589,106 @@ static ms_status step_enqueue(ms_batch* b, const float* actions, int n_steps, cu
     return MS_OK;
 }
 
-extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
+extern "C" ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, float* out, int flags,
+                                void* stream) {
     ms_status s = check_step_args(b, n_steps);
     if (s) return s;
+    if (flags & ~MS_STEP_PLAIN) return fail(MS_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (out && !b->D.T.on) return fail(MS_ERR_INVALID_ARG, "task records requested but no task is set");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (flags & MS_STEP_PLAIN) {
+        if ((s = ensure_plain(b)) != MS_OK) return s;
+        launch_plain(call_view(b, out), actions, n_steps, st);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(b->done, st));
+        return MS_OK;
+    }
     if (n_steps == 0) return MS_OK;
     if ((s = configure_fused(b)) != MS_OK) return s;
+    if ((s = step_enqueue(b, actions, n_steps, out, st)) != MS_OK) return s;
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
+}
+
+extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
+    return ms_step_ex(b, actions, n_steps, nullptr, 0, stream);
+}
+
+// ---------------------------------------------------------------- pick task
+extern "C" ms_status ms_set_task(ms_batch* b, const ms_task_desc* t, void* stream) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (!t) {
+        b->D.T = DevTask{};
+        return MS_OK;
+    }
+    if (t->n_joints != b->A) return fail(MS_ERR_INVALID_ARG, "task n_joints %d != the batch's A %d", t->n_joints, b->A);
+    if (b->A > 0 && (!t->delta_lo || !t->delta_hi)) return fail(MS_ERR_INVALID_ARG, "delta_lo / delta_hi NULL");
+    if (!(std::isfinite(t->grasp_tol) && t->grasp_tol >= 0.f && std::isfinite(t->touch_tol) && t->touch_tol >= 0.f))
+        return fail(MS_ERR_INVALID_ARG, "grasp_tol / touch_tol must be finite and >= 0");
+    for (int j = 0; j < b->A; j++)
+        if (!(std::isfinite(t->delta_lo[j]) && std::isfinite(t->delta_hi[j])))
+            return fail(MS_ERR_INVALID_ARG, "delta bound %d not finite", j);
+    for (int e = 0; e < b->E; e++) {
+        int nb = b->h_body_off[e + 1] - b->h_body_off[e], nj = b->h_joint_off[e + 1] - b->h_joint_off[e];
+        const int bodies[4] = {t->finger_a, t->finger_b, t->cube, t->table};
+        for (int k = 0; k < 4; k++)
+            if (bodies[k] < 0 || bodies[k] >= nb)
+                return fail(MS_ERR_INVALID_ARG, "env %d: task body index %d out of range [0, %d)", e, bodies[k], nb);
+        if (t->grip_joint < -1 || t->grip_joint >= nj)
+            return fail(MS_ERR_INVALID_ARG, "env %d: grip_joint %d out of range", e, t->grip_joint);
+        if (b->h_type[b->h_body_off[e] + t->cube] != MS_BOX) return fail(MS_ERR_INVALID_ARG, "env %d: cube is not a box", e);
+        if (b->h_type[b->h_body_off[e] + t->table] != MS_PLANE)
+            return fail(MS_ERR_INVALID_ARG, "env %d: table is not a plane", e);
+    }
+    ms_status s;
+    if (!b->d_task_half) {
+        if ((s = dmalloc(b, (void**)&b->d_task_half, sizeof(float) * std::max(b->A, 1))) != MS_OK) return s;
+        if ((s = dmalloc(b, (void**)&b->d_task_qR, sizeof(float) * std::max(b->NJ, 1))) != MS_OK) return s;
+    }
     cudaStream_t st = (cudaStream_t)stream;
-    if ((s = step_enqueue(b, actions, n_steps, st)) != MS_OK) return s;
+    b->h_task_half.assign(std::max(b->A, 1), 0.f);
+    for (int j = 0; j < b->A; j++) b->h_task_half[j] = 0.5f * (t->delta_hi[j] - t->delta_lo[j]);
+    CK(cudaMemcpyAsync(b->d_task_half, b->h_task_half.data(), sizeof(float) * b->h_task_half.size(),
+                       cudaMemcpyHostToDevice, st));
+    DevTask T{};
+    T.on = 1;
+    T.grip = t->grip_joint; T.fa = t->finger_a; T.fb = t->finger_b; T.cube = t->cube; T.table = t->table;
+    T.grasp_tol = t->grasp_tol; T.touch_tol = t->touch_tol;
+    T.half = b->d_task_half;
+    T.qR = b->d_task_qR;
+    T.out = nullptr;
+    T.D = 10 + 2 * b->A;
+    b->D.T = T;
+    launch_task_reset(b->D, nullptr, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));           // the host copy of the bounds is reused by the next call
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
+}
+
+extern "C" ms_status ms_task_reset(ms_batch* b, const uint8_t* env_mask, void* stream) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->D.T.on) return fail(MS_ERR_INVALID_ARG, "no task is set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t* dmask = nullptr;
+    if (env_mask) {
+        CK(cudaMemcpyAsync(b->d_mask, env_mask, (size_t)b->E, cudaMemcpyHostToDevice, st));
+        dmask = b->d_mask;
+    }
+    launch_task_reset(b->D, dmask, st);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
+}
+
+extern "C" int ms_task_record_len(const ms_batch* b) { return b && b->D.T.on ? b->D.T.D : 0; }
+
+extern "C" ms_status ms_task_observe(ms_batch* b, float* out, void* stream) {
+    if (!b || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->D.T.on) return fail(MS_ERR_INVALID_ARG, "no task is set");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_task_observe(b->D, out, st);
+    CK(cudaGetLastError());
     CK(cudaEventRecord(b->done, st));
     return MS_OK;
 }

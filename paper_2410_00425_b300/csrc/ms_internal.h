@@ -60,9 +60,22 @@ struct DevParams {
     int restit;                // some body of the batch has restitution > 0
 };
 
+// Pick task: delta joint-position controller and per-step records
+// (reward, indicators, tcp / cube positions, joint coordinates, targets).
+struct DevTask {
+    int on;                            // actions are normalised deltas; records may be written
+    int grip, fa, fb, cube, table;     // env-local gripper joint (-1: none), fingers, cube, table
+    float grasp_tol, touch_tol;
+    const float* half;                 // [A] (h - l) / 2 per joint slot
+    float* qR;                         // [NJ] joint coordinates at the last controller reset
+    float* out;                        // [n_steps][E][D] records of this call, or null
+    int D;                             // record length, 10 + 2 A
+};
+
 struct DevBatch {
     int E, NB, NJ, A;
     DevParams P;
+    DevTask T;
     const int* body_off;
     const int* joint_off;
     float4 *x, *q, *v, *w;
@@ -99,6 +112,10 @@ bool fused_supported(int G);
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,
                          int grid, int threads, size_t smem, cudaStream_t s);
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
+// pick task: controller reset of the masked envs (all if mask is null) and
+// the records of every env at the current state
+void launch_task_reset(const DevBatch& D, const uint8_t* mask, cudaStream_t s);
+void launch_task_observe(const DevBatch& D, float* out, cudaStream_t s);
 void set_last_error(const char* msg);   // the message ms_last_error() returns on this thread
 
 // read access to a batch's device view and sizes (for the step server)

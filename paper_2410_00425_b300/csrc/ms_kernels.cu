@@ -94,6 +94,7 @@ __device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b
     e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
     e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
     e.rest = D.rest + b0;
+    e.qR = D.T.qR ? D.T.qR + j0 : nullptr;
     bool w = active && D.wc;
     e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
     e.wc_n = w ? D.wc_n + env : nullptr;
@@ -137,7 +138,7 @@ __global__ void k_begin_step(DevBatch D, const float* actions, int step) {
     int env = blockIdx.x;
     EnvView e = plain_view(D, env);
     Grp g = warp_grp();
-    stage_actions(e, g, actions ? actions + ((size_t)step * D.E + env) * D.A : nullptr, D.A);
+    stage_actions(e, g, actions ? actions + ((size_t)step * D.E + env) * D.A : nullptr, D.A, D.T.on ? D.T.half : nullptr);
     stage_broadphase(e, g, D.P);
 }
 __global__ void k_narrow(DevBatch D) {
@@ -171,11 +172,14 @@ __global__ void k_end_substep(DevBatch D, int last) {
     }
     stage_unscale(e, g);
 }
-__global__ void k_check(DevBatch D) {
-    EnvView e = plain_view(D, blockIdx.x);
+__global__ void k_check(DevBatch D, int step) {
+    int env = blockIdx.x;
+    EnvView e = plain_view(D, env);
     Grp g = warp_grp();
     end_step_solve(e, g, D.P);
     stage_check(e, g);
+    if (D.T.out)
+        stage_task_record(e, g, D.T, D.A, D.T.out + ((size_t)step * D.E + env) * D.T.D, (*e.status & ST_NAN) != 0);
 }
 
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s) {
@@ -197,7 +201,7 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
             k_end_substep<<<grid, block, 0, s>>>(D, sub == D.P.substeps - 1);
             launches++;
         }
-        k_check<<<grid, block, 0, s>>>(D);
+        k_check<<<grid, block, 0, s>>>(D, k);
         launches++;
     }
     return launches;
@@ -250,13 +254,16 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
         e.nj = frozen ? 0 : nj;
         for (int k = 0; k < n_steps; k++) {
             const float* act = (actions && active) ? actions + ((size_t)k * D.E + env) * D.A : nullptr;
-            stage_actions(e, g, act, D.A);
+            stage_actions(e, g, act, D.A, D.T.on ? D.T.half : nullptr);
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
             begin_step_solve(e, g, D.P);
             for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
             end_step_solve(e, g, D.P);
             stage_check(e, g);
+            if (D.T.out)
+                stage_task_record(e, g, D.T, D.A, active ? D.T.out + ((size_t)k * D.E + env) * D.T.D : nullptr,
+                                  (*e.status & ST_NAN) != 0);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }
         for (int i0 = 0; i0 < nbmax; i0 += G) {
@@ -355,6 +362,45 @@ void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask
     if (b > 0) k_unpack_state<<<b, t, 0, s>>>(D, in, mask, body_env);
     int be = (D.E + t - 1) / t;
     if (be > 0) k_clear_status<<<be, t, 0, s>>>(D, mask);
+}
+
+// ---------------------------------------------------------------- pick task
+// an env's resident state and parameters (no workspace), one warp per env
+__device__ __forceinline__ EnvView kin_view(const DevBatch& D, int env) {
+    EnvView e;
+    int b0 = D.body_off[env], j0 = D.joint_off[env];
+    e.nb = D.body_off[env + 1] - b0;
+    e.nj = D.joint_off[env + 1] - j0;
+    e.x = D.x + b0; e.q = D.q + b0; e.v = D.v + b0; e.w = D.w + b0;
+    view_params(e, D, b0, j0, env, true);
+    e.status = D.status + env;
+    return e;
+}
+
+// controller reset after an env reset: target = q = q_reset
+__global__ void k_task_reset(DevBatch D, const uint8_t* env_mask) {
+    int env = blockIdx.x;
+    if (env_mask && !env_mask[env]) return;              // the whole warp
+    EnvView e = kin_view(D, env);
+    for (int j = threadIdx.x; j < e.nj; j += 32) {
+        float q = joint_coord(e, j);
+        e.jt[j] = q;
+        e.qR[j] = q;
+    }
+}
+
+__global__ void k_task_observe(DevBatch D, float* out) {
+    int env = blockIdx.x;
+    EnvView e = kin_view(D, env);
+    stage_task_record(e, warp_grp(), D.T, D.A, out + (size_t)env * D.T.D, (*e.status & ST_NAN) != 0);
+}
+
+void launch_task_reset(const DevBatch& D, const uint8_t* mask, cudaStream_t s) {
+    if (D.E > 0) k_task_reset<<<D.E, 32, 0, s>>>(D, mask);
+}
+
+void launch_task_observe(const DevBatch& D, float* out, cudaStream_t s) {
+    if (D.E > 0) k_task_observe<<<D.E, 32, 0, s>>>(D, out);
 }
 
 }  // namespace ms

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
         e.nj = frozen ? 0 : nj;
         for (int k = 0; k < n_steps; k++) {
             const float* act = (actions && active) ? actions + ((size_t)k * D.E + env) * D.A : nullptr;
-            stage_actions(e, g, act, D.A);
+            stage_actions(e, g, act, D.A, nullptr);
             stage_broadphase(e, g, D.P);
             stage_narrowphase(e, g, D.P);
             stage_color(e, g);

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
         e.nj = frozen ? 0 : nj;
         DevParams P = D.P;
         const float* act = (active && actions[it.x]) ? actions[it.x] + (size_t)env * D.A : nullptr;
-        stage_actions(e, g, act, D.A);
+        stage_actions(e, g, act, D.A, nullptr);
         stage_broadphase(e, g, P);
         stage_narrowphase(e, g, P);
         begin_step_solve(e, g, P);

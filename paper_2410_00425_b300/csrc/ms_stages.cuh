@@ -71,6 +71,7 @@ struct EnvView {
     const float4* jp;                 // lower, upper, kp, kd
     const int4* jm;                   // type, parent, child, -
     float* jt;                        // drive targets
+    float* qR;                        // pick task: joint coordinates at the controller reset (nullable)
     const float* rest;                // restitution per body
     float4* wc;                       // warm-start memory of the env (null: off): 2 per contact point
     int* wc_n;                        //   its count
@@ -153,14 +154,17 @@ MSD bool is_dyn(const EnvView& e, int i) { return i >= 0 && ((e.meta[i].x >> 8) 
 MSD int shape_type(const EnvView& e, int i) { return e.meta[i].x & 0xff; }
 
 // ---------------------------------------------------------------- actions
-MSD void stage_actions(EnvView& e, const Grp& g, const float* act, int A) {
+// An action is the joint's new drive target, or, with the pick task's delta
+// controller (half != null), a normalised delta: the target moves by
+// clip(a, -1, 1) (h - l) / 2.  NaN leaves the target unchanged.
+MSD void stage_actions(EnvView& e, const Grp& g, const float* act, int A, const float* half) {
     int n = act ? min(e.nj, A) : 0;
     int nmax = g.wmax(n);
     for (int j0 = 0; j0 < nmax; j0 += g.size) {
         int j = j0 + g.lane;
         if (j < n) {
             float t = act[j];
-            if (!isnan(t)) e.jt[j] = t;
+            if (!isnan(t)) e.jt[j] = half ? fmaf(fminf(fmaxf(t, -1.f), 1.f), half[j], e.jt[j]) : t;
         }
     }
     g.sync();
@@ -984,6 +988,103 @@ MSD void begin_step_solve(EnvView& e, const Grp& g, const Params& P) {
 // The end of a step: the warm-start memory.
 MSD void end_step_solve(EnvView& e, const Grp& g, const Params& P) {
     if (P.warm) stage_store_warm(e, g);
+}
+
+// ------------------------------------------------------------- pick task
+// The pick task of the paper's sim2real appendix (Observation Space,
+// Reward): joint coordinates, the is-grasped flag and the dense reward,
+// from the env's state after a step.
+
+// pose without the inertia factor (world body for i < 0)
+MSD BodyPose pose_kin(const EnvView& e, int i) {
+    BodyPose b;
+    b.x = i < 0 ? f3(0.f, 0.f, 0.f) : xyz(e.x[i]);
+    b.q = i < 0 ? make_float4(0.f, 0.f, 0.f, 1.f) : e.q[i];
+    b.R = qmat(b.q);
+    b.S = S3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    b.im = 0.f;
+    b.dyn = false;
+    return b;
+}
+
+// revolute angle or prismatic displacement, as the joint limits see it
+MSD float joint_coord(const EnvView& e, int j) {
+    int4 jm = e.jm[j];
+    return joint_geo(e, j, jm.x, pose_kin(e, jm.y), pose_kin(e, jm.z)).phi;
+}
+
+// signed distance from body i to the table plane (the table's local +z
+// through its origin): the body's lowest point along the normal
+MSD float plane_gap(const EnvView& e, int i, int table) {
+    float3 n = qrot(e.q[table], f3(0.f, 0.f, 1.f));
+    float off = dot(n, xyz(e.x[i]) - xyz(e.x[table]));
+    float4 s = e.shape[i];
+    int t = shape_type(e, i);
+    if (t == SH_SPHERE) return off - s.x;
+    float4 q = e.q[i];
+    if (t == SH_CAPSULE) return off - fabsf(dot(n, qrot(q, f3(0.f, 0.f, 1.f)))) * s.y - s.x;
+    if (t == SH_BOX)
+        return off - (fabsf(dot(n, qrot(q, f3(1.f, 0.f, 0.f)))) * s.x + fabsf(dot(n, qrot(q, f3(0.f, 1.f, 0.f)))) * s.y +
+                      fabsf(dot(n, qrot(q, f3(0.f, 0.f, 1.f)))) * s.z);
+    return off;
+}
+
+MSD float r_dist(float d, float z) { return 1.f - tanhf(z * d); }
+
+// The record of one env: reward, grasped, tcp_close, touch_table, x_tcp[3],
+// x_cube[3], q[A], target[A] (zero past the env's joints), with
+//   tcp = midpoint of the fingers, g = finger b - finger a, c = cube side,
+//   r = r_dist(|tcp - x_cube|, 15) + (1 - g.z/|g|)
+//       + 2 [|tcp - x_cube| <= c/2] r_dist(| |g| - c |, 40)
+//       + [grasped] (1 + 3 r_dist(|q - q_reset|, 4/pi)) - 2 [touch_table],
+// grasped = the gripper joint more than grasp_tol from its target, touch =
+// a finger within touch_tol of the table.  A frozen env writes NaN.  Every
+// lane of the warp calls this (group-wide reductions); rec = null writes
+// nothing.
+MSD void stage_task_record(const EnvView& e, const Grp& g, const DevTask& T, int A, float* rec, bool frozen) {
+    int nj = (rec && !frozen) ? e.nj : 0;
+    int amax = g.wmax(rec ? A : 0);
+    float part = 0.f;
+    bool gr = false;
+    for (int j0 = 0; j0 < amax; j0 += g.size) {
+        int j = j0 + g.lane;
+        if (j >= A || !rec) continue;
+        float q = 0.f, t = 0.f;
+        if (j < nj) {
+            q = joint_coord(e, j);
+            t = e.jt[j];
+            float d = q - e.qR[j];
+            part = fmaf(d, d, part);
+            if (j == T.grip) gr = fabsf(q - t) > T.grasp_tol;
+        }
+        rec[10 + j] = frozen ? __int_as_float(0x7fffffff) : q;
+        rec[10 + A + j] = frozen ? __int_as_float(0x7fffffff) : t;
+    }
+    for (int d = g.size >> 1; d > 0; d >>= 1) part += __shfl_xor_sync(FULL_MASK, part, d, g.size);
+    bool grasped = g.any(gr);
+    if (g.lane == 0 && rec) {
+        if (frozen) {
+            for (int k = 0; k < 10; k++) rec[k] = __int_as_float(0x7fffffff);
+        } else {
+            float3 xa = xyz(e.x[T.fa]), xb = xyz(e.x[T.fb]), xc = xyz(e.x[T.cube]);
+            float3 tcp = (xa + xb) * 0.5f;
+            float3 gv = xb - xa;
+            float gl = len(gv);
+            float c = 2.f * e.shape[T.cube].x;
+            float dtc = len(tcp - xc);
+            float r = r_dist(dtc, 15.f);
+            r += gl > 0.f ? 1.f - gv.z / gl : 1.f;
+            bool close = dtc <= 0.5f * c;
+            if (close) r += 2.f * r_dist(fabsf(gl - c), 40.f);
+            if (grasped) r += 1.f + 3.f * r_dist(sqrtf(part), 4.f / 3.14159265358979f);
+            bool touch = plane_gap(e, T.fa, T.table) <= T.touch_tol || plane_gap(e, T.fb, T.table) <= T.touch_tol;
+            if (touch) r -= 2.f;
+            rec[0] = r; rec[1] = grasped ? 1.f : 0.f; rec[2] = close ? 1.f : 0.f; rec[3] = touch ? 1.f : 0.f;
+            rec[4] = tcp.x; rec[5] = tcp.y; rec[6] = tcp.z;
+            rec[7] = xc.x; rec[8] = xc.y; rec[9] = xc.z;
+        }
+    }
+    g.sync();
 }
 
 }  // namespace ms
