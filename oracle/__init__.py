@@ -72,6 +72,7 @@ def lib():
         L.oracle_task_reset.argtypes = [P, up]
         L.oracle_step_task.argtypes = [P, dp, C.c_int, C.c_int, C.c_int, dp, up]
         L.oracle_task_observe.argtypes = [P, dp, up]
+        L.oracle_render.argtypes = [P, dp, dp, up, dp, ip, up, C.c_int]
         _lib = L
     return _lib
 
@@ -212,6 +213,22 @@ class Oracle:
         if lib().oracle_task_observe(self.h, _dp(out), _up(ties)) != 0:
             raise RuntimeError("no task set")
         return out, ties
+
+    def render(self, camera, body_rgb, threads=8):
+        """camera: dict eye, target, fov_y, near, width, height; body_rgb
+        [n_bodies][3].  Returns rgb uint8 [E,H,W,3], depth [E,H,W], seg int32
+        [E,H,W], ties uint8 [E,H,W]."""
+        W, H = int(camera["width"]), int(camera["height"])
+        cam = np.array([*camera["eye"], *camera["target"], camera["fov_y"], camera["near"], W, H], np.float64)
+        col = np.ascontiguousarray(body_rgb, np.float64)
+        assert col.shape == (self.nb, 3)
+        rgb = np.zeros((self.E, H, W, 3), np.uint8)
+        depth = np.zeros((self.E, H, W), np.float64)
+        seg = np.zeros((self.E, H, W), np.int32)
+        ties = np.zeros((self.E, H, W), np.uint8)
+        if lib().oracle_render(self.h, _dp(cam), _dp(col), _up(rgb), _dp(depth), _ip(seg), _up(ties), threads) != 0:
+            raise ValueError("degenerate camera")
+        return rgb, depth, seg, ties
 
     def state(self) -> np.ndarray:
         out = np.zeros((self.nb, 13), np.float64)

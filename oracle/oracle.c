@@ -1398,6 +1398,249 @@ static void task_reset_env(Env* e) {
     }
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* camera rendering: RGB, depth and segmentation of every env's camera (the  */
+/* paper's parallel rendering, Sec. "GPU Parallelized Simulation and          */
+/* Rendering"), restated as a plain triangle rasteriser                       */
+/* ------------------------------------------------------------------------- */
+/* Mesh of each primitive (body frame), triangles counter-clockwise seen from
+ * outside:
+ *   box      6 faces x 2 triangles (corners (+-hx, +-hy, +-hz))
+ *   sphere   UV sphere: rings at polar angles k pi/6 (k = 1..5), 12 points
+ *            per ring at azimuths 2 pi j/12, two poles: 120 triangles
+ *   capsule  the same rings, k = 1..3 shifted by +l along z and k = 3..5 by
+ *            -l (the equator ring twice, bounding the cylinder): 144
+ *   plane    the square [-2, 2]^2 at z = 0, normal +z: 2 triangles */
+enum { R_NLON = 12, R_NLAT = 6, R_MAXTRI = 144 };
+typedef struct { v3 p[3]; } Tri;
+
+static int box_mesh(const Body* b, Tri* t) {
+    static const int F[6][4][3] = {
+        {{1, -1, -1}, {1, 1, -1}, {1, 1, 1}, {1, -1, 1}},
+        {{-1, 1, -1}, {-1, -1, -1}, {-1, -1, 1}, {-1, 1, 1}},
+        {{1, 1, -1}, {-1, 1, -1}, {-1, 1, 1}, {1, 1, 1}},
+        {{-1, -1, -1}, {1, -1, -1}, {1, -1, 1}, {-1, -1, 1}},
+        {{-1, -1, 1}, {1, -1, 1}, {1, 1, 1}, {-1, 1, 1}},
+        {{-1, 1, -1}, {1, 1, -1}, {1, -1, -1}, {-1, -1, -1}}};
+    int n = 0;
+    for (int f = 0; f < 6; f++) {
+        v3 c[4];
+        for (int k = 0; k < 4; k++) c[k] = V(F[f][k][0] * b->p[0], F[f][k][1] * b->p[1], F[f][k][2] * b->p[2]);
+        t[n].p[0] = c[0]; t[n].p[1] = c[1]; t[n].p[2] = c[2]; n++;
+        t[n].p[0] = c[0]; t[n].p[1] = c[2]; t[n].p[2] = c[3]; n++;
+    }
+    return n;
+}
+
+/* sphere (l = 0, rings 1..5) or capsule (rings 1, 2, 3 at +l, 3, 4, 5 at -l) */
+static int round_mesh(double r, double l, int capsule, Tri* t) {
+    int ring_k[6], nr = 0;
+    double shift[6];
+    if (capsule) {
+        for (int k = 1; k <= 3; k++) { ring_k[nr] = k; shift[nr] = l; nr++; }
+        for (int k = 3; k <= 5; k++) { ring_k[nr] = k; shift[nr] = -l; nr++; }
+    } else {
+        for (int k = 1; k <= 5; k++) { ring_k[nr] = k; shift[nr] = 0.0; nr++; }
+    }
+    v3 ring[6][R_NLON];
+    for (int a = 0; a < nr; a++) {
+        double th = M_PI * ring_k[a] / R_NLAT;
+        for (int j = 0; j < R_NLON; j++) {
+            double ph = 2.0 * M_PI * j / R_NLON;
+            ring[a][j] = V(r * sin(th) * cos(ph), r * sin(th) * sin(ph), r * cos(th) + shift[a]);
+        }
+    }
+    v3 N = V(0, 0, r + shift[0]), S = V(0, 0, -r + shift[nr - 1]);
+    int n = 0;
+    for (int j = 0; j < R_NLON; j++) {
+        int j1 = (j + 1) % R_NLON;
+        t[n].p[0] = N; t[n].p[1] = ring[0][j]; t[n].p[2] = ring[0][j1]; n++;
+    }
+    for (int a = 0; a + 1 < nr; a++)
+        for (int j = 0; j < R_NLON; j++) {
+            int j1 = (j + 1) % R_NLON;
+            t[n].p[0] = ring[a][j]; t[n].p[1] = ring[a + 1][j]; t[n].p[2] = ring[a + 1][j1]; n++;
+            t[n].p[0] = ring[a][j]; t[n].p[1] = ring[a + 1][j1]; t[n].p[2] = ring[a][j1]; n++;
+        }
+    for (int j = 0; j < R_NLON; j++) {
+        int j1 = (j + 1) % R_NLON;
+        t[n].p[0] = S; t[n].p[1] = ring[nr - 1][j1]; t[n].p[2] = ring[nr - 1][j]; n++;
+    }
+    return n;
+}
+
+static int body_mesh(const Body* b, Tri* t) {
+    if (b->type == OR_BOX) return box_mesh(b, t);
+    if (b->type == OR_SPHERE) return round_mesh(b->p[0], 0.0, 0, t);
+    if (b->type == OR_CAPSULE) return round_mesh(b->p[0], b->p[1], 1, t);
+    v3 c[4] = {V(-2, -2, 0), V(2, -2, 0), V(2, 2, 0), V(-2, 2, 0)};
+    t[0].p[0] = c[0]; t[0].p[1] = c[1]; t[0].p[2] = c[2];
+    t[1].p[0] = c[0]; t[1].p[1] = c[2]; t[1].p[2] = c[3];
+    return 2;
+}
+
+typedef struct {
+    v3 eye, rt, up, fw;               /* view basis: right, up, forward */
+    double F, near;                   /* focal length (pixels), near plane */
+    int W, H;
+} Camera;
+
+static const double R_TIE_PX = 1e-3;  /* coverage decisions within 1e-3 pixel of an edge */
+static const double R_TIE_Z = 1e-5;   /* depth decisions within 1e-5 (relative) */
+
+/* one env's image; per pixel the covering triangle of least (depth, index) */
+static void render_env(const Env* e, const Camera* C, const double* rgb_body, unsigned char* rgb, double* depth,
+                       int* seg, unsigned char* ties) {
+    int W = C->W, H = C->H, P = W * H;
+    double* zb = (double*)malloc(sizeof(double) * P);
+    double* z2 = (double*)malloc(sizeof(double) * P);        /* second-nearest covering depth */
+    int* win = (int*)malloc(sizeof(int) * P);
+    for (int i = 0; i < P; i++) { zb[i] = INFINITY; z2[i] = INFINITY; win[i] = -1; seg[i] = 0; depth[i] = 0.0;
+                                  rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0; ties[i] = 0; }
+    v3 L = V(0.3, 0.2, 1.0);
+    L = scl(L, 1.0 / norm(L));
+    Tri mesh[R_MAXTRI];
+    int tri_index = 0;
+    /* shade and body of each winning triangle, by triangle index */
+    int cap = 64;
+    double* shade = (double*)malloc(sizeof(double) * cap);
+    int* tbody = (int*)malloc(sizeof(int) * cap);
+    for (int bi = 0; bi < e->nb; bi++) {
+        const Body* b = &e->bodies[bi];
+        int nt = body_mesh(b, mesh);
+        m3 R = qmat(b->q);
+        for (int ti = 0; ti < nt; ti++, tri_index++) {
+            if (tri_index >= cap) {
+                cap *= 2;
+                shade = (double*)realloc(shade, sizeof(double) * cap);
+                tbody = (int*)realloc(tbody, sizeof(int) * cap);
+            }
+            tbody[tri_index] = bi;
+            v3 w[3], vv[3];
+            for (int k = 0; k < 3; k++) {
+                w[k] = add(b->x, mv(&R, mesh[ti].p[k]));
+                v3 d = sub(w[k], C->eye);
+                vv[k] = V(dot(C->rt, d), dot(C->up, d), dot(C->fw, d));
+            }
+            v3 n = cross(sub(w[1], w[0]), sub(w[2], w[0]));
+            double nl = norm(n);
+            shade[tri_index] = nl > 0.0 ? 0.3 + 0.7 * fmax(0.0, dot(n, L) / nl) : 0.3;
+            /* back faces (facing away from the eye, or edge-on) are not drawn */
+            if (dot(n, sub(w[0], C->eye)) >= 0.0) continue;
+            /* clip against the near plane z >= near (view space) */
+            v3 poly[4];
+            int np = 0;
+            for (int k = 0; k < 3; k++) {
+                v3 a = vv[k], c = vv[(k + 1) % 3];
+                double da = a.z - C->near, dc = c.z - C->near;
+                if (da >= 0.0) poly[np++] = a;
+                if ((da >= 0.0) != (dc >= 0.0)) {
+                    double s = da / (da - dc);
+                    poly[np++] = add(a, scl(sub(c, a), s));
+                }
+            }
+            for (int f = 0; f + 2 < np; f++) {
+                v3 q[3] = {poly[0], poly[f + 1], poly[f + 2]};
+                double sx[3], sy[3], iz[3];
+                for (int k = 0; k < 3; k++) {
+                    sx[k] = 0.5 * W + C->F * q[k].x / q[k].z;
+                    sy[k] = 0.5 * H - C->F * q[k].y / q[k].z;
+                    iz[k] = 1.0 / q[k].z;
+                }
+                double A = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sy[1] - sy[0]) * (sx[2] - sx[0]);
+                if (A == 0.0) continue;
+                double sg = A > 0.0 ? 1.0 : -1.0;
+                for (int py = 0; py < H; py++)
+                    for (int px = 0; px < W; px++) {
+                        double x = px + 0.5, y = py + 0.5;
+                        double wk[3], dist_min = INFINITY;
+                        for (int k = 0; k < 3; k++) {
+                            int a = (k + 1) % 3, c = (k + 2) % 3;   /* edge a -> c, opposite vertex k */
+                            double ex = sx[c] - sx[a], ey = sy[c] - sy[a];
+                            wk[k] = sg * (ex * (y - sy[a]) - ey * (x - sx[a]));
+                            double el = sqrt(ex * ex + ey * ey);
+                            double dd = el > 0.0 ? wk[k] / el : wk[k];
+                            if (dd < dist_min) dist_min = dd;
+                        }
+                        int pix = py * W + px;
+                        if (fabs(dist_min) < R_TIE_PX) ties[pix] = 1;
+                        if (wk[0] < 0.0 || wk[1] < 0.0 || wk[2] < 0.0) continue;
+                        double sa = fabs(A);
+                        double izp = (wk[0] * iz[0] + wk[1] * iz[1] + wk[2] * iz[2]) / sa;
+                        double z = 1.0 / izp;
+                        if (z < zb[pix] || (z == zb[pix] && tri_index < win[pix])) {
+                            if (win[pix] != tri_index) z2[pix] = zb[pix];
+                            zb[pix] = z; win[pix] = tri_index;
+                        } else if (win[pix] != tri_index && z < z2[pix]) {
+                            z2[pix] = z;
+                        }
+                    }
+            }
+        }
+    }
+    for (int i = 0; i < P; i++) {
+        if (win[i] < 0) continue;
+        if (isfinite(z2[i]) && z2[i] - zb[i] <= R_TIE_Z * zb[i]) ties[i] = 1;
+        int bi = tbody[win[i]];
+        seg[i] = bi + 1;
+        depth[i] = zb[i];
+        for (int c = 0; c < 3; c++) {
+            double v = rgb_body[3 * bi + c] * shade[win[i]];
+            int q = (int)floor(v * 255.0 + 0.5);
+            rgb[3 * i + c] = (unsigned char)(q < 0 ? 0 : (q > 255 ? 255 : q));
+        }
+    }
+    free(zb); free(z2); free(win); free(shade); free(tbody);
+}
+
+typedef struct {
+    const oracle_world* w; const Camera* C; const double* rgb_body;
+    unsigned char* rgb; double* depth; int* seg; unsigned char* ties; int e0, e1;
+} RenderJob;
+
+static void* run_render(void* p) {
+    RenderJob* j = (RenderJob*)p;
+    size_t P = (size_t)j->C->W * j->C->H;
+    for (int ei = j->e0; ei < j->e1; ei++)
+        render_env(&j->w->envs[ei], j->C, j->rgb_body + 3 * j->w->body_off[ei], j->rgb + 3 * P * ei,
+                   j->depth + P * ei, j->seg + P * ei, j->ties + P * ei);
+    return NULL;
+}
+
+int oracle_render(const oracle_world* w, const double* cam, const double* rgb_body, unsigned char* rgb, double* depth,
+                  int* seg, unsigned char* ties, int n_threads) {
+    Camera C;
+    C.eye = V(cam[0], cam[1], cam[2]);
+    v3 f = sub(V(cam[3], cam[4], cam[5]), C.eye);
+    if (norm(f) == 0.0) return -1;
+    C.fw = scl(f, 1.0 / norm(f));
+    v3 r = cross(C.fw, V(0, 0, 1));
+    if (norm(r) < 1e-9) return -1;
+    C.rt = scl(r, 1.0 / norm(r));
+    C.up = cross(C.rt, C.fw);
+    C.W = (int)cam[8]; C.H = (int)cam[9];
+    C.F = 0.5 * C.H / tan(0.5 * cam[6]);
+    C.near = cam[7];
+    if (C.W < 1 || C.H < 1 || !(C.near > 0.0) || !(cam[6] > 0.0 && cam[6] < M_PI)) return -1;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > w->E) n_threads = w->E > 0 ? w->E : 1;
+    RenderJob* jobs = (RenderJob*)calloc((size_t)n_threads, sizeof(RenderJob));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; t++) {
+        RenderJob jb = {w, &C, rgb_body, rgb, depth, seg, ties,
+                        (int)((long long)w->E * t / n_threads), (int)((long long)w->E * (t + 1) / n_threads)};
+        jobs[t] = jb;
+    }
+    if (n_threads == 1) run_render(&jobs[0]);
+    else {
+        for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, run_render, &jobs[t]);
+        for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+    }
+    free(jobs); free(th);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* world API                                                                  */
 /* ------------------------------------------------------------------------- */

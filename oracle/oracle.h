@@ -139,6 +139,24 @@ int oracle_step_task(oracle_world* w, const double* actions, int A, int n_steps,
 /* The record of every env at the current state: out [E][D], ties [E]. */
 int oracle_task_observe(const oracle_world* w, double* out, unsigned char* ties);
 
+/* Camera images of every env at the current state (the paper's batched
+ * rendering, restated as a plain triangle rasteriser).  cam[10] = eye[3],
+ * target[3] (world up +z), fov_y (rad), near, W, H: a pinhole looking from
+ * eye to target, focal length (H/2)/tan(fov_y/2) pixels, pixel (i, j) centred
+ * at (i + 0.5, j + 0.5), row 0 at the top.  Each primitive is a fixed mesh
+ * (see oracle.c); back faces are skipped, triangles are clipped to view depth
+ * >= near, a pixel is covered when its centre is on the inner side of (or on)
+ * all three edges, and takes the covering triangle of least (view depth,
+ * triangle index), depth interpolated perspective-correctly.
+ * rgb_body [n_bodies][3] in [0, 1]; outputs per env and pixel: rgb [E][H][W][3]
+ * = round(255 base (0.3 + 0.7 max(0, n.l))), l = normalize(0.3, 0.2, 1);
+ * depth [E][H][W] (view depth, 0 = background); seg [E][H][W] (body + 1, 0 =
+ * background); ties [E][H][W] = 1 where a coverage decision was within 1e-3
+ * pixel of an edge or the two nearest depths within 1e-5 (relative).
+ * Returns -1 for a degenerate camera. */
+int oracle_render(const oracle_world* w, const double* cam, const double* rgb_body, unsigned char* rgb,
+                  double* depth, int* seg, unsigned char* ties, int n_threads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -423,6 +423,35 @@ def make_pick(n_envs=4096, seed=6, nan_frac=0.02, scale=0.7) -> Scene:
     return sc
 
 
+# ----------------------------------------------------------------------------
+# Cameras and body colours for the batched renderer (one camera per env, in
+# the env's own frame; the paper's 128 x 128 RGB observation).
+# ----------------------------------------------------------------------------
+def default_camera(name: str, width=128, height=128) -> Dict:
+    """A pinhole per env looking at the scene's working area."""
+    if name in ("arm", "pick"):
+        eye, target = (1.2, -0.9, 0.9), (0.25, 0.0, 0.25)
+    elif name == "hand":
+        eye, target = (0.25, -0.2, 0.25), (0.0, 0.0, 0.05)
+    else:
+        eye, target = (0.45, -0.35, 0.45), (0.0, 0.0, 0.05)
+    return dict(eye=eye, target=target, fov_y=math.radians(60.0), near=0.01, width=width, height=height)
+
+
+PALETTE = np.array([[0.85, 0.33, 0.10], [0.00, 0.45, 0.74], [0.93, 0.69, 0.13], [0.49, 0.18, 0.56],
+                    [0.47, 0.67, 0.19], [0.30, 0.75, 0.93], [0.64, 0.08, 0.18], [0.75, 0.75, 0.75]], np.float32)
+
+
+def body_colors(scene: "Scene") -> np.ndarray:
+    """float32 [n_bodies][3]: planes grey, other bodies by env-local index."""
+    out = np.empty((len(scene.bodies), 3), np.float32)
+    for e in range(scene.n_envs):
+        for i in range(scene.body_off[e], scene.body_off[e + 1]):
+            k = i - scene.body_off[e]
+            out[i] = (0.6, 0.6, 0.6) if scene.bodies["type"][i] == PLANE else PALETTE[k % len(PALETTE)]
+    return out
+
+
 CONFIGS = {
     "small": make_small,
     "arm": make_arm,
