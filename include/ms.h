@@ -276,6 +276,46 @@ enum { MS_STEP_PLAIN = 1 };
 ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, float* out, int flags, void* stream);
 
 /* ----------------------------------------------------------------------- */
+/* Batched camera rendering                                                 */
+/* ----------------------------------------------------------------------- */
+
+/* One pinhole camera per env, the same in every env's own frame (the
+ * paper's batched rendering of every env's camera; its observation is a 128 x
+ * 128 RGB image), rendered from the resident body poses by a CUDA triangle
+ * rasteriser: each primitive is a fixed mesh (box 12 triangles; sphere a UV
+ * mesh of 5 rings x 12 points and two poles, 120; capsule the same rings with
+ * the upper hemisphere at +l and the lower at -l, 144; plane the square
+ * [-2, 2]^2 of its local xy, 2).  eye looks at target with world up +z
+ * (the view must not be vertical); focal length (height / 2) / tan(fov_y / 2)
+ * pixels; pixel (i, j) is centred at (i + 0.5, j + 0.5), row 0 at the top.
+ * Back faces are skipped, triangles are clipped to view depth >= near, a
+ * pixel centre on or inside all three edges is covered, and the covering
+ * triangle of least (perspective-correct view depth, triangle index) wins.
+ * width x height <= 16384.  body_rgb: host float [n_bodies][3] in [0, 1],
+ * copied. */
+typedef struct {
+    float eye[3];
+    float target[3];
+    float fov_y;
+    float near;
+    int32_t width, height;
+    const float* body_rgb;
+} ms_camera_desc;
+
+/* Set the batch's camera (synchronous).  MS_ERR_INVALID_ARG for a degenerate
+ * or vertical view, a size out of range, colours outside [0, 1]. */
+ms_status ms_set_camera(ms_batch* b, const ms_camera_desc* c);
+
+/* Render every env at its current state on `stream` into device buffers
+ * (each nullable): rgba uint8 [n_envs][height][width][4] = round(255 base
+ * (0.3 + 0.7 max(0, n.l))) per channel, alpha 255, l = normalize(0.3, 0.2, 1),
+ * n the triangle's world normal, background 0; depth float [n_envs][height]
+ * [width] = view depth, background 0; seg uint16 [n_envs][height][width] =
+ * env-local body index + 1, background 0.  MS_ERR_INVALID_ARG without a
+ * camera. */
+ms_status ms_render(ms_batch* b, uint8_t* rgba, float* depth, uint16_t* seg, void* stream);
+
+/* ----------------------------------------------------------------------- */
 /* Introspection and tuning                                                */
 /* ----------------------------------------------------------------------- */
 

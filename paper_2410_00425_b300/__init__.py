@@ -65,6 +65,24 @@ class Batch:
         else:
             _ffi.ms_step_ex(self.h, actions, n_steps, out, _ffi.MS_STEP_PLAIN if plain else 0, stream)
 
+    # ------------------------------------------------------------- camera
+    def set_camera(self, camera, body_rgb):
+        """camera: dict eye, target, fov_y, near, width, height (see
+        scenegen.default_camera); body_rgb: [n_bodies][3] in [0, 1]."""
+        _ffi.ms_set_camera(self.h, camera, body_rgb)
+        self.camera = dict(camera)
+
+    def render(self, stream=None, rgba=True, depth=True, seg=True):
+        """Images of every env at the current state: rgba uint8 [E, H, W, 4],
+        depth float32 [E, H, W], seg int16-stored uint16 [E, H, W] (body + 1)."""
+        import torch
+        H, W = int(self.camera["height"]), int(self.camera["width"])
+        out_rgba = torch.empty((self.E, H, W, 4), dtype=torch.uint8, device="cuda") if rgba else None
+        out_depth = torch.empty((self.E, H, W), dtype=torch.float32, device="cuda") if depth else None
+        out_seg = torch.empty((self.E, H, W), dtype=torch.int16, device="cuda") if seg else None
+        _ffi.ms_render(self.h, out_rgba, out_depth, out_seg, stream)
+        return out_rgba, out_depth, out_seg
+
     # ---------------------------------------------------------- pick task
     def set_task(self, task, stream=None):
         """Set (dict, see scenegen.pick_task) or remove (None) the pick task;

@@ -65,6 +65,11 @@ class ms_task_desc(C.Structure):
 MS_STEP_PLAIN = 1
 
 
+class ms_camera_desc(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("fov_y", C.c_float), ("near", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("body_rgb", C.c_void_p)]
+
+
 class ms_tuning(C.Structure):
     _fields_ = [("lanes_per_env", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("rows_in_smem", C.c_int32), ("ctas_per_sm", C.c_int32)]
@@ -101,6 +106,8 @@ _SIGS = [
     ("ms_task_record_len", C.c_int, [C.c_void_p]),
     ("ms_task_observe", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_step_ex", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_set_camera", C.c_int, [C.c_void_p, C.POINTER(ms_camera_desc)]),
+    ("ms_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 EXPORTS = [s[0] for s in _SIGS]
@@ -223,6 +230,24 @@ def ms_task_record_len(b) -> int:
 
 def ms_task_observe(b, out, stream=None):
     return check(load().ms_task_observe(b, _ptr(out), _stream(stream)))
+
+
+def ms_set_camera(b, camera, body_rgb):
+    """camera: dict eye, target, fov_y, near, width, height; body_rgb
+    float [n_bodies][3] (host)."""
+    col = np.ascontiguousarray(body_rgb, np.float32)
+    c = ms_camera_desc()
+    for i in range(3):
+        c.eye[i] = camera["eye"][i]
+        c.target[i] = camera["target"][i]
+    c.fov_y = camera["fov_y"]; c.near = camera["near"]
+    c.width = int(camera["width"]); c.height = int(camera["height"])
+    c.body_rgb = col.ctypes.data
+    return check(load().ms_set_camera(b, C.byref(c)))
+
+
+def ms_render(b, rgba=None, depth=None, seg=None, stream=None):
+    return check(load().ms_render(b, _ptr(rgba), _ptr(depth), _ptr(seg), _stream(stream)))
 
 
 def ms_get_state(b) -> ms_state_view:

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmsim.so")
-SOURCES = ["ms_api.cu", "ms_kernels.cu", "ms_noalloc.cu", "ms_server.cu"]
+SOURCES = ["ms_api.cu", "ms_kernels.cu", "ms_noalloc.cu", "ms_server.cu", "ms_render.cu"]
 HEADERS = ["ms_math.cuh", "ms_narrow.cuh", "ms_stages.cuh", "ms_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 # -fmad=false: every fused multiply-add is written out in the source, so the

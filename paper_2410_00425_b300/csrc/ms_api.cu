@@ -96,6 +96,7 @@ struct ms_batch {
     float* d_task_half = nullptr;     // [A]
     float* d_task_qR = nullptr;       // [NJ]
     std::vector<float> h_task_half;
+    RenderState* render = nullptr;
 };
 
 // Device memory comes from the device's stream-ordered pool on the batch's
@@ -130,6 +131,8 @@ static void drop_graphs(ms_batch* b) {
 
 static void free_all(ms_batch* b) {
     drop_graphs(b);
+    render_destroy(b->render);
+    b->render = nullptr;
     for (void* p : b->allocs) cudaFreeAsync(p, b->setup);
     b->allocs.clear();
     if (b->setup) {
@@ -612,6 +615,26 @@ extern "C" ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, 
 
 extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
     return ms_step_ex(b, actions, n_steps, nullptr, 0, stream);
+}
+
+// ------------------------------------------------------------------ render
+extern "C" ms_status ms_set_camera(ms_batch* b, const ms_camera_desc* c) {
+    if (!b || !c || !c->body_rgb) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->render) b->render = render_create();
+    CK(cudaEventSynchronize(b->done));
+    const char* err = render_configure(b->render, b->D, c, b->h_type, b->h_body_off, b->max_nb, (int)b->smem_optin);
+    if (err) return fail(MS_ERR_INVALID_ARG, "camera: %s", err);
+    CK(cudaGetLastError());
+    return MS_OK;
+}
+
+extern "C" ms_status ms_render(ms_batch* b, uint8_t* rgba, float* depth, uint16_t* seg, void* stream) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (!render_ready(b->render)) return fail(MS_ERR_INVALID_ARG, "no camera is set");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(render_launch(b->render, b->D, rgba, depth, seg, st));
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
 }
 
 // ---------------------------------------------------------------- pick task

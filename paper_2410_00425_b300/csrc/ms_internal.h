@@ -4,6 +4,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/ms.h"
 #include "ms_math.cuh"
 
 struct ms_batch;   // include/ms.h
@@ -117,6 +120,17 @@ void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
 void launch_task_reset(const DevBatch& D, const uint8_t* mask, cudaStream_t s);
 void launch_task_observe(const DevBatch& D, float* out, cudaStream_t s);
 void set_last_error(const char* msg);   // the message ms_last_error() returns on this thread
+
+// batched camera rendering (ms_render.cu)
+struct RenderState;
+RenderState* render_create();
+void render_destroy(RenderState* r);
+const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_desc* c,
+                             const std::vector<uint8_t>& types, const std::vector<int>& body_off, int max_nb,
+                             int smem_optin);
+bool render_ready(const RenderState* r);
+cudaError_t render_launch(RenderState* r, const DevBatch& D, uint8_t* rgba, float* depth, uint16_t* seg,
+                          cudaStream_t s);
 
 // read access to a batch's device view and sizes (for the step server)
 const DevBatch& batch_dev(const ::ms_batch* b);
