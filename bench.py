@@ -39,6 +39,9 @@ WORKLOADS = {
     "small": "plane + 1 box + 3 spheres, 64 envs (dt 0.01 s, 4 substeps, 8+1 iterations)",
     "clutter": "1-32 boxes/spheres/capsules in a 5-box bin, 16384 envs (dt 0.01 s, 4 substeps, 8+1)",
     "hand": "16-DoF capsule hand holding a cube, 4096 envs (dt 1/120 s, 8 substeps, 16+1 iterations)",
+    "pick": "the arm envs driven by the pick task, 4096 envs: delta joint-position controller on normalised "
+            "actions, and per step a record of reward, grasp / tcp / table flags, tcp and cube positions, "
+            "joint coordinates and targets (dt 0.01 s, 4 substeps, 8+1 iterations)",
 }
 
 # FLOP weights per counted operation of the oracle (the step's algorithmic work model)
@@ -68,7 +71,7 @@ def make_workload(name, variants=False, **kw):
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 30.16e6, "kernel_sha": "95f4f474d2795775", "kernel": "k_fused<8>"},
+    ("arm", "8,1,0"): {"bytes": 30.11e6, "kernel_sha": "7004bfa723fc52af", "kernel": "k_fused<8>"},
 }
 KERNEL_SOURCES = ("ms_kernels.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
@@ -111,11 +114,14 @@ def algorithmic_flops_per_env_step(name, warmup, steps, sample_envs=32, variants
     sc = make_workload(name, variants, n_envs=min(sample_envs, scenegen.CONFIG_SIZES[name]))
     o = oracle.Oracle(sc)
     th = os.cpu_count() or 1
+    if sc.task is not None:
+        o.set_task(sc.task)
+    stepper = o.step_task if sc.task is not None else o.step
     if warmup:
-        o.step(warmup, threads=th)
+        stepper(warmup, threads=th)
     c0 = o.counters()
     n = max(1, min(steps, 200))
-    o.step(n, threads=th)
+    stepper(n, threads=th)
     c1 = o.counters()
     c = {k: c1[k] - c0[k] for k in c1}
     flops = sum(FLOP_WEIGHTS[k] * c[k] for k in FLOP_WEIGHTS)
@@ -241,8 +247,15 @@ def time_cpu_baseline(name, n_envs, steps, one_core=False, variants=False):
     o = oracle.Oracle(sc)
     acts = sc.actions(0, steps)
     cores = os.cpu_count() or 1
+
+    def run(o, n, a, th):
+        if sc.task is not None:
+            o.set_task(sc.task)
+            o.step_task(n, actions=a, threads=th)
+        else:
+            o.step(n, actions=a, threads=th)
     t0 = time.perf_counter()
-    o.step(steps, actions=acts, threads=cores)
+    run(o, steps, acts, cores)
     dt = time.perf_counter() - t0
     out = {"value": n_envs * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
            "sample": f"{n_envs} envs x {steps} steps of the {name} workload, FP64, {cores} threads "
@@ -252,7 +265,7 @@ def time_cpu_baseline(name, n_envs, steps, one_core=False, variants=False):
         n1 = max(1, n_envs // 16)
         o1 = oracle.Oracle(sc.subset(range(n1)))
         t0 = time.perf_counter()
-        o1.step(steps, actions=acts[:, :n1], threads=1)
+        run(o1, steps, np.ascontiguousarray(acts[:, :n1]), 1)
         d1 = time.perf_counter() - t0
         out["value_1core"] = n1 * steps / d1
         out["sample_1core"] = f"{n1} envs x {steps} steps, 1 thread ({d1:.1f} s)"
@@ -425,6 +438,7 @@ def main():
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000", help="arrival rates (requests/s) of --serve")
     ap.add_argument("--serve-life", type=float, default=500.0, help="mean session lifetime (requests) of --serve")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-render", action="store_true", help="skip the camera-rendering measurement")
     ap.add_argument("--variants", action="store_true",
                     help="velocity damping, restitution and warm starting across steps on")
     args = ap.parse_args()
@@ -467,6 +481,8 @@ def main():
         return None if acts is None else acts[i * n:(i + 1) * n]
 
     b = Batch(sc)
+    if sc.task is not None:
+        b.set_task(sc.task, stream=stream)
     tuning = None
     if args.tuning:
         G, W, R = (int(x) for x in args.tuning.split(","))
@@ -485,13 +501,21 @@ def main():
         tuning = b.tuning()
     b.close()
 
-    def timed(plain, launches_per_call):
+    def new_batch():
         bb = Batch(sc)
+        if sc.task is not None:
+            bb.set_task(sc.task, stream=stream)
+        return bb
+
+    def timed(plain, launches_per_call):
+        bb = new_batch()
         if not plain and tuning:
             bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
+        rec = (torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev)
+               if sc.task is not None else None)
         with torch.cuda.stream(stream):
             for i in range(args.warmup):
-                bb.step(act(i), n, stream=stream, plain=plain)
+                bb.step(act(i), n, stream=stream, plain=plain, out=rec)
         stream.synchronize()
         times = []
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -503,7 +527,7 @@ def main():
                 flush.fill_(float(i))                      # L2 flush, outside the events
                 stream.wait_stream(torch.cuda.current_stream())
                 ev[i][0].record(stream)
-                bb.step(act(args.warmup + i), n, stream=stream, plain=plain)
+                bb.step(act(args.warmup + i), n, stream=stream, plain=plain, out=rec)
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
         barrier(ws)
@@ -524,35 +548,94 @@ def main():
         plain_value = ws * E * n * args.steps / t_p
 
     # e2e: host actions in (pinned), state out to pinned host, every step
-    bb = Batch(sc)
+    # (with a task: the records -- observations and rewards -- instead of the state)
+    bb = new_batch()
     if tuning:
         bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
     h_act = None if acts_np is None else torch.from_numpy(acts_np).pin_memory()
     d_act = None if acts is None else torch.empty_like(acts[:n])
+    task = sc.task is not None
     h_state = torch.empty((bb.NB, 13), dtype=torch.float32).pin_memory()
+    d_rec = torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev) if task else None
+    h_rec = torch.empty((n, E, bb.record_len()), dtype=torch.float32).pin_memory() if task else None
+
+    def e2e_step(j):
+        if d_act is not None:
+            d_act.copy_(h_act[j * n:(j + 1) * n], non_blocking=True)
+        bb.step(d_act, n, stream=stream, out=d_rec)
+        if task:
+            h_rec.copy_(d_rec, non_blocking=True)
+        else:
+            bb.state_to_host(h_state, stream=stream)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            if d_act is not None:
-                d_act.copy_(h_act[i * n:(i + 1) * n], non_blocking=True)
-            bb.step(d_act, n, stream=stream)
-            bb.state_to_host(h_state, stream=stream)
+            e2e_step(i)
     stream.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
-            j = args.warmup + i
-            if d_act is not None:
-                d_act.copy_(h_act[j * n:(j + 1) * n], non_blocking=True)
-            bb.step(d_act, n, stream=stream)
-            bb.state_to_host(h_state, stream=stream)
+            e2e_step(args.warmup + i)
     e1.record(stream)
     stream.synchronize()
     t_e = reduce_max(e0.elapsed_time(e1) / 1e3, ws)
     bb.close()
     h2d = 0 if d_act is None else d_act.numel() * 4
-    d2h = h_state.numel() * 4
+    d2h = (h_rec.numel() if task else h_state.numel()) * 4
+
+    # batched camera rendering (one 128 x 128 camera per env): the render
+    # launch alone, and step + render per iteration (sim + render rate)
+    render = None
+    if not args.no_render:
+        from paper_2410_00425_b300 import _ffi
+        bb = new_batch()
+        if tuning:
+            bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
+        cam = scenegen.default_camera(name)
+        bb.set_camera(cam, scenegen.body_colors(sc))
+        Hc, Wc = cam["height"], cam["width"]
+        o_rgba = torch.empty((E, Hc, Wc, 4), dtype=torch.uint8, device=dev)
+        o_depth = torch.empty((E, Hc, Wc), dtype=torch.float32, device=dev)
+        o_seg = torch.empty((E, Hc, Wc), dtype=torch.int16, device=dev)
+        rec = (torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev)
+               if sc.task is not None else None)
+        reps = min(args.steps, 50)
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup):
+                bb.step(act(i), n, stream=stream, out=rec)
+                _ffi.ms_render(bb.h, o_rgba, o_depth, o_seg, stream)
+        stream.synchronize()
+        ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for i in range(reps):
+            flush.fill_(float(i))
+            stream.wait_stream(torch.cuda.current_stream())
+            ev_r[i][0].record(stream)
+            _ffi.ms_render(bb.h, o_rgba, o_depth, o_seg, stream)
+            ev_r[i][1].record(stream)
+        for i in range(reps):
+            flush.fill_(float(i))
+            stream.wait_stream(torch.cuda.current_stream())
+            ev_s[i][0].record(stream)
+            bb.step(act(args.warmup + i), n, stream=stream, out=rec)
+            _ffi.ms_render(bb.h, o_rgba, o_depth, o_seg, stream)
+            ev_s[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_r = statistics.mean(a.elapsed_time(z) for a, z in ev_r) / 1e3
+        t_s = statistics.mean(a.elapsed_time(z) for a, z in ev_s) / 1e3
+        bb.close()
+        # algorithmic bytes per launch: the images written (4 + 4 + 2 B per
+        # pixel) plus each body's pose, shape and colour read (60 B)
+        rbytes = E * Hc * Wc * 10 + int(sc.body_off[-1]) * 60
+        hbm = float(load_peaks().get("hbm_gbs", 6400.0))
+        render = {"renders_per_s": E / t_r, "ms_per_render": 1e3 * t_r, "image": f"{Wc}x{Hc} RGBA8 + depth + seg",
+                  "sim_render_env_steps_per_s": E * n / t_s, "ms_per_step_and_render": 1e3 * t_s,
+                  "roofline": {"bound": "hbm", "achieved": rbytes / t_r / 1e9, "peak": hbm, "unit": "GB/s",
+                               "frac": rbytes / t_r / 1e9 / hbm, "bytes_per_launch": rbytes,
+                               "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                  "l2": "flushed before every timed launch"}
 
     if rank != 0:
         return
@@ -584,6 +667,8 @@ def main():
         "status": code,
         "device": props.name,
     }
+    if render is not None:
+        line["render"] = render
     if not args.no_serve:
         pools = {t: scenegen.make_scene(t, n_envs=1024) for t in ("arm", "clutter", "hand")}
         # 2k requests/s: latency at load; 10k requests/s: over capacity, the

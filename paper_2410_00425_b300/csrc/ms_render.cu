@@ -121,6 +121,7 @@ struct RenderCfg {
     float3 eye, rt, up, fw;
     float F, near;
     int W, H;
+    int bands, band_rows;                  // image rows split over `bands` CTAs per env
     int max_tri;                           // largest triangle count of an env
     int max_nb;
     int v0[4], t0[4], nt[4];
@@ -145,7 +146,9 @@ __device__ __forceinline__ float3 local_vertex(float4 t, int type, float4 s) {
     return f3(t.x, t.y, t.z);
 }
 
-__device__ __forceinline__ void screen_tri(const RenderCfg& R, float3 a, float3 b, float3 c, ScreenTri& s) {
+// screen triangle of view-space a, b, c; its pixel bounding box is cut to rows [r0, r1)
+__device__ __forceinline__ void screen_tri(const RenderCfg& R, float3 a, float3 b, float3 c, int r0, int r1,
+                                           ScreenTri& s) {
     float3 q[3] = {a, b, c};
     float mnx = 3e38f, mxx = -3e38f, mny = 3e38f, mxy = -3e38f;
     for (int k = 0; k < 3; k++) {
@@ -162,75 +165,92 @@ __device__ __forceinline__ void screen_tri(const RenderCfg& R, float3 a, float3 
     mny = fminf(fmaxf(mny - 0.5f, -1.f), (float)R.H);
     mxy = fminf(fmaxf(mxy - 0.5f, -1.f), (float)R.H);
     s.x0 = max((int)ceilf(mnx), 0); s.x1 = min((int)floorf(mxx), R.W - 1);
-    s.y0 = max((int)ceilf(mny), 0); s.y1 = min((int)floorf(mxy), R.H - 1);
+    s.y0 = max((int)ceilf(mny), r0); s.y1 = min((int)floorf(mxy), r1 - 1);
     if (s.A == 0.f || !(s.A == s.A)) s.x1 = s.x0 - 1;          // degenerate or non-finite: nothing
 }
 
-// the fragments of one screen triangle, all lanes of the warp together
-__device__ __forceinline__ void raster_tri(const RenderCfg& R, const ScreenTri& s, unsigned id,
-                                           unsigned long long* zb, int lane) {
-    int bw = s.x1 - s.x0 + 1, bh = s.y1 - s.y0 + 1;
-    if (bw <= 0 || bh <= 0) return;
-    float sg = s.A > 0.f ? 1.f : -1.f, sa = fabsf(s.A);
-    int n = bw * bh;
-    for (int p = lane; p < n; p += 32) {
-        int py = s.y0 + p / bw, px = s.x0 + p % bw;
+// Screen triangle records in shared memory: 13 words each -- sx[3], sy[3],
+// iz[3], A, x0 | x1 << 16, y0 | y1 << 16, triangle index.
+constexpr int R_REC = 13;
+constexpr int R_WARPS = R_THREADS / 32;
+
+__device__ __forceinline__ void put_rec(float* rec, const ScreenTri& s, unsigned id) {
+    for (int k = 0; k < 3; k++) { rec[k] = s.sx[k]; rec[3 + k] = s.sy[k]; rec[6 + k] = s.iz[k]; }
+    rec[9] = s.A;
+    rec[10] = __int_as_float(s.x0 | s.x1 << 16);
+    rec[11] = __int_as_float(s.y0 | s.y1 << 16);
+    rec[12] = __uint_as_float(id);
+}
+
+// pixels [p0, p0 + n) (row-major in the record's bounding box), lanes of the
+// warp together; the surviving key per pixel is the least (depth, index)
+__device__ __forceinline__ void raster_span(const RenderCfg& R, const float* rec, int p0, int n,
+                                            unsigned long long* zb, int r0, int lane) {
+    float sx[3], sy[3], iz[3];
+    for (int k = 0; k < 3; k++) { sx[k] = rec[k]; sy[k] = rec[3 + k]; iz[k] = rec[6 + k]; }
+    float A = rec[9];
+    int bx = __float_as_int(rec[10]), by = __float_as_int(rec[11]);
+    unsigned id = __float_as_uint(rec[12]);
+    int x0 = bx & 0xffff, x1 = bx >> 16, y0 = by & 0xffff;
+    int bw = x1 - x0 + 1;
+    float sg = A > 0.f ? 1.f : -1.f, sa = fabsf(A);
+    for (int q = lane; q < n; q += 32) {
+        int p = p0 + q;
+        int py = y0 + p / bw, px = x0 + p % bw;
         float x = px + 0.5f, y = py + 0.5f;
         float w[3];
         for (int k = 0; k < 3; k++) {
             int a = k == 2 ? 0 : k + 1, c = k == 0 ? 2 : (k == 1 ? 0 : 1);
-            w[k] = sg * ((s.sx[c] - s.sx[a]) * (y - s.sy[a]) - (s.sy[c] - s.sy[a]) * (x - s.sx[a]));
+            w[k] = sg * ((sx[c] - sx[a]) * (y - sy[a]) - (sy[c] - sy[a]) * (x - sx[a]));
         }
         if (w[0] < 0.f || w[1] < 0.f || w[2] < 0.f) continue;
-        float izp = (w[0] * s.iz[0] + w[1] * s.iz[1] + w[2] * s.iz[2]) / sa;
+        float izp = (w[0] * iz[0] + w[1] * iz[1] + w[2] * iz[2]) / sa;
         float z = 1.f / izp;
         if (!(z > 0.f)) continue;
         unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | id;
-        atomicMin(zb + py * R.W + px, key);
+        atomicMin(zb + (py - r0) * R.W + px, key);
     }
-}
-
-__device__ __forceinline__ ScreenTri shfl_tri(const ScreenTri& s, int src) {
-    ScreenTri o;
-    for (int k = 0; k < 3; k++) {
-        o.sx[k] = __shfl_sync(R_FULL, s.sx[k], src);
-        o.sy[k] = __shfl_sync(R_FULL, s.sy[k], src);
-        o.iz[k] = __shfl_sync(R_FULL, s.iz[k], src);
-    }
-    o.A = __shfl_sync(R_FULL, s.A, src);
-    o.x0 = __shfl_sync(R_FULL, s.x0, src); o.x1 = __shfl_sync(R_FULL, s.x1, src);
-    o.y0 = __shfl_sync(R_FULL, s.y0, src); o.y1 = __shfl_sync(R_FULL, s.y1, src);
-    return o;
 }
 
 // shared-memory sections of k_render, each 16-byte aligned
 struct RenderSmem {
-    size_t vert, tri, rgb, base, total;
+    size_t vert, tri, rgb, base, list, pre, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline RenderSmem render_smem(int W, int H, int max_tri, int max_nb) {
+__host__ __device__ inline RenderSmem render_smem(int W, int band_rows, int max_tri, int max_nb) {
     RenderSmem m;
-    m.vert = align16((size_t)W * H * 8);
+    m.vert = align16((size_t)W * band_rows * 8);
     m.tri = m.vert + sizeof(float4) * R_NV;
     m.rgb = align16(m.tri + sizeof(int) * R_NT);
     m.base = align16(m.rgb + sizeof(uint32_t) * max_tri);
-    m.total = align16(m.base + sizeof(int) * (max_nb + 1));
+    m.list = align16(m.base + sizeof(int) * (max_nb + 2));                 // + the list count
+    m.pre = align16(m.list + sizeof(float) * R_REC * 2 * R_THREADS);       // two records per triangle of a chunk
+    m.total = align16(m.pre + sizeof(int) * (2 * R_THREADS + 1));
     return m;
 }
 
+// One CTA per env.  Triangles are taken R_THREADS at a time: each thread
+// sets up one (its packed colour, and up to two clipped screen triangles
+// appended to a shared list); then the list's pixel bounding boxes are laid
+// end to end and every warp rasterises an equal share of that pixel range,
+// so one large triangle (the ground) is spread over all warps.
 __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
     extern __shared__ __align__(16) char smem[];
-    const int P = R.W * R.H;
-    RenderSmem m = render_smem(R.W, R.H, R.max_tri, R.max_nb);
+    int env = blockIdx.x / R.bands, band = blockIdx.x % R.bands;
+    const int r0 = band * R.band_rows, r1 = min(R.H, r0 + R.band_rows);
+    const int P = R.W * (r1 - r0);                                     // this band's pixels
+    RenderSmem m = render_smem(R.W, R.band_rows, R.max_tri, R.max_nb);
     unsigned long long* zb = reinterpret_cast<unsigned long long*>(smem);
     float4* vert = reinterpret_cast<float4*>(smem + m.vert);
     int* tri = reinterpret_cast<int*>(smem + m.tri);
     uint32_t* trgb = reinterpret_cast<uint32_t*>(smem + m.rgb);         // packed colour per triangle
     int* tbase = reinterpret_cast<int*>(smem + m.base);                 // first triangle of each body, + total
-    int env = blockIdx.x;
+    float* list = reinterpret_cast<float*>(smem + m.list);
+    int* pre = reinterpret_cast<int*>(smem + m.pre);                    // exclusive prefix of the bbox areas
     int b0 = D.body_off[env], nb = D.body_off[env + 1] - b0;
+    int* cnt = tbase + nb + 1;
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long EMPTY = ~0ull;
     for (int i = tid; i < P; i += R_THREADS) zb[i] = EMPTY;
@@ -253,22 +273,20 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
     }
     __syncthreads();
     int ntri = tbase[nb];
-    float3 L = f3(0.3f, 0.2f, 1.f);                                  // light direction
+    float3 L = f3(0.3f, 0.2f, 1.f);                                    // light direction
     L = L * (1.f / len(L));
-    for (int c0 = warp * 32; c0 < ntri; c0 += R_THREADS) {
-        int t = c0 + lane;
-        ScreenTri s0, s1;                                              // empty unless set up below
-        s0.x0 = 0; s0.x1 = -1; s1.x0 = 0; s1.x1 = -1;
+    for (int c0 = 0; c0 < ntri; c0 += R_THREADS) {
+        if (tid == 0) *cnt = 0;
+        __syncthreads();
+        int t = c0 + tid;
         if (t < ntri) {
             int bi = 0;                                                // body of triangle t
             while (bi + 1 < nb && tbase[bi + 1] <= t) bi++;
             int type = D.meta[b0 + bi].x & 0xff;
-            int lt = t - tbase[bi];
-            int tv = tri[R.t0[type] + lt];
+            int tv = tri[R.t0[type] + t - tbase[bi]];
             float4 shp = D.shape[b0 + bi];
-            float4 q = D.q[b0 + bi];
             float3 x = xyz(D.x[b0 + bi]);
-            M3 Rb = qmat(q);
+            M3 Rb = qmat(D.q[b0 + bi]);
             float3 w[3], v[3];
             for (int k = 0; k < 3; k++) {
                 float3 p = local_vertex(vert[R.v0[type] + ((tv >> (8 * k)) & 0xff)], type, shp);
@@ -283,8 +301,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
             uint32_t rgba = 0xff000000u;
             for (int ch = 0; ch < 3; ch++) {
                 float val = floorf(base[ch] * shade * 255.f + 0.5f);
-                uint32_t u = (uint32_t)fminf(fmaxf(val, 0.f), 255.f);
-                rgba |= u << (8 * ch);
+                rgba |= (uint32_t)fminf(fmaxf(val, 0.f), 255.f) << (8 * ch);
             }
             trgb[t] = rgba;
             if (dot(n, w[0] - R.eye) < 0.f) {                          // front-facing
@@ -299,20 +316,58 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
                         poly[np++] = a + (c - a) * sgm;
                     }
                 }
-                if (np >= 3) screen_tri(R, poly[0], poly[1], poly[2], s0);
-                if (np == 4) screen_tri(R, poly[0], poly[2], poly[3], s1);
+                for (int f = 0; f + 2 < np; f++) {
+                    ScreenTri s;
+                    screen_tri(R, poly[0], poly[f + 1], poly[f + 2], r0, r1, s);
+                    if (s.x1 >= s.x0 && s.y1 >= s.y0) {
+                        int slot = atomicAdd(cnt, 1);                  // list order is free: keys decide
+                        put_rec(list + (size_t)R_REC * slot, s, (unsigned)t);
+                    }
+                }
             }
         }
-        for (int l = 0; l < 32; l++) {
-            unsigned id = (unsigned)(c0 + l);
-            ScreenTri a = shfl_tri(s0, l);
-            raster_tri(R, a, id, zb, lane);
-            ScreenTri b = shfl_tri(s1, l);
-            raster_tri(R, b, id, zb, lane);
+        __syncthreads();
+        int nl = *cnt;
+        if (warp == 0) {                                               // prefix of the bbox areas
+            int per = (nl + 31) / 32, lo = min(lane * per, nl), hi = min(lo + per, nl);
+            int sum = 0;
+            for (int i = lo; i < hi; i++) {
+                const float* r = list + (size_t)R_REC * i;
+                int bx = __float_as_int(r[10]), by = __float_as_int(r[11]);
+                sum += ((bx >> 16) - (bx & 0xffff) + 1) * ((by >> 16) - (by & 0xffff) + 1);
+            }
+            int incl = sum;
+            for (int d = 1; d < 32; d <<= 1) {
+                int u = __shfl_up_sync(R_FULL, incl, d);
+                if (lane >= d) incl += u;
+            }
+            int run = incl - sum;
+            for (int i = lo; i < hi; i++) {
+                pre[i] = run;
+                const float* r = list + (size_t)R_REC * i;
+                int bx = __float_as_int(r[10]), by = __float_as_int(r[11]);
+                run += ((bx >> 16) - (bx & 0xffff) + 1) * ((by >> 16) - (by & 0xffff) + 1);
+            }
+            if (lane == 31) pre[nl] = incl;
         }
+        __syncthreads();
+        int total = pre[nl];
+        int pos = (int)((long long)total * warp / R_WARPS), end = (int)((long long)total * (warp + 1) / R_WARPS);
+        if (pos < end) {
+            int lo = 0, hi = nl - 1;                                   // last entry with pre <= pos
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (pre[mid] <= pos) lo = mid; else hi = mid - 1;
+            }
+            for (int e = lo; pos < end && e < nl; e++) {
+                int stop = min(end, pre[e + 1]);
+                if (stop > pos) raster_span(R, list + (size_t)R_REC * e, pos - pre[e], stop - pos, zb, r0, lane);
+                pos = max(pos, stop);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    size_t o = (size_t)env * P;
+    size_t o = (size_t)env * R.W * R.H + (size_t)r0 * R.W;
     for (int i = tid; i < P; i += R_THREADS) {
         unsigned long long key = zb[i];
         uint32_t rgba = 0u;
@@ -332,7 +387,9 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
     }
 }
 
-size_t render_smem_bytes(int W, int H, int max_tri, int max_nb) { return render_smem(W, H, max_tri, max_nb).total; }
+size_t render_smem_bytes(int W, int band_rows, int max_tri, int max_nb) {
+    return render_smem(W, band_rows, max_tri, max_nb).total;
+}
 
 // ----------------------------------------------------------------- host side
 struct RenderState {
@@ -384,7 +441,17 @@ const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_
         for (int i = body_off[env]; i < body_off[env + 1]; i++) n += M.nt[types[i]];
         max_tri = std::max(max_tri, n);
     }
+    // rows per CTA: the fewest bands whose CTAs fit two to an SM (about 113
+    // KB of shared memory each), so that one CTA's barrier waits overlap the
+    // other's work; the whole image in one CTA if nothing smaller fits better
+    int bands = 1;
     size_t smem = render_smem_bytes(c->width, c->height, std::max(max_tri, 1), max_nb);
+    for (int nbands = 1; nbands <= 8; nbands *= 2) {
+        int rows = (c->height + nbands - 1) / nbands;
+        size_t sm = render_smem_bytes(c->width, rows, std::max(max_tri, 1), max_nb);
+        bands = nbands; smem = sm;
+        if (sm <= 110 * 1024) break;
+    }
     if (smem > (size_t)smem_optin) return "image too large for the shared-memory z-buffer";
     cudaFree(r->d_vert); cudaFree(r->d_tri); cudaFree(r->d_rgb);
     r->d_vert = nullptr; r->d_tri = nullptr; r->d_rgb = nullptr;
@@ -403,6 +470,8 @@ const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_
     R.F = (float)(0.5 * c->height / std::tan(0.5 * (double)c->fov_y));
     R.near = c->near;
     R.W = c->width; R.H = c->height;
+    R.bands = bands;
+    R.band_rows = (c->height + bands - 1) / bands;
     R.max_tri = std::max(max_tri, 1);
     R.max_nb = max_nb;
     for (int k = 0; k < 4; k++) { R.v0[k] = M.v0[k]; R.t0[k] = M.t0[k]; R.nt[k] = M.nt[k]; }
@@ -422,7 +491,7 @@ cudaError_t render_launch(RenderState* r, const DevBatch& D, uint8_t* rgba, floa
     R.out_rgba = reinterpret_cast<uint32_t*>(rgba);
     R.out_depth = depth;
     R.out_seg = seg;
-    if (D.E > 0) k_render<<<D.E, R_THREADS, r->smem, s>>>(D, R);
+    if (D.E > 0) k_render<<<D.E * R.bands, R_THREADS, r->smem, s>>>(D, R);
     return cudaGetLastError();
 }
 
