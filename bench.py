@@ -265,7 +265,7 @@ def time_cpu_baseline(name, n_envs, steps, one_core=False, variants=False):
         n1 = max(1, n_envs // 16)
         o1 = oracle.Oracle(sc.subset(range(n1)))
         t0 = time.perf_counter()
-        run(o1, steps, np.ascontiguousarray(acts[:, :n1]), 1)
+        run(o1, steps, None if acts is None else np.ascontiguousarray(acts[:, :n1]), 1)
         d1 = time.perf_counter() - t0
         out["value_1core"] = n1 * steps / d1
         out["sample_1core"] = f"{n1} envs x {steps} steps, 1 thread ({d1:.1f} s)"
