@@ -39,6 +39,8 @@ WORKLOADS = {
     "small": "plane + 1 box + 3 spheres, 64 envs (dt 0.01 s, 4 substeps, 8+1 iterations)",
     "clutter": "1-32 boxes/spheres/capsules in a 5-box bin, 16384 envs (dt 0.01 s, 4 substeps, 8+1)",
     "hand": "16-DoF capsule hand holding a cube, 4096 envs (dt 1/120 s, 8 substeps, 16+1 iterations)",
+    "mixed": "arm (9 joints), hand (16 joints) and clutter (no joint) envs interleaved in one batch, 4096 envs "
+             "(dt 0.01 s, 4 substeps, 8+1 iterations, capacities 704 pairs / 384 contacts)",
     "pick": "the arm envs driven by the pick task, 4096 envs: delta joint-position controller on normalised "
             "actions, and per step a record of reward, grasp / tcp / table flags, tcp and cube positions, "
             "joint coordinates and targets (dt 0.01 s, 4 substeps, 8+1 iterations)",

@@ -452,15 +452,34 @@ def body_colors(scene: "Scene") -> np.ndarray:
     return out
 
 
+# ----------------------------------------------------------------------------
+# Config "mixed": heterogeneous articulations with per-env DOF in one batch --
+# arm envs (9 joints), hand envs (16 joints) and clutter envs (no joint)
+# interleaved (env e is of type e mod 3), under one set of solver parameters.
+# ----------------------------------------------------------------------------
+def make_mixed(n_envs=4096, seed=7) -> Scene:
+    counts = [(n_envs + 2 - k) // 3 for k in range(3)]
+    parts = [make_arm(counts[0], seed), make_hand(counts[1], seed + 1), make_clutter(counts[2], seed + 2)]
+    common = default_params(contact_capacity=384, pair_capacity=704)
+    for p in parts:
+        p.params = dict(common)
+    sc = concat(parts, name="mixed")
+    offs = np.cumsum([0] + counts)
+    out = sc.subset([int(offs[e % 3] + e // 3) for e in range(n_envs)])
+    out.name = "mixed"
+    return out
+
+
 CONFIGS = {
     "small": make_small,
     "arm": make_arm,
     "clutter": make_clutter,
     "hand": make_hand,
     "pick": make_pick,
+    "mixed": make_mixed,
 }
 
-CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096, "pick": 4096}
+CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096, "pick": 4096, "mixed": 4096}
 
 
 def make_scene(name: str, n_envs: Optional[int] = None, seed: Optional[int] = None, **kw) -> Scene:

@@ -43,7 +43,7 @@ def test_freefall_closed_form():
     assert not status.any()
 
 
-CASES = [("small", 64), ("arm", 64), ("clutter", 256), ("hand", 64)]
+CASES = [("small", 64), ("arm", 64), ("clutter", 256), ("hand", 64), ("mixed", 96)]
 
 
 @pytest.mark.parametrize("name,n", CASES)
@@ -63,7 +63,8 @@ def test_one_step_parity(name, n):
         assert status[e] == o.status(e)
 
 
-@pytest.mark.parametrize("name,n,steps", [("small", 64, 200), ("arm", 32, 200), ("hand", 16, 100)])
+@pytest.mark.parametrize("name,n,steps", [("small", 64, 200), ("arm", 32, 200), ("hand", 16, 100),
+                                          ("mixed", 48, 100)])
 def test_rollout_parity_non_chaotic(name, n, steps):
     sc = scenegen.make_scene(name, n_envs=n)
     calm, ost = non_chaotic(sc, steps)
@@ -78,7 +79,7 @@ def test_rollout_parity_non_chaotic(name, n, steps):
     assert ok[clean].all(), f"envs {bad.tolist()} errors {err[bad].tolist()}"
 
 
-@pytest.mark.parametrize("name,n", [("arm", 48), ("clutter", 128), ("hand", 32)])
+@pytest.mark.parametrize("name,n", [("arm", 48), ("clutter", 128), ("hand", 32), ("mixed", 60)])
 def test_plain_path_bit_identical_to_batched(name, n):
     sc = scenegen.make_scene(name, n_envs=n)
     _, a, sa = gpu_run(sc, 3)
@@ -104,6 +105,24 @@ def test_env_result_independent_of_batch_composition():
     bo = sc.body_off
     got = np.concatenate([full[bo[e]:bo[e + 1]] for e in pick])
     assert np.array_equal(got, part)
+
+
+@pytest.mark.parametrize("tuning", [None, (4, 2, 0), (32, 1, 1)])
+def test_mixed_batch_env_equals_env_alone(tuning):
+    """Per-env DOF: each env of a batch of arms (9 joints), hands (16) and
+    clutter bins (0), stepped together, is bit-identical to the same env
+    stepped alone (actions padded to the batch's 16 slots with NaN)."""
+    sc = scenegen.make_scene("mixed", n_envs=30)
+    _, full, _ = gpu_run(sc, 5, tuning=tuning)
+    bo = sc.body_off
+    for e in (0, 1, 2, 13, 29):
+        one = sc.subset([e])
+        nj = int(sc.joint_off[e + 1] - sc.joint_off[e])         # the env's own action width
+        fn = one.action_fn
+        one.n_act = nj
+        one.action_fn = (lambda f, k: (lambda s0, n: np.ascontiguousarray(f(s0, n)[:, :, :k])))(fn, nj) if nj else None
+        _, alone, _ = gpu_run(one, 5)
+        assert np.array_equal(full[bo[e]:bo[e + 1]], alone), e
 
 
 def test_graph_replay_equals_eager_and_split_calls():
@@ -186,7 +205,7 @@ def test_pin_scenes_follow_oracle(scene_fn, steps):
     assert within(err, 10.0).all(), err
 
 
-@pytest.mark.parametrize("name", ["small", "arm", "clutter", "hand"])
+@pytest.mark.parametrize("name", ["small", "arm", "clutter", "hand", "mixed"])
 def test_full_size_sampled_envs(name):
     """Full-size batch in the benchmark's launch configuration (autotuned);
     32 sampled envs are checked against the oracle run on those envs alone."""
