@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "oracle.c")
 COUNTERS = ["steps", "pairs_tested", "pairs_candidate",
             "np_ss", "np_sc", "np_sb", "np_sp", "np_cc", "np_cb", "np_cp", "np_bb", "np_bp",
             "contact_points", "constraints", "rows_prep", "row_solve_2dyn", "row_solve_1dyn",
-            "warm_apply", "body_integrate", "body_inertia", "colors"]
+            "warm_apply", "body_integrate", "body_inertia", "colors", "np_sh", "np_xh", "np_hp"]
 
 ST_PAIR_OVERFLOW, ST_CONTACT_OVERFLOW, ST_COLOR_OVERFLOW = 1, 2, 4
 
@@ -49,6 +49,9 @@ def lib():
         lp = C.POINTER(C.c_longlong)
         L.oracle_create.restype = P
         L.oracle_create.argtypes = [C.c_int, lp, dp, lp, dp, dp]
+        L.oracle_create_hulls.restype = P
+        L.oracle_create_hulls.argtypes = [C.c_int, lp, dp, lp, dp, dp, C.c_int, ip, dp, ip, ip]
+        L.oracle_hull_inertia.argtypes = [dp, C.c_int, ip, C.c_int, C.c_double, dp]
         L.oracle_destroy.argtypes = [P]
         L.oracle_step.argtypes = [P, dp, C.c_int, C.c_int, C.c_int]
         L.oracle_get_state.argtypes = [P, dp]
@@ -152,8 +155,20 @@ class Oracle:
             self._b[:, 5:8] = state_override[:, 0:3]
         self._j = np.ascontiguousarray(joint_rows(scene.joints)) if self.nj else np.zeros((1, 22))
         self._p = param_row(scene.params)
-        self.h = L.oracle_create(self.E, _lp(self._bo), _dp(self._b), _lp(self._jo), _dp(self._j),
-                                 _dp(self._p))
+        hl = getattr(scene, "hulls", None)
+        if hl is None:
+            self.h = L.oracle_create(self.E, _lp(self._bo), _dp(self._b), _lp(self._jo), _dp(self._j),
+                                     _dp(self._p))
+        else:
+            self._hv = np.ascontiguousarray(hl["verts"], np.float64).reshape(-1)
+            self._hvo = np.ascontiguousarray(hl["vert_off"], np.int32)
+            self._ht = np.ascontiguousarray(hl["tris"], np.int32).reshape(-1)
+            self._hto = np.ascontiguousarray(hl["tri_off"], np.int32)
+            self.h = L.oracle_create_hulls(self.E, _lp(self._bo), _dp(self._b), _lp(self._jo), _dp(self._j),
+                                           _dp(self._p), len(self._hvo) - 1, _ip(self._hvo), _dp(self._hv),
+                                           _ip(self._hto), _ip(self._ht))
+            if not self.h:
+                raise ValueError("malformed hull in the library")
         self.A = scene.n_act
         self.steps_done = 0
 
@@ -302,6 +317,15 @@ def color(a, b, dyn):
     out = np.zeros(max(len(a), 1), np.int32)
     nc = lib().oracle_color(len(a), _ip(a), _ip(b), _ip(dyn), _ip(out))
     return nc, out[:len(a)]
+
+
+def hull_inertia(verts, tris, mass):
+    v = np.ascontiguousarray(verts, np.float64).reshape(-1)
+    t = np.ascontiguousarray(tris, np.int32).reshape(-1)
+    out = np.zeros(3, np.float64)
+    if lib().oracle_hull_inertia(_dp(v), len(v) // 3, _ip(t), len(t) // 3, mass, _dp(out)) != 0:
+        raise ValueError("malformed hull")
+    return out
 
 
 def inertia(body_row):

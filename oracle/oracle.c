@@ -89,8 +89,21 @@ static int basis_axis(v3 a) {
 /* ------------------------------------------------------------------------- */
 /* world data                                                                 */
 /* ------------------------------------------------------------------------- */
+/* convex hull asset (body frame = its principal frame): vertices, outward
+ * counter-clockwise triangles, and what the narrowphase derives from them */
+enum { H_MAXV = 16, H_MAXT = 2 * H_MAXV - 4, H_MAXE = 3 * H_MAXV - 6 };
+typedef struct {
+    int nv, nt, ne;
+    v3 v[H_MAXV];
+    int t[H_MAXT][3];
+    int e[H_MAXE][2], ef[H_MAXE][2];  /* edge vertices, its two triangles */
+    double rad;                       /* bounding radius about the origin */
+    double vol; v3 c2;                /* volume; diagonal second moments of unit density */
+} Hull;
+
 typedef struct {
     int type; double p[3]; double mass; int dyn;
+    const Hull* hull;                 /* hull bodies */
     double inv_mass; double inv_I[3]; double mu, rest; unsigned group, mask;
     v3 x; qt q; v3 v; v3 w;
     m3 invIw;                         /* world inverse inertia, per substep */
@@ -150,6 +163,7 @@ struct oracle_world {
     int task_on, t_grip, t_fa, t_fb, t_cube, t_table, t_A;
     double t_grasp_tol, t_touch_tol;
     double* t_half;                   /* [t_A] (h - l) / 2 of the delta controller */
+    int nh; Hull* hulls;              /* hull library */
     int nb_total, nj_total;
     long long* body_off; long long* joint_off;
 };
@@ -229,6 +243,9 @@ static void aabb(const Body* b, double half_margin, v3* lo, v3* hi) {
     v3 e;
     if (b->type == OR_SPHERE) {
         e = V(b->p[0], b->p[0], b->p[0]);
+    } else if (b->type == OR_HULL) {
+        /* a hull: the bounding sphere of its vertices about the body origin */
+        e = V(b->hull->rad, b->hull->rad, b->hull->rad);
     } else if (b->type == OR_BOX) {
         /* half-widths of a rotated box: |R| h */
         e = V(fabs(R.m[0][0]) * b->p[0] + fabs(R.m[0][1]) * b->p[1] + fabs(R.m[0][2]) * b->p[2],
@@ -284,18 +301,30 @@ static void broadphase(const oracle_world* w, Env* e) {
 /* d = n.(cA - cB) (< 0: penetration); a point is kept iff d < margin.       */
 /* ------------------------------------------------------------------------- */
 typedef struct { v3 cA, cB, n; double d; } Cand;
-typedef struct { int n; Cand c[8]; } CandSet;
+typedef struct { int n; Cand c[16]; } CandSet;
 
-typedef struct { v3 x; m3 R; qt q; int type; double p[3]; } Shape;
+typedef struct { v3 x; m3 R; qt q; int type; double p[3]; const Hull* hull; } Shape;
 
 static Shape shape_of(const Body* b) {
     Shape s; s.x = b->x; s.q = b->q; s.R = qmat(b->q); s.type = b->type;
     s.p[0] = b->p[0]; s.p[1] = b->p[1]; s.p[2] = b->p[2];
+    s.hull = b->hull;
     return s;
 }
 
+/* pair order of the narrowphase: sphere < capsule < box < hull < plane */
+static int shape_rank(int type) {
+    switch (type) {
+    case OR_SPHERE: return 0;
+    case OR_CAPSULE: return 1;
+    case OR_BOX: return 2;
+    case OR_HULL: return 3;
+    default: return 4;
+    }
+}
+
 static void push(CandSet* cs, v3 cA, v3 cB, v3 n, double d) {
-    if (cs->n < 8) { Cand* c = &cs->c[cs->n++]; c->cA = cA; c->cB = cB; c->n = n; c->d = d; }
+    if (cs->n < 16) { Cand* c = &cs->c[cs->n++]; c->cA = cA; c->cB = cB; c->n = n; c->d = d; }
 }
 
 /* two spheres (centres a, b; radii ra, rb); n = +z when centres coincide */
@@ -716,6 +745,224 @@ static void np_bb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
     }
 }
 
+
+/* ------------------------------------------------------------------ hulls */
+/* A convex polytope in world coordinates: a hull (triangular faces), or a
+ * box (8 corners, 6 quadrilateral faces).  Faces are counter-clockwise
+ * seen from outside; each edge lists its two faces. */
+enum { P_MAXV = 16, P_MAXF = 28, P_MAXE = 42 };
+typedef struct {
+    int nv, nf, ne;
+    v3 v[P_MAXV];
+    v3 fn[P_MAXF]; double fd[P_MAXF];  /* outward unit normal, offset fn.x = fd on the face */
+    int fv[P_MAXF][4], fnv[P_MAXF];
+    int e[P_MAXE][2], ef[P_MAXE][2];
+    v3 c;                              /* body origin (interior) */
+} Poly;
+
+static void poly_faces(Poly* P) {
+    for (int f = 0; f < P->nf; f++) {
+        v3 a = P->v[P->fv[f][0]], b = P->v[P->fv[f][1]], c = P->v[P->fv[f][2]];
+        v3 n = cross(sub(b, a), sub(c, a));
+        n = scl(n, 1.0 / norm(n));
+        P->fn[f] = n; P->fd[f] = dot(n, a);
+    }
+}
+
+static void poly_of(const Shape* S, Poly* P) {
+    P->c = S->x;
+    if (S->type == OR_BOX) {
+        static const int F[6][4] = {{1, 3, 7, 5}, {2, 0, 4, 6}, {3, 2, 6, 7}, {0, 1, 5, 4}, {4, 5, 7, 6}, {2, 3, 1, 0}};
+        P->nv = 8; P->nf = 6; P->ne = 0;
+        for (int k = 0; k < 8; k++)
+            P->v[k] = add(S->x, mv(&S->R, V((k & 1) ? S->p[0] : -S->p[0], (k & 2) ? S->p[1] : -S->p[1],
+                                              (k & 4) ? S->p[2] : -S->p[2])));
+        for (int f = 0; f < 6; f++) { P->fnv[f] = 4; for (int k = 0; k < 4; k++) P->fv[f][k] = F[f][k]; }
+        /* each edge once, from the face listing it a -> b with a < b; its
+         * other face lists b -> a */
+        for (int f = 0; f < 6; f++)
+            for (int k = 0; k < 4; k++) {
+                int a = F[f][k], b = F[f][(k + 1) % 4];
+                if (a > b) continue;
+                int g = -1;
+                for (int h = 0; h < 6 && g < 0; h++)
+                    for (int q = 0; q < 4; q++)
+                        if (F[h][q] == b && F[h][(q + 1) % 4] == a) { g = h; break; }
+                P->e[P->ne][0] = a; P->e[P->ne][1] = b; P->ef[P->ne][0] = f; P->ef[P->ne][1] = g; P->ne++;
+            }
+    } else {
+        const Hull* H = S->hull;
+        P->nv = H->nv; P->nf = H->nt; P->ne = H->ne;
+        for (int k = 0; k < H->nv; k++) P->v[k] = add(S->x, mv(&S->R, H->v[k]));
+        for (int f = 0; f < H->nt; f++) { P->fnv[f] = 3; for (int k = 0; k < 3; k++) P->fv[f][k] = H->t[f][k]; }
+        for (int k = 0; k < H->ne; k++) {
+            P->e[k][0] = H->e[k][0]; P->e[k][1] = H->e[k][1];
+            P->ef[k][0] = H->ef[k][0]; P->ef[k][1] = H->ef[k][1];
+        }
+    }
+    poly_faces(P);
+}
+
+/* hull - plane: every vertex within the margin (as box - plane) */
+static void np_hp(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)e;
+    v3 N = mcol(&B->R, 2);
+    const Hull* H = A->hull;
+    for (int k = 0; k < H->nv; k++) {
+        v3 v = add(A->x, mv(&A->R, H->v[k]));
+        double dist = dot(N, sub(v, B->x));
+        if (dist < m + 1e-4) push(cs, v, sub(v, scl(N, dist)), N, dist);   /* 1e-4: margin ties stay visible */
+    }
+}
+
+/* closest point of triangle (a, b, c) to p (Ericson 2005, 5.1.5) */
+static v3 closest_on_triangle(v3 p, v3 a, v3 b, v3 c) {
+    v3 ab = sub(b, a), ac = sub(c, a), ap = sub(p, a);
+    double d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) return a;
+    v3 bp = sub(p, b);
+    double d3 = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) return b;
+    double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) return add(a, scl(ab, d1 / (d1 - d3)));
+    v3 cp = sub(p, c);
+    double d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) return c;
+    double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) return add(a, scl(ac, d2 / (d2 - d6)));
+    double va = d3 * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0)
+        return add(b, scl(sub(c, b), (d4 - d3) / ((d4 - d3) + (d5 - d6))));
+    double den = 1.0 / (va + vb + vc);
+    return add(a, add(scl(ab, vb * den), scl(ac, vc * den)));
+}
+
+/* sphere - hull: centre inside (no face plane separates it): push out along
+ * the face of least penetration; outside: the closest point of the surface */
+static void np_sh(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    (void)m;
+    Poly P;
+    poly_of(B, &P);
+    v3 c = A->x;
+    double r = A->p[0];
+    double smax = -INFINITY, s2 = -INFINITY;
+    int fb = 0;
+    for (int f = 0; f < P.nf; f++) {
+        double sf = dot(P.fn[f], c) - P.fd[f];
+        if (sf > smax) { s2 = smax; smax = sf; fb = f; } else if (sf > s2) s2 = sf;
+    }
+    tie(e, smax, 0.0);
+    if (smax <= 0.0) {
+        tie(e, smax, s2);
+        v3 n = P.fn[fb];
+        push(cs, sub(c, scl(n, r)), sub(c, scl(n, smax)), n, smax - r);
+        return;
+    }
+    double best = INFINITY;
+    v3 q = c;
+    for (int f = 0; f < P.nf; f++) {
+        v3 t = closest_on_triangle(c, P.v[P.fv[f][0]], P.v[P.fv[f][1]], P.v[P.fv[f][2]]);
+        double d2 = dot(sub(c, t), sub(c, t));
+        if (d2 < best) { best = d2; q = t; }
+    }
+    double dist = sqrt(best);
+    v3 n = scl(sub(c, q), 1.0 / dist);
+    push(cs, sub(c, scl(n, r)), q, n, dist - r);
+}
+
+/* box or hull (A) - hull (B): separating axes over the face normals of A,
+ * then of B, then the cross products of edge pairs that bound a face of
+ * the Minkowski difference (their arcs on the Gauss map cross); a B face
+ * is the reference only if it beats the best A face by 1e-4 m, an edge
+ * pair only if it beats the best face by 1e-4 m.  Face case: the most
+ * anti-parallel face of the other polytope is clipped against the side
+ * planes of the reference face; edge case: one point, the closest points
+ * of the two edges. */
+static void np_poly(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    Poly PA, PB;
+    poly_of(A, &PA);
+    poly_of(B, &PB);
+    double sa = -INFINITY; int fa = 0;
+    for (int f = 0; f < PA.nf; f++) {
+        double sf = INFINITY;
+        for (int k = 0; k < PB.nv; k++) sf = fmin(sf, dot(PA.fn[f], PB.v[k]) - PA.fd[f]);
+        if (sf > sa) { sa = sf; fa = f; }
+    }
+    double sb = -INFINITY; int fb = 0;
+    for (int f = 0; f < PB.nf; f++) {
+        double sf = INFINITY;
+        for (int k = 0; k < PA.nv; k++) sf = fmin(sf, dot(PB.fn[f], PA.v[k]) - PB.fd[f]);
+        if (sf > sb) { sb = sf; fb = f; }
+    }
+    double se = -INFINITY; int ea = -1, eb = -1; v3 axe = V(0, 0, 0);
+    for (int i = 0; i < PA.ne; i++) {
+        v3 a = PA.fn[PA.ef[i][0]], b = PA.fn[PA.ef[i][1]];
+        v3 bxa = cross(b, a);
+        v3 ua = sub(PA.v[PA.e[i][1]], PA.v[PA.e[i][0]]);
+        for (int j = 0; j < PB.ne; j++) {
+            v3 c = neg(PB.fn[PB.ef[j][0]]), d = neg(PB.fn[PB.ef[j][1]]);
+            v3 dxc = cross(d, c);
+            double cba = dot(c, bxa), dba = dot(d, bxa), adc = dot(a, dxc), bdc = dot(b, dxc);
+            /* a pair on the verge of this test has its axis next to a face
+             * normal and that face's separation, so the 1e-4 m face
+             * preference below decides the outcome either way: no tie */
+            if (!(cba * dba < 0.0 && adc * bdc < 0.0 && cba * bdc > 0.0)) continue;
+            v3 ub = sub(PB.v[PB.e[j][1]], PB.v[PB.e[j][0]]);
+            v3 ax = cross(ua, ub);
+            double l = norm(ax), lim = 1e-5 * norm(ua) * norm(ub);
+            tie_w(e, l, lim, TIE_DIR * norm(ua) * norm(ub));
+            if (l < lim) continue;
+            ax = scl(ax, 1.0 / l);
+            if (dot(ax, sub(PA.v[PA.e[i][0]], PA.c)) < 0.0) ax = neg(ax);
+            double sij = dot(ax, sub(PB.v[PB.e[j][0]], PA.v[PA.e[i][0]]));
+            if (sij > se) { se = sij; ea = i; eb = j; axe = ax; }
+        }
+    }
+    double maxsep = fmax(fmax(sa, sb), se);
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
+    double sf = fmax(sa, sb);
+    if (ea >= 0) tie(e, se, sf + 1e-4);
+    if (ea >= 0 && se > sf + 1e-4) {
+        v3 pa, pb;
+        closest_segments(PA.v[PA.e[ea][0]], PA.v[PA.e[ea][1]], PB.v[PB.e[eb][0]], PB.v[PB.e[eb][1]], &pa, &pb);
+        v3 n = neg(axe);
+        push(cs, pa, pb, n, dot(n, sub(pa, pb)));
+        return;
+    }
+    tie(e, sb, sa + 1e-4);
+    int refB = sb > sa + 1e-4;
+    const Poly* R = refB ? &PB : &PA;
+    const Poly* I = refB ? &PA : &PB;
+    int rf = refB ? fb : fa;
+    v3 nref = R->fn[rf];
+    int inc = 0; double best = INFINITY, second = INFINITY;
+    for (int g = 0; g < I->nf; g++) {
+        double dd = dot(I->fn[g], nref);
+        if (dd < best) { second = best; best = dd; inc = g; } else if (dd < second) second = dd;
+    }
+    tie_w(e, best, second, TIE_DIR);
+    v3 bufa[8], bufb[8];
+    v3* src = bufa; v3* dst = bufb;
+    int np = I->fnv[inc];
+    for (int k = 0; k < np; k++) src[k] = I->v[I->fv[inc][k]];
+    int nr = R->fnv[rf];
+    for (int k = 0; k < nr; k++) {
+        v3 p0 = R->v[R->fv[rf][k]], p1 = R->v[R->fv[rf][(k + 1) % nr]];
+        v3 side = cross(sub(p1, p0), nref);
+        side = scl(side, 1.0 / norm(side));
+        np = clip_plane(src, np, dst, side, p0, 0.0, e);
+        v3* t = src; src = dst; dst = t;
+    }
+    v3 pref = R->v[R->fv[rf][0]];
+    for (int k = 0; k < np; k++) {
+        v3 x = src[k];
+        double dist = dot(nref, sub(x, pref));
+        if (!refB) push(cs, sub(x, scl(nref, dist)), x, neg(nref), dist);
+        else push(cs, x, sub(x, scl(nref, dist)), nref, dist);
+    }
+}
+
 static int first_unused(const int* used, int n) {
     for (int k = 0; k < n; k++) if (!used[k]) return k;
     return 0;
@@ -723,7 +970,7 @@ static int first_unused(const int* used, int n) {
 
 /* reduce > 4 candidates to 4, selection order p1..p4 (positions: cB) */
 static int reduce4(Env* e, const Cand* c, int n, int* sel) {
-    int used[8] = {0};
+    int used[16] = {0};
     int i1 = 0;
     for (int k = 1; k < n; k++) if (c[k].d < c[i1].d) i1 = k;
     for (int k = 0; k < n; k++) if (k != i1) tie(e, c[k].d, c[i1].d);
@@ -775,8 +1022,12 @@ static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, 
     else if (ta == OR_CAPSULE && tb == OR_PLANE) { np_cp(e, A, B, m, &cs); slot = OC_NP_CP; }
     else if (ta == OR_BOX && tb == OR_BOX) { np_bb(e, A, B, m, &cs); slot = OC_NP_BB; }
     else if (ta == OR_BOX && tb == OR_PLANE) { np_bp(e, A, B, m, &cs); slot = OC_NP_BP; }
+    else if (ta == OR_SPHERE && tb == OR_HULL) { np_sh(e, A, B, m, &cs); slot = OC_NP_SH; }
+    else if ((ta == OR_BOX || ta == OR_HULL) && tb == OR_HULL) { np_poly(e, A, B, m, &cs); slot = OC_NP_XH; }
+    else if (ta == OR_HULL && tb == OR_PLANE) { np_hp(e, A, B, m, &cs); slot = OC_NP_HP; }
+    /* capsule - hull: no contact (not built) */
     if (slot >= 0) e->cnt[slot]++;
-    Cand kept[8]; int nk = 0;
+    Cand kept[16]; int nk = 0;
     *margin_tie = 0;
     for (int i = 0; i < cs.n; i++) {
         if (fabs(cs.c[i].d - m) < TIE_EPS) { *margin_tie = 1; e->ties++; }
@@ -800,7 +1051,7 @@ static void narrowphase(const oracle_world* w, Env* e) {
         const Body* Bi = &e->bodies[i]; const Body* Bj = &e->bodies[j];
         /* order by shape rank, then index */
         int a = i, b = j;
-        if (Bj->type < Bi->type) { a = j; b = i; }
+        if (shape_rank(Bj->type) < shape_rank(Bi->type)) { a = j; b = i; }
         Shape A = shape_of(&e->bodies[a]), B = shape_of(&e->bodies[b]);
         Cand pts[4]; int mt;
         int np = collide(e, &A, &B, w->margin, pts, &mt);
@@ -1471,6 +1722,12 @@ static int round_mesh(double r, double l, int capsule, Tri* t) {
 }
 
 static int body_mesh(const Body* b, Tri* t) {
+    if (b->type == OR_HULL) {
+        const Hull* H = b->hull;
+        for (int f = 0; f < H->nt; f++)
+            for (int k = 0; k < 3; k++) t[f].p[k] = H->v[H->t[f][k]];
+        return H->nt;
+    }
     if (b->type == OR_BOX) return box_mesh(b, t);
     if (b->type == OR_SPHERE) return round_mesh(b->p[0], 0.0, 0, t);
     if (b->type == OR_CAPSULE) return round_mesh(b->p[0], b->p[1], 1, t);
@@ -1644,9 +1901,84 @@ int oracle_render(const oracle_world* w, const double* cam, const double* rgb_bo
 /* ------------------------------------------------------------------------- */
 /* world API                                                                  */
 /* ------------------------------------------------------------------------- */
+/* A hull asset: edges from its triangles (each once, with its two
+ * triangles), bounding radius, volume and diagonal second moments of unit
+ * density over the tetrahedra (origin, triangle): a tetrahedron with a
+ * vertex at the origin has second moments (V/20)(a a^T + b b^T + c c^T +
+ * s s^T), s = a + b + c.  Returns 0, or -1 for a mesh that is not closed. */
+static int build_hull(Hull* H, const double* v, int nv, const int* t, int nt) {
+    if (nv < 4 || nv > H_MAXV || nt < 4 || nt > H_MAXT) return -1;
+    H->nv = nv; H->nt = nt;
+    H->rad = 0.0;
+    for (int k = 0; k < nv; k++) {
+        H->v[k] = V(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
+        H->rad = fmax(H->rad, norm(H->v[k]));
+    }
+    for (int f = 0; f < nt; f++)
+        for (int k = 0; k < 3; k++) {
+            H->t[f][k] = t[3 * f + k];
+            if (H->t[f][k] < 0 || H->t[f][k] >= nv) return -1;
+        }
+    H->ne = 0;
+    for (int f = 0; f < nt; f++)
+        for (int k = 0; k < 3; k++) {
+            int a = H->t[f][k], b = H->t[f][(k + 1) % 3];
+            if (a > b) continue;
+            int g = -1;
+            for (int h = 0; h < nt && g < 0; h++)
+                for (int q = 0; q < 3; q++)
+                    if (H->t[h][q] == b && H->t[h][(q + 1) % 3] == a) { g = h; break; }
+            if (g < 0 || H->ne >= H_MAXE) return -1;
+            H->e[H->ne][0] = a; H->e[H->ne][1] = b; H->ef[H->ne][0] = f; H->ef[H->ne][1] = g; H->ne++;
+        }
+    if (2 * H->ne != 3 * nt) return -1;
+    H->vol = 0.0; H->c2 = V(0, 0, 0);
+    for (int f = 0; f < nt; f++) {
+        v3 a = H->v[H->t[f][0]], b = H->v[H->t[f][1]], c = H->v[H->t[f][2]];
+        double v6 = dot(a, cross(b, c));
+        H->vol += v6 / 6.0;
+        v3 sm = add(add(a, b), c);
+        double w = v6 / 120.0;
+        H->c2.x += w * (a.x * a.x + b.x * b.x + c.x * c.x + sm.x * sm.x);
+        H->c2.y += w * (a.y * a.y + b.y * b.y + c.y * c.y + sm.y * sm.y);
+        H->c2.z += w * (a.z * a.z + b.z * b.z + c.z * c.z + sm.z * sm.z);
+    }
+    return H->vol > 0.0 ? 0 : -1;
+}
+
+/* inertia of a hull of the given mass about its (principal) body axes */
+static void hull_inertia(const Hull* H, double mass, double* I) {
+    double rho = mass / H->vol;
+    I[0] = rho * (H->c2.y + H->c2.z);
+    I[1] = rho * (H->c2.x + H->c2.z);
+    I[2] = rho * (H->c2.x + H->c2.y);
+}
+
+int oracle_hull_inertia(const double* verts, int nv, const int* tris, int nt, double mass, double* out3) {
+    Hull H;
+    if (build_hull(&H, verts, nv, tris, nt) != 0) return -1;
+    hull_inertia(&H, mass, out3);
+    return 0;
+}
+
 oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
                             const long long* joint_off, const double* joints, const double* params) {
+    return oracle_create_hulls(n_envs, body_off, bodies, joint_off, joints, params, 0, NULL, NULL, NULL, NULL);
+}
+
+oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const double* bodies,
+                                  const long long* joint_off, const double* joints, const double* params,
+                                  int n_hulls, const int* vert_off, const double* verts, const int* tri_off,
+                                  const int* tris) {
     oracle_world* w = (oracle_world*)calloc(1, sizeof(oracle_world));
+    w->nh = n_hulls;
+    w->hulls = (Hull*)calloc((size_t)(n_hulls > 0 ? n_hulls : 1), sizeof(Hull));
+    for (int h = 0; h < n_hulls; h++)
+        if (build_hull(&w->hulls[h], verts + 3 * vert_off[h], vert_off[h + 1] - vert_off[h], tris + 3 * tri_off[h],
+                       tri_off[h + 1] - tri_off[h]) != 0) {
+            free(w->hulls); free(w);
+            return NULL;
+        }
     w->E = n_envs;
     w->dt = params[0]; w->substeps = (int)params[1]; w->pos_iters = (int)params[2];
     w->vel_iters = (int)params[3]; w->g = V(params[4], params[5], params[6]);
@@ -1665,7 +1997,20 @@ oracle_world* oracle_create(int n_envs, const long long* body_off, const double*
         e->nj = (int)(joint_off[ei + 1] - joint_off[ei]);
         e->bodies = (Body*)calloc((size_t)(e->nb > 0 ? e->nb : 1), sizeof(Body));
         e->joints = (Joint*)calloc((size_t)(e->nj > 0 ? e->nj : 1), sizeof(Joint));
-        for (int i = 0; i < e->nb; i++) body_from_desc(&e->bodies[i], bodies + 22 * (body_off[ei] + i));
+        for (int i = 0; i < e->nb; i++) {
+            Body* b = &e->bodies[i];
+            body_from_desc(b, bodies + 22 * (body_off[ei] + i));
+            if (b->type == OR_HULL) {
+                int id = (int)b->p[0];
+                if (id < 0 || id >= n_hulls) id = 0;             /* the caller checks the ids */
+                b->hull = &w->hulls[id];
+                if (b->dyn) {
+                    double I[3];
+                    hull_inertia(b->hull, b->mass, I);
+                    for (int k = 0; k < 3; k++) b->inv_I[k] = 1.0 / I[k];
+                }
+            }
+        }
         for (int i = 0; i < e->nj; i++) {
             const double* d = joints + 22 * (joint_off[ei] + i);
             Joint* j = &e->joints[i];
@@ -1696,7 +2041,7 @@ void oracle_destroy(oracle_world* w) {
         free(e->bodies); free(e->joints); free(e->pairs); free(e->tiepairs); free(e->man);
         free(e->cons); free(e->order); free(e->rows); free(e->prev); free(e->qR);
     }
-    free(w->envs); free(w->body_off); free(w->joint_off); free(w->t_half); free(w);
+    free(w->envs); free(w->body_off); free(w->joint_off); free(w->t_half); free(w->hulls); free(w);
 }
 
 typedef struct {

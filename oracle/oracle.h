@@ -51,7 +51,7 @@ extern "C" {
 
 typedef struct oracle_world oracle_world;
 
-enum { OR_SPHERE = 0, OR_CAPSULE = 1, OR_BOX = 2, OR_PLANE = 3 };
+enum { OR_SPHERE = 0, OR_CAPSULE = 1, OR_BOX = 2, OR_PLANE = 3, OR_HULL = 4 };
 enum { OR_REVOLUTE = 0, OR_PRISMATIC = 1 };
 enum { OR_ST_PAIR_OVERFLOW = 1, OR_ST_CONTACT_OVERFLOW = 2, OR_ST_COLOR_OVERFLOW = 4 };
 
@@ -60,12 +60,28 @@ enum {
     OC_STEPS = 0, OC_PAIRS_TESTED, OC_PAIRS_CANDIDATE,
     OC_NP_SS, OC_NP_SC, OC_NP_SB, OC_NP_SP, OC_NP_CC, OC_NP_CB, OC_NP_CP, OC_NP_BB, OC_NP_BP,
     OC_CONTACT_POINTS, OC_CONSTRAINTS, OC_ROWS_PREP, OC_ROW_SOLVE_2DYN, OC_ROW_SOLVE_1DYN,
-    OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NUM
+    OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NP_SH, OC_NP_XH, OC_NP_HP, OC_NUM
 };
 
 oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
                             const long long* joint_off, const double* joints,
                             const double* params);
+/* The same with a hull library: hull h has vertices verts[vert_off[h] ..
+ * vert_off[h + 1]) (x, y, z, body frame = its principal frame) and outward
+ * counter-clockwise triangles tris[tri_off[h] .. tri_off[h + 1]) (3 vertex
+ * indices local to the hull); a HULL body has p0 = its hull index.  Hulls:
+ * 4..16 vertices, a closed mesh.  Returns NULL for a malformed hull.
+ * Contacts: hull - plane (vertices within the margin), sphere - hull (face
+ * of least penetration inside, closest surface point outside), box or
+ * hull - hull (SAT over face normals and Gauss-map edge pairs, face
+ * clipping or one edge-edge point); capsule - hull pairs make no contact. */
+oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const double* bodies,
+                                  const long long* joint_off, const double* joints, const double* params,
+                                  int n_hulls, const int* vert_off, const double* verts, const int* tri_off,
+                                  const int* tris);
+/* Diagonal inertia of a hull of the given mass about its body axes (uniform
+ * density); -1 for a malformed hull. */
+int oracle_hull_inertia(const double* verts, int nv, const int* tris, int nt, double mass, double* out3);
 void oracle_destroy(oracle_world* w);
 
 /* Advance every env n_steps steps.  actions: [n_steps][n_envs][A] drive

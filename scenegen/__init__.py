@@ -23,7 +23,7 @@ from typing import Callable, Dict, List, Optional
 
 import numpy as np
 
-SPHERE, CAPSULE, BOX, PLANE = 0, 1, 2, 3
+SPHERE, CAPSULE, BOX, PLANE, HULL = 0, 1, 2, 3, 4
 REVOLUTE, PRISMATIC = 0, 1
 
 BODY_DTYPE = np.dtype([
@@ -66,6 +66,7 @@ class Scene:
     seed: int
     action_fn: Optional[Callable[[int, int], np.ndarray]] = None
     task: Optional[Dict] = None  # pick task (pick_task); actions are then normalised deltas
+    hulls: Optional[Dict] = None  # hull library (scenegen.hulls.library) of HULL bodies
 
     @property
     def n_envs(self) -> int:
@@ -98,7 +99,7 @@ class Scene:
                      np.asarray(bo, np.int32),
                      np.concatenate(jl) if jl else np.zeros(0, JOINT_DTYPE),
                      np.asarray(jo, np.int32), dict(self.params), self.n_act,
-                     self.seed, fn if self.action_fn else None, self.task)
+                     self.seed, fn if self.action_fn else None, self.task, self.hulls)
 
 
 def rng(seed: int, env: int, stream: int) -> np.random.Generator:
@@ -470,6 +471,46 @@ def make_mixed(n_envs=4096, seed=7) -> Scene:
     return out
 
 
+# ----------------------------------------------------------------------------
+# Config "hulls": convex pieces of decomposed meshes dropped into a bin --
+# random convex hulls (6-12 points in an ellipsoid), boxes as in clutter.
+# ----------------------------------------------------------------------------
+def make_hulls(n_envs=4096, seed=8, pool=128) -> Scene:
+    """A pool of `pool` hull assets (asset k drawn from its own stream, so the
+    pool does not depend on the batch); each env drops 1-12 of them, chosen
+    and posed from the env's own stream, into the clutter bin."""
+    from . import hulls as H
+    params = default_params(contact_capacity=256, pair_capacity=256)
+    assets = []
+    for k in range(pool):
+        ga = rng(seed, 1_000_000 + k, 1)
+        semi = ga.uniform(0.015, 0.04, 3)
+        assets.append(H.hull_asset(H.random_points(ga, int(ga.integers(6, 13)), semi)))
+    radius = [H.bound_radius(v) for v, _ in assets]
+    vol = [H.volume(v, t) for v, t in assets]
+    envs_b, envs_j = [], []
+    for e in range(n_envs):
+        g = rng(seed, e, 0)
+        bl = [
+            body(BOX, (0.15, 0.15, 0.01), 0.0, (0, 0, -0.01), mu=0.5, group=1),
+            body(BOX, (0.01, 0.17, 0.1), 0.0, (0.16, 0, 0.1), mu=0.5, group=1),
+            body(BOX, (0.01, 0.17, 0.1), 0.0, (-0.16, 0, 0.1), mu=0.5, group=1),
+            body(BOX, (0.17, 0.01, 0.1), 0.0, (0, 0.16, 0.1), mu=0.5, group=1),
+            body(BOX, (0.17, 0.01, 0.1), 0.0, (0, -0.16, 0.1), mu=0.5, group=1),
+        ]
+        placed = []
+        for _ in range(int(g.integers(1, 13))):
+            k = int(g.integers(0, pool))
+            c = _place(g, radius[k], np.array([-0.12, -0.12, 0.03]), np.array([0.12, 0.12, 0.5]), placed)
+            placed.append((c, radius[k]))
+            bl.append(body(HULL, (k, 0, 0), g.uniform(500.0, 2000.0) * vol[k], c, quat=shoemake_quat(g),
+                           mu=float(g.uniform(0.3, 1.0)), group=2))
+        envs_b.append(bl); envs_j.append([])
+    sc = pack("hulls", envs_b, envs_j, params, 0, seed)
+    sc.hulls = H.library(assets)
+    return sc
+
+
 CONFIGS = {
     "small": make_small,
     "arm": make_arm,
@@ -477,9 +518,10 @@ CONFIGS = {
     "hand": make_hand,
     "pick": make_pick,
     "mixed": make_mixed,
+    "hulls": make_hulls,
 }
 
-CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096, "pick": 4096, "mixed": 4096}
+CONFIG_SIZES = {"small": 64, "arm": 4096, "clutter": 16384, "hand": 4096, "pick": 4096, "mixed": 4096, "hulls": 4096}
 
 
 def make_scene(name: str, n_envs: Optional[int] = None, seed: Optional[int] = None, **kw) -> Scene:
