@@ -39,6 +39,8 @@ WORKLOADS = {
     "small": "plane + 1 box + 3 spheres, 64 envs (dt 0.01 s, 4 substeps, 8+1 iterations)",
     "clutter": "1-32 boxes/spheres/capsules in a 5-box bin, 16384 envs (dt 0.01 s, 4 substeps, 8+1)",
     "hand": "16-DoF capsule hand holding a cube, 4096 envs (dt 1/120 s, 8 substeps, 16+1 iterations)",
+    "hulls": "1-12 convex hulls (6-12 points, from a pool of 128) dropped into the 5-box bin, 4096 envs "
+             "(dt 0.01 s, 4 substeps, 8+1 iterations)",
     "mixed": "arm (9 joints), hand (16 joints) and clutter (no joint) envs interleaved in one batch, 4096 envs "
              "(dt 0.01 s, 4 substeps, 8+1 iterations, capacities 704 pairs / 384 contacts)",
     "pick": "the arm envs driven by the pick task, 4096 envs: delta joint-position controller on normalised "
@@ -51,7 +53,7 @@ FLOP_WEIGHTS = {
     "row_solve_2dyn": 61, "row_solve_1dyn": 31, "rows_prep": 40, "body_inertia": 45,
     "body_integrate": 40, "warm_apply": 25, "pairs_tested": 10,
     "np_ss": 20, "np_sc": 40, "np_sb": 60, "np_sp": 15, "np_cc": 120, "np_cb": 300, "np_cp": 30,
-    "np_bb": 1000, "np_bp": 150,
+    "np_bb": 1000, "np_bp": 150, "np_sh": 400, "np_xh": 3000, "np_hp": 150,
 }
 FP32_LANES_PER_SM = 128
 

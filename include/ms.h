@@ -60,11 +60,12 @@ enum {
     MS_ENV_INVALID = 16u            /* ms_step_noalloc: descriptors out of range; the env is skipped */
 };
 
-enum { MS_SPHERE = 0, MS_CAPSULE = 1, MS_BOX = 2, MS_PLANE = 3 };
+enum { MS_SPHERE = 0, MS_CAPSULE = 1, MS_BOX = 2, MS_PLANE = 3, MS_HULL = 4 };
 enum { MS_REVOLUTE = 0, MS_PRISMATIC = 1 };
 
 /* Body descriptor (84 bytes, no padding).
- *   p: sphere {r}, capsule {r, half_length}, box {hx, hy, hz}, plane unused.
+ *   p: sphere {r}, capsule {r, half_length}, box {hx, hy, hz}, plane unused,
+ *   hull {index into the batch's hull library (an integer), unused, unused}.
  *   mass 0 (and every plane) = static: never moves; its velocities are ignored.
  *   Two bodies may touch iff (group_a & mask_b) && (group_b & mask_a). */
 typedef struct {
@@ -162,6 +163,36 @@ ms_status ms_create_batch(const ms_scene_desc* descs, int n_envs, const ms_sim_p
 ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_off,
                                const ms_joint_desc* joints, const int32_t* joint_off,
                                int n_envs, const ms_sim_params* p, ms_batch** out);
+
+/* Convex hull library (the convex pieces of decomposed meshes), host arrays,
+ * copied at creation.  Hull h has vertices verts[vert_off[h] .. vert_off[h + 1])
+ * (x, y, z; 4..16 vertices) and outward counter-clockwise triangles
+ * tris[tri_off[h] .. tri_off[h + 1]) (3 vertex indices local to the hull),
+ * forming a closed mesh.  The body frame of a hull body is the hull's
+ * principal frame: its centroid at the origin and its principal axes of
+ * inertia along x, y, z (the library's vertices are given in that frame).
+ * Contacts: hull - plane (vertices within the margin), sphere - hull (face
+ * of least penetration when the centre is inside, else the closest surface
+ * point), box or hull - hull (separating axes over face normals and the edge
+ * pairs bounding the Minkowski difference; face clipping or one edge-edge
+ * point).  Capsule - hull pairs make no contact.  The inertia is that of
+ * the uniform solid; the broadphase bounds a hull by its vertices' bounding
+ * sphere about the body origin. */
+typedef struct {
+    int32_t n_hulls;
+    const int32_t* vert_off;
+    const float* verts;
+    const int32_t* tri_off;
+    const int32_t* tris;
+} ms_hull_lib;
+
+/* ms_create_batch_flat with a hull library (NULL: none); MS_HULL bodies
+ * need one.  MS_ERR_INVALID_ARG names a malformed hull (not closed, a
+ * vertex count out of range, no volume) or a body's hull index out of
+ * range. */
+ms_status ms_create_batch_hulls(const ms_body_desc* bodies, const int32_t* body_off,
+                                const ms_joint_desc* joints, const int32_t* joint_off, int n_envs,
+                                const ms_sim_params* p, const ms_hull_lib* hulls, ms_batch** out);
 
 /* Advance every env n_steps steps on `stream` (cudaStream_t; NULL = legacy
  * default stream) with the batched path: one persistent launch pops envs

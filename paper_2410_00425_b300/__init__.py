@@ -30,7 +30,7 @@ class Batch:
         self.NJ = int(scene.joint_off[-1])
         self.A = int((scene.joint_off[1:] - scene.joint_off[:-1]).max()) if self.E else 0
         self.h = _ffi.ms_create_batch_flat(scene.bodies, scene.body_off, scene.joints,
-                                           scene.joint_off, scene.params)
+                                           scene.joint_off, scene.params, getattr(scene, "hulls", None))
         if record_contacts:
             _ffi.ms_set_record_contacts(self.h, True)
 

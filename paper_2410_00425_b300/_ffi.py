@@ -65,6 +65,11 @@ class ms_task_desc(C.Structure):
 MS_STEP_PLAIN = 1
 
 
+class ms_hull_lib(C.Structure):
+    _fields_ = [("n_hulls", C.c_int32), ("vert_off", C.c_void_p), ("verts", C.c_void_p), ("tri_off", C.c_void_p),
+                ("tris", C.c_void_p)]
+
+
 class ms_camera_desc(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("fov_y", C.c_float), ("near", C.c_float),
                 ("width", C.c_int32), ("height", C.c_int32), ("body_rgb", C.c_void_p)]
@@ -107,6 +112,8 @@ _SIGS = [
     ("ms_task_observe", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_step_ex", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     ("ms_set_camera", C.c_int, [C.c_void_p, C.POINTER(ms_camera_desc)]),
+    ("ms_create_batch_hulls", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                        C.POINTER(ms_sim_params), C.POINTER(ms_hull_lib), C.POINTER(C.c_void_p)]),
     ("ms_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
@@ -170,8 +177,24 @@ def make_params(p: dict) -> ms_sim_params:
 
 # ---- thin wrappers with the C names -------------------------------------
 def ms_create_batch_flat(bodies: np.ndarray, body_off: np.ndarray, joints: np.ndarray,
-                         joint_off: np.ndarray, params: dict) -> int:
+                         joint_off: np.ndarray, params: dict, hulls=None) -> int:
+    """hulls: a hull library dict (verts, vert_off, tris, tri_off) or None."""
     L = load()
+    if hulls is not None:
+        hv = np.ascontiguousarray(hulls["verts"], np.float32)
+        hvo = np.ascontiguousarray(hulls["vert_off"], np.int32)
+        ht = np.ascontiguousarray(hulls["tris"], np.int32)
+        hto = np.ascontiguousarray(hulls["tri_off"], np.int32)
+        lib = ms_hull_lib(len(hvo) - 1, hvo.ctypes.data, hv.ctypes.data, hto.ctypes.data, ht.ctypes.data)
+        bodies = np.ascontiguousarray(bodies)
+        joints = np.ascontiguousarray(joints)
+        bo = np.ascontiguousarray(body_off, np.int32)
+        jo = np.ascontiguousarray(joint_off, np.int32)
+        out = C.c_void_p()
+        sp = make_params(params)
+        check(L.ms_create_batch_hulls(bodies.ctypes.data, bo.ctypes.data, joints.ctypes.data if len(joints) else None,
+                                      jo.ctypes.data, len(bo) - 1, C.byref(sp), C.byref(lib), C.byref(out)))
+        return out.value
     bodies = np.ascontiguousarray(bodies)
     joints = np.ascontiguousarray(joints)
     bo = np.ascontiguousarray(body_off, np.int32)

@@ -92,6 +92,7 @@ struct ms_batch {
     size_t smem_optin = 0;
     std::vector<int> h_body_off, h_joint_off;
     std::vector<uint8_t> h_type;      // shape type per body
+    std::vector<int> h_hull_nt;       // triangles of each hull body's mesh (0 otherwise)
     // pick task
     float* d_task_half = nullptr;     // [A]
     float* d_task_qR = nullptr;       // [NJ]
@@ -177,6 +178,83 @@ static void body_inertia(const ms_body_desc& d, float out[3]) {
     }
 }
 
+// ------------------------------------------------------------------- hulls
+// The library's derived data: edges (each once, from the triangle listing it
+// a -> b with a < b, with the triangle listing b -> a), local face planes,
+// bounding radius; volume and diagonal second moments of unit density from
+// the tetrahedra (origin, triangle), each (V/20)(a a + b b + c c + s s),
+// s = a + b + c, per axis.
+struct HostHulls {
+    int n = 0;
+    std::vector<float4> v, n4;
+    std::vector<int4> t, e;
+    std::vector<int> vo{0}, to{0}, eo{0};
+    std::vector<float> rad;
+    std::vector<double> vol, c2;          // c2: 3 per hull
+};
+
+static ms_status build_hulls(const ms_hull_lib* L, HostHulls& H) {
+    if (!L) return MS_OK;
+    if (L->n_hulls < 0 || (L->n_hulls > 0 && (!L->vert_off || !L->verts || !L->tri_off || !L->tris)))
+        return fail(MS_ERR_INVALID_ARG, "hull library: NULL table");
+    H.n = L->n_hulls;
+    for (int h = 0; h < H.n; h++) {
+        int v0 = L->vert_off[h], nv = L->vert_off[h + 1] - v0, t0 = L->tri_off[h], nt = L->tri_off[h + 1] - t0;
+        if (nv < 4 || nv > 16 || nt < 4 || nt > 2 * 16 - 4) return fail(MS_ERR_INVALID_ARG, "hull %d: %d vertices / %d triangles", h, nv, nt);
+        std::vector<double> pv(3 * nv);
+        double rad = 0.0;
+        for (int k = 0; k < nv; k++) {
+            const float* q = L->verts + 3 * (size_t)(v0 + k);
+            if (!finite3(q, 3)) return fail(MS_ERR_INVALID_ARG, "hull %d: non-finite vertex", h);
+            for (int c = 0; c < 3; c++) pv[3 * k + c] = q[c];
+            rad = std::max(rad, std::sqrt(pv[3 * k] * pv[3 * k] + pv[3 * k + 1] * pv[3 * k + 1] + pv[3 * k + 2] * pv[3 * k + 2]));
+            H.v.push_back(make_float4(q[0], q[1], q[2], 0.f));
+        }
+        const int32_t* tt = L->tris + 3 * (size_t)t0;
+        for (int f = 0; f < 3 * nt; f++)
+            if (tt[f] < 0 || tt[f] >= nv) return fail(MS_ERR_INVALID_ARG, "hull %d: vertex index out of range", h);
+        double vol = 0.0, c2[3] = {0.0, 0.0, 0.0};
+        for (int f = 0; f < nt; f++) {
+            const double* a = &pv[3 * tt[3 * f]];
+            const double* b = &pv[3 * tt[3 * f + 1]];
+            const double* c = &pv[3 * tt[3 * f + 2]];
+            double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+            double n[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2], ab[0] * ac[1] - ab[1] * ac[0]};
+            double nl = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            if (!(nl > 0.0)) return fail(MS_ERR_INVALID_ARG, "hull %d: degenerate triangle %d", h, f);
+            for (double& x : n) x /= nl;
+            H.n4.push_back(make_float4((float)n[0], (float)n[1], (float)n[2], (float)(n[0] * a[0] + n[1] * a[1] + n[2] * a[2])));
+            H.t.push_back(make_int4(tt[3 * f], tt[3 * f + 1], tt[3 * f + 2], 0));
+            double v6 = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+            vol += v6 / 6.0;
+            for (int k = 0; k < 3; k++) {
+                double sm = a[k] + b[k] + c[k];
+                c2[k] += v6 / 120.0 * (a[k] * a[k] + b[k] * b[k] + c[k] * c[k] + sm * sm);
+            }
+        }
+        int ne = 0;
+        for (int f = 0; f < nt; f++)
+            for (int k = 0; k < 3; k++) {
+                int a = tt[3 * f + k], bb = tt[3 * f + (k + 1) % 3];
+                if (a > bb) continue;
+                int g = -1;
+                for (int o = 0; o < nt && g < 0; o++)
+                    for (int q = 0; q < 3; q++)
+                        if (tt[3 * o + q] == bb && tt[3 * o + (q + 1) % 3] == a) { g = o; break; }
+                if (g < 0) return fail(MS_ERR_INVALID_ARG, "hull %d: mesh not closed", h);
+                H.e.push_back(make_int4(a, bb, f, g));
+                ne++;
+            }
+        if (2 * ne != 3 * nt) return fail(MS_ERR_INVALID_ARG, "hull %d: mesh not closed", h);
+        if (!(vol > 0.0)) return fail(MS_ERR_INVALID_ARG, "hull %d: no volume (inward triangles?)", h);
+        H.vo.push_back((int)H.v.size()); H.to.push_back((int)H.t.size()); H.eo.push_back((int)H.e.size());
+        H.rad.push_back((float)rad);
+        H.vol.push_back(vol);
+        for (int k = 0; k < 3; k++) H.c2.push_back(c2[k]);
+    }
+    return MS_OK;
+}
+
 static ms_status validate_params(const ms_sim_params* p) {
     if (!p) return fail(MS_ERR_INVALID_ARG, "params is NULL");
     if (!(p->dt > 0.f) || !std::isfinite(p->dt)) return fail(MS_ERR_INVALID_ARG, "dt must be > 0");
@@ -199,14 +277,17 @@ static ms_status validate_params(const ms_sim_params* p) {
     return MS_OK;
 }
 
-static ms_status validate_env(int e, const ms_body_desc* bd, int nb, const ms_joint_desc* jd, int nj) {
+static ms_status validate_env(int e, const ms_body_desc* bd, int nb, const ms_joint_desc* jd, int nj, int n_hulls) {
     if (nb < 1 || nb > 64) return fail(MS_ERR_INVALID_ARG, "env %d: n_bodies %d not in [1, 64]", e, nb);
     if (nj < 0 || nj > 512) return fail(MS_ERR_INVALID_ARG, "env %d: n_joints %d not in [0, 512]", e, nj);
     if (!bd) return fail(MS_ERR_INVALID_ARG, "env %d: bodies is NULL", e);
     if (nj > 0 && !jd) return fail(MS_ERR_INVALID_ARG, "env %d: joints is NULL", e);
     for (int i = 0; i < nb; i++) {
         const ms_body_desc& d = bd[i];
-        if (d.type < MS_SPHERE || d.type > MS_PLANE) return fail(MS_ERR_INVALID_ARG, "env %d body %d: bad type %d", e, i, d.type);
+        if (d.type < MS_SPHERE || d.type > MS_HULL) return fail(MS_ERR_INVALID_ARG, "env %d body %d: bad type %d", e, i, d.type);
+        if (d.type == MS_HULL && !(d.p[0] >= 0.f && d.p[0] < (float)n_hulls && d.p[0] == std::floor(d.p[0])))
+            return fail(MS_ERR_INVALID_ARG, "env %d body %d: hull index %g not in the library (%d hulls)", e, i, d.p[0],
+                        n_hulls);
         if (!finite3(d.pos, 3) || !finite3(d.quat, 4) || !finite3(d.linvel, 3) || !finite3(d.angvel, 3) ||
             !std::isfinite(d.mass) || !std::isfinite(d.mu))
             return fail(MS_ERR_INVALID_ARG, "env %d body %d: non-finite field", e, i);
@@ -247,14 +328,17 @@ static void normq(const float* q, float* o) {
 }
 
 static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb_of, const ms_joint_desc* const* joints_of,
-                             const int* nj_of, int E, const ms_sim_params* p, ms_batch** out) {
+                             const int* nj_of, int E, const ms_sim_params* p, ms_batch** out,
+                             const ms_hull_lib* hull_lib = nullptr) {
     if (!out) return fail(MS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (E < 1) return fail(MS_ERR_INVALID_ARG, "n_envs must be >= 1");
     ms_status st = validate_params(p);
     if (st) return st;
+    HostHulls hh;
+    if ((st = build_hulls(hull_lib, hh)) != MS_OK) return st;
     for (int e = 0; e < E; e++) {
-        st = validate_env(e, bodies_of[e], nb_of[e], joints_of[e], nj_of[e]);
+        st = validate_env(e, bodies_of[e], nb_of[e], joints_of[e], nj_of[e], hh.n);
         if (st) return st;
     }
     ms_batch* b = new ms_batch();
@@ -295,6 +379,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     std::vector<int4> jm(b->NJ);
     std::vector<float> jt(b->NJ);
     b->h_type.assign(b->NB, 0);
+    b->h_hull_nt.assign(b->NB, 0);
     for (int e = 0; e < E; e++) {
         int b0 = b->h_body_off[e], j0 = b->h_joint_off[e];
         for (int i = 0; i < nb_of[e]; i++) {
@@ -311,7 +396,13 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
             w[k] = dyn ? make_float4(d.angvel[0], d.angvel[1], d.angvel[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             shape[k] = make_float4(d.p[0], d.p[1], d.p[2], d.mu);
             rest[k] = d.restitution;
-            if (dyn) {
+            if (dyn && d.type == MS_HULL) {
+                int h = (int)d.p[0];
+                double rho = (double)d.mass / hh.vol[h];
+                const double* c2 = &hh.c2[3 * h];
+                inv[k] = make_float4((float)(1.0 / (rho * (c2[1] + c2[2]))), (float)(1.0 / (rho * (c2[0] + c2[2]))),
+                                     (float)(1.0 / (rho * (c2[0] + c2[1]))), (float)(1.0 / (double)d.mass));
+            } else if (dyn) {
                 float I[3];
                 body_inertia(d, I);
                 inv[k] = make_float4(1.f / I[0], 1.f / I[1], 1.f / I[2], (float)(1.0 / (double)d.mass));
@@ -321,6 +412,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
             meta[k] = make_int2(d.type | (dyn ? 1 << 8 : 0), (int)((unsigned)d.group | ((unsigned)d.mask << 16)));
             body_env[k] = e;
             b->h_type[k] = (uint8_t)d.type;
+            if (d.type == MS_HULL) b->h_hull_nt[k] = hh.to[(int)d.p[0] + 1] - hh.to[(int)d.p[0]];
         }
         for (int j = 0; j < nj_of[e]; j++) {
             const ms_joint_desc& d = joints_of[e][j];
@@ -370,6 +462,18 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     float* d_rest;
     UP(&d_rest, rest);
     D.rest = d_rest;
+    D.hulls = nullptr;
+    if (hh.n > 0) {
+        // the library on the device, and a HullLib of device pointers to it
+        float4 *hv, *hn; int4 *ht, *he; int *hvo, *hto, *heo; float* hrad;
+        UP(&hv, hh.v); UP(&hn, hh.n4); UP(&ht, hh.t); UP(&he, hh.e);
+        UP(&hvo, hh.vo); UP(&hto, hh.to); UP(&heo, hh.eo); UP(&hrad, hh.rad);
+        std::vector<HullLib> lib(1);
+        lib[0] = HullLib{hv, ht, hn, he, hvo, hto, heo, hrad};
+        HullLib* dl;
+        UP(&dl, lib);
+        D.hulls = dl;
+    }
     D.wc = nullptr; D.wc_n = nullptr; D.wjl = nullptr;
     if (p->warm_start) {
         // warm-start memory: 2 float4 per (env, contact point), a count per
@@ -418,6 +522,12 @@ extern "C" ms_status ms_create_batch(const ms_scene_desc* descs, int n_envs, con
 
 extern "C" ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_off, const ms_joint_desc* joints,
                                           const int32_t* joint_off, int n_envs, const ms_sim_params* p, ms_batch** out) {
+    return ms_create_batch_hulls(bodies, body_off, joints, joint_off, n_envs, p, nullptr, out);
+}
+
+extern "C" ms_status ms_create_batch_hulls(const ms_body_desc* bodies, const int32_t* body_off,
+                                           const ms_joint_desc* joints, const int32_t* joint_off, int n_envs,
+                                           const ms_sim_params* p, const ms_hull_lib* hulls, ms_batch** out) {
     if (!bodies || !body_off || !joint_off) return fail(MS_ERR_INVALID_ARG, "NULL table");
     if (n_envs < 1) return fail(MS_ERR_INVALID_ARG, "n_envs must be >= 1");
     std::vector<const ms_body_desc*> bo(n_envs);
@@ -432,7 +542,7 @@ extern "C" ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int3
         nb[e] = body_off[e + 1] - body_off[e];
         nj[e] = joint_off[e + 1] - joint_off[e];
     }
-    return create_impl(bo.data(), nb.data(), jo.data(), nj.data(), n_envs, p, out);
+    return create_impl(bo.data(), nb.data(), jo.data(), nj.data(), n_envs, p, out, hulls);
 }
 
 // --------------------------------------------------------------- plain path
@@ -622,7 +732,8 @@ extern "C" ms_status ms_set_camera(ms_batch* b, const ms_camera_desc* c) {
     if (!b || !c || !c->body_rgb) return fail(MS_ERR_INVALID_ARG, "NULL argument");
     if (!b->render) b->render = render_create();
     CK(cudaEventSynchronize(b->done));
-    const char* err = render_configure(b->render, b->D, c, b->h_type, b->h_body_off, b->max_nb, (int)b->smem_optin);
+    const char* err = render_configure(b->render, b->D, c, b->h_type, b->h_hull_nt, b->h_body_off, b->max_nb,
+                                       (int)b->smem_optin);
     if (err) return fail(MS_ERR_INVALID_ARG, "camera: %s", err);
     CK(cudaGetLastError());
     return MS_OK;

@@ -63,6 +63,20 @@ struct DevParams {
     int restit;                // some body of the batch has restitution > 0
 };
 
+// Hull library of a batch on the device (see HullRef): hull h's vertices
+// v[vo[h] .. vo[h + 1]), triangles t[to[h] ..) with local planes n[..],
+// edges e[eo[h] ..), bounding radius rad[h].
+struct HullLib {
+    const float4* v;
+    const int4* t;
+    const float4* n;
+    const int4* e;
+    const int* vo;
+    const int* to;
+    const int* eo;
+    const float* rad;
+};
+
 // Pick task: delta joint-position controller and per-step records
 // (reward, indicators, tcp / cube positions, joint coordinates, targets).
 struct DevTask {
@@ -91,6 +105,7 @@ struct DevBatch {
     const int4* jm;
     float* jt;
     const float* rest;                 // restitution per body
+    const HullLib* hulls;              // device copy of the hull library, or null
     float4* wc;                        // warm start: 2 per (env, contact point): (a | b << 16, aA), (ln, friction)
     int* wc_n;                         //   contact points cached per env
     float* wjl;                        //   8 impulses per joint
@@ -126,8 +141,8 @@ struct RenderState;
 RenderState* render_create();
 void render_destroy(RenderState* r);
 const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_desc* c,
-                             const std::vector<uint8_t>& types, const std::vector<int>& body_off, int max_nb,
-                             int smem_optin);
+                             const std::vector<uint8_t>& types, const std::vector<int>& hull_nt,
+                             const std::vector<int>& body_off, int max_nb, int smem_optin);
 bool render_ready(const RenderState* r);
 cudaError_t render_launch(RenderState* r, const DevBatch& D, uint8_t* rgba, float* depth, uint16_t* seg,
                           cudaStream_t s);

@@ -95,6 +95,7 @@ __device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b
     e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
     e.rest = D.rest + b0;
     e.qR = D.T.qR ? D.T.qR + j0 : nullptr;
+    e.hulls = D.hulls;
     bool w = active && D.wc;
     e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
     e.wc_n = w ? D.wc_n + env : nullptr;

@@ -1,7 +1,7 @@
 // Primitive narrowphase, one pair per lane.
 //
-// Pair convention: A is the lower shape rank (sphere < capsule < box <
-// plane), the lower env-local index on equal ranks; the normal n points from
+// Pair convention: A is the lower shape rank (sphere < capsule < box < hull
+// < plane), the lower env-local index on equal ranks; the normal n points from
 // B toward A; d = n.(cA - cB) is negative when penetrating; a point is kept
 // iff d < margin (speculative contacts inside the margin).  Methods: closest
 // points of primitives and the separating-axis test with Sutherland-Hodgman
@@ -13,13 +13,29 @@
 
 namespace ms {
 
-enum { SH_SPHERE = 0, SH_CAPSULE = 1, SH_BOX = 2, SH_PLANE = 3 };
+enum { SH_SPHERE = 0, SH_CAPSULE = 1, SH_BOX = 2, SH_PLANE = 3, SH_HULL = 4 };
+
+// pair order of the narrowphase: sphere < capsule < box < hull < plane
+MSD int shape_rank(int t) { return t == SH_HULL ? 3 : (t == SH_PLANE ? 4 : t); }
+
+// A convex hull of the batch's library (body frame = its principal frame):
+// vertices, outward counter-clockwise triangles with their local planes
+// (n, n.v = d), and edges (a, b, triangle listing a -> b, triangle listing
+// b -> a), each edge once.
+struct HullRef {
+    const float4* v;
+    const int4* t;
+    const float4* n;
+    const int4* e;
+    int nv, nt, ne;
+};
 
 struct Shape {
     float3 x;
     M3 R;
     int type;
     float p0, p1, p2;
+    HullRef hull;                 // hull bodies
 };
 
 struct Cand {
@@ -29,9 +45,9 @@ struct Cand {
 
 struct CandSet {
     int n;
-    Cand c[8];
+    Cand c[16];
     MSD void push(float3 cA, float3 cB, float3 nn, float d) {
-        if (n < 8) { c[n].cA = cA; c[n].cB = cB; c[n].n = nn; c[n].d = d; n++; }
+        if (n < 16) { c[n].cA = cA; c[n].cB = cB; c[n].n = nn; c[n].d = d; n++; }
     }
 };
 
@@ -477,6 +493,229 @@ MSD void reduce4(const Cand* c, int n, int* sel) {
     sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
 }
 
+
+// ------------------------------------------------------------------- hulls
+// A convex polytope in world coordinates for the separating-axis test: a
+// box (8 corners, 6 quadrilateral faces) or a hull (triangles).  World
+// vertices and face planes are formed once; face vertex lists and edges
+// are read from the hull library or the box tables.
+constexpr int PV_MAXV = 16, PV_MAXF = 28;
+
+// box faces +x, -x, +y, -y, +z, -z, counter-clockwise from outside; corner
+// k has signs (bit 0: x, bit 1: y, bit 2: z)
+__device__ __constant__ int c_box_face[6][4] = {{1, 3, 7, 5}, {2, 0, 4, 6}, {3, 2, 6, 7},
+                                               {0, 1, 5, 4}, {4, 5, 7, 6}, {2, 3, 1, 0}};
+// box edges (a, b, face listing a -> b, face listing b -> a): each edge once,
+// from the first face (in face order) that lists it with a < b
+__device__ __constant__ int c_box_edge[12][4] = {{1, 3, 0, 5}, {3, 7, 0, 2}, {0, 4, 1, 3}, {4, 6, 1, 4},
+                                                {2, 6, 2, 1}, {6, 7, 2, 4}, {0, 1, 3, 5}, {1, 5, 3, 0},
+                                                {4, 5, 4, 3}, {5, 7, 4, 0}, {2, 3, 5, 2}, {0, 2, 5, 1}};
+
+struct Poly {
+    bool box;
+    int nv, nf, ne;
+    float3 c;                        // body origin (interior)
+    float3 v[PV_MAXV];
+    float4 f[PV_MAXF];               // world face plane (n, n.x on the face)
+    const int4* tri;
+    const int4* edge;
+};
+
+MSD void poly_of(const Shape& S, Poly& P) {
+    P.c = S.x;
+    if (S.type == SH_BOX) {
+        P.box = true; P.nv = 8; P.nf = 6; P.ne = 12;
+        for (int k = 0; k < 8; k++)
+            P.v[k] = S.x + mv(S.R, f3((k & 1) ? S.p0 : -S.p0, (k & 2) ? S.p1 : -S.p1, (k & 4) ? S.p2 : -S.p2));
+        const float h[3] = {S.p0, S.p1, S.p2};
+        for (int f = 0; f < 6; f++) {
+            float3 n = mcol(S.R, f >> 1) * ((f & 1) ? -1.f : 1.f);
+            P.f[f] = f4(n, dot(n, S.x) + h[f >> 1]);
+        }
+        P.tri = nullptr; P.edge = nullptr;
+    } else {
+        const HullRef& H = S.hull;
+        P.box = false; P.nv = H.nv; P.nf = H.nt; P.ne = H.ne;
+        for (int k = 0; k < H.nv; k++) P.v[k] = S.x + mv(S.R, xyz(H.v[k]));
+        for (int f = 0; f < H.nt; f++) {
+            float4 ln = H.n[f];
+            float3 n = mv(S.R, xyz(ln));
+            P.f[f] = f4(n, dot(n, S.x) + ln.w);
+        }
+        P.tri = H.t; P.edge = H.e;
+    }
+}
+
+MSD int poly_face(const Poly& P, int f, int* idx) {
+    if (P.box) {
+        for (int k = 0; k < 4; k++) idx[k] = c_box_face[f][k];
+        return 4;
+    }
+    int4 t = P.tri[f];
+    idx[0] = t.x; idx[1] = t.y; idx[2] = t.z;
+    return 3;
+}
+
+MSD int4 poly_edge(const Poly& P, int k) {
+    if (P.box) return make_int4(c_box_edge[k][0], c_box_edge[k][1], c_box_edge[k][2], c_box_edge[k][3]);
+    return P.edge[k];
+}
+
+// hull - plane: every vertex within the margin (as box - plane)
+MSD void np_hp(const Shape& A, const Shape& B, float m, CandSet& cs) {
+    float3 N = mcol(B.R, 2);
+    for (int k = 0; k < A.hull.nv; k++) {
+        float3 v = A.x + mv(A.R, xyz(A.hull.v[k]));
+        float dist = dot(N, v - B.x);
+        if (dist < m + 1e-4f) cs.push(v, v - N * dist, N, dist);
+    }
+}
+
+// closest point of triangle (a, b, c) to p (Ericson 2005, 5.1.5)
+MSD float3 closest_on_triangle(float3 p, float3 a, float3 b, float3 c) {
+    float3 ab = b - a, ac = c - a, ap = p - a;
+    float d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) return a;
+    float3 bp = p - b;
+    float d3 = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3 >= 0.f && d4 <= d3) return b;
+    float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) return a + ab * (d1 / (d1 - d3));
+    float3 cp = p - c;
+    float d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= 0.f && d5 <= d6) return c;
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) return a + ac * (d2 / (d2 - d6));
+    float va = d3 * d6 - d5 * d4;
+    if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) return b + (c - b) * ((d4 - d3) / ((d4 - d3) + (d5 - d6)));
+    float den = 1.f / (va + vb + vc);
+    return a + ab * (vb * den) + ac * (vc * den);
+}
+
+// sphere - hull: centre inside every face plane: out along the face of
+// least penetration; outside: the closest point of the surface
+MSD void np_sh(const Shape& A, const Shape& B, CandSet& cs) {
+    Poly P;
+    poly_of(B, P);
+    float3 c = A.x;
+    float r = A.p0;
+    float smax = -3e38f;
+    int fb = 0;
+    for (int f = 0; f < P.nf; f++) {
+        float sf = dot(xyz(P.f[f]), c) - P.f[f].w;
+        if (sf > smax) { smax = sf; fb = f; }
+    }
+    if (smax <= 0.f) {
+        float3 n = xyz(P.f[fb]);
+        cs.push(c - n * r, c - n * smax, n, smax - r);
+        return;
+    }
+    float best = 3e38f;
+    float3 q = c;
+    for (int f = 0; f < P.nf; f++) {
+        int idx[4];
+        poly_face(P, f, idx);
+        float3 t = closest_on_triangle(c, P.v[idx[0]], P.v[idx[1]], P.v[idx[2]]);
+        float d2 = dot(c - t, c - t);
+        if (d2 < best) { best = d2; q = t; }
+    }
+    float dist = sqrtf(best);
+    float3 n = (c - q) * (1.f / dist);
+    cs.push(c - n * r, q, n, dist - r);
+}
+
+// box or hull (A) - hull (B): separating axes over the face normals of A,
+// then of B, then the cross products of edge pairs whose arcs on the Gauss
+// map cross (the faces of the Minkowski difference); a B face is the
+// reference only if it beats the best A face by 1e-4 m, an edge pair only
+// if it beats the best face by 1e-4 m.  Face case: the most anti-parallel
+// face of the other polytope clipped against the side planes of the
+// reference face; edge case: the closest points of the two edges.
+MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
+    Poly PA, PB;
+    poly_of(A, PA);
+    poly_of(B, PB);
+    float sa = -3e38f; int fa = 0;
+    for (int f = 0; f < PA.nf; f++) {
+        float sf = 3e38f;
+        float3 n = xyz(PA.f[f]);
+        for (int k = 0; k < PB.nv; k++) sf = fminf(sf, dot(n, PB.v[k]) - PA.f[f].w);
+        if (sf > sa) { sa = sf; fa = f; }
+    }
+    float sb = -3e38f; int fb = 0;
+    for (int f = 0; f < PB.nf; f++) {
+        float sf = 3e38f;
+        float3 n = xyz(PB.f[f]);
+        for (int k = 0; k < PA.nv; k++) sf = fminf(sf, dot(n, PA.v[k]) - PB.f[f].w);
+        if (sf > sb) { sb = sf; fb = f; }
+    }
+    float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
+    for (int i = 0; i < PA.ne; i++) {
+        int4 EA = poly_edge(PA, i);
+        float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
+        float3 bxa = cross(b, a);
+        float3 ua = PA.v[EA.y] - PA.v[EA.x];
+        for (int j = 0; j < PB.ne; j++) {
+            int4 EB = poly_edge(PB, j);
+            float3 c = -xyz(PB.f[EB.z]), d = -xyz(PB.f[EB.w]);
+            float3 dxc = cross(d, c);
+            float cba = dot(c, bxa), dba = dot(d, bxa), adc = dot(a, dxc), bdc = dot(b, dxc);
+            if (!(cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
+            float3 ub = PB.v[EB.y] - PB.v[EB.x];
+            float3 ax = cross(ua, ub);
+            float l = len(ax);
+            if (l < 1e-5f * len(ua) * len(ub)) continue;
+            ax = ax * (1.f / l);
+            if (dot(ax, PA.v[EA.x] - PA.c) < 0.f) ax = -ax;
+            float sij = dot(ax, PB.v[EB.x] - PA.v[EA.x]);
+            if (sij > se) { se = sij; ea = i; eb = j; axe = ax; }
+        }
+    }
+    float maxsep = fmaxf(fmaxf(sa, sb), se);
+    if (maxsep >= m) return;
+    float sf = fmaxf(sa, sb);
+    if (ea >= 0 && se > sf + 1e-4f) {
+        int4 EA = poly_edge(PA, ea), EB = poly_edge(PB, eb);
+        float3 pa, pb;
+        closest_segments(PA.v[EA.x], PA.v[EA.y], PB.v[EB.x], PB.v[EB.y], pa, pb);
+        float3 n = -axe;
+        cs.push(pa, pb, n, dot(n, pa - pb));
+        return;
+    }
+    bool refB = sb > sa + 1e-4f;
+    const Poly& R = refB ? PB : PA;
+    const Poly& I = refB ? PA : PB;
+    int rf = refB ? fb : fa;
+    float3 nref = xyz(R.f[rf]);
+    int inc = 0;
+    float best = 3e38f;
+    for (int g = 0; g < I.nf; g++) {
+        float dd = dot(xyz(I.f[g]), nref);
+        if (dd < best) { best = dd; inc = g; }
+    }
+    float3 bufa[8], bufb[8];
+    int ii[4], ri[4];
+    int np = poly_face(I, inc, ii);
+    for (int k = 0; k < np; k++) bufa[k] = I.v[ii[k]];
+    int nr = poly_face(R, rf, ri);
+    for (int k = 0; k < nr; k++) {
+        float3 p0 = R.v[ri[k]], p1 = R.v[ri[k + 1 == nr ? 0 : k + 1]];
+        float3 side = cross(p1 - p0, nref);
+        side = side * (1.f / len(side));
+        // alternate the buffers: even k reads bufa, odd k reads bufb
+        if ((k & 1) == 0) np = clip_plane(bufa, np, bufb, side, p0, 0.f);
+        else np = clip_plane(bufb, np, bufa, side, p0, 0.f);
+    }
+    const float3* res = (nr & 1) ? bufb : bufa;
+    float3 pref = R.v[ri[0]];
+    for (int k = 0; k < np; k++) {
+        float3 x = res[k];
+        float dist = dot(nref, x - pref);
+        if (!refB) cs.push(x - nref * dist, x, -nref, dist);
+        else cs.push(x, x - nref * dist, nref, dist);
+    }
+}
+
 // Narrowphase of the ordered pair (A, B): up to 4 kept points in out.
 MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
     CandSet cs;
@@ -486,16 +725,22 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
         if (tb == SH_SPHERE) np_ss(A, B, cs);
         else if (tb == SH_CAPSULE) np_sc(A, B, cs);
         else if (tb == SH_BOX) np_sb(A, B, cs);
+        else if (tb == SH_HULL) { if (B.hull.v) np_sh(A, B, cs); }
         else np_sp(A, B, cs);
     } else if (ta == SH_CAPSULE) {
         if (tb == SH_CAPSULE) np_cc(A, B, cs);
         else if (tb == SH_BOX) np_cb(A, B, m, cs);
-        else np_cp(A, B, cs);
+        else if (tb == SH_PLANE) np_cp(A, B, cs);
     } else if (ta == SH_BOX) {
         if (tb == SH_BOX) np_bb(A, B, m, cs);
+        else if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
         else np_bp(A, B, cs);
+    } else if (ta == SH_HULL && A.hull.v) {
+        if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
+        else if (tb == SH_PLANE) np_hp(A, B, m, cs);
     }
-    Cand kept[8];
+    // capsule - hull: no contact
+    Cand kept[16];
     int nk = 0;
     for (int i = 0; i < cs.n; i++)
         if (cs.c[i].d < m) kept[nk++] = cs.c[i];

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
     e.jt = nat<float>(gl, L.jt);
     float* rst = nat<float>(gl, L.rest);
     e.rest = rst;
+    e.hulls = nullptr;                 // no hull library on this path
     e.wc = nullptr; e.wc_n = nullptr; e.wjl = nullptr;       // no warm-start memory on this path
     view_workspace(e, s, gl, L);
     e.status = nat<unsigned>(s, L.status);
@@ -133,6 +134,14 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
             // counts exceed the declared maxima would overrun its slot
             if (nb < 1 || nb > D.max_nb || nj < 0 || nj > D.max_nj) { invalid = true; nb = 0; nj = 0; }
         }
+        // primitives only (no hull library here): any other type invalidates the env
+        bool badtype = false;
+        int nbm = g.wmax(nb);
+        for (int i0 = 0; i0 < nbm; i0 += G) {
+            int i = i0 + g.lane;
+            if (i < nb) { int t = D.bodies[b0 + i].type; badtype |= t < MS_SPHERE || t > MS_PLANE; }
+        }
+        if (g.any(badtype)) { invalid = true; nb = 0; nj = 0; }
         int nbmax = g.wmax(nb), njmax = g.wmax(nj);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;

@@ -260,7 +260,16 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
         int run = 0;
         for (int i0 = 0; i0 < nb; i0 += 32) {
             int i = i0 + lane;
-            int n = i < nb ? R.nt[D.meta[b0 + i].x & 0xff] : 0;
+            int n = 0;
+            if (i < nb) {
+                int ty = D.meta[b0 + i].x & 0xff;
+                if (ty == MS_HULL) {
+                    int h = (int)D.shape[b0 + i].x;
+                    n = D.hulls ? D.hulls->to[h + 1] - D.hulls->to[h] : 0;
+                } else {
+                    n = R.nt[ty];
+                }
+            }
             int incl = n;
             for (int d = 1; d < 32; d <<= 1) {
                 int t = __shfl_up_sync(R_FULL, incl, d);
@@ -283,13 +292,23 @@ __global__ void __launch_bounds__(R_THREADS) k_render(DevBatch D, RenderCfg R) {
             int bi = 0;                                                // body of triangle t
             while (bi + 1 < nb && tbase[bi + 1] <= t) bi++;
             int type = D.meta[b0 + bi].x & 0xff;
-            int tv = tri[R.t0[type] + t - tbase[bi]];
             float4 shp = D.shape[b0 + bi];
             float3 x = xyz(D.x[b0 + bi]);
             M3 Rb = qmat(D.q[b0 + bi]);
             float3 w[3], v[3];
+            int tv = 0;
+            const float4* hv = nullptr;
+            if (type == MS_HULL) {                                     // a hull: its library mesh
+                int h = (int)shp.x;
+                int4 ht = D.hulls->t[D.hulls->to[h] + t - tbase[bi]];
+                tv = ht.x | ht.y << 8 | ht.z << 16;
+                hv = D.hulls->v + D.hulls->vo[h];
+            } else {
+                tv = tri[R.t0[type] + t - tbase[bi]];
+            }
             for (int k = 0; k < 3; k++) {
-                float3 p = local_vertex(vert[R.v0[type] + ((tv >> (8 * k)) & 0xff)], type, shp);
+                int vi = (tv >> (8 * k)) & 0xff;
+                float3 p = hv ? xyz(hv[vi]) : local_vertex(vert[R.v0[type] + vi], type, shp);
                 w[k] = x + mv(Rb, p);
                 float3 d = w[k] - R.eye;
                 v[k] = f3(dot(R.rt, d), dot(R.up, d), dot(R.fw, d));
@@ -414,8 +433,8 @@ void render_destroy(RenderState* r) {
 // validates the camera and uploads the meshes and colours; returns an
 // error message or null
 const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_desc* c,
-                             const std::vector<uint8_t>& types, const std::vector<int>& body_off, int max_nb,
-                             int smem_optin) {
+                             const std::vector<uint8_t>& types, const std::vector<int>& hull_nt,
+                             const std::vector<int>& body_off, int max_nb, int smem_optin) {
     if (!(c->width >= 1 && c->height >= 1 && (long long)c->width * c->height <= 16384))
         return "width x height must be in [1, 16384]";
     if (!(c->fov_y > 0.f && c->fov_y < 3.14159f) || !(c->near > 0.f) || !std::isfinite(c->near))
@@ -438,7 +457,7 @@ const char* render_configure(RenderState* r, const DevBatch& D, const ms_camera_
     int max_tri = 0;
     for (int env = 0; env < E; env++) {
         int n = 0;
-        for (int i = body_off[env]; i < body_off[env + 1]; i++) n += M.nt[types[i]];
+        for (int i = body_off[env]; i < body_off[env + 1]; i++) n += types[i] == MS_HULL ? hull_nt[i] : M.nt[types[i]];
         max_tri = std::max(max_tri, n);
     }
     // rows per CTA: the fewest bands whose CTAs fit two to an SM (about 113

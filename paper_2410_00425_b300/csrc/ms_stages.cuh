@@ -72,6 +72,7 @@ struct EnvView {
     const int4* jm;                   // type, parent, child, -
     float* jt;                        // drive targets
     float* qR;                        // pick task: joint coordinates at the controller reset (nullable)
+    const HullLib* hulls;             // hull library of the batch (nullable)
     const float* rest;                // restitution per body
     float4* wc;                       // warm-start memory of the env (null: off): 2 per contact point
     int* wc_n;                        //   its count
@@ -184,6 +185,10 @@ MSD void aabb_of(const EnvView& e, int i, float hm, float4& lo, float4& hi) {
             ext = f3(fmaf(fabsf(R.m[2]), s.z, fmaf(fabsf(R.m[1]), s.y, fabsf(R.m[0]) * s.x)),
                      fmaf(fabsf(R.m[5]), s.z, fmaf(fabsf(R.m[4]), s.y, fabsf(R.m[3]) * s.x)),
                      fmaf(fabsf(R.m[8]), s.z, fmaf(fabsf(R.m[7]), s.y, fabsf(R.m[6]) * s.x)));
+        } else if (t == SH_HULL) {
+            // the bounding sphere of the hull's vertices about the body origin
+            float r = e.hulls ? e.hulls->rad[(int)s.x] : 0.f;
+            ext = f3(r, r, r);
         } else {
             float3 ax = mcol(R, 2);
             ext = f3(fmaf(fabsf(ax.x), s.y, s.x), fmaf(fabsf(ax.y), s.y, s.x), fmaf(fabsf(ax.z), s.y, s.x));
@@ -262,6 +267,13 @@ MSD Shape shape_at(const EnvView& e, int i) {
     s.type = shape_type(e, i);
     float4 p = e.shape[i];
     s.p0 = p.x; s.p1 = p.y; s.p2 = p.z;
+    s.hull = HullRef{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+    if (s.type == SH_HULL && e.hulls) {
+        const HullLib& L = *e.hulls;
+        int h = (int)p.x;
+        int v0 = L.vo[h], t0 = L.to[h], e0 = L.eo[h];
+        s.hull = HullRef{L.v + v0, L.t + t0, L.n + t0, L.e + e0, L.vo[h + 1] - v0, L.to[h + 1] - t0, L.eo[h + 1] - e0};
+    }
     return s;
 }
 
@@ -279,7 +291,7 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
             int pr = e.pairs[p];
             int i = pr & 0xffff, j = pr >> 16;
             a = i; b = j;
-            if (shape_type(e, j) < shape_type(e, i)) { a = j; b = i; }
+            if (shape_rank(shape_type(e, j)) < shape_rank(shape_type(e, i))) { a = j; b = i; }
             SA = shape_at(e, a);
             SB = shape_at(e, b);
             n = collide(SA, SB, P.margin, pts);

@@ -434,6 +434,8 @@ def default_camera(name: str, width=128, height=128) -> Dict:
         eye, target = (1.2, -0.9, 0.9), (0.25, 0.0, 0.25)
     elif name == "hand":
         eye, target = (0.25, -0.2, 0.25), (0.0, 0.0, 0.05)
+    elif name == "hulls":
+        eye, target = (0.25, -0.2, 0.6), (0.0, 0.0, 0.02)
     else:
         eye, target = (0.45, -0.35, 0.45), (0.0, 0.0, 0.05)
     return dict(eye=eye, target=target, fov_y=math.radians(60.0), near=0.01, width=width, height=height)
