@@ -649,6 +649,10 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
         for (int k = 0; k < PA.nv; k++) sf = fminf(sf, dot(n, PA.v[k]) - PB.f[f].w);
         if (sf > sb) { sb = sf; fb = f; }
     }
+    // the face axes already separate by the margin: no contact whatever the
+    // edge pairs give (the largest separation is >= m); the bounding-sphere
+    // broadphase passes many such pairs
+    if (fmaxf(sa, sb) >= m) return;
     float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
     for (int i = 0; i < PA.ne; i++) {
         int4 EA = poly_edge(PA, i);
