@@ -499,7 +499,7 @@ MSD void reduce4(const Cand* c, int n, int* sel) {
 // box (8 corners, 6 quadrilateral faces) or a hull (triangles).  World
 // vertices and face planes are formed once; face vertex lists and edges
 // are read from the hull library or the box tables.
-constexpr int PV_MAXV = 16, PV_MAXF = 28;
+constexpr int PV_MAXV = 16, PV_MAXF = 28, PV_MAXE = 42;
 
 // box faces +x, -x, +y, -y, +z, -z, counter-clockwise from outside; corner
 // k has signs (bit 0: x, bit 1: y, bit 2: z)
@@ -653,6 +653,15 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     // edge pairs give (the largest separation is >= m); the bounding-sphere
     // broadphase passes many such pairs
     if (fmaxf(sa, sb) >= m) return;
+    // B's edges as arcs on the Gauss map of -B: the negated normals of
+    // their two faces and the arcs' plane normal, formed once per pair
+    float3 bc[PV_MAXE], bd[PV_MAXE], bdxc[PV_MAXE];
+    for (int j = 0; j < PB.ne; j++) {
+        int4 EB = poly_edge(PB, j);
+        bc[j] = -xyz(PB.f[EB.z]);
+        bd[j] = -xyz(PB.f[EB.w]);
+        bdxc[j] = cross(bd[j], bc[j]);
+    }
     float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
     for (int i = 0; i < PA.ne; i++) {
         int4 EA = poly_edge(PA, i);
@@ -660,11 +669,10 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
         float3 bxa = cross(b, a);
         float3 ua = PA.v[EA.y] - PA.v[EA.x];
         for (int j = 0; j < PB.ne; j++) {
-            int4 EB = poly_edge(PB, j);
-            float3 c = -xyz(PB.f[EB.z]), d = -xyz(PB.f[EB.w]);
-            float3 dxc = cross(d, c);
+            float3 c = bc[j], d = bd[j], dxc = bdxc[j];
             float cba = dot(c, bxa), dba = dot(d, bxa), adc = dot(a, dxc), bdc = dot(b, dxc);
             if (!(cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
+            int4 EB = poly_edge(PB, j);
             float3 ub = PB.v[EB.y] - PB.v[EB.x];
             float3 ax = cross(ua, ub);
             float l = len(ax);
