@@ -53,7 +53,10 @@ FLOP_WEIGHTS = {
     "row_solve_2dyn": 61, "row_solve_1dyn": 31, "rows_prep": 40, "body_inertia": 45,
     "body_integrate": 40, "warm_apply": 25, "pairs_tested": 10,
     "np_ss": 20, "np_sc": 40, "np_sb": 60, "np_sp": 15, "np_cc": 120, "np_cb": 300, "np_cp": 30,
-    "np_bb": 1000, "np_bp": 150, "np_sh": 400, "np_xh": 3000, "np_hp": 150,
+    "np_bb": 1000, "np_bp": 150, "np_sh": 400, "np_xh": 500, "np_hp": 150,
+    # the hull SAT's own work: a face-vertex projection (6 flop), an edge pair's
+    # Gauss-map test (2 cross products' worth and 4 dot products, 20 flop)
+    "sat_face_vert": 6, "sat_edge_pair": 20,
 }
 FP32_LANES_PER_SM = 128
 

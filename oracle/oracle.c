@@ -883,6 +883,7 @@ static void np_poly(Env* e, const Shape* A, const Shape* B, double m, CandSet* c
     poly_of(A, &PA);
     poly_of(B, &PB);
     double sa = -INFINITY; int fa = 0;
+    e->cnt[OC_SAT_FACE_VERT] += PA.nf * PB.nv + PB.nf * PA.nv;
     for (int f = 0; f < PA.nf; f++) {
         double sf = INFINITY;
         for (int k = 0; k < PB.nv; k++) sf = fmin(sf, dot(PA.fn[f], PB.v[k]) - PA.fd[f]);
@@ -895,6 +896,7 @@ static void np_poly(Env* e, const Shape* A, const Shape* B, double m, CandSet* c
         if (sf > sb) { sb = sf; fb = f; }
     }
     double se = -INFINITY; int ea = -1, eb = -1; v3 axe = V(0, 0, 0);
+    if (fmax(sa, sb) < m) e->cnt[OC_SAT_EDGE_PAIR] += PA.ne * PB.ne;   /* the work that remains after the face axes */
     for (int i = 0; i < PA.ne; i++) {
         v3 a = PA.fn[PA.ef[i][0]], b = PA.fn[PA.ef[i][1]];
         v3 bxa = cross(b, a);

@@ -60,7 +60,8 @@ enum {
     OC_STEPS = 0, OC_PAIRS_TESTED, OC_PAIRS_CANDIDATE,
     OC_NP_SS, OC_NP_SC, OC_NP_SB, OC_NP_SP, OC_NP_CC, OC_NP_CB, OC_NP_CP, OC_NP_BB, OC_NP_BP,
     OC_CONTACT_POINTS, OC_CONSTRAINTS, OC_ROWS_PREP, OC_ROW_SOLVE_2DYN, OC_ROW_SOLVE_1DYN,
-    OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NP_SH, OC_NP_XH, OC_NP_HP, OC_NUM
+    OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NP_SH, OC_NP_XH, OC_NP_HP,
+    OC_SAT_FACE_VERT, OC_SAT_EDGE_PAIR, OC_NUM
 };
 
 oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
