@@ -496,10 +496,13 @@ def main():
         b.set_tuning(G, W, R)
         tuning = b.tuning()
     elif not args.no_autotune:
-        # tune on a state of the workload (arm moving, contacts made), not on
-        # the initial poses: the trials restore this state after each candidate
+        # tune on a state of the workload (arms moving, objects landed and in
+        # contact), not on the initial poses: the trials restore this state
+        # after each candidate.  60 steps: dropped objects have landed by then
+        # (tuned on the falling phase, the hulls workload picked a launch
+        # shape 1.5x slower over the run)
         with torch.cuda.stream(stream):
-            for i in range(min(args.warmup + 15, total_calls)):
+            for i in range(min(args.warmup + 60, total_calls)):
                 b.step(act(i), n, stream=stream)
         stream.synchronize()
         tuning = b.autotune(n, cache_path=os.path.join(ROOT, "paper_2410_00425_b300", "tuning_cache.json"),
