@@ -56,7 +56,7 @@ FLOP_WEIGHTS = {
     "np_bb": 1000, "np_bp": 150, "np_sh": 400, "np_xh": 500, "np_hp": 150,
     # the hull SAT's own work: a face-vertex projection (6 flop), an edge pair's
     # Gauss-map test (2 cross products' worth and 4 dot products, 20 flop)
-    "sat_face_vert": 6, "sat_edge_pair": 20,
+    "sat_face_vert": 6, "sat_edge_pair": 20, "np_ch": 2000,
 }
 FP32_LANES_PER_SM = 128
 

@@ -175,7 +175,10 @@ ms_status ms_create_batch_flat(const ms_body_desc* bodies, const int32_t* body_o
  * of least penetration when the centre is inside, else the closest surface
  * point), box or hull - hull (separating axes over face normals and the edge
  * pairs bounding the Minkowski difference; face clipping or one edge-edge
- * point).  Capsule - hull pairs make no contact.  The inertia is that of
+ * point), capsule - hull (separating axes over the hull's face normals and
+ * the segment x edge directions; the segment clipped to the best face, up
+ * to two points, else the exact closest points of segment and surface).
+ * The inertia is that of
  * the uniform solid; the broadphase bounds a hull by its vertices' bounding
  * sphere about the body origin. */
 typedef struct {

@@ -22,7 +22,7 @@ COUNTERS = ["steps", "pairs_tested", "pairs_candidate",
             "np_ss", "np_sc", "np_sb", "np_sp", "np_cc", "np_cb", "np_cp", "np_bb", "np_bp",
             "contact_points", "constraints", "rows_prep", "row_solve_2dyn", "row_solve_1dyn",
             "warm_apply", "body_integrate", "body_inertia", "colors", "np_sh", "np_xh", "np_hp",
-            "sat_face_vert", "sat_edge_pair"]
+            "sat_face_vert", "sat_edge_pair", "np_ch"]
 
 ST_PAIR_OVERFLOW, ST_CONTACT_OVERFLOW, ST_COLOR_OVERFLOW = 1, 2, 4
 

@@ -106,6 +106,7 @@ typedef struct {
     const Hull* hull;                 /* hull bodies */
     double inv_mass; double inv_I[3]; double mu, rest; unsigned group, mask;
     v3 x; qt q; v3 v; v3 w;
+    qt q0;                            /* orientation at the start of the step */
     m3 invIw;                         /* world inverse inertia, per substep */
 } Body;
 
@@ -219,6 +220,7 @@ static void body_from_desc(Body* b, const double* d) {
     b->dyn = (b->type != OR_PLANE) && d[4] > 0.0;
     b->x = V(d[5], d[6], d[7]);
     b->q = qnormalize(Q(d[8], d[9], d[10], d[11]));
+    b->q0 = b->q;
     b->mu = d[18];
     b->rest = d[19];
     b->group = (unsigned)d[20]; b->mask = (unsigned)d[21];
@@ -965,6 +967,106 @@ static void np_poly(Env* e, const Shape* A, const Shape* B, double m, CandSet* c
     }
 }
 
+/* closest points of segment [s0, s1] and the surface of polytope P (its
+ * triangles): for each triangle, the segment's ends against the triangle
+ * and the segment against the triangle's edges; the overall least distance */
+static double segment_poly_closest(const Poly* P, v3 s0, v3 s1, v3* ps, v3* pq) {
+    double best = INFINITY;
+    for (int f = 0; f < P->nf; f++) {
+        v3 t[3] = {P->v[P->fv[f][0]], P->v[P->fv[f][1]], P->v[P->fv[f][2]]};
+        v3 q = closest_on_triangle(s0, t[0], t[1], t[2]);
+        double d2 = dot(sub(s0, q), sub(s0, q));
+        if (d2 < best) { best = d2; *ps = s0; *pq = q; }
+        q = closest_on_triangle(s1, t[0], t[1], t[2]);
+        d2 = dot(sub(s1, q), sub(s1, q));
+        if (d2 < best) { best = d2; *ps = s1; *pq = q; }
+        for (int k = 0; k < 3; k++) {
+            v3 a, b;
+            closest_segments(s0, s1, t[k], t[(k + 1) % 3], &a, &b);
+            d2 = dot(sub(a, b), sub(a, b));
+            if (d2 < best) { best = d2; *ps = a; *pq = b; }
+        }
+    }
+    return sqrt(best);
+}
+
+/* capsule - hull: separating axes over the hull's face normals and the
+ * cross products of the segment with the hull's edges (each edge axis in
+ * the orientation that separates more); an edge axis only if it beats the
+ * best face by 1e-4 m.  Face case: the segment clipped to the face's side
+ * planes, up to two points, or, when nothing of it lies over the face, the
+ * exact closest points of segment and hull surface; edge case: those exact
+ * closest points (the edge that gives the axis need not support the hull
+ * along it). */
+static void np_ch(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs) {
+    double r = A->p[0];
+    v3 s0, s1;
+    capsule_ends(A, &s0, &s1);
+    v3 u = sub(s1, s0);
+    double ul = norm(u);
+    Poly P;
+    poly_of(B, &P);
+    double sf = -INFINITY; int bf = 0;
+    for (int f = 0; f < P.nf; f++) {
+        double sg = fmin(dot(P.fn[f], s0), dot(P.fn[f], s1)) - P.fd[f] - r;
+        if (sg > sf) { sf = sg; bf = f; }
+    }
+    double se = -INFINITY; int be = -1; v3 le = V(0, 0, 0);
+    for (int k = 0; k < P.ne; k++) {
+        v3 ev = sub(P.v[P.e[k][1]], P.v[P.e[k][0]]);
+        v3 c = cross(ev, u);
+        double cn = norm(c), lim = 1e-5 * norm(ev) * ul;
+        tie_w(e, cn, lim, TIE_DIR * norm(ev) * ul);
+        if (!(cn > lim)) continue;
+        v3 L = scl(c, 1.0 / cn);
+        double hmax = -INFINITY, hmin = INFINITY;
+        for (int q = 0; q < P.nv; q++) { double t = dot(L, P.v[q]); hmax = fmax(hmax, t); hmin = fmin(hmin, t); }
+        double sp = fmin(dot(L, s0), dot(L, s1)) - hmax - r;    /* capsule on the +L side */
+        double sn = hmin - fmax(dot(L, s0), dot(L, s1)) - r;    /* capsule on the -L side */
+        tie(e, sp, sn);
+        if (sn > sp) { sp = sn; L = neg(L); }
+        if (sp > se) { se = sp; be = k; le = L; }
+    }
+    double maxsep = fmax(sf, se);
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
+    if (be >= 0) tie(e, se, sf + 1e-4);
+    v3 n = P.fn[bf];
+    int empty = 0;
+    double tlo = 0.0, thi = 1.0;
+    if (be >= 0 && se > sf + 1e-4) {
+        /* the edge that gave the axis need not be the hull's support along
+         * it: the exact closest points of segment and surface */
+        empty = 1;
+        n = le;
+    }
+    for (int k = 0; k < P.fnv[bf] && !empty; k++) {
+        v3 p0 = P.v[P.fv[bf][k]], p1 = P.v[P.fv[bf][(k + 1) % P.fnv[bf]]];
+        v3 sd = cross(sub(p1, p0), n);
+        sd = scl(sd, 1.0 / norm(sd));
+        double g0 = dot(sd, sub(s0, p0)), gu = dot(sd, u);
+        if (gu == 0.0) { if (g0 > 0.0) empty = 1; continue; }
+        double t = -g0 / gu;
+        if (gu > 0.0) thi = fmin(thi, t); else tlo = fmax(tlo, t);
+    }
+    tie(e, tlo, thi);
+    if (tlo > thi) empty = 1;
+    if (!empty) {
+        double ts[2] = {tlo, thi};
+        int cnt = tlo == thi ? 1 : 2;
+        for (int a = 0; a < cnt; a++) {
+            v3 q = add(s0, scl(u, ts[a]));
+            double dist = dot(n, q) - P.fd[bf];
+            push(cs, sub(q, scl(n, r)), sub(q, scl(n, dist)), n, dist - r);
+        }
+        return;
+    }
+    v3 ps = s0, pq = P.v[0];
+    double dist = segment_poly_closest(&P, s0, s1, &ps, &pq);
+    v3 nn = dist > 1e-12 ? scl(sub(ps, pq), 1.0 / dist) : n;
+    push(cs, sub(ps, scl(nn, r)), pq, nn, dist - r);
+}
+
 static int first_unused(const int* used, int n) {
     for (int k = 0; k < n; k++) if (!used[k]) return k;
     return 0;
@@ -1027,7 +1129,7 @@ static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, 
     else if (ta == OR_SPHERE && tb == OR_HULL) { np_sh(e, A, B, m, &cs); slot = OC_NP_SH; }
     else if ((ta == OR_BOX || ta == OR_HULL) && tb == OR_HULL) { np_poly(e, A, B, m, &cs); slot = OC_NP_XH; }
     else if (ta == OR_HULL && tb == OR_PLANE) { np_hp(e, A, B, m, &cs); slot = OC_NP_HP; }
-    /* capsule - hull: no contact (not built) */
+    else if (ta == OR_CAPSULE && tb == OR_HULL) { np_ch(e, A, B, m, &cs); slot = OC_NP_CH; }
     if (slot >= 0) e->cnt[slot]++;
     Cand kept[16]; int nk = 0;
     *margin_tie = 0;
@@ -1151,19 +1253,19 @@ static void build_constraints(Env* e) {
 /* ------------------------------------------------------------------------- */
 /* constraint rows (per substep)                                              */
 /* ------------------------------------------------------------------------- */
-typedef struct { v3 x; qt q; m3 R; v3 v, w; double im; m3 iI; int dyn; } BodyView;
+typedef struct { v3 x; qt q; m3 R; v3 v, w; double im; m3 iI; int dyn; qt q0; } BodyView;
 
 static BodyView view(const Env* e, int i) {
     BodyView bv;
     if (i < 0) {
         bv.x = V(0, 0, 0); bv.q = Q(0, 0, 0, 1); bv.R = qmat(bv.q);
-        bv.v = V(0, 0, 0); bv.w = V(0, 0, 0); bv.im = 0.0; bv.dyn = 0;
+        bv.v = V(0, 0, 0); bv.w = V(0, 0, 0); bv.im = 0.0; bv.dyn = 0; bv.q0 = bv.q;
         memset(&bv.iI, 0, sizeof(bv.iI));
         return bv;
     }
     const Body* b = &e->bodies[i];
     bv.x = b->x; bv.q = b->q; bv.R = qmat(b->q); bv.v = b->v; bv.w = b->w;
-    bv.im = b->inv_mass; bv.iI = b->invIw; bv.dyn = b->dyn;
+    bv.im = b->inv_mass; bv.iI = b->invIw; bv.dyn = b->dyn; bv.q0 = b->q0;
     return bv;
 }
 
@@ -1224,6 +1326,28 @@ static JointGeo joint_geo(const Joint* j, const BodyView* P, const BodyView* C) 
     return g;
 }
 
+/* Contact point geometry inside a step.  The anchors keep the orientation of
+ * the step start (r = R0 a) and the separation follows the bodies' motion to
+ * first order in their rotation since then, theta = 2 sgn(w) vec(q q0^-1):
+ *     d = n . ((x_A + r_A + theta_A x r_A) - (x_B + r_B + theta_B x r_B)),
+ * the temporal-Gauss-Seidel scheme of the engine the paper builds on.  The
+ * exact re-evaluation with rotating anchors lets a rolling body sink by
+ * r (1 - cos theta) and be pushed back up each step, a gain of energy. */
+static v3 rot_since(qt q, qt q0) {
+    qt d = qmul(q, qconj(q0));
+    double s = d.w >= 0.0 ? 2.0 : -2.0;
+    return V(s * d.x, s * d.y, s * d.z);
+}
+
+static double contact_sep(const CPoint* p, const BodyView* A, const BodyView* B, v3* rA, v3* rB) {
+    m3 RA0 = qmat(A->q0), RB0 = qmat(B->q0);
+    *rA = mv(&RA0, p->aA);
+    *rB = mv(&RB0, p->aB);
+    v3 pa = add(add(A->x, *rA), cross(rot_since(A->q, A->q0), *rA));
+    v3 pb = add(add(B->x, *rB), cross(rot_since(B->q, B->q0), *rB));
+    return dot(p->n, sub(pa, pb));
+}
+
 static double contact_bias(double d, double h, double vmax) {
     return d >= 0.0 ? d / h : fmax(d / h, -vmax);
 }
@@ -1239,8 +1363,8 @@ static void prep(const oracle_world* w, Env* e, double h) {
             double mu = 0.5 * (e->bodies[M->a].mu + e->bodies[M->b].mu);
             for (int k = 0; k < M->np; k++) {
                 CPoint* p = &M->p[k];
-                v3 rA = mv(&A.R, p->aA), rB = mv(&B.R, p->aB);
-                double d = dot(p->n, sub(add(A.x, rA), add(B.x, rB)));
+                v3 rA, rB;
+                double d = contact_sep(p, &A, &B, &rA, &rB);
                 v3 t1, t2;
                 tangents(p->n, &t1, &t2);
                 tie_basis(e, p->n);
@@ -1330,9 +1454,8 @@ static void relax_bias(Env* e, double h) {
         if (c->kind == 1) {
             Manifold* M = &e->man[c->idx];
             for (int k = 0; k < M->np; k++) {
-                CPoint* p = &M->p[k];
-                v3 rA = mv(&A.R, p->aA), rB = mv(&B.R, p->aB);
-                double d = dot(p->n, sub(add(A.x, rA), add(B.x, rB)));
+                v3 rA, rB;
+                double d = contact_sep(&M->p[k], &A, &B, &rA, &rB);
                 R[k].relax_bias = fmax(d, 0.0) / h;
             }
             for (int r = M->np; r < c->nrows; r++) R[r].relax_bias = 0.0;
@@ -1518,6 +1641,7 @@ static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
                 e->joints[j].target = act[j];
             }
         }
+    for (int i = 0; i < e->nb; i++) e->bodies[i].q0 = e->bodies[i].q;
     broadphase(w, e);
     narrowphase(w, e);
     build_constraints(e);
@@ -2159,6 +2283,7 @@ void oracle_set_state(oracle_world* w, const double* in) {
             const double* o = in + 13 * (w->body_off[ei] + i);
             b->x = V(o[0], o[1], o[2]);
             b->q = Q(o[3], o[4], o[5], o[6]);
+            b->q0 = b->q;
             if (b->dyn) { b->v = V(o[7], o[8], o[9]); b->w = V(o[10], o[11], o[12]); }
         }
         /* a set state starts without warm-start memory */

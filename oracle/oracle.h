@@ -61,7 +61,7 @@ enum {
     OC_NP_SS, OC_NP_SC, OC_NP_SB, OC_NP_SP, OC_NP_CC, OC_NP_CB, OC_NP_CP, OC_NP_BB, OC_NP_BP,
     OC_CONTACT_POINTS, OC_CONSTRAINTS, OC_ROWS_PREP, OC_ROW_SOLVE_2DYN, OC_ROW_SOLVE_1DYN,
     OC_WARM_APPLY, OC_BODY_INTEGRATE, OC_BODY_INERTIA, OC_COLORS, OC_NP_SH, OC_NP_XH, OC_NP_HP,
-    OC_SAT_FACE_VERT, OC_SAT_EDGE_PAIR, OC_NUM
+    OC_SAT_FACE_VERT, OC_SAT_EDGE_PAIR, OC_NP_CH, OC_NUM
 };
 
 oracle_world* oracle_create(int n_envs, const long long* body_off, const double* bodies,
@@ -75,7 +75,9 @@ oracle_world* oracle_create(int n_envs, const long long* body_off, const double*
  * Contacts: hull - plane (vertices within the margin), sphere - hull (face
  * of least penetration inside, closest surface point outside), box or
  * hull - hull (SAT over face normals and Gauss-map edge pairs, face
- * clipping or one edge-edge point); capsule - hull pairs make no contact. */
+ * clipping or one edge-edge point), capsule - hull (SAT over face normals
+ * and segment x edge axes; the segment clipped to the face, else the exact
+ * segment - surface closest points). */
 oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const double* bodies,
                                   const long long* joint_off, const double* joints, const double* params,
                                   int n_hulls, const int* vert_off, const double* verts, const int* tri_off,

@@ -36,7 +36,7 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     } else {
         L.x = L.q = L.v = L.w = -1;
     }
-    L.sq = take(32 * nb, 16);
+    L.sq = take(48 * nb, 16);
     L.color_off = take(4 * (MAX_COLORS + 1), 4);
     L.cnt = take(4 * C_NUM, 16);
     L.status = take(4, 4);

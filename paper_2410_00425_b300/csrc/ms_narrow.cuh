@@ -728,6 +728,106 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     }
 }
 
+
+// closest points of segment [s0, s1] and the surface of polytope P (its
+// triangles): per triangle, the segment's ends against the triangle and the
+// segment against its edges; the least distance
+MSD float segment_poly_closest(const Poly& P, float3 s0, float3 s1, float3& ps, float3& pq) {
+    float best = 3e38f;
+    for (int f = 0; f < P.nf; f++) {
+        int idx[4];
+        poly_face(P, f, idx);
+        float3 tv[3] = {P.v[idx[0]], P.v[idx[1]], P.v[idx[2]]};
+        float3 q = closest_on_triangle(s0, tv[0], tv[1], tv[2]);
+        float d2 = dot(s0 - q, s0 - q);
+        if (d2 < best) { best = d2; ps = s0; pq = q; }
+        q = closest_on_triangle(s1, tv[0], tv[1], tv[2]);
+        d2 = dot(s1 - q, s1 - q);
+        if (d2 < best) { best = d2; ps = s1; pq = q; }
+        for (int k = 0; k < 3; k++) {
+            float3 a, b;
+            closest_segments(s0, s1, tv[k], tv[k == 2 ? 0 : k + 1], a, b);
+            d2 = dot(a - b, a - b);
+            if (d2 < best) { best = d2; ps = a; pq = b; }
+        }
+    }
+    return sqrtf(best);
+}
+
+// capsule - hull: separating axes over the hull's face normals and the
+// segment x hull-edge axes (each in the orientation that separates more);
+// an edge axis only if it beats the best face by 1e-4 m.  Face case: the
+// segment clipped to the face's side planes (up to two points), or, when
+// nothing of it lies over the face, the exact segment - surface closest
+// points; edge case: those exact closest points (the edge that gives the
+// axis need not support the hull along it).
+MSD void np_ch(const Shape& A, const Shape& B, float m, CandSet& cs) {
+    float r = A.p0;
+    float3 s0, s1;
+    capsule_ends(A, s0, s1);
+    float3 u = s1 - s0;
+    float ul = len(u);
+    Poly P;
+    poly_of(B, P);
+    float sf = -3e38f; int bf = 0;
+    for (int f = 0; f < P.nf; f++) {
+        float3 n = xyz(P.f[f]);
+        float sg = fminf(dot(n, s0), dot(n, s1)) - P.f[f].w - r;
+        if (sg > sf) { sf = sg; bf = f; }
+    }
+    float se = -3e38f; int be = -1; float3 le = f3(0.f, 0.f, 0.f);
+    for (int k = 0; k < P.ne; k++) {
+        int4 E = poly_edge(P, k);
+        float3 ev = P.v[E.y] - P.v[E.x];
+        float3 c = cross(ev, u);
+        float cn = len(c), lim = 1e-5f * len(ev) * ul;
+        if (!(cn > lim)) continue;
+        float3 L = c * (1.f / cn);
+        float hmax = -3e38f, hmin = 3e38f;
+        for (int q = 0; q < P.nv; q++) { float t = dot(L, P.v[q]); hmax = fmaxf(hmax, t); hmin = fminf(hmin, t); }
+        float sp = fminf(dot(L, s0), dot(L, s1)) - hmax - r;
+        float sn = hmin - fmaxf(dot(L, s0), dot(L, s1)) - r;
+        if (sn > sp) { sp = sn; L = -L; }
+        if (sp > se) { se = sp; be = k; le = L; }
+    }
+    float maxsep = fmaxf(sf, se);
+    if (maxsep >= m) return;
+    float3 n = xyz(P.f[bf]);
+    float tlo = 0.f, thi = 1.f;
+    bool empty = false;
+    if (be >= 0 && se > sf + 1e-4f) {
+        // the edge that gave the axis need not be the hull's support along
+        // it: the exact closest points of segment and surface
+        empty = true;
+        n = le;
+    }
+    int idx[4];
+    int nfv = poly_face(P, bf, idx);
+    for (int k = 0; k < nfv && !empty; k++) {
+        float3 p0 = P.v[idx[k]], p1 = P.v[idx[k + 1 == nfv ? 0 : k + 1]];
+        float3 sd = cross(p1 - p0, n);
+        sd = sd * (1.f / len(sd));
+        float g0 = dot(sd, s0 - p0), gu = dot(sd, u);
+        if (gu == 0.f) { if (g0 > 0.f) empty = true; continue; }
+        float t = -g0 / gu;
+        if (gu > 0.f) thi = fminf(thi, t); else tlo = fmaxf(tlo, t);
+    }
+    if (tlo > thi) empty = true;
+    if (!empty) {
+        int cnt = tlo == thi ? 1 : 2;
+        for (int a = 0; a < cnt; a++) {
+            float3 q = s0 + u * (a == 0 ? tlo : thi);
+            float dist = dot(n, q) - P.f[bf].w;
+            cs.push(q - n * r, q - n * dist, n, dist - r);
+        }
+        return;
+    }
+    float3 ps = s0, pq = P.v[0];
+    float dist = segment_poly_closest(P, s0, s1, ps, pq);
+    float3 nn = dist > 1e-12f ? (ps - pq) * (1.f / dist) : n;
+    cs.push(ps - nn * r, pq, nn, dist - r);
+}
+
 // Narrowphase of the ordered pair (A, B): up to 4 kept points in out.
 MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
     CandSet cs;
@@ -743,6 +843,7 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
         if (tb == SH_CAPSULE) np_cc(A, B, cs);
         else if (tb == SH_BOX) np_cb(A, B, m, cs);
         else if (tb == SH_PLANE) np_cp(A, B, cs);
+        else if (tb == SH_HULL) { if (B.hull.v) np_ch(A, B, m, cs); }
     } else if (ta == SH_BOX) {
         if (tb == SH_BOX) np_bb(A, B, m, cs);
         else if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
@@ -751,7 +852,6 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
         if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
         else if (tb == SH_PLANE) np_hp(A, B, m, cs);
     }
-    // capsule - hull: no contact
     Cand kept[16];
     int nk = 0;
     for (int i = 0; i < cs.n; i++)

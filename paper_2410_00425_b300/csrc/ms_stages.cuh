@@ -77,7 +77,7 @@ struct EnvView {
     float4* wc;                       // warm-start memory of the env (null: off): 2 per contact point
     int* wc_n;                        //   its count
     float* wjl;                       //   8 impulses per joint
-    float4* sq;                       // S per body, 2 float4: (xx, xy, xz, yy), (yz, zz, -, -)
+    float4* sq;                       // per body, 3 float4: S = (xx, xy, xz, yy), (yz, zz, -, -); q at the step start
     float4* aabb;                     // 2 per body
     int* pairs;                       // i | j << 16
     int4* man;                        // a, b, npts, first point
@@ -362,9 +362,14 @@ MSD void stage_color(EnvView& e, const Grp& g) {
             e.cons[i] = make_int4(M.x, M.y, 3 * M.w, place | (M.z << 2) | (m << 8));
         }
     }
+    // colour masks cleared; the orientations at the start of the step, which
+    // the contact rows keep
     int nbmax = g.wmax(e.nb);
     for (int b0 = 0; b0 < nbmax; b0 += g.size)
-        if (b0 + g.lane < e.nb) e.used[b0 + g.lane] = 0ull;
+        if (b0 + g.lane < e.nb) {
+            e.used[b0 + g.lane] = 0ull;
+            e.sq[3 * (b0 + g.lane) + 2] = e.q[b0 + g.lane];
+        }
     g.sync();
     if (g.lane == 0 && live) {
         // greedy colours; color_off counts the members of each colour
@@ -431,7 +436,7 @@ struct BodyPose {
 };
 
 MSD S3 load_sq(const EnvView& e, int i) {
-    float4 a = e.sq[2 * i], b = e.sq[2 * i + 1];
+    float4 a = e.sq[3 * i], b = e.sq[3 * i + 1];
     return S3{a.x, a.y, a.z, a.w, b.x, b.y};
 }
 
@@ -512,6 +517,37 @@ MSD void tangents(float3 n, float3& t1, float3& t2) {
     t2 = cross(n, t1);
 }
 
+// Contact point geometry inside a step: the anchors keep the orientation of
+// the step start (r = R0 a) and the separation follows each body's motion to
+// first order in its rotation since then, theta = 2 sgn(w) vec(q q0^-1),
+//     d = n . ((x_A + r_A + theta_A x r_A) - (x_B + r_B + theta_B x r_B)),
+// the temporal-Gauss-Seidel scheme of the engine the paper builds on.  (With
+// anchors turned with the body, a rolling body sinks by r (1 - cos theta)
+// inside a step and is pushed back up: it gains energy.)
+struct StepFrame {
+    M3 R0;          // rotation at the step start
+    float3 th;      // rotation since then, to first order
+};
+
+MSD StepFrame step_frame(const EnvView& e, int i, float4 q) {
+    StepFrame f;
+    float4 q0 = i >= 0 ? e.sq[3 * i + 2] : make_float4(0.f, 0.f, 0.f, 1.f);
+    f.R0 = qmat(q0);
+    float4 d = qmul(q, qconj(q0));
+    float s = d.w >= 0.f ? 2.f : -2.f;
+    f.th = f3(s * d.x, s * d.y, s * d.z);
+    return f;
+}
+
+MSD float contact_sep(const float4* pt, const BodyPose& A, const BodyPose& B, const StepFrame& FA,
+                      const StepFrame& FB, float3& rA, float3& rB) {
+    rA = mv(FA.R0, xyz(pt[0]));
+    rB = mv(FB.R0, xyz(pt[1]));
+    float3 pa = (A.x + rA) + cross(FA.th, rA);
+    float3 pb = (B.x + rB) + cross(FB.th, rB);
+    return dot(xyz(pt[2]), pa - pb);
+}
+
 MSD Row* cons_rows(const EnvView& e, int4 c) {
     int place = c.w & 3;
     return (place == CP_JOINT ? e.rows_j : (place == CP_MAN_S ? e.rows_cs : e.rows_cg)) + c.z;
@@ -527,11 +563,11 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
         int4 M = e.man[idx];
         int np = M.z;
         float mu = 0.5f * (e.shape[M.x].w + e.shape[M.y].w);
+        StepFrame FA = step_frame(e, c.x, A.q), FB = step_frame(e, c.y, B.q);
         for (int k = 0; k < np; k++) {
             const float4* pt = e.pts + 3 * (M.w + k);
-            float3 aA = xyz(pt[0]), aB = xyz(pt[1]), n = xyz(pt[2]);
-            float3 rA = mv(A.R, aA), rB = mv(B.R, aB);
-            float d = dot(n, (A.x + rA) - (B.x + rB));
+            float3 n = xyz(pt[2]), rA, rB;
+            float d = contact_sep(pt, A, B, FA, FB, rA, rB);
             float3 t1, t2;
             tangents(n, t1, t2);
             point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), 0.f);
@@ -611,12 +647,12 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
             M3 R = qmat(e.q[i]);
             S3 S = rdrt(R, sd);
             S3 Si = rdrt(R, f3(1.f / sd.x, 1.f / sd.y, 1.f / sd.z));
-            e.sq[2 * i] = make_float4(S.xx, S.xy, S.xz, S.yy);
-            e.sq[2 * i + 1] = make_float4(S.yz, S.zz, 0.f, 0.f);
+            e.sq[3 * i] = make_float4(S.xx, S.xy, S.xz, S.yy);
+            e.sq[3 * i + 1] = make_float4(S.yz, S.zz, 0.f, 0.f);
             e.w[i] = f4(smv(Si, xyz(e.w[i]) * P.adw), 0.f);
         } else {
-            e.sq[2 * i] = make_float4(1.f, 0.f, 0.f, 1.f);
-            e.sq[2 * i + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
+            e.sq[3 * i] = make_float4(1.f, 0.f, 0.f, 1.f);
+            e.sq[3 * i + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
         }
     }
     g.sync();
@@ -759,10 +795,10 @@ MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
     BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
     if (!joint) {
         int4 M = e.man[idx];
+        StepFrame FA = step_frame(e, c.x, A.q), FB = step_frame(e, c.y, B.q);
         for (int k = 0; k < M.z; k++) {
-            const float4* pt = e.pts + 3 * (M.w + k);
-            float3 rA = mv(A.R, xyz(pt[0])), rB = mv(B.R, xyz(pt[1]));
-            float d = dot(xyz(pt[2]), (A.x + rA) - (B.x + rB));
+            float3 rA, rB;
+            float d = contact_sep(e.pts + 3 * (M.w + k), A, B, FA, FB, rA, rB);
             R[k].c.w = fmaxf(d, 0.f) / h;
         }
     } else {

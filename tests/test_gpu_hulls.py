@@ -112,6 +112,41 @@ def test_spheres_on_a_hull_follow_the_oracle():
     assert within(env_errors(sc, g2, o2.state()))[clean2].all()
 
 
+def test_capsules_on_a_hull_follow_the_oracle():
+    """Capsule - hull contacts: capsules at several tilts dropped onto a
+    static random hull and onto a box-shaped one.  A rollout to 40 steps
+    (through the first contacts), and one step from the states the oracle
+    reaches at 17 and 26 steps, when most capsules touch their hull."""
+    from scenegen import CAPSULE
+    g = np.random.default_rng(6)
+    assets = [H.hull_asset(H.random_points(g, 12, np.array([0.06, 0.05, 0.04]))), H.box_asset(0.05, 0.05, 0.02)]
+    envs = []
+    for k in range(16):
+        q = scenegen.axis_angle_quat((1.0, 0.3 * (k % 3), 0.0), 0.25 * k)
+        envs.append([body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)),
+                     body(HULL, (k % 2, 0, 0), 0.0, (0, 0, 0.08)),
+                     body(CAPSULE, (0.01, 0.02, 0), 0.03, (0.006 * (k - 8), 0.003 * (k % 5), 0.2), quat=q)])
+    sc = pack("capsule_hull", envs, [[] for _ in envs], scenegen.default_params(), 0, 0)
+    sc.hulls = H.library(assets)
+    calm, ost = non_chaotic(sc, 40)
+    o = oracle_run(sc, 40)
+    _, st, _ = gpu_run(sc, 40)
+    assert sum(len(o.manifolds(e)[0]) for e in range(16)) >= 8             # on the hulls
+    clean = calm & tie_free(o, sc)
+    assert clean.sum() >= 6
+    err = env_errors(sc, st, ost)
+    assert within(err, 10.0)[clean].all(), (np.nonzero(clean & ~within(err, 10.0))[0].tolist(), err[clean].max(0))
+    for settle in (17, 26):
+        b2, o2, g2, status = _one_step_from(sc, oracle_run(sc, settle).state())
+        clean2 = tie_free(o2, sc)
+        assert clean2.sum() >= 8
+        on_hull = [e for e in range(16) if any(tuple(p) in ((2, 1), (1, 2)) for p in o2.manifolds(e)[0])]
+        assert len(on_hull) >= 6
+        assert not [e for e in pair_sets_match(b2, o2, sc) if clean2[e]]
+        assert within(env_errors(sc, g2, o2.state()))[clean2].all()
+        assert not status.any()
+
+
 def test_box_hull_on_a_plane_moves_like_the_box():
     hx, hy, hz = 0.03, 0.02, 0.025
     q = scenegen.axis_angle_quat(np.array([0.3, 1.0, 0.2]) / np.linalg.norm([0.3, 1.0, 0.2]), 0.4)

@@ -162,3 +162,101 @@ def test_box_hull_renders_like_the_box():
     np.testing.assert_array_equal(rb, rh)
     np.testing.assert_allclose(dh, db, rtol=1e-12)
     assert (sh == 2).sum() > 100
+
+
+def test_capsule_over_a_hull_face_gets_two_points():
+    """A capsule along x lying 3 mm above the top face of a box-shaped hull,
+    over one of the face's two triangles: its two ends, at the gap."""
+    from scenegen import CAPSULE
+    hv, ht = H.box_asset(0.05, 0.05, 0.05)
+    r, l = 0.01, 0.02
+    q = scenegen.axis_angle_quat((0, 1, 0), math.pi / 2)              # capsule axis along x
+    pairs, npts, pts = _manifold([body(CAPSULE, (r, l, 0), 0.1, (0.0, -0.03, 0.05 + r + 0.003), quat=q),
+                                  body(HULL, (0, 0, 0), 0.0, (0, 0, 0))], [(hv, ht)])
+    assert npts[0] == 2
+    np.testing.assert_allclose(pts[0, :2, 9], 0.003, atol=1e-7)
+    np.testing.assert_allclose(sorted(pts[0, :2, 3]), [-l, l], atol=1e-7)   # cB x = the segment's ends
+    np.testing.assert_allclose(pts[0, :2, 6:9], [[0, 0, 1], [0, 0, 1]], atol=1e-7)
+
+
+def test_capsule_beside_a_hull_corner_takes_the_closest_points():
+    """A vertical capsule whose lower end sits outside the corner (0.05,
+    0.05, 0.05): no face region holds it, so the exact closest points give
+    the gap |end - corner| - r."""
+    from scenegen import CAPSULE
+    hv, ht = H.box_asset(0.05, 0.05, 0.05)
+    r, l = 0.01, 0.02
+    end = np.array([0.06, 0.06, 0.055])
+    pairs, npts, pts = _manifold([body(CAPSULE, (r, l, 0), 0.1, tuple(end + [0, 0, l])),
+                                  body(HULL, (0, 0, 0), 0.0, (0, 0, 0))], [(hv, ht)])
+    gap = np.linalg.norm(end - 0.05)
+    assert npts[0] == 1
+    assert abs(pts[0, 0, 9] - (gap - r)) < 1e-7
+    np.testing.assert_allclose(pts[0, 0, 6:9], (end - 0.05) / gap, atol=1e-6)
+    np.testing.assert_allclose(pts[0, 0, 3:6], [0.05, 0.05, 0.05], atol=1e-7)
+
+
+def test_capsule_across_a_hull_edge_takes_the_edge_axis():
+    """A capsule in the xz plane crossing over the top +x edge (along y) of a
+    box-shaped hull, skew to it, 4 mm out along the edge's outward bisector:
+    the segment x edge axis separates most; the gap is 4 mm."""
+    from scenegen import CAPSULE
+    hv, ht = H.box_asset(0.05, 0.05, 0.05)
+    r, l = 0.01, 0.02
+    bis = np.array([1.0, 0.0, 1.0]) / math.sqrt(2)
+    c = np.array([0.05, 0.0, 0.05]) + bis * (r + 0.004)
+    q = scenegen.axis_angle_quat((0, 1, 0), -math.pi / 4)             # capsule axis (1, 0, -1)/sqrt(2)
+    pairs, npts, pts = _manifold([body(CAPSULE, (r, l, 0), 0.1, tuple(c), quat=q),
+                                  body(HULL, (0, 0, 0), 0.0, (0, 0, 0))], [(hv, ht)])
+    assert npts[0] == 1
+    assert abs(pts[0, 0, 9] - 0.004) < 1e-6
+    np.testing.assert_allclose(pts[0, 0, 6:9], bis, atol=1e-6)
+
+
+def test_capsule_dropped_on_a_hull_lands_and_keeps_its_energy():
+    """A capsule dropped onto a static hull bounces off it onto the plane:
+    it stays above both, its energy never grows after the first contact,
+    and once it rolls on the plane (no rolling resistance in the model) its
+    speed is constant and its centre stays at height r."""
+    from scenegen import CAPSULE
+    g = np.random.default_rng(9)
+    assets = [H.hull_asset(H.random_points(g, 12, np.array([0.06, 0.05, 0.03])))]
+    r, l, m = 0.01, 0.02, 0.05
+    sc = pack("cap_hull", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)), body(HULL, (0, 0, 0), 0.0, (0, 0, 0.03)),
+                            body(CAPSULE, (r, l, 0), m, (0.005, 0.0, 0.15),
+                                 quat=scenegen.axis_angle_quat((1, 0, 0), 1.2))]], [[]],
+              scenegen.default_params(), 0, 0)
+    sc.hulls = H.library(assets)
+    o = oracle.Oracle(sc)
+    # principal moments of the capsule about its axis (z) and across it
+    vc, vs = math.pi * r * r * 2 * l, 4.0 / 3.0 * math.pi * r ** 3
+    mc, ms_ = m * vc / (vc + vs), m * vs / (vc + vs)
+    Iz = mc * r * r / 2 + ms_ * 2 * r * r / 5
+    Ix = (mc * (3 * r * r + 4 * l * l) / 12 + ms_ * (2 * r * r / 5 + l * l + 3 * l * r / 4))
+
+    def energy(st):
+        x, q, v, w = st[2, 0:3], st[2, 3:7], st[2, 7:10], st[2, 10:13]
+        R = _qmat(q)
+        wl = R.T @ w
+        return 0.5 * m * v @ v + 0.5 * (Ix * (wl[0] ** 2 + wl[1] ** 2) + Iz * wl[2] ** 2) + m * 9.81 * x[2]
+
+    es, zs = [], []
+    for k in range(40):
+        o.step(10)
+        st = o.state()
+        assert np.isfinite(st).all()
+        es.append(energy(st))
+        zs.append(st[2, 2])
+    assert min(zs) > r - 1e-3                                         # never through the plane
+    e = np.array(es[2:])                                              # after the first contact
+    assert (np.diff(e) <= 1e-6 * e[0]).all(), np.diff(e).max()
+    st = o.state()
+    assert abs(st[2, 2] - r) < 1e-4 and abs(st[2, 9]) < 1e-6          # rolling on the plane
+    np.testing.assert_allclose(es[-1], es[-10], rtol=1e-6)
+
+
+def _qmat(q):
+    x, y, z, w = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])

@@ -167,6 +167,38 @@ def test_resting_stack_stays_put():
     assert worst < 1e-4, worst
 
 
+# ------------------------------------------------------------------ rolling
+@pytest.mark.parametrize("kind", ["sphere", "capsule"])
+def test_rolling_without_slip_keeps_its_speed(kind):
+    """A sphere, and a capsule rolling on its side about its own axis, on a
+    horizontal plane with v = w x (0, 0, r): Coulomb friction does no work
+    on a rolling contact and nothing in the model resists rolling, so v and
+    w stay exactly what they were and the centre stays at height r.  (With
+    the contact anchors turned with the body inside a step, a rolling body
+    sank by r (1 - cos theta) and was pushed back each step: it sped up.)"""
+    from scenegen import CAPSULE, PLANE, SPHERE, body, pack
+    r = 0.01
+    if kind == "sphere":
+        b = body(SPHERE, (r, 0, 0), 0.05, (0.0, 0.0, r))
+        w = np.array([0.0, 20.0, 0.0])
+    else:
+        b = body(CAPSULE, (r, 0.02, 0), 0.05, (0.0, 0.0, r), quat=scenegen.axis_angle_quat((1, 0, 0), math.pi / 2))
+        w = np.array([0.0, -20.0, 0.0])                  # along the capsule axis (world y)
+    sc = pack("roll", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), mu=0.8), b]], [[]], scenegen.default_params(), 0, 0)
+    o = oracle.Oracle(sc)
+    st = o.state()
+    v = np.cross(w, [0.0, 0.0, r])
+    st[1, 7:10] = v
+    st[1, 10:13] = w
+    o.set_state(st)
+    o.step(300)
+    st = o.state()
+    np.testing.assert_allclose(st[1, 7:10], v, atol=1e-9)
+    np.testing.assert_allclose(st[1, 10:13], w, atol=1e-7)
+    assert abs(st[1, 2] - r) < 1e-9
+    assert abs(st[1, 0] - v[0] * 3.0) < 1e-6                 # 300 steps of 10 ms
+
+
 # ---------------------------------------------------------------- pendulum
 def _pend_phi(st):
     q = st[0, 3:7]
