@@ -708,10 +708,13 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 va = c.x >= 0 ? x.v[c.x] : z4, wa4 = c.x >= 0 ? x.w[c.x] : z4;
     float4 vb = c.y >= 0 ? x.v[c.y] : z4, wb4 = c.y >= 0 ? x.w[c.y] : z4;
-    float imA = va.w, imB = vb.w;
+    float imA = va.w, imB = vb.w, imS = imA + imB;
     // a static body's velocity enters Jv but no impulse changes it
     bool dynA = imA > 0.f, dynB = imB > 0.f;
-    float3 vA = xyz(va), wA = xyz(wa4), vB = xyz(vb), wB = xyz(wb4);
+    // the loop keeps v_A and the relative velocity dv = v_A - v_B, which is
+    // all that the linear part of Jv needs: J v = lin . dv + sa . w_A + sb . w_B
+    float3 vA = xyz(va), wA = xyz(wa4), wB = xyz(wb4);
+    float3 dv = vA - xyz(vb);
     float4 n0 = R[0].a, n1 = R[0].b, n2 = R[0].c;
     for (int r = 0; r < nrmax; r++) {
         float4 ra = n0, rb = n1, rc = n2;
@@ -720,9 +723,7 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
         bool live = r < nrows;
         int ri = min(r, last) * st;
         float3 lin = xyz(ra), sa = xyz(rb), sb = xyz(rc);
-        // off the dependency chain: the body-scaled directions and, below,
-        // everything in lambda' except Jv
-        float3 linA = lin * imA, linB = lin * (-imB);
+        // off the dependency chain: everything in lambda' except Jv
         float old = L[ri];
         float dl;
         if (MODE == 0) {
@@ -740,20 +741,20 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
             float lim = rb.w * ln;
             float lo = fric ? -lim : ((eq || drive) ? -INFINITY : 0.f);
             float hi = fric ? lim : INFINITY;
-            // Jv as four independent products
-            float jv = (dot(lin, vA) + dot(sa, wA)) - (dot(lin, vB) - dot(sb, wB));
+            // Jv as three independent products
+            float jv = (dot(lin, dv) + dot(sa, wA)) + dot(sb, wB);
             float nl = fmaf(-jv, ik, c1);
             nl = fminf(fmaxf(nl, lo), hi);
             if (live) L[ri] = nl;
             dl = live ? nl - old : 0.f;
         }
-        vA = madd(vA, linA, dl);
+        vA = madd(vA, lin, dl * imA);
+        dv = madd(dv, lin, dl * imS);
         wA = madd(wA, sa, dynA ? dl : 0.f);
-        vB = madd(vB, linB, dl);
         wB = madd(wB, sb, dynB ? dl : 0.f);
     }
     if (has && dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
-    if (has && dynB) { x.v[c.y] = f4(vB, imB); x.w[c.y] = f4(wB, 0.f); }
+    if (has && dynB) { x.v[c.y] = f4(vA - dv, imB); x.w[c.y] = f4(wB, 0.f); }
 }
 
 template <int MODE>
