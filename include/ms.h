@@ -366,6 +366,22 @@ ms_status ms_set_record_contacts(ms_batch* b, int record);
 ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t* npts,
                           float* pts, int* count);
 
+/* Contact forces per body: the readout behind the touch sensors of the
+ * paper's dextrous-manipulation tasks (appendix "Environments and Robots
+ * List", "Dextrous Manipulation"), a force per link from the solver's
+ * contact impulses.  ms_enable_contact_forces(b, 1) makes every later step
+ * of ms_step / ms_step_plain write, for each body, the impulses of the
+ * contact rows of every manifold that involves it over the step's last
+ * substep, divided by the substep h: (F[3], f_n) with F = the sum of
+ * +-dir lambda (+ for the manifold's body a, - for body b; the normal and
+ * both friction rows) and f_n = the sum of its normal impulses.  A body at
+ * rest on a support reads F = -m g.  0 turns it off (the buffer is kept).
+ * The step server and the no-allocation path do not write it.
+ * ms_contact_forces copies the last step's values into out (device float
+ * [n_bodies][4], ordered on stream); MS_ERR_INVALID_ARG when off. */
+ms_status ms_enable_contact_forces(ms_batch* b, int on);
+ms_status ms_contact_forces(ms_batch* b, float* out, void* stream);
+
 /* Batched-path launch shape.  lanes_per_env in {1, 2, 4, 8, 16, 32}: a warp
  * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 8];
  * rows_in_smem: 1 keeps every constraint row in shared memory when one

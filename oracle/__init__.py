@@ -56,6 +56,7 @@ def lib():
         L.oracle_destroy.argtypes = [P]
         L.oracle_step.argtypes = [P, dp, C.c_int, C.c_int, C.c_int]
         L.oracle_get_state.argtypes = [P, dp]
+        L.oracle_contact_forces.argtypes = [P, dp]
         L.oracle_set_state.argtypes = [P, dp]
         L.oracle_get_targets.argtypes = [P, dp]
         L.oracle_set_targets.argtypes = [P, dp]
@@ -249,6 +250,13 @@ class Oracle:
     def state(self) -> np.ndarray:
         out = np.zeros((self.nb, 13), np.float64)
         lib().oracle_get_state(self.h, _dp(out))
+        return out
+
+    def contact_forces(self) -> np.ndarray:
+        """Per body (F[3], f_n) of the last step: contact impulses over the
+        last substep / h (oracle_contact_forces)."""
+        out = np.zeros((self.nb, 4), np.float64)
+        lib().oracle_contact_forces(self.h, _dp(out))
         return out
 
     def set_state(self, st):

@@ -2275,6 +2275,37 @@ void oracle_get_state(const oracle_world* w, double* out) {
     }
 }
 
+/* Contact forces of the last step (the touch-sensor readout of the
+ * dextrous-manipulation tasks): for every manifold, F = sum over its rows
+ * (normal, then both friction rows of each point) of lin lambda, and
+ * f_n = the sum of its normal impulses, both divided by h; body a gets +F,
+ * body b -F, each gets f_n. */
+void oracle_contact_forces(const oracle_world* w, double* out) {
+    double h = w->dt / w->substeps;
+    memset(out, 0, sizeof(double) * 4 * (size_t)w->body_off[w->E]);
+    for (int ei = 0; ei < w->E; ei++) {
+        const Env* e = &w->envs[ei];
+        double* o = out + 4 * w->body_off[ei];
+        for (int m = 0; m < e->nman; m++) {
+            const Manifold* M = &e->man[m];
+            const Constraint* c = &e->cons[e->nj + m];
+            const Row* R = &e->rows[c->row0];
+            v3 F = V(0, 0, 0);
+            double fn = 0.0;
+            for (int r = 0; r < c->nrows; r++) {
+                F = add(F, scl(R[r].lin, R[r].lambda));
+                if (R[r].kind == RK_NORMAL) fn += R[r].lambda;
+            }
+            F = scl(F, 1.0 / h);
+            fn /= h;
+            double* a = o + 4 * M->a;
+            double* b = o + 4 * M->b;
+            a[0] += F.x; a[1] += F.y; a[2] += F.z; a[3] += fn;
+            b[0] -= F.x; b[1] -= F.y; b[2] -= F.z; b[3] += fn;
+        }
+    }
+}
+
 void oracle_set_state(oracle_world* w, const double* in) {
     for (int ei = 0; ei < w->E; ei++) {
         Env* e = &w->envs[ei];

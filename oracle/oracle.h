@@ -94,6 +94,11 @@ int oracle_step(oracle_world* w, const double* actions, int A, int n_steps, int 
 
 /* State of all bodies, [n_bodies][13] = pos[3], quat[4], linvel[3], angvel[3]. */
 void oracle_get_state(const oracle_world* w, double* out);
+/* Contact forces of the last step, [n_bodies][4] = F[3], f_n: per body, the
+ * impulses of the contact rows of every manifold that involves it over the
+ * last substep, divided by h (+ on the manifold's body a, - on body b), and
+ * the sum of its normal impulses / h. */
+void oracle_contact_forces(const oracle_world* w, double* out);
 /* Overwrite the state of all bodies (same layout); used for restart tests. */
 void oracle_set_state(oracle_world* w, const double* in);
 /* Current drive targets [n_joints]. */

@@ -124,6 +124,18 @@ class Batch:
     def contacts(self, env: int, cap: int = 1024):
         return _ffi.ms_get_contacts(self.h, env, cap)
 
+    def enable_contact_forces(self, on=True):
+        """Make every later step write each body's contact force (touch
+        sensors, ms_enable_contact_forces)."""
+        _ffi.ms_enable_contact_forces(self.h, on)
+
+    def contact_forces(self, stream=None):
+        """Per body (F[3], f_n) of the last step, device float32 [n_bodies, 4]."""
+        import torch
+        out = torch.empty((self.NB, 4), dtype=torch.float32, device="cuda")
+        _ffi.ms_contact_forces(self.h, out, stream)
+        return out
+
     def set_tuning(self, lanes_per_env=32, warps_per_cta=4, rows_in_smem=1):
         _ffi.ms_set_tuning(self.h, lanes_per_env, warps_per_cta, rows_in_smem)
 

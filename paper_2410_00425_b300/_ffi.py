@@ -96,6 +96,8 @@ _SIGS = [
     ("ms_destroy", C.c_int, [C.c_void_p]),
     ("ms_last_error", C.c_char_p, []),
     ("ms_set_record_contacts", C.c_int, [C.c_void_p, C.c_int]),
+    ("ms_enable_contact_forces", C.c_int, [C.c_void_p, C.c_int]),
+    ("ms_contact_forces", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_get_contacts", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_int)]),
     ("ms_set_tuning", C.c_int, [C.c_void_p, C.POINTER(ms_tuning)]),
@@ -307,6 +309,14 @@ def ms_last_error() -> str:
 
 def ms_set_record_contacts(b, record=True):
     return check(load().ms_set_record_contacts(b, int(record)))
+
+
+def ms_enable_contact_forces(b, on=True):
+    return check(load().ms_enable_contact_forces(b, int(on)))
+
+
+def ms_contact_forces(b, out, stream=None):
+    return check(load().ms_contact_forces(b, _ptr(out), _stream(stream)))
 
 
 def ms_get_contacts(b, env, cap=1024):

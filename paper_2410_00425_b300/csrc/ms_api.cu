@@ -98,6 +98,7 @@ struct ms_batch {
     float* d_task_qR = nullptr;       // [NJ]
     std::vector<float> h_task_half;
     RenderState* render = nullptr;
+    float4* d_force = nullptr;        // contact forces per body (allocated on first use)
 };
 
 // Device memory comes from the device's stream-ordered pool on the batch's
@@ -500,6 +501,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     if ((s = dmalloc(b, (void**)&b->d_mask, (size_t)E)) != MS_OK) { free_all(b); delete b; return s; }
     D.plain_ws = nullptr;
     D.rec_man = nullptr; D.rec_pts = nullptr; D.rec_cnt = nullptr;
+    D.force = nullptr;
     cudaError_t ce = cudaStreamSynchronize(b->setup);
     if (ce != cudaSuccess) { free_all(b); delete b; return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(ce)); }
     *out = b;
@@ -928,6 +930,29 @@ extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
     b->record = record != 0;
     if (!b->record) { b->D.rec_man = nullptr; b->D.rec_pts = nullptr; b->D.rec_cnt = nullptr; }
     drop_graphs(b);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_enable_contact_forces(ms_batch* b, int on) {
+    if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
+    if (on && !b->d_force) {
+        void* f = nullptr;
+        ms_status s = dmalloc(b, &f, sizeof(float4) * (size_t)b->NB);
+        if (s != MS_OK) return s;
+        CK(cudaMemsetAsync(f, 0, sizeof(float4) * (size_t)b->NB, b->setup));
+        CK(cudaStreamSynchronize(b->setup));
+        b->d_force = (float4*)f;
+    }
+    b->D.force = on ? b->d_force : nullptr;
+    drop_graphs(b);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_contact_forces(ms_batch* b, float* out, void* stream) {
+    if (!b || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->D.force) return fail(MS_ERR_INVALID_ARG, "contact forces are off");
+    CK(cudaMemcpyAsync(out, b->D.force, sizeof(float4) * (size_t)b->NB, cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
     return MS_OK;
 }
 

@@ -115,6 +115,7 @@ struct DevBatch {
     int4* rec_man;
     float* rec_pts;
     int* rec_cnt;
+    float4* force;                     // contact force per body of the last step (null: off)
 };
 
 struct FusedCfg {

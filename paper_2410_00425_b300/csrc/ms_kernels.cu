@@ -100,6 +100,7 @@ __device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b
     e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
     e.wc_n = w ? D.wc_n + env : nullptr;
     e.wjl = w ? D.wjl + 8 * (size_t)j0 : nullptr;
+    e.force = (D.force && active) ? D.force + b0 : nullptr;
 }
 
 __device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
@@ -178,6 +179,7 @@ __global__ void k_check(DevBatch D, int step) {
     EnvView e = plain_view(D, env);
     Grp g = warp_grp();
     end_step_solve(e, g, D.P);
+    if (D.force) stage_contact_forces(e, g, D.P);
     stage_check(e, g);
     if (D.T.out)
         stage_task_record(e, g, D.T, D.A, D.T.out + ((size_t)step * D.E + env) * D.T.D, (*e.status & ST_NAN) != 0);
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             begin_step_solve(e, g, D.P);
             for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
             end_step_solve(e, g, D.P);
+            if (D.force) stage_contact_forces(e, g, D.P);
             stage_check(e, g);
             if (D.T.out)
                 stage_task_record(e, g, D.T, D.A, active ? D.T.out + ((size_t)k * D.E + env) * D.T.D : nullptr,

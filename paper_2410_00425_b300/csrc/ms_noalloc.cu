@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
     float* rst = nat<float>(gl, L.rest);
     e.rest = rst;
     e.hulls = nullptr;                 // no hull library on this path
+    e.force = nullptr;
     e.wc = nullptr; e.wc_n = nullptr; e.wjl = nullptr;       // no warm-start memory on this path
     view_workspace(e, s, gl, L);
     e.status = nat<unsigned>(s, L.status);

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
         e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
         e.rest = D.rest + b0;
         e.hulls = D.hulls;
+        e.force = nullptr;
         bool wm = active && D.wc;
         e.wc = wm ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
         e.wc_n = wm ? D.wc_n + env : nullptr;

@@ -98,6 +98,7 @@ struct EnvView {
     int4* rec_man;                    // recorded manifolds (nullable)
     float* rec_pts;                   // recorded points [contact_cap][10]
     int* rec_cnt;
+    float4* force;                    // contact force per body (nullable)
 };
 
 // Workspace pointers of one env from its layout (s: shared part, gl: global part).
@@ -874,6 +875,37 @@ MSD void stage_check(EnvView& e, const Grp& g) {
 // previous step's manifold of the same body pair.
 MSD Row* man_rows(const EnvView& e, int4 M) {
     return (M.w + M.z <= e.pts_s ? e.rows_cs : e.rows_cg) + 3 * M.w;
+}
+
+// Contact forces of a step (touch sensors): per body, the impulses of the
+// contact rows of every manifold that involves it over the last substep,
+// divided by h: sum of +-lin lambda (+ on body a, - on body b) and the sum of
+// the normal impulses.  One lane per body, manifolds in list order, rows in
+// order.  Every lane of the warp runs it (an idle lane group with nb = 0).
+MSD void stage_contact_forces(EnvView& e, const Grp& g, const Params& P) {
+    int nb = e.nb, nman = nb > 0 ? e.cnt[C_NMAN] : 0;
+    float ih = 1.f / P.h;
+    const float* L0 = e.lam + 8 * e.njs;
+    int nbmax = g.wmax(nb);
+    for (int i0 = 0; i0 < nbmax; i0 += g.size) {
+        int i = i0 + g.lane;
+        if (i >= nb) continue;
+        float3 F = f3(0.f, 0.f, 0.f);
+        float fn = 0.f;
+        for (int m = 0; m < nman; m++) {
+            int4 M = e.man[m];
+            if (M.x != i && M.y != i) continue;
+            float sg = M.x == i ? 1.f : -1.f;
+            const Row* R = man_rows(e, M);
+            const float* L = L0 + 3 * M.w;
+            for (int r = 0; r < 3 * M.z; r++) {
+                F = madd(F, xyz(R[r].a), sg * L[r]);
+                if (r < M.z) fn += L[r];
+            }
+        }
+        if (e.force) e.force[i] = make_float4(F.x * ih, F.y * ih, F.z * ih, fn * ih);
+    }
+    g.sync();
 }
 
 // Every lane of the warp runs these stages (their loops end in warp-wide

@@ -101,6 +101,8 @@ def test_null_arguments(lib):
     assert lib.ms_set_state(None, None, 0, None, None) == 1
     assert lib.ms_get_state(None, None) == 1
     assert lib.ms_get_contacts(None, 0, 0, None, None, None, None) == 1
+    assert lib.ms_enable_contact_forces(None, 1) == 1
+    assert lib.ms_contact_forces(None, None, None) == 1
     assert lib.ms_set_tuning(None, None) == 1
     assert lib.ms_autotune(None, 1, None, None, None) == 1
     assert len(_ffi.ms_last_error()) > 0

@@ -92,6 +92,44 @@ def test_incline_slides_iff_tan_exceeds_mu(dtan):
         assert np.linalg.norm(st[1, 0:3] - x0) < 1e-4
 
 
+# ----------------------------------------------------------- contact forces
+def test_contact_forces_of_a_resting_stack_balance_gravity():
+    """Two boxes stacked on the plane, settled: the contact force on each box
+    is -m g (it does not accelerate), the top box's normal force is m2 g and
+    the bottom box's is (m1 + m2) g from the plane plus m2 g from the top
+    box; the plane reads the reaction -(m1 + m2) g."""
+    from scenegen import BOX, PLANE, body, pack
+    m1, m2, h1, h2 = 0.2, 0.05, 0.03, 0.02
+    sc = pack("stack2", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)),
+                          body(BOX, (h1, h1, h1), m1, (0, 0, h1)),
+                          body(BOX, (h2, h2, h2), m2, (0.005, -0.004, 2 * h1 + h2))]], [[]],
+              scenegen.default_params(pos_iters=64), 0, 0)
+    o = oracle.Oracle(sc)
+    o.step(200)
+    f = o.contact_forces()
+    np.testing.assert_allclose(f[1, :3], [0, 0, m1 * G], atol=1e-9 * m1 * G + 1e-12)
+    np.testing.assert_allclose(f[2, :3], [0, 0, m2 * G], atol=1e-9)
+    np.testing.assert_allclose(f[0, :3], [0, 0, -(m1 + m2) * G], atol=1e-9)
+    np.testing.assert_allclose(f[:, 3], [(m1 + m2) * G, (m1 + 2 * m2) * G, m2 * G], rtol=1e-7)
+
+
+def test_contact_force_of_a_sliding_box_is_normal_plus_kinetic_friction():
+    """A box sliding down a ramp with tan theta > mu: the contact force on it
+    is m g cos theta (n - mu s), s the down-slope direction (the pyramid row
+    along the slope sits at its bound)."""
+    mu, th, m = 0.5, math.atan(0.6), 0.1
+    sc = V.incline([th], mu=mu, mass=m)
+    o = oracle.Oracle(sc)
+    o.step(100)
+    f = o.contact_forces()
+    n = np.array([math.sin(th), 0.0, math.cos(th)])
+    s_dir = np.array([math.cos(th), 0.0, -math.sin(th)])
+    fn = m * G * math.cos(th)
+    np.testing.assert_allclose(f[1, :3], fn * (n - mu * s_dir), rtol=0, atol=1e-6 * fn)
+    np.testing.assert_allclose(f[1, 3], fn, rtol=1e-6)
+    np.testing.assert_allclose(f[0, :3], -f[1, :3], atol=1e-12)
+
+
 # ----------------------------------------------------------------- momentum
 def _momenta(sc, st):
     m = sc.bodies["mass"].astype(np.float64)
