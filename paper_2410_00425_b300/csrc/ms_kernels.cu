@@ -9,6 +9,8 @@
 // joints into shared-memory slots, runs all n_steps for all of them in
 // lockstep (G lanes per env) and writes the state back once.  No wait in
 // either kernel spins on another thread.
+#include <nvtx3/nvToolsExt.h>
+
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -185,25 +187,46 @@ __global__ void k_check(DevBatch D, int step) {
         stage_task_record(e, g, D.T, D.A, D.T.out + ((size_t)step * D.E + env) * D.T.D, (*e.status & ST_NAN) != 0);
 }
 
+// NVTX ranges name the launches of each stage (host-side enqueue ranges; a
+// profiler can select kernels by them, e.g. ncu --nvtx --nvtx-include).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s) {
     int launches = 0;
     dim3 grid(D.E), block(32);
+    NvtxRange all("ms_step_plain");
     for (int k = 0; k < n_steps; k++) {
-        k_begin_step<<<grid, block, 0, s>>>(D, actions, k);
-        k_narrow<<<grid, block, 0, s>>>(D);
-        k_color<<<grid, block, 0, s>>>(D);
-        launches += 3;
-        for (int sub = 0; sub < D.P.substeps; sub++) {
-            k_prep<<<grid, block, 0, s>>>(D);
-            k_sweep<<<grid, block, 0, s>>>(D, 0);
-            launches += 2;
-            for (int it = 0; it < D.P.pos_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 1); launches++; }
-            k_integrate<<<grid, block, 0, s>>>(D);
-            launches++;
-            for (int it = 0; it < D.P.vel_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 2); launches++; }
-            k_end_substep<<<grid, block, 0, s>>>(D, sub == D.P.substeps - 1);
-            launches++;
+        {
+            NvtxRange r("broadphase+narrowphase+colour");
+            k_begin_step<<<grid, block, 0, s>>>(D, actions, k);
+            k_narrow<<<grid, block, 0, s>>>(D);
+            k_color<<<grid, block, 0, s>>>(D);
+            launches += 3;
         }
+        for (int sub = 0; sub < D.P.substeps; sub++) {
+            {
+                NvtxRange r("prep+warm");
+                k_prep<<<grid, block, 0, s>>>(D);
+                k_sweep<<<grid, block, 0, s>>>(D, 0);
+                launches += 2;
+            }
+            {
+                NvtxRange r("position sweeps");
+                for (int it = 0; it < D.P.pos_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 1); launches++; }
+            }
+            {
+                NvtxRange r("integrate+relax sweeps");
+                k_integrate<<<grid, block, 0, s>>>(D);
+                launches++;
+                for (int it = 0; it < D.P.vel_iters; it++) { k_sweep<<<grid, block, 0, s>>>(D, 2); launches++; }
+                k_end_substep<<<grid, block, 0, s>>>(D, sub == D.P.substeps - 1);
+                launches++;
+            }
+        }
+        NvtxRange r("check");
         k_check<<<grid, block, 0, s>>>(D, k);
         launches++;
     }
@@ -313,6 +336,7 @@ cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, c
     const void* fn = fused_fn(G);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&D, (void*)&actions, (void*)&n_steps, (void*)&C};
+    NvtxRange r("ms_step (fused)");
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
 }
 
