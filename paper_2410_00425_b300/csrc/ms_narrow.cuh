@@ -515,7 +515,7 @@ struct Poly {
     bool box;
     int nv, nf, ne;
     float3 c;                        // body origin (interior)
-    float3 v[PV_MAXV];
+    float4 v[PV_MAXV];               // world vertices (w unused: 16-byte loads)
     float4 f[PV_MAXF];               // world face plane (n, n.x on the face)
     const int4* tri;
     const int4* edge;
@@ -526,7 +526,7 @@ MSD void poly_of(const Shape& S, Poly& P) {
     if (S.type == SH_BOX) {
         P.box = true; P.nv = 8; P.nf = 6; P.ne = 12;
         for (int k = 0; k < 8; k++)
-            P.v[k] = S.x + mv(S.R, f3((k & 1) ? S.p0 : -S.p0, (k & 2) ? S.p1 : -S.p1, (k & 4) ? S.p2 : -S.p2));
+            P.v[k] = f4(S.x + mv(S.R, f3((k & 1) ? S.p0 : -S.p0, (k & 2) ? S.p1 : -S.p1, (k & 4) ? S.p2 : -S.p2)), 0.f);
         const float h[3] = {S.p0, S.p1, S.p2};
         for (int f = 0; f < 6; f++) {
             float3 n = mcol(S.R, f >> 1) * ((f & 1) ? -1.f : 1.f);
@@ -536,7 +536,7 @@ MSD void poly_of(const Shape& S, Poly& P) {
     } else {
         const HullRef& H = S.hull;
         P.box = false; P.nv = H.nv; P.nf = H.nt; P.ne = H.ne;
-        for (int k = 0; k < H.nv; k++) P.v[k] = S.x + mv(S.R, xyz(H.v[k]));
+        for (int k = 0; k < H.nv; k++) P.v[k] = f4(S.x + mv(S.R, xyz(H.v[k])), 0.f);
         for (int f = 0; f < H.nt; f++) {
             float4 ln = H.n[f];
             float3 n = mv(S.R, xyz(ln));
@@ -615,7 +615,7 @@ MSD void np_sh(const Shape& A, const Shape& B, CandSet& cs) {
     for (int f = 0; f < P.nf; f++) {
         int idx[4];
         poly_face(P, f, idx);
-        float3 t = closest_on_triangle(c, P.v[idx[0]], P.v[idx[1]], P.v[idx[2]]);
+        float3 t = closest_on_triangle(c, xyz(P.v[idx[0]]), xyz(P.v[idx[1]]), xyz(P.v[idx[2]]));
         float d2 = dot(c - t, c - t);
         if (d2 < best) { best = d2; q = t; }
     }
@@ -639,14 +639,14 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     for (int f = 0; f < PA.nf; f++) {
         float sf = 3e38f;
         float3 n = xyz(PA.f[f]);
-        for (int k = 0; k < PB.nv; k++) sf = fminf(sf, dot(n, PB.v[k]) - PA.f[f].w);
+        for (int k = 0; k < PB.nv; k++) sf = fminf(sf, dot(n, xyz(PB.v[k])) - PA.f[f].w);
         if (sf > sa) { sa = sf; fa = f; }
     }
     float sb = -3e38f; int fb = 0;
     for (int f = 0; f < PB.nf; f++) {
         float sf = 3e38f;
         float3 n = xyz(PB.f[f]);
-        for (int k = 0; k < PA.nv; k++) sf = fminf(sf, dot(n, PA.v[k]) - PB.f[f].w);
+        for (int k = 0; k < PA.nv; k++) sf = fminf(sf, dot(n, xyz(PA.v[k])) - PB.f[f].w);
         if (sf > sb) { sb = sf; fb = f; }
     }
     // the face axes already separate by the margin: no contact whatever the
@@ -655,31 +655,32 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     if (fmaxf(sa, sb) >= m) return;
     // B's edges as arcs on the Gauss map of -B: the negated normals of
     // their two faces and the arcs' plane normal, formed once per pair
-    float3 bc[PV_MAXE], bd[PV_MAXE], bdxc[PV_MAXE];
+    float4 bc[PV_MAXE], bd[PV_MAXE], bdxc[PV_MAXE];   // float4: one 16-byte load each
     for (int j = 0; j < PB.ne; j++) {
         int4 EB = poly_edge(PB, j);
-        bc[j] = -xyz(PB.f[EB.z]);
-        bd[j] = -xyz(PB.f[EB.w]);
-        bdxc[j] = cross(bd[j], bc[j]);
+        float3 c = -xyz(PB.f[EB.z]), d = -xyz(PB.f[EB.w]);
+        bc[j] = f4(c, 0.f);
+        bd[j] = f4(d, 0.f);
+        bdxc[j] = f4(cross(d, c), 0.f);
     }
     float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
     for (int i = 0; i < PA.ne; i++) {
         int4 EA = poly_edge(PA, i);
         float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
         float3 bxa = cross(b, a);
-        float3 ua = PA.v[EA.y] - PA.v[EA.x];
+        float3 ua = xyz(PA.v[EA.y]) - xyz(PA.v[EA.x]);
         for (int j = 0; j < PB.ne; j++) {
-            float3 c = bc[j], d = bd[j], dxc = bdxc[j];
+            float3 c = xyz(bc[j]), d = xyz(bd[j]), dxc = xyz(bdxc[j]);
             float cba = dot(c, bxa), dba = dot(d, bxa), adc = dot(a, dxc), bdc = dot(b, dxc);
             if (!(cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
             int4 EB = poly_edge(PB, j);
-            float3 ub = PB.v[EB.y] - PB.v[EB.x];
+            float3 ub = xyz(PB.v[EB.y]) - xyz(PB.v[EB.x]);
             float3 ax = cross(ua, ub);
             float l = len(ax);
             if (l < 1e-5f * len(ua) * len(ub)) continue;
             ax = ax * (1.f / l);
-            if (dot(ax, PA.v[EA.x] - PA.c) < 0.f) ax = -ax;
-            float sij = dot(ax, PB.v[EB.x] - PA.v[EA.x]);
+            if (dot(ax, xyz(PA.v[EA.x]) - PA.c) < 0.f) ax = -ax;
+            float sij = dot(ax, xyz(PB.v[EB.x]) - xyz(PA.v[EA.x]));
             if (sij > se) { se = sij; ea = i; eb = j; axe = ax; }
         }
     }
@@ -689,7 +690,7 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     if (ea >= 0 && se > sf + 1e-4f) {
         int4 EA = poly_edge(PA, ea), EB = poly_edge(PB, eb);
         float3 pa, pb;
-        closest_segments(PA.v[EA.x], PA.v[EA.y], PB.v[EB.x], PB.v[EB.y], pa, pb);
+        closest_segments(xyz(PA.v[EA.x]), xyz(PA.v[EA.y]), xyz(PB.v[EB.x]), xyz(PB.v[EB.y]), pa, pb);
         float3 n = -axe;
         cs.push(pa, pb, n, dot(n, pa - pb));
         return;
@@ -708,10 +709,10 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     float3 bufa[8], bufb[8];
     int ii[4], ri[4];
     int np = poly_face(I, inc, ii);
-    for (int k = 0; k < np; k++) bufa[k] = I.v[ii[k]];
+    for (int k = 0; k < np; k++) bufa[k] = xyz(I.v[ii[k]]);
     int nr = poly_face(R, rf, ri);
     for (int k = 0; k < nr; k++) {
-        float3 p0 = R.v[ri[k]], p1 = R.v[ri[k + 1 == nr ? 0 : k + 1]];
+        float3 p0 = xyz(R.v[ri[k]]), p1 = xyz(R.v[ri[k + 1 == nr ? 0 : k + 1]]);
         float3 side = cross(p1 - p0, nref);
         side = side * (1.f / len(side));
         // alternate the buffers: even k reads bufa, odd k reads bufb
@@ -719,7 +720,7 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
         else np = clip_plane(bufb, np, bufa, side, p0, 0.f);
     }
     const float3* res = (nr & 1) ? bufb : bufa;
-    float3 pref = R.v[ri[0]];
+    float3 pref = xyz(R.v[ri[0]]);
     for (int k = 0; k < np; k++) {
         float3 x = res[k];
         float dist = dot(nref, x - pref);
@@ -737,7 +738,7 @@ MSD float segment_poly_closest(const Poly& P, float3 s0, float3 s1, float3& ps, 
     for (int f = 0; f < P.nf; f++) {
         int idx[4];
         poly_face(P, f, idx);
-        float3 tv[3] = {P.v[idx[0]], P.v[idx[1]], P.v[idx[2]]};
+        float3 tv[3] = {xyz(P.v[idx[0]]), xyz(P.v[idx[1]]), xyz(P.v[idx[2]])};
         float3 q = closest_on_triangle(s0, tv[0], tv[1], tv[2]);
         float d2 = dot(s0 - q, s0 - q);
         if (d2 < best) { best = d2; ps = s0; pq = q; }
@@ -778,13 +779,13 @@ MSD void np_ch(const Shape& A, const Shape& B, float m, CandSet& cs) {
     float se = -3e38f; int be = -1; float3 le = f3(0.f, 0.f, 0.f);
     for (int k = 0; k < P.ne; k++) {
         int4 E = poly_edge(P, k);
-        float3 ev = P.v[E.y] - P.v[E.x];
+        float3 ev = xyz(P.v[E.y]) - xyz(P.v[E.x]);
         float3 c = cross(ev, u);
         float cn = len(c), lim = 1e-5f * len(ev) * ul;
         if (!(cn > lim)) continue;
         float3 L = c * (1.f / cn);
         float hmax = -3e38f, hmin = 3e38f;
-        for (int q = 0; q < P.nv; q++) { float t = dot(L, P.v[q]); hmax = fmaxf(hmax, t); hmin = fminf(hmin, t); }
+        for (int q = 0; q < P.nv; q++) { float t = dot(L, xyz(P.v[q])); hmax = fmaxf(hmax, t); hmin = fminf(hmin, t); }
         float sp = fminf(dot(L, s0), dot(L, s1)) - hmax - r;
         float sn = hmin - fmaxf(dot(L, s0), dot(L, s1)) - r;
         if (sn > sp) { sp = sn; L = -L; }
@@ -804,7 +805,7 @@ MSD void np_ch(const Shape& A, const Shape& B, float m, CandSet& cs) {
     int idx[4];
     int nfv = poly_face(P, bf, idx);
     for (int k = 0; k < nfv && !empty; k++) {
-        float3 p0 = P.v[idx[k]], p1 = P.v[idx[k + 1 == nfv ? 0 : k + 1]];
+        float3 p0 = xyz(P.v[idx[k]]), p1 = xyz(P.v[idx[k + 1 == nfv ? 0 : k + 1]]);
         float3 sd = cross(p1 - p0, n);
         sd = sd * (1.f / len(sd));
         float g0 = dot(sd, s0 - p0), gu = dot(sd, u);
@@ -822,7 +823,7 @@ MSD void np_ch(const Shape& A, const Shape& B, float m, CandSet& cs) {
         }
         return;
     }
-    float3 ps = s0, pq = P.v[0];
+    float3 ps = s0, pq = xyz(P.v[0]);
     float dist = segment_poly_closest(P, s0, s1, ps, pq);
     float3 nn = dist > 1e-12f ? (ps - pq) * (1.f / dist) : n;
     cs.push(ps - nn * r, pq, nn, dist - r);
