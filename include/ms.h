@@ -57,7 +57,9 @@ enum {
     MS_ENV_CONTACT_OVERFLOW = 2u,   /* more contact points than contact_capacity  */
     MS_ENV_COLOR_OVERFLOW = 4u,     /* a constraint found none of 64 colours free */
     MS_ENV_NAN = 8u,                /* non-finite state; the env is frozen        */
-    MS_ENV_INVALID = 16u            /* ms_step_noalloc: descriptors out of range; the env is skipped */
+    MS_ENV_INVALID = 16u,           /* ms_step_noalloc: descriptors out of range; the env is skipped */
+    MS_ENV_BOUNDS = 32u             /* debug library only: an index past its buffer was caught; the
+                                       env's contacts and constraints were dropped for that step */
 };
 
 enum { MS_SPHERE = 0, MS_CAPSULE = 1, MS_BOX = 2, MS_PLANE = 3, MS_HULL = 4 };

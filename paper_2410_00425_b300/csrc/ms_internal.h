@@ -25,7 +25,7 @@ namespace ms {
 struct Layout {
     int s_bytes;
     int x, q, v, w;                          // body state copies (batched path only)
-    int sq;                                  // S = (world inverse inertia)^(1/2), 2 float4 per body
+    int sq;                                  // S = (world inverse inertia)^(1/2), 2 float4, and the step-start q, per body
     int scons, color_off, lam, cnt, status;  // shared part unless lists_shared is false
     bool lists_shared;                       // scons and lam in the shared part
     bool rows_j_shared;                      // joint rows in the shared part

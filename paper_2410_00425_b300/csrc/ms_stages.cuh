@@ -278,6 +278,63 @@ MSD Shape shape_at(const EnvView& e, int i) {
     return s;
 }
 
+#ifdef MS_DEBUG_BOUNDS
+// Debug builds (-DMS_DEBUG_BOUNDS): the invariants that every later stage
+// indexes by, checked after the narrowphase (pair, manifold and point counts
+// within their capacities; manifold bodies and point ranges in range) and
+// after the colouring (colour and constraint counts; each colour-ordered
+// record's bodies, joint or manifold index and row range).  An env that
+// breaks one gets MS_ENV_BOUNDS and its counts are cleared, so no later stage
+// reads past a buffer; nothing traps.  Every lane of the warp runs it.
+MSD void stage_check_bounds(EnvView& e, const Grp& g, const Params& P, bool after_color) {
+    bool live = e.nb > 0;
+    int nb = e.nb, nj = e.nj;
+    int npairs = live ? e.cnt[C_NPAIRS] : 0, nman = live ? e.cnt[C_NMAN] : 0, npts = live ? e.cnt[C_NPTS] : 0;
+    bool bad = live && (npairs < 0 || npairs > P.pair_cap || nman < 0 || nman > P.pair_cap || npts < 0 ||
+                        npts > P.contact_cap);
+    int nm = bad ? 0 : nman;
+    int mmax = g.wmax(nm);
+    for (int m0 = 0; m0 < mmax; m0 += g.size) {
+        int m = m0 + g.lane;
+        if (m >= nm) continue;
+        int4 M = e.man[m];
+        bad |= M.x < 0 || M.x >= nb || M.y < 0 || M.y >= nb || M.z < 1 || M.z > 4 || M.w < 0 ||
+               M.w + M.z > npts;
+    }
+    if (after_color && live) {
+        int ncol = e.cnt[C_NCOLORS], ncons = e.cnt[C_NCONS];
+        bad |= ncol < 0 || ncol > MAX_COLORS || ncons < 0 || ncons > nj + nman;
+        bad |= ncol >= 0 && ncol <= MAX_COLORS && (e.color_off[0] != 0 || e.color_off[ncol] != ncons);
+    }
+    int nc = (after_color && live && !bad) ? e.cnt[C_NCONS] : 0;
+    int cmax = g.wmax(nc);
+    for (int k0 = 0; k0 < cmax; k0 += g.size) {
+        int k = k0 + g.lane;
+        if (k >= nc) continue;
+        int4 c = e.scons[k];
+        int place = c.w & 3, idx = c.w >> 8, np = (c.w >> 2) & 7;
+        bad |= c.x < -1 || c.x >= nb || c.y < -1 || c.y >= nb;
+        if (place == CP_JOINT) {
+            bad |= idx < 0 || idx >= nj || c.z != idx;
+        } else {
+            bad |= place == 3 || idx < 0 || idx >= nman || np < 1 || np > 4 || c.z < 0 || c.z % 3 != 0 ||
+                   c.z / 3 + np > npts || (place == CP_MAN_S && c.z / 3 + np > e.pts_s);
+        }
+    }
+    bool any = g.any(bad);
+    if (g.lane == 0 && any) {
+        *e.status |= (unsigned)MS_ENV_BOUNDS;
+        e.cnt[C_NPAIRS] = 0; e.cnt[C_NMAN] = 0; e.cnt[C_NPTS] = 0;
+        e.cnt[C_NCONS] = 0; e.cnt[C_NCOLORS] = 0;
+        e.color_off[0] = 0;
+    }
+    g.sync();
+}
+#define MS_CHECK_BOUNDS(e, g, P, after_color) stage_check_bounds(e, g, P, after_color)
+#else
+#define MS_CHECK_BOUNDS(e, g, P, after_color) ((void)0)
+#endif
+
 MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
     int npairs = e.nb > 0 ? e.cnt[C_NPAIRS] : 0;
     int pmax = g.wmax(npairs);
@@ -337,6 +394,7 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
         if (e.rec_cnt) *e.rec_cnt = nman;
     }
     g.sync();
+    MS_CHECK_BOUNDS(e, g, P, false);
 }
 
 // -------------------------------------------------------------- colouring
@@ -1063,6 +1121,7 @@ MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
 // every lane of a warp, so the branches are warp-uniform.
 MSD void begin_step_solve(EnvView& e, const Grp& g, const Params& P) {
     stage_color(e, g);
+    MS_CHECK_BOUNDS(e, g, P, true);
     if (P.warm) stage_warm_init(e, g);
 }
 

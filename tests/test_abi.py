@@ -39,6 +39,16 @@ def test_every_declared_symbol_is_exported(lib):
     server.lib()                                  # binds every server signature
 
 
+def test_debug_library_exports_the_same_entry_points():
+    """The bounds-checked twin (-DMS_DEBUG_BOUNDS) builds and exports the
+    same C ABI (it is loaded only by its own GPU test)."""
+    path = build.build(debug=True)
+    raw = C.CDLL(path)
+    for n in declared("ms.h") + declared("ms_server.h"):
+        assert hasattr(raw, n), n
+    assert raw.ms_step(None, None, 1, None) == 1
+
+
 def test_struct_layouts_match(lib):
     sizes = (C.c_int32 * 5)()
     lib.ms_abi_sizes(sizes)
