@@ -17,8 +17,12 @@
  *   colouring        greedy graph colouring over the constraint list
  *   solver           substepped sequential impulses with soft drives
  *                    (Catto 2005; Catto 2011 soft constraints; Macklin et al.
- *                    2019 "Small Steps"), Coulomb friction pyramid
+ *                    2019 "Small Steps"), Coulomb friction pyramid; contact
+ *                    anchors keep their step-start orientation and the
+ *                    separation advances to first order in each body's
+ *                    rotation since the step start (temporal Gauss-Seidel)
  *   integration      symplectic Euler with quaternion renormalisation
+ *   contact forces   per body, the last substep's contact impulses / h
  *
  * Descriptor rows are doubles (converted losslessly from the float32 scene):
  *   body  [22]: type, p0, p1, p2, mass, pos[3], quat[4] (x,y,z,w), linvel[3],
