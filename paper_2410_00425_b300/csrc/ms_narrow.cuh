@@ -664,24 +664,38 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
         bdxc[j] = f4(cross(d, c), 0.f);
     }
     float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
-    for (int i = 0; i < PA.ne; i++) {
-        int4 EA = poly_edge(PA, i);
-        float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
-        float3 bxa = cross(b, a);
-        float3 ua = xyz(PA.v[EA.y]) - xyz(PA.v[EA.x]);
-        for (int j = 0; j < PB.ne; j++) {
-            float3 c = xyz(bc[j]), d = xyz(bd[j]), dxc = xyz(bdxc[j]);
-            float cba = dot(c, bxa), dba = dot(d, bxa), adc = dot(a, dxc), bdc = dot(b, dxc);
-            if (!(cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
-            int4 EB = poly_edge(PB, j);
-            float3 ub = xyz(PB.v[EB.y]) - xyz(PB.v[EB.x]);
-            float3 ax = cross(ua, ub);
-            float l = len(ax);
-            if (l < 1e-5f * len(ua) * len(ub)) continue;
-            ax = ax * (1.f / l);
-            if (dot(ax, xyz(PA.v[EA.x]) - PA.c) < 0.f) ax = -ax;
-            float sij = dot(ax, xyz(PB.v[EB.x]) - xyz(PA.v[EA.x]));
-            if (sij > se) { se = sij; ea = i; eb = j; axe = ax; }
+    // B's arcs four at a time in registers against every edge of A: an arc
+    // is loaded once per four (i, j) tests instead of once per test.  The
+    // pairs are visited tile by tile, so the tie rule (equal separations:
+    // the lowest i, then the lowest j) keeps the first maximum in i-major
+    // order, as a plain double loop would find it.
+    for (int j0 = 0; j0 < PB.ne; j0 += 4) {
+        float3 cc[4], dd[4], xx[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            int j = min(j0 + t, PB.ne - 1);               // clamped; tests past ne are skipped
+            cc[t] = xyz(bc[j]); dd[t] = xyz(bd[j]); xx[t] = xyz(bdxc[j]);
+        }
+        for (int i = 0; i < PA.ne; i++) {
+            int4 EA = poly_edge(PA, i);
+            float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
+            float3 bxa = cross(b, a);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                int j = j0 + t;
+                float cba = dot(cc[t], bxa), dba = dot(dd[t], bxa), adc = dot(a, xx[t]), bdc = dot(b, xx[t]);
+                if (!(j < PB.ne && cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
+                int4 EB = poly_edge(PB, j);
+                float3 ua = xyz(PA.v[EA.y]) - xyz(PA.v[EA.x]);
+                float3 ub = xyz(PB.v[EB.y]) - xyz(PB.v[EB.x]);
+                float3 ax = cross(ua, ub);
+                float l = len(ax);
+                if (l < 1e-5f * len(ua) * len(ub)) continue;
+                ax = ax * (1.f / l);
+                if (dot(ax, xyz(PA.v[EA.x]) - PA.c) < 0.f) ax = -ax;
+                float sij = dot(ax, xyz(PB.v[EB.x]) - xyz(PA.v[EA.x]));
+                if (sij > se || (sij == se && (i < ea || (i == ea && j < eb)))) { se = sij; ea = i; eb = j; axe = ax; }
+            }
         }
     }
     float maxsep = fmaxf(fmaxf(sa, sb), se);
