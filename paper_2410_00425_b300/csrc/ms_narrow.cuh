@@ -631,24 +631,42 @@ MSD void np_sh(const Shape& A, const Shape& B, CandSet& cs) {
 // if it beats the best face by 1e-4 m.  Face case: the most anti-parallel
 // face of the other polytope clipped against the side planes of the
 // reference face; edge case: the closest points of the two edges.
+// The face axes of P against Q: the largest over P's faces of the least
+// signed distance of Q's vertices to the face plane, and that face (the
+// first maximum in face order).  Four planes at a time in registers, so a
+// vertex of Q is loaded once per four faces.
+MSD void face_axes(const Poly& P, const Poly& Q, float& smax, int& fmax_) {
+    float s = -3e38f;
+    int fi = 0;
+    for (int f0 = 0; f0 < P.nf; f0 += 4) {
+        float4 pl[4];
+        float mn[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            pl[t] = P.f[min(f0 + t, P.nf - 1)];             // clamped; faces past nf are skipped
+            mn[t] = 3e38f;
+        }
+        for (int k = 0; k < Q.nv; k++) {
+            float3 v = xyz(Q.v[k]);
+#pragma unroll
+            for (int t = 0; t < 4; t++) mn[t] = fminf(mn[t], dot(xyz(pl[t]), v) - pl[t].w);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+            if (f0 + t < P.nf && mn[t] > s) { s = mn[t]; fi = f0 + t; }
+    }
+    smax = s;
+    fmax_ = fi;
+}
+
 MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
     Poly PA, PB;
     poly_of(A, PA);
     poly_of(B, PB);
-    float sa = -3e38f; int fa = 0;
-    for (int f = 0; f < PA.nf; f++) {
-        float sf = 3e38f;
-        float3 n = xyz(PA.f[f]);
-        for (int k = 0; k < PB.nv; k++) sf = fminf(sf, dot(n, xyz(PB.v[k])) - PA.f[f].w);
-        if (sf > sa) { sa = sf; fa = f; }
-    }
-    float sb = -3e38f; int fb = 0;
-    for (int f = 0; f < PB.nf; f++) {
-        float sf = 3e38f;
-        float3 n = xyz(PB.f[f]);
-        for (int k = 0; k < PA.nv; k++) sf = fminf(sf, dot(n, xyz(PA.v[k])) - PB.f[f].w);
-        if (sf > sb) { sb = sf; fb = f; }
-    }
+    float sa, sb;
+    int fa, fb;
+    face_axes(PA, PB, sa, fa);
+    face_axes(PB, PA, sb, fb);
     // the face axes already separate by the margin: no contact whatever the
     // edge pairs give (the largest separation is >= m); the bounding-sphere
     // broadphase passes many such pairs
