@@ -698,11 +698,17 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
             int4 EA = poly_edge(PA, i);
             float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
             float3 bxa = cross(b, a);
+            // the four Gauss-map tests unrolled; the rare pairs that pass
+            // them go through one copy of the axis code, in order of j
+            unsigned pass = 0u;
 #pragma unroll
             for (int t = 0; t < 4; t++) {
-                int j = j0 + t;
                 float cba = dot(cc[t], bxa), dba = dot(dd[t], bxa), adc = dot(a, xx[t]), bdc = dot(b, xx[t]);
-                if (!(j < PB.ne && cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f)) continue;
+                if (j0 + t < PB.ne && cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f) pass |= 1u << t;
+            }
+            while (pass) {
+                int j = j0 + __ffs(pass) - 1;
+                pass &= pass - 1u;
                 int4 EB = poly_edge(PB, j);
                 float3 ua = xyz(PA.v[EA.y]) - xyz(PA.v[EA.x]);
                 float3 ub = xyz(PB.v[EB.y]) - xyz(PB.v[EB.x]);
