@@ -682,15 +682,15 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
         bdxc[j] = f4(cross(d, c), 0.f);
     }
     float se = -3e38f; int ea = -1, eb = -1; float3 axe = f3(0.f, 0.f, 0.f);
-    // B's arcs four at a time in registers against every edge of A: an arc
-    // is loaded once per four (i, j) tests instead of once per test.  The
+    // B's arcs eight at a time in registers against every edge of A: an arc
+    // is loaded once per eight (i, j) tests instead of once per test.  The
     // pairs are visited tile by tile, so the tie rule (equal separations:
     // the lowest i, then the lowest j) keeps the first maximum in i-major
     // order, as a plain double loop would find it.
-    for (int j0 = 0; j0 < PB.ne; j0 += 4) {
-        float3 cc[4], dd[4], xx[4];
+    for (int j0 = 0; j0 < PB.ne; j0 += 8) {
+        float3 cc[8], dd[8], xx[8];
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
+        for (int t = 0; t < 8; t++) {
             int j = min(j0 + t, PB.ne - 1);               // clamped; tests past ne are skipped
             cc[t] = xyz(bc[j]); dd[t] = xyz(bd[j]); xx[t] = xyz(bdxc[j]);
         }
@@ -698,11 +698,11 @@ MSD void np_poly(const Shape& A, const Shape& B, float m, CandSet& cs) {
             int4 EA = poly_edge(PA, i);
             float3 a = xyz(PA.f[EA.z]), b = xyz(PA.f[EA.w]);
             float3 bxa = cross(b, a);
-            // the four Gauss-map tests unrolled; the rare pairs that pass
+            // the eight Gauss-map tests unrolled; the rare pairs that pass
             // them go through one copy of the axis code, in order of j
             unsigned pass = 0u;
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
+            for (int t = 0; t < 8; t++) {
                 float cba = dot(cc[t], bxa), dba = dot(dd[t], bxa), adc = dot(a, xx[t]), bdc = dot(b, xx[t]);
                 if (j0 + t < PB.ne && cba * dba < 0.f && adc * bdc < 0.f && cba * bdc > 0.f) pass |= 1u << t;
             }
