@@ -872,6 +872,8 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
     CandSet cs;
     cs.n = 0;
     int ta = A.type, tb = B.type;
+    // box or hull against hull: one call site below, so the SAT is compiled once
+    bool poly = false;
     if (ta == SH_SPHERE) {
         if (tb == SH_SPHERE) np_ss(A, B, cs);
         else if (tb == SH_CAPSULE) np_sc(A, B, cs);
@@ -885,12 +887,13 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
         else if (tb == SH_HULL) { if (B.hull.v) np_ch(A, B, m, cs); }
     } else if (ta == SH_BOX) {
         if (tb == SH_BOX) np_bb(A, B, m, cs);
-        else if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
+        else if (tb == SH_HULL) poly = B.hull.v != nullptr;
         else np_bp(A, B, cs);
     } else if (ta == SH_HULL && A.hull.v) {
-        if (tb == SH_HULL) { if (B.hull.v) np_poly(A, B, m, cs); }
+        if (tb == SH_HULL) poly = B.hull.v != nullptr;
         else if (tb == SH_PLANE) np_hp(A, B, m, cs);
     }
+    if (poly) np_poly(A, B, m, cs);
     Cand kept[16];
     int nk = 0;
     for (int i = 0; i < cs.n; i++)
