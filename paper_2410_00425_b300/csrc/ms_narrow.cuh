@@ -436,10 +436,14 @@ MSD void np_bb(const Shape& A, const Shape& B, float m, CandSet& cs) {
     poly[2] = fc - e1 - e2;
     poly[3] = fc + e1 - e2;
     int np = 4;
-    np = clip_plane(poly, np, tmp, uu, cref, hu);
-    np = clip_plane(tmp, np, poly, -uu, cref, hu);
-    np = clip_plane(poly, np, tmp, vv, cref, hv);
-    np = clip_plane(tmp, np, poly, -vv, cref, hv);
+    // the four side slabs +u, -u, +v, -v through one copy of the clipper
+    // (even passes read poly and write tmp, odd passes the reverse)
+    for (int c = 0; c < 4; c++) {
+        float3 dir = c < 2 ? uu : vv;
+        if (c & 1) dir = -dir;
+        float hh = c < 2 ? hu : hv;
+        np = clip_plane((c & 1) ? tmp : poly, np, (c & 1) ? poly : tmp, dir, cref, hh);
+    }
     for (int t = 0; t < np; t++) {
         float3 x = poly[t];
         float dist = dot(nref, x - cref);
