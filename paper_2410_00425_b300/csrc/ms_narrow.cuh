@@ -248,7 +248,7 @@ MSD void np_cb(const Shape& A, const Shape& B, float m, CandSet& cs) {
     float sep[6];
     float3 ax[6];
     bool valid[6];
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 6; i++) {
         float3 L;
         valid[i] = true;
@@ -367,7 +367,7 @@ MSD void np_bb(const Shape& A, const Shape& B, float m, CandSet& cs) {
     float sep[15];
     float3 ax[15];
     bool valid[15];
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 15; k++) {
         float3 L;
         valid[k] = true;
