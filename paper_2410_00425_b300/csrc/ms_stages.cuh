@@ -619,7 +619,10 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     Row* R = cons_rows(e, c);
     float h = P.h;
     if (!joint) {
-        int4 M = e.man[idx];
+        // the colour-ordered record carries the manifold: bodies c.x, c.y,
+        // first row c.z = 3 x first point, point count in c.w (no load of
+        // the manifold header)
+        int4 M = make_int4(c.x, c.y, (c.w >> 2) & 7, c.z / 3);
         int np = M.z;
         float mu = 0.5f * (e.shape[M.x].w + e.shape[M.y].w);
         StepFrame FA = step_frame(e, c.x, A.q), FB = step_frame(e, c.y, B.q);
@@ -854,7 +857,7 @@ MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
     float h = P.h;
     BodyPose A = pose_of(e, c.x), B = pose_of(e, c.y);
     if (!joint) {
-        int4 M = e.man[idx];
+        int4 M = make_int4(c.x, c.y, (c.w >> 2) & 7, c.z / 3);   // as in prep_constraint
         StepFrame FA = step_frame(e, c.x, A.q), FB = step_frame(e, c.y, B.q);
         for (int k = 0; k < M.z; k++) {
             float3 rA, rB;
