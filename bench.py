@@ -80,7 +80,7 @@ def make_workload(name, variants=False, **kw):
 NCU_TRAFFIC = {
     ("arm", "8,1,0"): {"bytes": 30.26e6, "kernel_sha": "38e078bdea175039", "kernel": "k_fused<8>"},
 }
-KERNEL_SOURCES = ("ms_kernels.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
+KERNEL_SOURCES = ("ms_fused.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
 
 def kernel_sha():

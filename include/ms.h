@@ -420,6 +420,20 @@ ms_status ms_estimate_bytes(const int32_t* body_off, const int32_t* joint_off, i
 void ms_abi_sizes(int32_t* out5);
 
 /* ----------------------------------------------------------------------- */
+/* Measurement                                                             */
+/* ----------------------------------------------------------------------- */
+
+/* The FP32 fused-multiply-add rate of the current device, measured: a
+ * full-occupancy grid whose threads each run 8 independent chains of
+ * dependent FMAs, timed with CUDA events over about `seconds` (in (0, 10])
+ * on the legacy default stream, synchronously.  *flops_per_s receives the
+ * rate (2 flop per FMA); sm_count and measured_s (nullable) receive the SM
+ * count and the timed duration.  This is the peak the batched step's ALU
+ * roofline divides by (the step is not a dense contraction, so tensor-core
+ * rates do not apply).  It allocates and frees a small device buffer. */
+ms_status ms_measure_fp32_peak(double seconds, double* flops_per_s, int* sm_count, double* measured_s);
+
+/* ----------------------------------------------------------------------- */
 /* Stepping without any device allocation                                  */
 /* ----------------------------------------------------------------------- */
 

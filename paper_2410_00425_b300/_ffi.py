@@ -117,6 +117,8 @@ _SIGS = [
     ("ms_create_batch_hulls", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                         C.POINTER(ms_sim_params), C.POINTER(ms_hull_lib), C.POINTER(C.c_void_p)]),
     ("ms_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ms_measure_fp32_peak", C.c_int, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]),
 ]
 
 EXPORTS = [s[0] for s in _SIGS]
@@ -368,3 +370,11 @@ def ms_estimate_bytes(body_off, joint_off, params: dict) -> int:
     sp = make_params(params)
     check(load().ms_estimate_bytes(bo.ctypes.data, jo.ctypes.data, len(bo) - 1, C.byref(sp), C.byref(n)))
     return n.value
+
+
+def ms_measure_fp32_peak(seconds: float = 0.5):
+    """Measured FP32 FMA rate of the current device: (flop/s, SMs, timed s)."""
+    L = load()
+    f, n, t = C.c_double(), C.c_int(), C.c_double()
+    check(L.ms_measure_fp32_peak(seconds, C.byref(f), C.byref(n), C.byref(t)))
+    return f.value, n.value, t.value

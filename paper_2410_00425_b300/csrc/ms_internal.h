@@ -126,6 +126,13 @@ struct FusedCfg {
 };
 
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s);
+// k_fused<G> of each lane-group size (ms_fused.cu, one translation unit per G)
+const void* fused_kernel_1();
+const void* fused_kernel_2();
+const void* fused_kernel_4();
+const void* fused_kernel_8();
+const void* fused_kernel_16();
+const void* fused_kernel_32();
 cudaError_t fused_occupancy(int G, int threads, size_t smem, int* blocks_per_sm);
 bool fused_supported(int G);
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G,

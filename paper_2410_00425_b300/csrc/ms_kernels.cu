@@ -90,31 +90,6 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
     return L;
 }
 
-// the env's parameters and warm-start memory, read in place from the
-// resident arrays (an idle lane group has no warm-start memory)
-__device__ __forceinline__ void view_params(EnvView& e, const DevBatch& D, int b0, int j0, int env, bool active) {
-    e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
-    e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
-    e.rest = D.rest + b0;
-    e.qR = D.T.qR ? D.T.qR + j0 : nullptr;
-    e.hulls = D.hulls;
-    bool w = active && D.wc;
-    e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
-    e.wc_n = w ? D.wc_n + env : nullptr;
-    e.wjl = w ? D.wjl + 8 * (size_t)j0 : nullptr;
-    e.force = (D.force && active) ? D.force + b0 : nullptr;
-}
-
-__device__ __forceinline__ void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
-    if (D.rec_man && active) {
-        e.rec_man = D.rec_man + (size_t)env * D.P.pair_cap;
-        e.rec_pts = D.rec_pts + (size_t)env * D.P.contact_cap * 10;
-        e.rec_cnt = D.rec_cnt + env;
-    } else {
-        e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
-    }
-}
-
 // ------------------------------------------------------------- plain path
 __device__ __forceinline__ EnvView plain_view(const DevBatch& D, int env) {
     EnvView e;
@@ -234,82 +209,15 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
 }
 
 // ----------------------------------------------------------- batched path
-template <int G>
-__global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
-    extern __shared__ __align__(16) char smem[];
-    const Layout& L = C.layout;
-    constexpr int K = 32 / G;                  // envs per warp
-    int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-    int gi = wl / G;
-    Grp g;
-    g.lane = wl % G; g.size = G; g.base = gi * G;
-    int slot_id = warp * K + gi;
-    char* s = smem + (size_t)slot_id * L.s_bytes;
-    size_t gslot = ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * K + gi;
-    char* gl = C.gscratch + gslot * (size_t)L.g_bytes;
-
-    EnvView e;
-    e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
-    view_workspace(e, s, gl, L);
-    e.status = at<unsigned>(s, L.status);
-
-    for (;;) {
-        int t0 = 0;
-        if (wl == 0) t0 = atomicAdd(C.queue, K);
-        t0 = __shfl_sync(FULL_MASK, t0, 0);
-        if (t0 >= D.E) break;                            // warp-uniform
-        int t = t0 + gi;
-        bool active = t < D.E;
-        int env = active ? C.order[t] : 0;
-        int b0 = 0, j0 = 0, nb = 0, nj = 0;
-        if (active) {
-            b0 = D.body_off[env]; j0 = D.joint_off[env];
-            nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
-        }
-        view_params(e, D, b0, j0, env, active);
-        int nbmax = g.wmax(nb);
-        for (int i0 = 0; i0 < nbmax; i0 += G) {
-            int i = i0 + g.lane;
-            if (i < nb) { e.x[i] = D.x[b0 + i]; e.q[i] = D.q[b0 + i]; e.v[i] = D.v[b0 + i]; e.w[i] = D.w[b0 + i]; }
-        }
-        if (g.lane == 0) *e.status = active ? D.status[env] : 0u;
-        view_record(e, D, env, active);
-        g.sync();
-        bool frozen = (*e.status & ST_NAN) != 0;
-        e.nb = frozen ? 0 : nb;
-        e.nj = frozen ? 0 : nj;
-        for (int k = 0; k < n_steps; k++) {
-            const float* act = (actions && active) ? actions + ((size_t)k * D.E + env) * D.A : nullptr;
-            stage_actions(e, g, act, D.A, D.T.on ? D.T.half : nullptr);
-            stage_broadphase(e, g, D.P);
-            stage_narrowphase(e, g, D.P);
-            begin_step_solve(e, g, D.P);
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
-            end_step_solve(e, g, D.P);
-            if (D.force) stage_contact_forces(e, g, D.P);
-            stage_check(e, g);
-            if (D.T.out)
-                stage_task_record(e, g, D.T, D.A, active ? D.T.out + ((size_t)k * D.E + env) * D.T.D : nullptr,
-                                  (*e.status & ST_NAN) != 0);
-            if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
-        }
-        for (int i0 = 0; i0 < nbmax; i0 += G) {
-            int i = i0 + g.lane;
-            if (i < nb) { D.x[b0 + i] = e.x[i]; D.q[b0 + i] = e.q[i]; D.v[b0 + i] = e.v[i]; D.w[b0 + i] = e.w[i]; }
-        }
-        if (g.lane == 0 && active) D.status[env] = *e.status;
-        g.sync();
-    }
-}
-
+// k_fused<G> lives in ms_fused.cu, one translation unit per G.
 static const void* fused_fn(int G) {
     switch (G) {
-    case 1: return (const void*)k_fused<1>;
-    case 2: return (const void*)k_fused<2>;
-    case 4: return (const void*)k_fused<4>;
-    case 8: return (const void*)k_fused<8>;
-    case 16: return (const void*)k_fused<16>;
-    case 32: return (const void*)k_fused<32>;
+    case 1: return fused_kernel_1();
+    case 2: return fused_kernel_2();
+    case 4: return fused_kernel_4();
+    case 8: return fused_kernel_8();
+    case 16: return fused_kernel_16();
+    case 32: return fused_kernel_32();
     default: return nullptr;
     }
 }

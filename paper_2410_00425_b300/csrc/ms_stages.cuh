@@ -1230,4 +1230,30 @@ MSD void stage_task_record(const EnvView& e, const Grp& g, const DevTask& T, int
     g.sync();
 }
 
+// ------------------------------------------------- env views of a batch
+// the env's parameters and warm-start memory, read in place from the
+// resident arrays (an idle lane group has no warm-start memory)
+MSD void view_params(EnvView& e, const DevBatch& D, int b0, int j0, int env, bool active) {
+    e.shape = D.shape + b0; e.inv = D.inv + b0; e.meta = D.meta + b0; e.adj = D.adj + b0;
+    e.jf = D.jf + 4 * (size_t)j0; e.jp = D.jp + j0; e.jm = D.jm + j0; e.jt = D.jt + j0;
+    e.rest = D.rest + b0;
+    e.qR = D.T.qR ? D.T.qR + j0 : nullptr;
+    e.hulls = D.hulls;
+    bool w = active && D.wc;
+    e.wc = w ? D.wc + 2 * (size_t)env * (size_t)D.P.contact_cap : nullptr;
+    e.wc_n = w ? D.wc_n + env : nullptr;
+    e.wjl = w ? D.wjl + 8 * (size_t)j0 : nullptr;
+    e.force = (D.force && active) ? D.force + b0 : nullptr;
+}
+
+MSD void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
+    if (D.rec_man && active) {
+        e.rec_man = D.rec_man + (size_t)env * D.P.pair_cap;
+        e.rec_pts = D.rec_pts + (size_t)env * D.P.contact_cap * 10;
+        e.rec_cnt = D.rec_cnt + env;
+    } else {
+        e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
+    }
+}
+
 }  // namespace ms
