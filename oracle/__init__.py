@@ -71,6 +71,9 @@ def lib():
         L.oracle_get_rows.argtypes = [P, C.c_int, C.c_int, dp]
         L.oracle_collide.argtypes = [dp, dp, C.c_double, dp]
         L.oracle_color.argtypes = [C.c_int, ip, ip, ip, ip]
+        L.oracle_candidates.argtypes = [dp, dp, C.c_double, dp]
+        L.oracle_reduce4.argtypes = [C.c_int, dp, ip]
+        L.oracle_tangents.argtypes = [dp, dp, dp]
         L.oracle_inertia.argtypes = [dp, dp]
         up = C.POINTER(C.c_ubyte)
         L.oracle_set_task.argtypes = [P, ip, dp, C.c_int, dp, dp]
@@ -317,6 +320,33 @@ def collide(body_a, body_b, margin=0.01):
     out = np.zeros((8, 10), np.float64)
     n = lib().oracle_collide(_dp(a), _dp(b), margin, _dp(out))
     return out[:n]
+
+
+def candidates(body_a, body_b, margin=0.01):
+    """Candidate points of one ordered pair (22-rows) before the margin
+    filter and the reduction to 4: [n][10] = cA, cB, n, d."""
+    a = np.ascontiguousarray(body_a, np.float64)
+    b = np.ascontiguousarray(body_b, np.float64)
+    out = np.zeros((16, 10), np.float64)
+    n = lib().oracle_candidates(_dp(a), _dp(b), margin, _dp(out))
+    return out[:n]
+
+
+def reduce4(pts):
+    """Indices p1..p4 the manifold reduction keeps of [n][10] candidates."""
+    p = np.ascontiguousarray(pts, np.float64)
+    sel = np.zeros(4, np.int32)
+    if lib().oracle_reduce4(len(p), _dp(p), _ip(sel)) != 4:
+        raise ValueError("5 to 16 candidates")
+    return sel
+
+
+def tangents(n):
+    """Contact tangent basis (t1, t2) of a unit normal."""
+    nn = np.ascontiguousarray(n, np.float64)
+    t1, t2 = np.zeros(3), np.zeros(3)
+    lib().oracle_tangents(_dp(nn), _dp(t1), _dp(t2))
+    return t1, t2
 
 
 def color(a, b, dyn):

@@ -1113,7 +1113,7 @@ static int reduce4(Env* e, const Cand* c, int n, int* sel) {
 
 /* Narrowphase of the ordered pair (A, B); returns kept points in `out`.
  * *margin_tie is set when a candidate's d lies within 1e-5 of the margin. */
-static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, int* margin_tie) {
+static void candidates(Env* e, const Shape* A, const Shape* B, double m, CandSet* out) {
     CandSet cs; cs.n = 0;
     int ta = A->type, tb = B->type;
     int slot = -1;
@@ -1131,6 +1131,12 @@ static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, 
     else if (ta == OR_HULL && tb == OR_PLANE) { np_hp(e, A, B, m, &cs); slot = OC_NP_HP; }
     else if (ta == OR_CAPSULE && tb == OR_HULL) { np_ch(e, A, B, m, &cs); slot = OC_NP_CH; }
     if (slot >= 0) e->cnt[slot]++;
+    *out = cs;
+}
+
+static int collide(Env* e, const Shape* A, const Shape* B, double m, Cand* out, int* margin_tie) {
+    CandSet cs;
+    candidates(e, A, B, m, &cs);
     Cand kept[16]; int nk = 0;
     *margin_tie = 0;
     for (int i = 0; i < cs.n; i++) {
@@ -2387,6 +2393,42 @@ int oracle_get_rows(const oracle_world* w, int env, int cap, double* out) {
         o[12] = R->k; o[13] = R->bias; o[14] = R->lambda; o[15] = R->mu;
     }
     return e->nrows;
+}
+
+static void put_cand(double* o, const Cand* c) {
+    o[0] = c->cA.x; o[1] = c->cA.y; o[2] = c->cA.z;
+    o[3] = c->cB.x; o[4] = c->cB.y; o[5] = c->cB.z;
+    o[6] = c->n.x; o[7] = c->n.y; o[8] = c->n.z; o[9] = c->d;
+}
+
+int oracle_candidates(const double* da, const double* db, double margin, double* out) {
+    Env e; memset(&e, 0, sizeof(e));
+    Body A, B;
+    body_from_desc(&A, da); body_from_desc(&B, db);
+    Shape SA = shape_of(&A), SB = shape_of(&B);
+    CandSet cs;
+    candidates(&e, &SA, &SB, margin, &cs);
+    for (int k = 0; k < cs.n; k++) put_cand(out + 10 * k, &cs.c[k]);
+    return cs.n;
+}
+
+int oracle_reduce4(int n, const double* pts, int* sel) {
+    if (n < 5 || n > 16) return -1;
+    Env e; memset(&e, 0, sizeof(e));
+    Cand c[16];
+    for (int k = 0; k < n; k++) {
+        const double* p = pts + 10 * k;
+        c[k].cA = V(p[0], p[1], p[2]); c[k].cB = V(p[3], p[4], p[5]);
+        c[k].n = V(p[6], p[7], p[8]); c[k].d = p[9];
+    }
+    return reduce4(&e, c, n, sel);
+}
+
+void oracle_tangents(const double* n, double* t1, double* t2) {
+    v3 a, b;
+    tangents(V(n[0], n[1], n[2]), &a, &b);
+    t1[0] = a.x; t1[1] = a.y; t1[2] = a.z;
+    t2[0] = b.x; t2[1] = b.y; t2[2] = b.z;
 }
 
 int oracle_collide(const double* da, const double* db, double margin, double* out) {

@@ -136,6 +136,17 @@ int oracle_get_rows(const oracle_world* w, int env, int cap, double* rows);
  * the margin filter and the reduction to 4. */
 int oracle_collide(const double* bodyA, const double* bodyB, double margin, double* out);
 
+/* The candidate points of one pair before the margin filter and the
+ * reduction to 4 (clip output order for box - box faces), same layout as
+ * oracle_collide, out [16][10].  Returns the candidate count. */
+int oracle_candidates(const double* bodyA, const double* bodyB, double margin, double* out);
+/* The manifold reduction of n (5..16) candidates [n][10] (cB at 3..5, d at
+ * 9): sel [4] receives the indices p1..p4.  Returns 4, or -1 for n out of
+ * range. */
+int oracle_reduce4(int n, const double* pts, int* sel);
+/* The contact tangent basis of a unit normal n[3]: t1, t2 [3]. */
+void oracle_tangents(const double* n, double* t1, double* t2);
+
 /* Greedy colouring of a constraint list given as body pairs (-1 = static);
  * dyn[i] != 0 marks body i dynamic.  Returns the colour count or -1 on
  * overflow of 64 colours. */
