@@ -119,7 +119,20 @@ typedef struct {
  *   the k-th point of a manifold takes the normal and (world-vector)
  *   friction impulses of the k-th point of the previous step's manifold of
  *   the same body pair.  ms_set_state clears this memory for the envs it
- *   sets. */
+ *   sets.
+ * Soft rows (the "soft step" of Box2D v3; 0 Hz = rigid): in the position
+ *   sweeps a soft row is a spring-damper of natural frequency f (Hz) and
+ *   damping ratio zeta on the row's own effective mass, integrated
+ *   implicitly over the substep: with w = 2 pi f, a1 = 2 zeta + h w,
+ *   a2 = h w a1, its bias is (w / a1) C and its update
+ *   dlambda = -a2/(1 + a2) (Jv + bias)/k - lambda/(1 + a2).  Relax sweeps
+ *   treat every row as rigid.
+ *   contact_hertz, contact_damping_ratio: every contact normal row; a
+ *   penetrating point (d < 0) takes the bias (w / a1) d (at most
+ *   max_depen_vel), a separated one keeps its speculative bias d / h.  The
+ *   frequency is capped at a quarter of the substep rate, 0.25 / h.
+ *   joint_hertz, joint_damping_ratio: the equality rows of every joint (point
+ *   and angular rows; not limits or drives). */
 typedef struct {
     float dt;
     int32_t substeps, pos_iters, vel_iters;
@@ -131,6 +144,8 @@ typedef struct {
     float linear_damping, angular_damping;
     float bounce_threshold;
     int32_t warm_start;
+    float contact_hertz, contact_damping_ratio;
+    float joint_hertz, joint_damping_ratio;
 } ms_sim_params;
 
 typedef struct ms_batch ms_batch;
@@ -355,8 +370,9 @@ ms_status ms_render(ms_batch* b, uint8_t* rgba, float* depth, uint16_t* seg, voi
 /* Introspection and tuning                                                */
 /* ----------------------------------------------------------------------- */
 
-/* Record the contact manifolds of every env's last step (off by default;
- * costs one extra global write per contact).  record = 0 / 1. */
+/* Record the contact manifolds and the constraint colours of every env's
+ * last step (off by default; costs one extra global write per contact and
+ * per constraint).  record = 0 / 1. */
 ms_status ms_set_record_contacts(ms_batch* b, int record);
 
 /* Contact manifolds recorded at env `env`'s last step, in pair order:
@@ -365,6 +381,14 @@ ms_status ms_set_record_contacts(ms_batch* b, int record);
  * (n points from b toward a, d = n.(cA - cB)).  Host buffers; synchronises.
  * *count receives the number of manifolds (at most cap are written).
  * MS_ERR_INVALID_ARG if recording is off. */
+/* Colours recorded at env `env`'s last step: colors int32 [cap], one per
+ * constraint of the greedy colouring's list -- the env's joints in index
+ * order, then its manifolds in pair order (those ms_get_contacts returns);
+ * -1 for a constraint that found none of the 64 colours free.  Host buffer;
+ * synchronises.  *count receives the constraint count.  MS_ERR_INVALID_ARG if
+ * recording is off. */
+ms_status ms_get_colors(ms_batch* b, int env, int cap, int32_t* colors, int* count);
+
 ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pairs, int32_t* npts,
                           float* pts, int* count);
 

@@ -54,6 +54,7 @@ def lib():
         L.oracle_create_hulls.argtypes = [C.c_int, lp, dp, lp, dp, dp, C.c_int, ip, dp, ip, ip]
         L.oracle_hull_inertia.argtypes = [dp, C.c_int, ip, C.c_int, C.c_double, dp]
         L.oracle_destroy.argtypes = [P]
+        L.oracle_set_round32.argtypes = [P, C.c_int]
         L.oracle_step.argtypes = [P, dp, C.c_int, C.c_int, C.c_int]
         L.oracle_get_state.argtypes = [P, dp]
         L.oracle_contact_forces.argtypes = [P, dp]
@@ -140,7 +141,9 @@ def param_row(p) -> np.ndarray:
     return np.array([p["dt"], p["substeps"], p["pos_iters"], p["vel_iters"], g[0], g[1], g[2],
                      p["margin"], p["max_depen_vel"], p["contact_capacity"], p["pair_capacity"],
                      p.get("linear_damping", 0.0), p.get("angular_damping", 0.0),
-                     p.get("bounce_threshold", 1.0), p.get("warm_start", 0)],
+                     p.get("bounce_threshold", 1.0), p.get("warm_start", 0),
+                     p.get("contact_hertz", 0.0), p.get("contact_damping_ratio", 0.0),
+                     p.get("joint_hertz", 0.0), p.get("joint_damping_ratio", 0.0)],
                     np.float64)
 
 
@@ -261,6 +264,10 @@ class Oracle:
         out = np.zeros((self.nb, 4), np.float64)
         lib().oracle_contact_forces(self.h, _dp(out))
         return out
+
+    def set_round32(self, on: bool):
+        """Test probe: store state, rows, impulses and contact data as float32."""
+        lib().oracle_set_round32(self.h, 1 if on else 0)
 
     def set_state(self, st):
         st = np.ascontiguousarray(st, np.float64)

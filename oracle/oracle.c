@@ -41,6 +41,9 @@ static v3 with_comp(v3 a, int i, double s) {
     return a;
 }
 static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+/* float32 rounding, for the storage probe (oracle_set_round32) */
+static double r32(double x) { return (double)(float)x; }
+static v3 r32v(v3 a) { return V(r32(a.x), r32(a.y), r32(a.z)); }
 
 static qt Q(double x, double y, double z, double w) { qt r = {x, y, z, w}; return r; }
 static qt qmul(qt a, qt b) {
@@ -129,6 +132,16 @@ typedef struct { int a, b, np; CPoint p[4]; } Manifold;
 
 enum { RK_NORMAL = 0, RK_FRICTION = 1, RK_EQ = 2, RK_LIMIT = 3, RK_DRIVE = 4 };
 
+/* Soft constraint of a row in the position iterations (Box2D v3's "soft
+ * step"): a spring-damper of natural frequency hz and damping ratio zeta
+ * relative to the row's own effective mass, integrated implicitly over a
+ * substep h.  With omega = 2 pi hz, a1 = 2 zeta + h omega, a2 = h omega a1:
+ *   bias = (omega / a1) C,  mass scale = a2 / (1 + a2),  impulse scale = 1 / (1 + a2),
+ *   dlambda = -(mass scale) (Jv + bias) / k - (impulse scale) lambda.
+ * It is the implicit-Euler update (1 + 2 zeta omega h + h^2 omega^2) v' =
+ * v - h omega^2 C of an isolated row.  on = 0: rigid. */
+typedef struct { int on; double bias_rate, mass_scale, impulse_scale; } Soft;
+
 typedef struct {
     int kind, a, b;                   /* a, b: env-local bodies, -1 = world */
     v3 lin, angA, angB;
@@ -137,6 +150,7 @@ typedef struct {
     double lambda, gamma, mu;
     int partner;                      /* friction: index of its normal row */
     int pt;                           /* contact point / limit side, for relax bias */
+    int soft;                         /* soft in the position iterations (contact normal, joint equality) */
 } Row;
 
 typedef struct { int kind, idx, a, b, color, row0, nrows; } Constraint;
@@ -152,6 +166,7 @@ typedef struct {
     int nprev; PrevPoint* prev;       /* contact points of the previous step (warm start) */
     double* qR;                       /* pick task: joint coordinates at the last reset */
     unsigned status; long long ties;
+    int round32;                      /* probe: velocities and poses stored as float32 */
     long long cnt[OC_NUM];
 } Env;
 
@@ -160,6 +175,7 @@ struct oracle_world {
     double dt; int substeps, pos_iters, vel_iters; v3 g; double margin, vmax;
     int contact_cap, pair_cap;
     double lin_damp, ang_damp, bounce; int warm;
+    Soft csoft, jsoft;                /* soft contact normals, soft joint equality rows */
     /* pick task (off unless set): gripper joint, fingers, object, table */
     int task_on, t_grip, t_fa, t_fb, t_cube, t_table, t_A;
     double t_grasp_tol, t_touch_tol;
@@ -535,7 +551,9 @@ static void np_cb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
     double h[3] = {B->p[0], B->p[1], B->p[2]};
     double ul = norm(u);
     v3 uh = ul > 0 ? scl(u, 1.0 / ul) : V(0, 0, 0);
-    double sep[6]; v3 ax[6]; int valid[6];
+    /* near[i]: an edge axis whose |cross| lies within TIE_DIR of the skip
+     * threshold; psep[i] its separation had it been kept */
+    double sep[6], psep[6]; v3 ax[6]; int valid[6], near[6] = {0};
     for (int i = 0; i < 6; i++) {
         v3 L;
         valid[i] = 1;
@@ -543,22 +561,28 @@ static void np_cb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
         else {
             v3 c = cross(unit_axis(i - 3), uh);
             double cn = norm(c);
-            tie_w(e, cn, 1e-5, TIE_DIR);
-            if (cn < 1e-5) { valid[i] = 0; sep[i] = -1e300; continue; }
+            near[i] = cn > 0.0 && cn != 1e-5 && fabs(cn - 1e-5) < TIE_DIR;
+            valid[i] = cn >= 1e-5;
+            if (!valid[i] && !near[i]) { sep[i] = -1e300; continue; }
             L = scl(c, 1.0 / cn);
         }
         if (dot(mid, L) < 0) L = neg(L);
         double hb = h[0] * fabs(L.x) + h[1] * fabs(L.y) + h[2] * fabs(L.z);
         double p0 = dot(s0, L), p1 = dot(s1, L);
-        sep[i] = fmin(p0, p1) - hb - r;
+        psep[i] = sep[i] = fmin(p0, p1) - hb - r;
+        if (!valid[i]) sep[i] = -1e300;
         ax[i] = L;
     }
     double maxsep = -1e300;
     for (int i = 0; i < 6; i++) if (valid[i] && sep[i] > maxsep) maxsep = sep[i];
-    tie(e, maxsep, m);
-    if (maxsep >= m) return;
     int bf = 0;
     for (int i = 1; i < 3; i++) if (sep[i] > sep[bf]) bf = i;
+    /* keeping or skipping a near-threshold axis matters only where it could
+     * end the test (margin) or win over the faces: a tie only there */
+    for (int i = 3; i < 6; i++)
+        if (near[i] && psep[i] >= fmin(m, sep[bf] + 1e-4) - TIE_EPS) e->ties++;
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
     int be = -1;
     for (int i = 3; i < 6; i++) if (valid[i] && (be < 0 || sep[i] > sep[be])) be = i;
     if (be >= 0) tie(e, sep[be], sep[bf] + 1e-4);
@@ -658,7 +682,9 @@ static void np_bb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
     for (int i = 0; i < 3; i++) { a[i] = mcol(&A->R, i); b[i] = mcol(&B->R, i); }
     const double* hA = A->p; const double* hB = B->p;
     v3 dl = sub(A->x, B->x);
-    double sep[15]; v3 ax[15]; int valid[15];
+    /* near[k]: an edge axis whose |cross| lies within TIE_DIR of the skip
+     * threshold; psep[k] its separation had it been kept */
+    double sep[15], psep[15]; v3 ax[15]; int valid[15], near[15] = {0};
     for (int k = 0; k < 15; k++) {
         v3 L;
         valid[k] = 1;
@@ -667,25 +693,31 @@ static void np_bb(Env* e, const Shape* A, const Shape* B, double m, CandSet* cs)
         else {
             v3 c = cross(a[(k - 6) / 3], b[(k - 6) % 3]);
             double cn = norm(c);
-            tie_w(e, cn, 1e-5, TIE_DIR);
-            if (cn < 1e-5) { valid[k] = 0; sep[k] = -1e300; continue; }
+            near[k] = cn > 0.0 && cn != 1e-5 && fabs(cn - 1e-5) < TIE_DIR;
+            valid[k] = cn >= 1e-5;
+            if (!valid[k] && !near[k]) { sep[k] = -1e300; continue; }
             L = scl(c, 1.0 / cn);
         }
         if (dot(dl, L) < 0) L = neg(L);
         double ra = hA[0] * fabs(dot(a[0], L)) + hA[1] * fabs(dot(a[1], L)) + hA[2] * fabs(dot(a[2], L));
         double rb = hB[0] * fabs(dot(b[0], L)) + hB[1] * fabs(dot(b[1], L)) + hB[2] * fabs(dot(b[2], L));
-        sep[k] = dot(dl, L) - ra - rb;
+        psep[k] = sep[k] = dot(dl, L) - ra - rb;
+        if (!valid[k]) sep[k] = -1e300;
         ax[k] = L;
     }
     double maxsep = -1e300;
     for (int k = 0; k < 15; k++) if (valid[k] && sep[k] > maxsep) maxsep = sep[k];
-    tie(e, maxsep, m);
-    if (maxsep >= m) return;
     int fa = 0, fb = 3, be = -1;
     for (int k = 1; k < 3; k++) if (sep[k] > sep[fa]) fa = k;
     for (int k = 4; k < 6; k++) if (sep[k] > sep[fb]) fb = k;
     for (int k = 6; k < 15; k++) if (valid[k] && (be < 0 || sep[k] > sep[be])) be = k;
     double sf = fmax(sep[fa], sep[fb]);
+    /* a near-threshold axis is a tie only where it could end the test or
+     * win over the faces */
+    for (int k = 6; k < 15; k++)
+        if (near[k] && psep[k] >= fmin(m, sf + 1e-4) - TIE_EPS) e->ties++;
+    tie(e, maxsep, m);
+    if (maxsep >= m) return;
     if (be >= 0) tie(e, sep[be], sf + 1e-4);
     if (be >= 0 && sep[be] > sf + 1e-4) {
         v3 L = ax[be];
@@ -1178,6 +1210,7 @@ static void narrowphase(const oracle_world* w, Env* e) {
             c->cA = pts[k].cA; c->cB = pts[k].cB; c->n = pts[k].n; c->d = pts[k].d;
             c->aA = mtv(&RA, sub(c->cA, BA->x));   /* body-local anchors */
             c->aB = mtv(&RB, sub(c->cB, BB->x));
+            if (e->round32) { c->n = r32v(c->n); c->aA = r32v(c->aA); c->aB = r32v(c->aB); }
             /* approach speed along n at the step-start velocities */
             v3 uA = add(BA->v, cross(BA->w, sub(c->cA, BA->x)));
             v3 uB = add(BB->v, cross(BB->w, sub(c->cB, BB->x)));
@@ -1354,6 +1387,22 @@ static double contact_sep(const CPoint* p, const BodyView* A, const BodyView* B,
     return dot(p->n, sub(pa, pb));
 }
 
+static Soft make_soft(double hz, double zeta, double h) {
+    Soft S = {0, 0.0, 1.0, 0.0};
+    if (!(hz > 0.0)) return S;
+    double om = 2.0 * M_PI * hz, a1 = 2.0 * zeta + h * om, a2 = h * om * a1;
+    S.on = 1;
+    S.bias_rate = om / a1;
+    S.mass_scale = a2 / (1.0 + a2);
+    S.impulse_scale = 1.0 / (1.0 + a2);
+    return S;
+}
+
+/* bias of a joint equality row with error C: C / h rigid, (omega / a1) C soft */
+static double eq_bias(const oracle_world* w, double C, double h) {
+    return w->jsoft.on ? w->jsoft.bias_rate * C : C / h;
+}
+
 static double contact_bias(double d, double h, double vmax) {
     return d >= 0.0 ? d / h : fmax(d / h, -vmax);
 }
@@ -1377,11 +1426,17 @@ static void prep(const oracle_world* w, Env* e, double h) {
                 Row* rn = &R[k];
                 rn->kind = RK_NORMAL; set_point_row(rn, p->n, rA, rB);
                 rn->bias = contact_bias(d, h, w->vmax); rn->pt = k;
+                /* soft normal rows: a separated point keeps its speculative
+                 * bias d / h, a penetrating one takes (w / a1) d (the bias is
+                 * continuous at d = 0, so softness makes no discrete decision) */
+                rn->soft = w->csoft.on;
+                if (rn->soft && d < 0.0) rn->bias = fmax(w->csoft.bias_rate * d, -w->vmax);
                 Row* rt1 = &R[M->np + 2 * k];
                 Row* rt2 = &R[M->np + 2 * k + 1];
                 rt1->kind = rt2->kind = RK_FRICTION;
                 set_point_row(rt1, t1, rA, rB); set_point_row(rt2, t2, rA, rB);
                 rt1->bias = rt2->bias = 0.0;
+                rt1->soft = rt2->soft = 0;
                 rt1->partner = rt2->partner = c->row0 + k;
                 rt1->mu = rt2->mu = mu;
             }
@@ -1398,15 +1453,15 @@ static void prep(const oracle_world* w, Env* e, double h) {
                 for (int t = 0; t < 3; t++) {
                     v3 ee = unit_axis(t);
                     R[r].kind = RK_EQ; set_point_row(&R[r], ee, g.rP, g.rC);
-                    R[r].bias = dot(ee, sub(g.wP, g.wC)) / h; r++;
+                    R[r].bias = eq_bias(w, dot(ee, sub(g.wP, g.wC)), h); r++;
                 }
                 int k = basis_axis(g.a);
                 tie_basis(e, g.a);
                 v3 b1 = cross(g.a, unit_axis(k)); b1 = scl(b1, 1.0 / norm(b1));
                 v3 b2 = cross(g.a, b1);
                 v3 axc = cross(g.a, g.c);
-                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b1), b1); R[r].bias = dot(b1, axc) / h; r++;
-                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b2), b2); R[r].bias = dot(b2, axc) / h; r++;
+                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b1), b1); R[r].bias = eq_bias(w, dot(b1, axc), h); r++;
+                R[r].kind = RK_EQ; set_ang_row(&R[r], neg(b2), b2); R[r].bias = eq_bias(w, dot(b2, axc), h); r++;
                 R[r].kind = RK_LIMIT; set_ang_row(&R[r], neg(g.a), g.a); R[r].pt = 0;
                 R[r].bias = contact_bias(g.phi - j->lower, h, w->vmax); r++;
                 R[r].kind = RK_LIMIT; set_ang_row(&R[r], g.a, neg(g.a)); R[r].pt = 1;
@@ -1418,15 +1473,15 @@ static void prep(const oracle_world* w, Env* e, double h) {
                 v3 b1 = cross(g.a, unit_axis(k)); b1 = scl(b1, 1.0 / norm(b1));
                 v3 b2 = cross(g.a, b1);
                 R[r].kind = RK_EQ; set_point_row(&R[r], b1, g.rP, g.rC);
-                R[r].bias = dot(b1, sub(g.wP, g.wC)) / h; r++;
+                R[r].bias = eq_bias(w, dot(b1, sub(g.wP, g.wC)), h); r++;
                 R[r].kind = RK_EQ; set_point_row(&R[r], b2, g.rP, g.rC);
-                R[r].bias = dot(b2, sub(g.wP, g.wC)) / h; r++;
+                R[r].bias = eq_bias(w, dot(b2, sub(g.wP, g.wC)), h); r++;
                 qt qe = qmul(g.qPw, qconj(g.qCw));
                 double sg = qe.w >= 0.0 ? 1.0 : -1.0;
                 v3 th = V(2.0 * sg * qe.x, 2.0 * sg * qe.y, 2.0 * sg * qe.z);
                 for (int t = 0; t < 3; t++) {
                     v3 ee = unit_axis(t);
-                    R[r].kind = RK_EQ; set_ang_row(&R[r], ee, neg(ee)); R[r].bias = comp(th, t) / h; r++;
+                    R[r].kind = RK_EQ; set_ang_row(&R[r], ee, neg(ee)); R[r].bias = eq_bias(w, comp(th, t), h); r++;
                 }
                 R[r].kind = RK_LIMIT; set_point_row(&R[r], neg(g.a), g.rP, g.rC); R[r].pt = 0;
                 R[r].bias = contact_bias(g.phi - j->lower, h, w->vmax); r++;
@@ -1444,10 +1499,17 @@ static void prep(const oracle_world* w, Env* e, double h) {
             for (int t = 0; t < 8; t++) {
                 R[t].a = c->a; R[t].b = c->b;
                 R[t].k = row_k(&A, &B, &R[t]);
+                R[t].soft = R[t].kind == RK_EQ && w->jsoft.on;
             }
             if (den <= 0.0) dr->k = 0.0;  /* no drive */
         }
         e->cnt[OC_ROWS_PREP] += c->nrows;
+        if (e->round32)
+            for (int r = 0; r < c->nrows; r++) {
+                Row* q = &R[r];
+                q->lin = r32v(q->lin); q->angA = r32v(q->angA); q->angB = r32v(q->angB);
+                q->k = r32(q->k); q->bias = r32(q->bias); q->gamma = r32(q->gamma); q->mu = r32(q->mu);
+            }
     }
 }
 
@@ -1478,6 +1540,7 @@ static void relax_bias(Env* e, double h) {
 /* ------------------------------------------------------------------------- */
 /* solver                                                                     */
 /* ------------------------------------------------------------------------- */
+
 static void apply_impulse(Env* e, const Row* r, double dl) {
     if (r->a >= 0 && e->bodies[r->a].dyn) {
         Body* A = &e->bodies[r->a];
@@ -1489,6 +1552,10 @@ static void apply_impulse(Env* e, const Row* r, double dl) {
         B->v = sub(B->v, scl(r->lin, B->inv_mass * dl));
         B->w = add(B->w, scl(mv(&B->invIw, r->angB), dl));
     }
+    if (e->round32) {
+        if (r->a >= 0) { e->bodies[r->a].v = r32v(e->bodies[r->a].v); e->bodies[r->a].w = r32v(e->bodies[r->a].w); }
+        if (r->b >= 0) { e->bodies[r->b].v = r32v(e->bodies[r->b].v); e->bodies[r->b].w = r32v(e->bodies[r->b].w); }
+    }
 }
 
 static double row_jv(const Env* e, const Row* r) {
@@ -1498,7 +1565,7 @@ static double row_jv(const Env* e, const Row* r) {
     return dot(r->lin, sub(va, vb)) + dot(r->angA, wa) + dot(r->angB, wb);
 }
 
-static void solve_row(Env* e, Row* r, int relax) {
+static void solve_row(const oracle_world* w, Env* e, Row* r, int relax) {
     if (r->k <= 0.0) return;               /* inert row (no dynamic body) */
     if (relax && r->kind == RK_DRIVE) return;
     double jv = row_jv(e, r);
@@ -1506,10 +1573,13 @@ static void solve_row(Env* e, Row* r, int relax) {
     int ndyn = (r->a >= 0 && e->bodies[r->a].dyn) + (r->b >= 0 && e->bodies[r->b].dyn);
     e->cnt[ndyn == 2 ? OC_ROW_SOLVE_2DYN : OC_ROW_SOLVE_1DYN]++;
     double bias = relax ? r->relax_bias : r->bias;
+    /* soft rows in the position iterations; every row is rigid in relax */
+    const Soft* S = (!relax && r->soft) ? (r->kind == RK_NORMAL ? &w->csoft : &w->jsoft) : NULL;
     switch (r->kind) {
     case RK_NORMAL:
     case RK_LIMIT:
-        nl = fmax(old - (jv + bias) / r->k, 0.0);
+        if (S) nl = fmax(old - S->mass_scale * (jv + bias) / r->k - S->impulse_scale * old, 0.0);
+        else nl = fmax(old - (jv + bias) / r->k, 0.0);
         break;
     case RK_FRICTION: {
         double lim = r->mu * e->rows[r->partner].lambda;
@@ -1517,22 +1587,23 @@ static void solve_row(Env* e, Row* r, int relax) {
         break;
     }
     case RK_EQ:
-        nl = old - (jv + (relax ? 0.0 : r->bias)) / r->k;
+        if (S) nl = old - S->mass_scale * (jv + bias) / r->k - S->impulse_scale * old;
+        else nl = old - (jv + (relax ? 0.0 : r->bias)) / r->k;
         break;
     default: /* RK_DRIVE: dl = -(Jv + b + gamma lambda) / (1/m + gamma) */
         nl = old - (jv + r->bias + r->gamma * old) / (r->k + r->gamma);
         break;
     }
-    r->lambda = nl;
-    apply_impulse(e, r, nl - old);
+    r->lambda = e->round32 ? r32(nl) : nl;
+    apply_impulse(e, r, r->lambda - old);
 }
 
-static void sweep(Env* e, int relax) {
+static void sweep(const oracle_world* w, Env* e, int relax) {
     for (int o = 0; o < e->ncons; o++) {
         int ci = e->order[o];
         if (ci < 0) break;
         Constraint* c = &e->cons[ci];
-        for (int r = 0; r < c->nrows; r++) solve_row(e, &e->rows[c->row0 + r], relax);
+        for (int r = 0; r < c->nrows; r++) solve_row(w, e, &e->rows[c->row0 + r], relax);
     }
 }
 
@@ -1559,6 +1630,7 @@ static void integrate(Env* e, double h) {
         qt wq = qmul(Q(b->w.x, b->w.y, b->w.z, 0.0), b->q);
         b->q = qnormalize(Q(b->q.x + 0.5 * h * wq.x, b->q.y + 0.5 * h * wq.y,
                             b->q.z + 0.5 * h * wq.z, b->q.w + 0.5 * h * wq.w));
+        if (e->round32) { b->x = r32v(b->x); b->q = Q(r32(b->q.x), r32(b->q.y), r32(b->q.z), r32(b->q.w)); }
         e->cnt[OC_BODY_INTEGRATE]++;
     }
 }
@@ -1668,13 +1740,14 @@ static void env_step(const oracle_world* w, Env* e, const double* act, int A) {
             if (e->bodies[i].dyn) {
                 e->bodies[i].v = add(scl(e->bodies[i].v, al), scl(w->g, h));
                 e->bodies[i].w = scl(e->bodies[i].w, aw);
+                if (e->round32) { e->bodies[i].v = r32v(e->bodies[i].v); e->bodies[i].w = r32v(e->bodies[i].w); }
             }
         prep(w, e, h);
         warm_start(e);
-        for (int it = 0; it < w->pos_iters; it++) sweep(e, 0);
+        for (int it = 0; it < w->pos_iters; it++) sweep(w, e, 0);
         integrate(e, h);
         relax_bias(e, h);
-        for (int it = 0; it < w->vel_iters; it++) sweep(e, 1);
+        for (int it = 0; it < w->vel_iters; it++) sweep(w, e, 1);
         for (int m = 0; m < e->nman; m++) {
             Manifold* M = &e->man[m];
             const Row* R = &e->rows[e->cons[e->nj + m].row0];
@@ -2117,6 +2190,13 @@ oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const d
     w->margin = params[7]; w->vmax = params[8];
     w->contact_cap = (int)params[9]; w->pair_cap = (int)params[10];
     w->lin_damp = params[11]; w->ang_damp = params[12]; w->bounce = params[13]; w->warm = (int)params[14];
+    {
+        /* contact softness at most a quarter of the substep rate (Box2D v3) */
+        double h = w->dt / w->substeps;
+        double chz = params[15] < 0.25 / h ? params[15] : 0.25 / h;
+        w->csoft = make_soft(chz, params[16], h);
+        w->jsoft = make_soft(params[17], params[18], h);
+    }
     w->nb_total = (int)body_off[n_envs]; w->nj_total = (int)joint_off[n_envs];
     w->body_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
     w->joint_off = (long long*)malloc(sizeof(long long) * (n_envs + 1));
@@ -2164,6 +2244,10 @@ oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const d
         e->prev = (PrevPoint*)calloc((size_t)(w->contact_cap > 0 ? w->contact_cap : 1), sizeof(PrevPoint));
     }
     return w;
+}
+
+void oracle_set_round32(oracle_world* w, int on) {
+    for (int e = 0; e < w->E; e++) w->envs[e].round32 = on;
 }
 
 void oracle_destroy(oracle_world* w) {

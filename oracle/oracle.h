@@ -29,9 +29,22 @@
  *               angvel[3], mu, restitution, group, mask
  *   joint [22]: type, parent, child, parent_frame[7] (pos, quat), child_frame[7],
  *               lower, upper, kp, kd, target0
- *   params[15]: dt, substeps, pos_iters, vel_iters, gx, gy, gz, margin,
+ *   params[19]: dt, substeps, pos_iters, vel_iters, gx, gy, gz, margin,
  *               max_depen_vel, contact_capacity, pair_capacity,
- *               linear_damping, angular_damping, bounce_threshold, warm_start
+ *               linear_damping, angular_damping, bounce_threshold, warm_start,
+ *               contact_hertz, contact_damping_ratio, joint_hertz,
+ *               joint_damping_ratio
+ *
+ * Soft rows (Box2D v3's "soft step"; a frequency of 0 makes them rigid): in
+ * the position iterations, every contact normal row (contact_hertz, capped
+ * at a quarter of the substep rate) and every joint equality row
+ * (joint_hertz) is a spring-damper on the row's own effective mass,
+ * integrated implicitly over the substep: with w = 2 pi hz,
+ * a1 = 2 zeta + h w, a2 = h w a1,
+ *     dlambda = -a2/(1 + a2) (Jv + bias)/k - lambda/(1 + a2),
+ * bias = (w / a1) C for a joint error C, (w / a1) d for a penetrating
+ * contact (d < 0, floored at -max_depen_vel) and d / h (speculative) for a
+ * separated one; relax iterations solve every row rigid.
  *
  * Optional solver variants (all off in the default parameters):
  *   damping          per substep v <- v / (1 + h c_lin) + h g,
@@ -90,6 +103,14 @@ oracle_world* oracle_create_hulls(int n_envs, const long long* body_off, const d
  * density); -1 for a malformed hull. */
 int oracle_hull_inertia(const double* verts, int nv, const int* tris, int nt, double mass, double* out3);
 void oracle_destroy(oracle_world* w);
+/* Test probe (off by default): on != 0 stores, rounded to float32, what a
+ * float32 implementation stores: every body's velocities and pose after each
+ * update (impulse, gravity, integration), each constraint row (Jacobian,
+ * effective mass, bias, softness, friction coefficient) when it is prepared,
+ * each accumulated impulse after its update, and each contact point's normal
+ * and body-local anchors; the arithmetic stays FP64.  Used to select envs
+ * whose rollout is insensitive to that rounding. */
+void oracle_set_round32(oracle_world* w, int on);
 
 /* Advance every env n_steps steps.  actions: [n_steps][n_envs][A] drive
  * targets (NaN keeps the previous target) or NULL.  n_threads >= 1 splits the

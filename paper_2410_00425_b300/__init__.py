@@ -124,6 +124,11 @@ class Batch:
     def contacts(self, env: int, cap: int = 1024):
         return _ffi.ms_get_contacts(self.h, env, cap)
 
+    def colors(self, env: int, cap: int = 4096):
+        """Colour of each constraint (joints, then manifolds) of the env's
+        last step; needs record_contacts."""
+        return _ffi.ms_get_colors(self.h, env, cap)
+
     def enable_contact_forces(self, on=True):
         """Make every later step write each body's contact force (touch
         sensors, ms_enable_contact_forces)."""

@@ -34,7 +34,9 @@ class ms_sim_params(C.Structure):
                 ("vel_iters", C.c_int32), ("gravity", C.c_float * 3), ("margin", C.c_float),
                 ("max_depen_vel", C.c_float), ("contact_capacity", C.c_int32),
                 ("pair_capacity", C.c_int32), ("linear_damping", C.c_float), ("angular_damping", C.c_float),
-                ("bounce_threshold", C.c_float), ("warm_start", C.c_int32)]
+                ("bounce_threshold", C.c_float), ("warm_start", C.c_int32),
+                ("contact_hertz", C.c_float), ("contact_damping_ratio", C.c_float),
+                ("joint_hertz", C.c_float), ("joint_damping_ratio", C.c_float)]
 
 
 class ms_scene_desc(C.Structure):
@@ -98,6 +100,7 @@ _SIGS = [
     ("ms_set_record_contacts", C.c_int, [C.c_void_p, C.c_int]),
     ("ms_enable_contact_forces", C.c_int, [C.c_void_p, C.c_int]),
     ("ms_contact_forces", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ms_get_colors", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
     ("ms_get_contacts", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_int)]),
     ("ms_set_tuning", C.c_int, [C.c_void_p, C.POINTER(ms_tuning)]),
@@ -176,6 +179,8 @@ def make_params(p: dict) -> ms_sim_params:
     sp.contact_capacity = p["contact_capacity"]; sp.pair_capacity = p["pair_capacity"]
     sp.linear_damping = p.get("linear_damping", 0.0); sp.angular_damping = p.get("angular_damping", 0.0)
     sp.bounce_threshold = p.get("bounce_threshold", 1.0); sp.warm_start = int(p.get("warm_start", 0))
+    sp.contact_hertz = p.get("contact_hertz", 0.0); sp.contact_damping_ratio = p.get("contact_damping_ratio", 0.0)
+    sp.joint_hertz = p.get("joint_hertz", 0.0); sp.joint_damping_ratio = p.get("joint_damping_ratio", 0.0)
     return sp
 
 
@@ -378,3 +383,11 @@ def ms_measure_fp32_peak(seconds: float = 0.5):
     f, n, t = C.c_double(), C.c_int(), C.c_double()
     check(L.ms_measure_fp32_peak(seconds, C.byref(f), C.byref(n), C.byref(t)))
     return f.value, n.value, t.value
+
+
+def ms_get_colors(b, env: int, cap: int = 4096) -> np.ndarray:
+    """Colours of env `env`'s constraints at its last step (recording on)."""
+    out = np.zeros(cap, np.int32)
+    n = C.c_int()
+    check(load().ms_get_colors(b, env, cap, out.ctypes.data, C.byref(n)))
+    return out[:min(n.value, cap)]

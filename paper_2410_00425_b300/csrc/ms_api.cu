@@ -76,6 +76,8 @@ struct ms_batch {
     size_t gscratch_bytes = 0;
     size_t bytes = 0;
     bool record = false;
+    void* rec_keep[4] = {nullptr, nullptr, nullptr, nullptr};   // record buffers, kept while recording is off
+    int rec_stride = 0;                                       // colours per env in the record
     // batched path
     Tuning tune;
     Layout fused_layout{};
@@ -275,6 +277,7 @@ static ms_status validate_params(const ms_sim_params* p) {
     if (!(p->bounce_threshold >= 0.f) || !std::isfinite(p->bounce_threshold))
         return fail(MS_ERR_INVALID_ARG, "bounce_threshold must be finite and >= 0");
     if (p->warm_start != 0 && p->warm_start != 1) return fail(MS_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    if (!soft_params_ok(p)) return fail(MS_ERR_INVALID_ARG, "soft-row frequencies and damping ratios must be finite and >= 0");
     return MS_OK;
 }
 
@@ -445,6 +448,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     D.P.adw = (float)(1.0 / (1.0 + (double)D.P.h * p->angular_damping));
     D.P.bounce = p->bounce_threshold;
     D.P.warm = p->warm_start;
+    set_soft_params(D.P, p);
     D.P.restit = 0;
     for (float r : rest) D.P.restit |= r > 0.f;
     ms_status s = MS_OK;
@@ -500,7 +504,7 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     if ((s = dmalloc(b, (void**)&b->d_staging, sizeof(float) * 13 * (size_t)b->NB)) != MS_OK) { free_all(b); delete b; return s; }
     if ((s = dmalloc(b, (void**)&b->d_mask, (size_t)E)) != MS_OK) { free_all(b); delete b; return s; }
     D.plain_ws = nullptr;
-    D.rec_man = nullptr; D.rec_pts = nullptr; D.rec_cnt = nullptr;
+    D.rec_man = nullptr; D.rec_pts = nullptr; D.rec_cnt = nullptr; D.rec_col = nullptr; D.rec_col_stride = 0;
     D.force = nullptr;
     cudaError_t ce = cudaStreamSynchronize(b->setup);
     if (ce != cudaSuccess) { free_all(b); delete b; return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(ce)); }
@@ -917,18 +921,26 @@ bool ms::batch_has_graph(const ::ms_batch* b, int n_steps) {
 // ------------------------------------------------------------ introspection
 extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
     if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
-    if (record && !b->D.rec_man) {
-        void *m = nullptr, *p = nullptr, *c = nullptr;
+    if (record && !b->rec_keep[0]) {
+        void *m = nullptr, *p = nullptr, *c = nullptr, *k = nullptr;
         ms_status s;
+        int stride = b->max_nj + b->params.pair_capacity;
         if ((s = dmalloc(b, &m, sizeof(int4) * (size_t)b->E * b->params.pair_capacity)) != MS_OK) return s;
         if ((s = dmalloc(b, &p, sizeof(float) * 10 * (size_t)b->E * b->params.contact_capacity)) != MS_OK) return s;
         if ((s = dmalloc(b, &c, sizeof(int) * (size_t)b->E)) != MS_OK) return s;
+        if ((s = dmalloc(b, &k, sizeof(int) * (size_t)b->E * stride)) != MS_OK) return s;
         CK(cudaMemsetAsync(c, 0, sizeof(int) * (size_t)b->E, b->setup));
         CK(cudaStreamSynchronize(b->setup));
-        b->D.rec_man = (int4*)m; b->D.rec_pts = (float*)p; b->D.rec_cnt = (int*)c;
+        b->rec_keep[0] = m; b->rec_keep[1] = p; b->rec_keep[2] = c; b->rec_keep[3] = k;
+        b->rec_stride = stride;
     }
     b->record = record != 0;
-    if (!b->record) { b->D.rec_man = nullptr; b->D.rec_pts = nullptr; b->D.rec_cnt = nullptr; }
+    if (b->record) {
+        b->D.rec_man = (int4*)b->rec_keep[0]; b->D.rec_pts = (float*)b->rec_keep[1];
+        b->D.rec_cnt = (int*)b->rec_keep[2]; b->D.rec_col = (int*)b->rec_keep[3]; b->D.rec_col_stride = b->rec_stride;
+    } else {
+        b->D.rec_man = nullptr; b->D.rec_pts = nullptr; b->D.rec_cnt = nullptr; b->D.rec_col = nullptr;
+    }
     drop_graphs(b);
     return MS_OK;
 }
@@ -980,6 +992,22 @@ extern "C" ms_status ms_get_contacts(ms_batch* b, int env, int cap, int32_t* pai
                     pts[(size_t)40 * i + 10 * k + f] = k < man[i].z ? P[10 * (size_t)(man[i].w + k) + f] : 0.f;
         }
     }
+    return MS_OK;
+}
+
+extern "C" ms_status ms_get_colors(ms_batch* b, int env, int cap, int32_t* colors, int* count) {
+    if (!b || !count) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+    if (!b->D.rec_col) return fail(MS_ERR_INVALID_ARG, "contact recording is off");
+    if (env < 0 || env >= b->E) return fail(MS_ERR_INVALID_ARG, "env %d out of range", env);
+    CK(cudaEventSynchronize(b->done));
+    int nman = 0;
+    CK(cudaMemcpy(&nman, b->D.rec_cnt + env, sizeof(int), cudaMemcpyDeviceToHost));
+    int nj = b->h_joint_off[env + 1] - b->h_joint_off[env];
+    int n = nj + nman;
+    *count = n;
+    int m = std::min(n, cap);
+    if (m <= 0 || !colors) return MS_OK;
+    CK(cudaMemcpy(colors, b->D.rec_col + (size_t)env * b->rec_stride, sizeof(int) * m, cudaMemcpyDeviceToHost));
     return MS_OK;
 }
 

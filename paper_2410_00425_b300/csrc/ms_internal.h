@@ -61,7 +61,35 @@ struct DevParams {
     float bounce;              // restitution threshold (approach speed, m/s)
     int warm;                  // impulses carried across steps
     int restit;                // some body of the batch has restitution > 0
+    // soft rows in the position sweeps (rate = bias per unit error, ms =
+    // mass scale, is = impulse scale, ims = 1 / ms; is = 0: rigid)
+    float c_rate, c_ms, c_is, c_ims;     // contact normals of penetrating points
+    float j_rate, j_ms, j_is, j_ims;     // joint equality rows
 };
+
+// Soft-row parameters are finite and >= 0 (host).
+inline bool soft_params_ok(const ms_sim_params* p) {
+    const float v[4] = {p->contact_hertz, p->contact_damping_ratio, p->joint_hertz, p->joint_damping_ratio};
+    for (float x : v)
+        if (!(x >= 0.f) || !(x < 3.0e38f)) return false;
+    return true;
+}
+
+// The soft-row constants of DevParams from the ABI parameters (host; h set).
+inline void set_soft_params(DevParams& P, const ms_sim_params* p) {
+    auto soft = [&](double hz, double zeta, float& rate, float& ms, float& is, float& ims) {
+        rate = 0.f; ms = 1.f; is = 0.f; ims = 1.f;
+        if (!(hz > 0.0)) return;
+        double h = P.h, om = 2.0 * 3.14159265358979323846 * hz, a1 = 2.0 * zeta + h * om, a2 = h * om * a1;
+        rate = (float)(om / a1);
+        ms = (float)(a2 / (1.0 + a2));
+        is = (float)(1.0 / (1.0 + a2));
+        ims = (float)((1.0 + a2) / a2);
+    };
+    double chz = p->contact_hertz < 0.25 / P.h ? (double)p->contact_hertz : 0.25 / P.h;
+    soft(chz, p->contact_damping_ratio, P.c_rate, P.c_ms, P.c_is, P.c_ims);
+    soft(p->joint_hertz, p->joint_damping_ratio, P.j_rate, P.j_ms, P.j_is, P.j_ims);
+}
 
 // Hull library of a batch on the device (see HullRef): hull h's vertices
 // v[vo[h] .. vo[h + 1]), triangles t[to[h] ..) with local planes n[..],
@@ -115,6 +143,8 @@ struct DevBatch {
     int4* rec_man;
     float* rec_pts;
     int* rec_cnt;
+    int* rec_col;                      // colour per constraint (joints, then manifolds), [E][rec_col_stride]
+    int rec_col_stride;
     float4* force;                     // contact force per body of the last step (null: off)
 };
 

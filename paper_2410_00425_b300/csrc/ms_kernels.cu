@@ -134,7 +134,7 @@ __global__ void k_prep(DevBatch D) {
 }
 __global__ void k_sweep(DevBatch D, int mode) {
     EnvView e = plain_view(D, blockIdx.x);
-    stage_sweep(e, warp_grp(), mode);
+    stage_sweep(e, warp_grp(), mode, D.P);
 }
 __global__ void k_integrate(DevBatch D) {
     EnvView e = plain_view(D, blockIdx.x);

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
     e.wc = nullptr; e.wc_n = nullptr; e.wjl = nullptr;       // no warm-start memory on this path
     view_workspace(e, s, gl, L);
     e.status = nat<unsigned>(s, L.status);
-    e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
+    e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr; e.rec_col = nullptr;
 
     for (;;) {
         int t0 = 0;
@@ -274,6 +274,8 @@ extern "C" ms_status ms_step_noalloc(const ms_noalloc_batch* nb, const ms_sim_pa
         !(p->angular_damping >= 0.f) || !(p->bounce_threshold >= 0.f))
         return nfail(MS_ERR_INVALID_ARG, "invalid ms_sim_params");
     if (p->warm_start) return nfail(MS_ERR_INVALID_ARG, "warm_start needs the memory of a batch (ms_create_batch)");
+    if (!soft_params_ok(p))
+        return nfail(MS_ERR_INVALID_ARG, "soft-row frequencies and damping ratios must be finite and >= 0");
     if (n_steps == 0) return MS_OK;
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -334,6 +336,7 @@ extern "C" ms_status ms_step_noalloc(const ms_noalloc_batch* nb, const ms_sim_pa
     D.P.adw = (float)(1.0 / (1.0 + (double)D.P.h * p->angular_damping));
     D.P.bounce = p->bounce_threshold;
     D.P.warm = 0;
+    set_soft_params(D.P, p);
     D.P.restit = 1;                          // the descriptors live on the device: always check
     D.body_off = nb->body_off; D.joint_off = nb->joint_off;
     D.bodies = nb->bodies; D.joints = nb->joints;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
     e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
     view_workspace(e, s, gl, L);
     e.status = at<unsigned>(s, L.status);
-    e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
+    e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr; e.rec_col = nullptr;
 
     for (;;) {
         int t0 = 0;

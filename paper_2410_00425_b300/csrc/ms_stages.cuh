@@ -98,6 +98,7 @@ struct EnvView {
     int4* rec_man;                    // recorded manifolds (nullable)
     float* rec_pts;                   // recorded points [contact_cap][10]
     int* rec_cnt;
+    int* rec_col;                     // recorded colour per constraint (nullable)
     float4* force;                    // contact force per body (nullable)
 };
 
@@ -452,7 +453,14 @@ MSD void stage_color(EnvView& e, const Grp& g) {
         e.cnt[C_NCONS] = acc;                          // constraints with a colour
         e.cnt[C_NCOLORS] = ncol;
         if (overflow) *e.status |= ST_COLOR;
+        if (e.rec_col)
+            for (int i = 0; i < ncons; i++) e.rec_col[i] = e.colr[i];
     }
+    g.sync();
+    // x.w marks the bodies that carry a constraint this step (a colour bit);
+    // the others keep their angular velocity in world space (S = identity)
+    for (int b0 = 0; b0 < nbmax; b0 += g.size)
+        if (b0 + g.lane < e.nb) e.x[b0 + g.lane].w = e.used[b0 + g.lane] != 0ull ? 1.f : 0.f;
     g.sync();
     // stable scatter into colour order: color_off[c] runs from the start to
     // the end of colour c, then is shifted back into start offsets
@@ -499,6 +507,13 @@ MSD S3 load_sq(const EnvView& e, int i) {
     return S3{a.x, a.y, a.z, a.w, b.x, b.y};
 }
 
+// world angular velocity of a dynamic body from its w^ (e.w during a
+// substep): S w^ minus the round-trip error r recorded at the prep
+MSD float3 world_w(const EnvView& e, int i) {
+    float4 b = e.sq[3 * i + 1], w = e.w[i];
+    return smv(load_sq(e, i), xyz(w)) - f3(b.z, b.w, w.w);
+}
+
 MSD BodyPose pose_of(const EnvView& e, int i) {
     BodyPose b;
     if (i < 0) {
@@ -520,6 +535,9 @@ MSD BodyPose pose_of(const EnvView& e, int i) {
 }
 
 MSD float contact_bias(float d, float h, float vmax) { return d >= 0.f ? d / h : fmaxf(d / h, -vmax); }
+
+// bias of a joint equality row with error C: C / h rigid, rate x C soft
+MSD float eq_bias(const Params& P, float C) { return P.j_is > 0.f ? P.j_rate * C : C / P.h; }
 
 // Writes the row and returns its effective mass k (static bodies add no
 // angular term).
@@ -632,7 +650,13 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
             float d = contact_sep(pt, A, B, FA, FB, rA, rB);
             float3 t1, t2;
             tangents(n, t1, t2);
-            point_row(R[k], n, rA, rB, A, B, contact_bias(d, h, P.vmax), 0.f);
+            // soft normal rows keep mass scale / k; a separated point keeps
+            // its speculative bias d / h, a penetrating one takes rate x d
+            // (continuous at d = 0)
+            bool soft = P.c_is > 0.f;
+            point_row(R[k], n, rA, rB, A, B, (soft && d < 0.f) ? fmaxf(P.c_rate * d, -P.vmax) : contact_bias(d, h, P.vmax),
+                      0.f);
+            if (soft) R[k].a.w *= P.c_ms;
             point_row(R[np + 2 * k], t1, rA, rB, A, B, mu, 0.f);
             point_row(R[np + 2 * k + 1], t2, rA, rB, A, B, mu, 0.f);
         }
@@ -646,15 +670,15 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     if (jm.x == 0) {
         for (int t = 0; t < 3; t++) {
             float3 ee = axis3(t);
-            point_row(R[t * J], ee, gj.rP, gj.rC, A, B, dot(ee, gj.wP - gj.wC) / h, 0.f);
+            point_row(R[t * J], ee, gj.rP, gj.rC, A, B, eq_bias(P, dot(ee, gj.wP - gj.wC)), 0.f);
         }
         int k = basis_axis(gj.a);
         float3 b1 = cross(gj.a, axis3(k));
         b1 = b1 * (1.f / len(b1));
         float3 b2 = cross(gj.a, b1);
         float3 axc = cross(gj.a, gj.c);
-        ang_row(R[3 * J], -b1, b1, A, B, dot(b1, axc) / h, 0.f);
-        ang_row(R[4 * J], -b2, b2, A, B, dot(b2, axc) / h, 0.f);
+        ang_row(R[3 * J], -b1, b1, A, B, eq_bias(P, dot(b1, axc)), 0.f);
+        ang_row(R[4 * J], -b2, b2, A, B, eq_bias(P, dot(b2, axc)), 0.f);
         ang_row(R[5 * J], -gj.a, gj.a, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
         ang_row(R[6 * J], gj.a, -gj.a, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
         kd7 = ang_row(R[7 * J], -gj.a, gj.a, A, B, 0.f, 0.f);
@@ -663,19 +687,22 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
         float3 b1 = cross(gj.a, axis3(k));
         b1 = b1 * (1.f / len(b1));
         float3 b2 = cross(gj.a, b1);
-        point_row(R[0 * J], b1, gj.rP, gj.rC, A, B, dot(b1, gj.wP - gj.wC) / h, 0.f);
-        point_row(R[1 * J], b2, gj.rP, gj.rC, A, B, dot(b2, gj.wP - gj.wC) / h, 0.f);
+        point_row(R[0 * J], b1, gj.rP, gj.rC, A, B, eq_bias(P, dot(b1, gj.wP - gj.wC)), 0.f);
+        point_row(R[1 * J], b2, gj.rP, gj.rC, A, B, eq_bias(P, dot(b2, gj.wP - gj.wC)), 0.f);
         float4 qe = qmul(gj.qPw, qconj(gj.qCw));
         float sg = qe.w >= 0.f ? 1.f : -1.f;
         float3 th = f3(2.f * sg * qe.x, 2.f * sg * qe.y, 2.f * sg * qe.z);
         for (int t = 0; t < 3; t++) {
             float3 ee = axis3(t);
-            ang_row(R[(2 + t) * J], ee, -ee, A, B, comp(th, t) / h, 0.f);
+            ang_row(R[(2 + t) * J], ee, -ee, A, B, eq_bias(P, comp(th, t)), 0.f);
         }
         point_row(R[5 * J], -gj.a, gj.rP, gj.rC, A, B, contact_bias(gj.phi - jp.x, h, P.vmax), 0.f);
         point_row(R[6 * J], gj.a, gj.rP, gj.rC, A, B, contact_bias(jp.y - gj.phi, h, P.vmax), 0.f);
         kd7 = point_row(R[7 * J], -gj.a, gj.rP, gj.rC, A, B, 0.f, 0.f);
     }
+    // soft equality rows keep mass scale / k
+    if (P.j_is > 0.f)
+        for (int t = 0; t < 5; t++) R[t * J].a.w *= P.j_ms;
     // PD drive as an implicit spring-damper: gamma = 1/(h (h kp + kd)),
     // b = kp C / (h kp + kd), C = phi - target; the row keeps
     // 1/(k + gamma) so that each iteration is one multiply
@@ -699,20 +726,32 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
     for (int i0 = 0; i0 < nbmax; i0 += g.size) {
         int i = i0 + g.lane;
         if (i >= nb) continue;
+        // a dynamic body without a constraint this step (x.w = 0) keeps S =
+        // identity: its angular velocity is carried exactly, not through S^-1
+        // and back
         if (is_dyn(e, i)) {
             // implicit damping (factor 1 / (1 + h c); exactly 1 without) and gravity
             float4 v = e.v[i];
             v.x = fmaf(h, P.gx, v.x * P.adl); v.y = fmaf(h, P.gy, v.y * P.adl); v.z = fmaf(h, P.gz, v.z * P.adl);
             e.v[i] = v;
+        }
+        if (is_dyn(e, i) && e.x[i].w != 0.f) {
             float4 iv = e.inv[i];
             float3 sd = f3(sqrtf(iv.x), sqrtf(iv.y), sqrtf(iv.z));
             M3 R = qmat(e.q[i]);
             S3 S = rdrt(R, sd);
             S3 Si = rdrt(R, f3(1.f / sd.x, 1.f / sd.y, 1.f / sd.z));
+            // w^ = S^-1 w, and the round trip's error r = S w^ - w, which
+            // every later S w^ subtracts: only the substep's change of w^
+            // goes through S (w.w and sq[3i+1].zw hold r)
+            float3 w0 = xyz(e.w[i]) * P.adw;
+            float3 wh = smv(Si, w0);
+            float3 r = smv(S, wh) - w0;
             e.sq[3 * i] = make_float4(S.xx, S.xy, S.xz, S.yy);
-            e.sq[3 * i + 1] = make_float4(S.yz, S.zz, 0.f, 0.f);
-            e.w[i] = f4(smv(Si, xyz(e.w[i]) * P.adw), 0.f);
+            e.sq[3 * i + 1] = make_float4(S.yz, S.zz, r.x, r.y);
+            e.w[i] = f4(wh, r.z);
         } else {
+            if (is_dyn(e, i)) e.w[i] = f4(xyz(e.w[i]) * P.adw, 0.f);
             e.sq[3 * i] = make_float4(1.f, 0.f, 0.f, 1.f);
             e.sq[3 * i + 1] = make_float4(0.f, 1.f, 0.f, 0.f);
         }
@@ -749,9 +788,12 @@ struct SolveCtx {
     const Row* rcg;
     float* lam;
     int njs;
+    float c_is, c_ims, j_is, j_ims;      // soft rows: impulse scale, 1 / mass scale
 };
 
-MSD SolveCtx solve_ctx(const EnvView& e) { return SolveCtx{e.v, e.w, e.rows_j, e.rows_cs, e.rows_cg, e.lam, e.njs}; }
+MSD SolveCtx solve_ctx(const EnvView& e, const Params& P) {
+    return SolveCtx{e.v, e.w, e.rows_j, e.rows_cs, e.rows_cg, e.lam, e.njs, P.c_is, P.c_ims, P.j_is, P.j_ims};
+}
 
 // Every lane of the warp runs the same number of row iterations (nrmax, the
 // warp's largest row count) through straight-line code: rows past a lane's
@@ -794,10 +836,18 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
             bool fric = !joint && r >= np;
             bool drive = joint && r == 7;
             bool eq = joint && r < 5;
-            float ik = (MODE == 2 && drive) ? 0.f : ra.w;
+            // soft rows (contact normals, joint equality rows): in position
+            // sweeps dl = -ms (Jv + bias) / k - is lambda with ms / k stored;
+            // relax sweeps solve them rigid, 1 / k
+            bool softc = !joint && !fric && x.c_is > 0.f;
+            bool softj = eq && x.j_is > 0.f;
+            float ik = (MODE == 2 && drive) ? 0.f
+                     : (MODE == 2 ? ra.w * (softc ? x.c_ims : (softj ? x.j_ims : 1.f)) : ra.w);
+            float isv = MODE == 2 ? 0.f : (softc ? x.c_is : (softj ? x.j_is : 0.f));
             float bias = fric ? 0.f : (MODE == 2 ? (drive ? 0.f : rc.w) : rb.w);
             float gam = drive ? rc.w : 0.f;
-            float c1 = fmaf(-fmaf(gam, old, bias), ik, old);   // old - (bias + gamma old) / (k + gamma)
+            // old (1 - is) - (bias + gamma old) / (k + gamma)
+            float c1 = fmaf(-fmaf(gam, old, bias), ik, fmaf(-isv, old, old));
             // friction bound from the point's normal impulse (a valid index for every row)
             float ln = L[(fric && live) ? (r - np) >> 1 : ri];
             float lim = rb.w * ln;
@@ -815,13 +865,13 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
         wA = madd(wA, sa, dynA ? dl : 0.f);
         wB = madd(wB, sb, dynB ? dl : 0.f);
     }
-    if (has && dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, 0.f); }
-    if (has && dynB) { x.v[c.y] = f4(vA - dv, imB); x.w[c.y] = f4(wB, 0.f); }
+    if (has && dynA) { x.v[c.x] = f4(vA, imA); x.w[c.x] = f4(wA, wa4.w); }
+    if (has && dynB) { x.v[c.y] = f4(vA - dv, imB); x.w[c.y] = f4(wB, wb4.w); }
 }
 
 template <int MODE>
-MSD void sweep_mode(EnvView& e, const Grp& g) {
-    SolveCtx x = solve_ctx(e);
+MSD void sweep_mode(EnvView& e, const Grp& g, const Params& P) {
+    SolveCtx x = solve_ctx(e, P);
     const int4* sc = e.scons;
     const int* off = e.color_off;
     int ncol = e.nb > 0 ? e.cnt[C_NCOLORS] : 0;
@@ -843,10 +893,10 @@ MSD void sweep_mode(EnvView& e, const Grp& g) {
     }
 }
 
-MSD void stage_sweep(EnvView& e, const Grp& g, int mode) {
-    if (mode == 0) sweep_mode<0>(e, g);
-    else if (mode == 1) sweep_mode<1>(e, g);
-    else sweep_mode<2>(e, g);
+MSD void stage_sweep(EnvView& e, const Grp& g, int mode, const Params& P) {
+    if (mode == 0) sweep_mode<0>(e, g, P);
+    else if (mode == 1) sweep_mode<1>(e, g, P);
+    else sweep_mode<2>(e, g, P);
 }
 
 // -------------------------------------------------------------- integrate
@@ -883,7 +933,7 @@ MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
         if (i >= nb || !is_dyn(e, i)) continue;
         float4 x = e.x[i], q = e.q[i];
         float3 v = xyz(e.v[i]);
-        float3 w = smv(load_sq(e, i), xyz(e.w[i]));
+        float3 w = world_w(e, i);
         x.x = fmaf(h, v.x, x.x); x.y = fmaf(h, v.y, x.y); x.z = fmaf(h, v.z, x.z);
         float4 wq = qmul(make_float4(w.x, w.y, w.z, 0.f), q);
         float hh = 0.5f * h;
@@ -908,7 +958,7 @@ MSD void stage_unscale(EnvView& e, const Grp& g) {
     int nbmax = g.wmax(nb);
     for (int i0 = 0; i0 < nbmax; i0 += g.size) {
         int i = i0 + g.lane;
-        if (i < nb && is_dyn(e, i)) e.w[i] = f4(smv(load_sq(e, i), xyz(e.w[i])), 0.f);
+        if (i < nb && is_dyn(e, i)) e.w[i] = f4(world_w(e, i), 0.f);
     }
     g.sync();
 }
@@ -1089,7 +1139,8 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
                 float3 lin = xyz(ra), sa = xyz(rb), sb = xyz(rc);
                 float vn = (dot(lin, vA) + dot(sa, wA)) - (dot(lin, vB) - dot(sb, wB));
                 float old = L[k];
-                float nl = fmaxf(fmaf(-fmaf(er, vn0, vn), ra.w, old), 0.f);
+                float ik = P.c_is > 0.f ? ra.w * P.c_ims : ra.w;   // rigid 1 / k
+                float nl = fmaxf(fmaf(-fmaf(er, vn0, vn), ik, old), 0.f);
                 L[k] = nl;
                 float dl = nl - old;
                 vA = madd(vA, lin * imA, dl);
@@ -1097,8 +1148,8 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
                 vB = madd(vB, lin * (-imB), dl);
                 wB = madd(wB, sb, dynB ? dl : 0.f);
             }
-            if (dynA) { e.v[c.x] = f4(vA, imA); e.w[c.x] = f4(wA, 0.f); }
-            if (dynB) { e.v[c.y] = f4(vB, imB); e.w[c.y] = f4(wB, 0.f); }
+            if (dynA) { e.v[c.x] = f4(vA, imA); e.w[c.x] = f4(wA, wa4.w); }
+            if (dynB) { e.v[c.y] = f4(vB, imB); e.w[c.y] = f4(wB, wb4.w); }
         }
         g.sync();
         k0 = k1;
@@ -1109,10 +1160,10 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
 // sweeps, the contact impulse record and (last substep) restitution, unscale.
 MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
     stage_prep(e, g, P);
-    stage_sweep(e, g, 0);
-    for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1);
+    stage_sweep(e, g, 0, P);
+    for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1, P);
     stage_integrate(e, g, P);
-    for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2);
+    for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2, P);
     if (P.restit) {
         stage_track_impulse(e, g);
         if (last) stage_restitution(e, g, P);
@@ -1251,8 +1302,9 @@ MSD void view_record(EnvView& e, const DevBatch& D, int env, bool active) {
         e.rec_man = D.rec_man + (size_t)env * D.P.pair_cap;
         e.rec_pts = D.rec_pts + (size_t)env * D.P.contact_cap * 10;
         e.rec_cnt = D.rec_cnt + env;
+        e.rec_col = D.rec_col + (size_t)env * D.rec_col_stride;
     } else {
-        e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr;
+        e.rec_man = nullptr; e.rec_pts = nullptr; e.rec_cnt = nullptr; e.rec_col = nullptr;
     }
 }
 

@@ -48,7 +48,8 @@ def default_params(**kw) -> Dict:
     p = dict(dt=0.01, substeps=4, pos_iters=8, vel_iters=1,
              gravity=(0.0, 0.0, -9.81), margin=0.01, max_depen_vel=1.0,
              contact_capacity=64, pair_capacity=128,
-             linear_damping=0.0, angular_damping=0.0, bounce_threshold=1.0, warm_start=0)
+             linear_damping=0.0, angular_damping=0.0, bounce_threshold=1.0, warm_start=0,
+             contact_hertz=30.0, contact_damping_ratio=10.0, joint_hertz=60.0, joint_damping_ratio=2.0)
     p.update(kw)
     return p
 

@@ -11,7 +11,15 @@ import math
 import numpy as np
 
 from . import (BOX, CAPSULE, PLANE, PRISMATIC, REVOLUTE, SPHERE, axis_angle_quat, body,
-               default_params, joint, pack, rng, shoemake_quat)
+               joint, pack, rng, shoemake_quat)
+from . import default_params as _workload_params
+
+
+def default_params(**kw):
+    """The workloads' parameters with rigid rows (contact_hertz = joint_hertz
+    = 0) unless asked otherwise: the closed forms these scenes pin are those
+    of rigid constraints; the soft rows have pins of their own."""
+    return _workload_params(**dict(dict(contact_hertz=0.0, joint_hertz=0.0), **kw))
 
 
 def freefall(n_envs=16, seed=0, **pk):

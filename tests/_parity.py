@@ -7,24 +7,28 @@ import numpy as np
 import oracle
 import scenegen
 
-# tolerances after one step (positions m, velocities m/s, quaternion
-# components); rollouts of non-chaotic envs use 10x these.  Angular
-# velocity is held to the velocity bar at the body's material points:
-# |dw| * r_bound <= TOL_V, r_bound the body's bounding radius.
-TOL_X, TOL_V, TOL_Q = 1e-5, 1e-4, 1e-5
+# tolerances after one step (positions m, velocities m/s, angular
+# velocities rad/s, quaternion components); rollouts of non-chaotic envs use
+# 10x these.  Angular velocity is also held to the velocity bar at the
+# body's material points: |dw| * r_bound <= TOL_V, r_bound the body's
+# bounding radius.
+TOL_X, TOL_V, TOL_W, TOL_Q = 1e-5, 1e-4, 1e-4, 1e-5
 TIE_EPS = 1e-5
-# relative velocity noise per step of the non-chaotic probe: four float32
-# ulps.  A velocity component takes ~40 row impulses per step (4 substeps x
-# 10 sweeps), each rounded once in float32; as a random walk that is ~6 ulps.
-VEL_NOISE = 4 * 2.0**-24
 
 
-def bound_radius(bodies):
+def bound_radius(bodies, hulls=None):
+    """Radius of each body's bounding sphere about its origin (0 for planes;
+    a hull's from its vertices in the scene's hull library)."""
     p = bodies["p"].astype(np.float64)
     t = bodies["type"]
     r = np.where(t == scenegen.SPHERE, p[:, 0],
                  np.where(t == scenegen.CAPSULE, p[:, 0] + p[:, 1],
                           np.where(t == scenegen.BOX, np.linalg.norm(p, axis=1), 0.0)))
+    if hulls is not None:
+        v, vo = np.asarray(hulls["verts"], np.float64), np.asarray(hulls["vert_off"])
+        for i in np.nonzero(t == scenegen.HULL)[0]:
+            h = int(p[i, 0])
+            r[i] = np.linalg.norm(v[vo[h]:vo[h + 1]], axis=1).max()
     return r
 
 
@@ -88,11 +92,11 @@ def oracle_run(scene, n_steps, threads=8, perturb=0.0, records=None):
 def env_errors(scene, a, b):
     """Per-env max errors between two [NB,13] states: position (m), linear
     velocity (m/s), angular velocity as material-point speed |dw| r_bound
-    (m/s), quaternion (sign-insensitive)."""
+    (m/s), quaternion (sign-insensitive), angular velocity (rad/s)."""
     bo = scene.body_off
     E = scene.n_envs
-    rb = bound_radius(scene.bodies)
-    out = np.zeros((E, 4))
+    rb = bound_radius(scene.bodies, getattr(scene, "hulls", None))
+    out = np.zeros((E, 5))
     for e in range(E):
         s = slice(bo[e], bo[e + 1])
         A, B = a[s], b[s]
@@ -101,12 +105,13 @@ def env_errors(scene, a, b):
         out[e, 2] = (np.abs(A[:, 10:13] - B[:, 10:13]).max(1) * rb[s]).max()
         dq = np.minimum(np.abs(A[:, 3:7] - B[:, 3:7]).max(1), np.abs(A[:, 3:7] + B[:, 3:7]).max(1))
         out[e, 3] = dq.max()
+        out[e, 4] = np.abs(A[:, 10:13] - B[:, 10:13]).max()
     return out
 
 
 def within(err, scale=1.0):
     return ((err[:, 0] <= TOL_X * scale) & (err[:, 1] <= TOL_V * scale) &
-            (err[:, 2] <= TOL_V * scale) & (err[:, 3] <= TOL_Q * scale))
+            (err[:, 2] <= TOL_V * scale) & (err[:, 3] <= TOL_Q * scale) & (err[:, 4] <= TOL_W * scale))
 
 
 def pair_sets_match(batch, o, scene):
@@ -125,41 +130,37 @@ def pair_sets_match(batch, o, scene):
     return bad
 
 
-def non_chaotic(scene, n_steps, threads=8, seed=11, seeds=None, margin=1.0):
+def non_chaotic(scene, n_steps, threads=8):
     """Envs whose rollout is insensitive to perturbations of the size the
-    float32 path introduces.  Both must hold after n_steps:
+    float32 path introduces.  At every step of the rollout:
       * two FP64 runs from positions 1e-9 m apart stay within 1e-6 m;
-      * an FP64 run whose state is rounded to float32 after every step, and
-        whose velocities then take VEL_NOISE of relative noise (random sign,
-        seeded), stays within the one-step bars (1e-5 m, 1e-4 m/s, 1e-4 m/s,
-        1e-5) of the plain FP64 run.  Float32 state storage, amplified
-        through the d/h and C/h position-correction biases, and the float32
-        solve arithmetic are the perturbations actually present in the
-        comparison; a body spinning for many radians accumulates the latter
-        as orientation phase.
-    seeds (several noise draws, all must pass) and margin (a fraction of
-    the one-step bars) make the selection stricter for scenes whose envs
-    sit near the edge: stiff drives pressed against a limit, fast fingers.
+      * an FP64 run that stores every velocity and pose as float32 after each
+        update (impulse, gravity, integration) -- the storage precision of
+        the float32 path, at the places it rounds -- stays within the
+        one-step bars of the plain FP64 run (an impact can amplify the
+        rounding for a few steps and recover; such an env is sensitive).
     Returns (mask, state of the plain FP64 run)."""
-    base = oracle_run(scene, n_steps, threads).state()
-    pert = oracle_run(scene, n_steps, threads, perturb=1e-9).state()
-    calm = env_errors(scene, base, pert)[:, 0] < 1e-6
-    for sd in (seeds if seeds is not None else (seed,)):
-        o = oracle.Oracle(scene)
+    runs = [oracle.Oracle(scene) for _ in range(3)]
+    base, pert, r32 = runs
+    st = pert.state()
+    st[scene.bodies["mass"] > 0, 0] += 1e-9
+    pert.set_state(st)
+    r32.set_round32(True)
+    for o in runs:
         if scene.task is not None:
             o.set_task(scene.task)
-        rng = np.random.default_rng(sd)
-        for k in range(n_steps):
+    calm = np.ones(scene.n_envs, bool)
+    for k in range(n_steps):
+        a = scene.actions(k, 1)
+        for o in runs:
             if scene.task is not None:
-                o.step_task(1, threads=threads)
+                o.step_task(1, actions=a, threads=threads)
             else:
-                o.step(1, threads=threads)
-            st = o.state().astype(np.float32).astype(np.float64)
-            st[:, 7:13] *= 1.0 + rng.choice([-1.0, 1.0], size=st[:, 7:13].shape) * VEL_NOISE
-            o.set_state(st)
-        err = env_errors(scene, base, o.state())
-        calm &= within(err, margin)
-    return calm, base
+                o.step(1, actions=a, threads=threads)
+        ref = base.state()
+        calm &= env_errors(scene, ref, pert.state())[:, 0] < 1e-6
+        calm &= within(env_errors(scene, ref, r32.state()))
+    return calm, base.state()
 
 
 def tie_free(o, scene):

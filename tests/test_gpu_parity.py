@@ -1,8 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Bars: contact pair sets bit-exact except oracle margin ties; after one step
-|dx| <= 1e-5 m, |dv| <= 1e-4 m/s, |dw| r_bound <= 1e-4 m/s (angular velocity at the body's
-material points), quaternion <= 1e-5;
+|dx| <= 1e-5 m, |dv| <= 1e-4 m/s, |dw| <= 1e-4 rad/s and |dw| r_bound <= 1e-4 m/s
+(angular velocity at the body's material points), quaternion <= 1e-5;
 200-step rollouts of non-chaotic envs within 10x those bounds.  Envs with a
 tie-adjacent discrete decision in the oracle are counted and excluded from
 the strict comparison."""
@@ -63,17 +63,23 @@ def test_one_step_parity(name, n):
         assert status[e] == o.status(e)
 
 
-@pytest.mark.parametrize("name,n,steps", [("small", 64, 200), ("arm", 32, 200), ("hand", 16, 100),
-                                          ("mixed", 48, 100)])
-def test_rollout_parity_non_chaotic(name, n, steps):
+# (workload, envs, steps, envs that must be compared): the hand's finger
+# capsules pass near the capsule - box SAT thresholds often, so its rollout
+# is shorter
+ROLLOUTS = [("small", 128, 200, 20), ("arm", 256, 200, 30), ("hand", 64, 20, 10), ("mixed", 96, 100, 20)]
+
+
+@pytest.mark.parametrize("name,n,steps,need", ROLLOUTS)
+def test_rollout_parity_non_chaotic(name, n, steps, need):
     sc = scenegen.make_scene(name, n_envs=n)
     calm, ost = non_chaotic(sc, steps)
     o = oracle_run(sc, steps)
     _, st, _ = gpu_run(sc, steps)
     err = env_errors(sc, st, ost)
     clean = calm & tie_free(o, sc)
-    print(f"{name}: {calm.sum()} of {n} envs non-chaotic, {clean.sum()} also tie-free")
-    assert clean.sum() >= 1
+    print(f"{name}: {calm.sum()} of {n} envs non-chaotic, {clean.sum()} also tie-free; "
+          f"worst {err[clean].max(0) if clean.any() else None}")
+    assert clean.sum() >= need
     ok = within(err, 10.0)
     bad = np.nonzero(clean & ~ok)[0]
     assert ok[clean].all(), f"envs {bad.tolist()} errors {err[bad].tolist()}"
@@ -191,6 +197,10 @@ def test_partial_reset_touches_only_masked_envs():
     (lambda: V.slider(), 30),
     (lambda: V.incline([math.atan(0.6)]), 100),
     (lambda: V.limit(), 100),
+    # soft rows: the resting stack at the small workload's settings with warm
+    # start, and a soft joint row off its axis
+    (lambda: V.stack(contact_hertz=30.0, contact_damping_ratio=10.0, warm_start=1), 300),
+    (lambda: V.slider(kp=0.0, kd=0.0, joint_hertz=60.0, joint_damping_ratio=2.0), 30),
 ])
 def test_pin_scenes_follow_oracle(scene_fn, steps):
     sc = scene_fn()

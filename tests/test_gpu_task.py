@@ -50,11 +50,8 @@ def _compare(g, o, ties, A, rows=None):
 
 @pytest.mark.parametrize("steps", [60])
 def test_pick_rollout_follows_oracle(steps):
-    # fingers pressed against their limits by kp = 1000 drives make some envs
-    # sensitive beyond the default probe: three noise draws, half the bars
-    # (11 of 128 envs non-chaotic and tie-free over 60 steps)
     sc = scenegen.make_scene("pick", n_envs=128)
-    calm, ost = non_chaotic(sc, steps, seeds=(11, 12, 13), margin=0.5)
+    calm, ost = non_chaotic(sc, steps)
     orec = []
     o = oracle_run(sc, steps, records=orec)
     (orecs, oties), = orec

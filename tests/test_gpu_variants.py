@@ -36,8 +36,11 @@ def _with(sc, restitution=None, **pk):
     return sc
 
 
-@pytest.mark.parametrize("name,n,steps", [("small", 64, 100), ("clutter", 64, 40)])
-def test_rollout_with_variants_follows_oracle(name, n, steps):
+@pytest.mark.parametrize("name,n,steps,need", [("small", 128, 100, 8), ("clutter", 64, 40, 1),
+                                               ("arm", 128, 200, 30)])
+def test_rollout_with_variants_follows_oracle(name, n, steps, need):
+    """The arm case is the warm-started arm: with soft joint rows it no
+    longer gains speed, so its rollouts are compared with the oracle."""
     sc = _with(scenegen.make_scene(name, n_envs=n), restitution=0.4, **VARIANTS)
     calm, ost = non_chaotic(sc, steps)
     o = oracle_run(sc, steps)
@@ -45,7 +48,7 @@ def test_rollout_with_variants_follows_oracle(name, n, steps):
     err = env_errors(sc, st, ost)
     clean = calm & tie_free(o, sc)
     print(f"{name}: {clean.sum()} of {n} envs non-chaotic and tie-free")
-    assert clean.sum() >= 1
+    assert clean.sum() >= need
     ok = within(err, 10.0)
     bad = np.nonzero(clean & ~ok)[0]
     assert ok[clean].all(), f"envs {bad.tolist()} errors {err[bad].tolist()}"

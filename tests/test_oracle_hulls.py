@@ -14,12 +14,14 @@ import pytest
 
 import oracle
 import scenegen
+from scenegen import validation as V
 from scenegen import BOX, HULL, PLANE, SPHERE, body, pack
 from scenegen import hulls as H
 
 
 def _scene(bodies, assets, **pk):
-    sc = pack("hull_probe", [bodies], [[]], scenegen.default_params(**pk), 0, 0)
+    """A probe scene with rigid rows, like the other pin scenes."""
+    sc = pack("hull_probe", [bodies], [[]], V.default_params(**pk), 0, 0)
     sc.hulls = H.library(assets)
     return sc
 
@@ -225,7 +227,7 @@ def test_capsule_dropped_on_a_hull_lands_and_keeps_its_energy():
     sc = pack("cap_hull", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)), body(HULL, (0, 0, 0), 0.0, (0, 0, 0.03)),
                             body(CAPSULE, (r, l, 0), m, (0.005, 0.0, 0.15),
                                  quat=scenegen.axis_angle_quat((1, 0, 0), 1.2))]], [[]],
-              scenegen.default_params(), 0, 0)
+              V.default_params(), 0, 0)
     sc.hulls = H.library(assets)
     o = oracle.Oracle(sc)
     # principal moments of the capsule about its axis (z) and across it

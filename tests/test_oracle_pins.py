@@ -103,7 +103,7 @@ def test_contact_forces_of_a_resting_stack_balance_gravity():
     sc = pack("stack2", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)),
                           body(BOX, (h1, h1, h1), m1, (0, 0, h1)),
                           body(BOX, (h2, h2, h2), m2, (0.005, -0.004, 2 * h1 + h2))]], [[]],
-              scenegen.default_params(pos_iters=64), 0, 0)
+              V.default_params(pos_iters=64), 0, 0)
     o = oracle.Oracle(sc)
     o.step(200)
     f = o.contact_forces()
@@ -222,7 +222,7 @@ def test_rolling_without_slip_keeps_its_speed(kind):
     else:
         b = body(CAPSULE, (r, 0.02, 0), 0.05, (0.0, 0.0, r), quat=scenegen.axis_angle_quat((1, 0, 0), math.pi / 2))
         w = np.array([0.0, -20.0, 0.0])                  # along the capsule axis (world y)
-    sc = pack("roll", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), mu=0.8), b]], [[]], scenegen.default_params(), 0, 0)
+    sc = pack("roll", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), mu=0.8), b]], [[]], V.default_params(), 0, 0)
     o = oracle.Oracle(sc)
     st = o.state()
     v = np.cross(w, [0.0, 0.0, r])
@@ -328,7 +328,7 @@ def test_single_row_one_iteration_is_exact():
     sc = scenegen.pack("row", [[scenegen.body(scenegen.PLANE, (0, 0, 0), 0, (0, 0, 0), mu=0.0),
                                 scenegen.body(scenegen.SPHERE, (0.05, 0, 0), 1.0, (0.1, 0.2, 0.05),
                                               linvel=(0.3, -0.1, -1.0), mu=0.0)]], [[]],
-                       scenegen.default_params(substeps=1, pos_iters=1, vel_iters=0), 0, 0)
+                       V.default_params(substeps=1, pos_iters=1, vel_iters=0), 0, 0)
     o = oracle.Oracle(sc)
     o.step(1)
     st = o.state()
@@ -602,3 +602,109 @@ def test_static_bodies_never_move():
     static = sc.bodies["mass"] == 0
     np.testing.assert_array_equal(st[static, 0:3], sc.bodies["pos"][static].astype(np.float64))
     assert np.all(st[static, 7:13] == 0)
+
+
+# ------------------------------------------------------------------ soft rows
+def _soft(hz, zeta, h):
+    om = 2 * math.pi * hz
+    return om, 1.0 + 2 * zeta * om * h + (h * om) ** 2
+
+
+@pytest.mark.parametrize("vel_iters", [0, 1])
+@pytest.mark.parametrize("delta,v0", [(0.004, 0.0), (-0.002, 0.3)])
+def test_isolated_soft_joint_row_is_implicit_euler(vel_iters, delta, v0):
+    """A soft joint equality row is a spring-damper of frequency omega and
+    damping ratio zeta on the row's effective mass, integrated implicitly:
+    a body on a world prismatic joint (axis x, no drive, g = 0), off the axis
+    by delta along y with speed v0 along y.  One substep of position
+    iterations gives (1 + 2 zeta omega h + h^2 omega^2) v' = v0 - h omega^2
+    delta, the position then moves by h v'; a relax sweep (rigid, zero
+    bias) then removes v' along the row."""
+    hz, zeta = 60.0, 2.0
+    sc = V.slider(kp=0.0, kd=0.0, substeps=1, pos_iters=4, vel_iters=vel_iters, joint_hertz=hz,
+                  joint_damping_ratio=zeta)
+    sc.bodies["pos"][0, 1] = delta
+    sc.bodies["linvel"][0, 1] = v0
+    d = oracle.body_rows(sc.bodies)
+    delta, v0 = d[0, 6], d[0, 13]                       # as stored (float32)
+    o = oracle.Oracle(sc)
+    o.step(1)
+    st = o.state()
+    h = sc.params["dt"]
+    om, den = _soft(hz, zeta, h)
+    v1 = (v0 - h * om * om * delta) / den
+    assert abs(st[0, 1] - (delta + h * v1)) < 1e-12
+    assert abs(st[0, 8] - (0.0 if vel_iters else v1)) < 1e-12
+
+
+def test_soft_joint_rows_off_are_rigid():
+    """joint_hertz = 0: the equality row removes the whole error in one
+    substep (bias C / h) -- the rigid row."""
+    sc = V.slider(kp=0.0, kd=0.0, substeps=1, pos_iters=4, vel_iters=0)
+    sc.bodies["pos"][0, 1] = 0.004
+    o = oracle.Oracle(sc)
+    o.step(1)
+    assert abs(o.state()[0, 1]) < 1e-12
+
+
+def _box_stack(n, **pk):
+    from scenegen import BOX, PLANE, body, pack
+    h, m = 0.02, 0.1
+    bl = [body(PLANE, (0, 0, 0), 0.0, (0, 0, 0), mu=0.5, group=1)]
+    bl += [body(BOX, (h, h, h), m, (0, 0, h + 2 * h * k), mu=0.5, group=2) for k in range(n)]
+    return pack("stack", [bl], [[]], scenegen.default_params(**pk), 0, 0), h
+
+
+def test_soft_contact_rest_sinks_by_g_over_omega_squared():
+    """A box resting on the plane under soft contacts (30 Hz): each point is a
+    spring of stiffness m_eff omega^2 and the four points share the weight,
+    so the box settles g / omega^2 into the plane and stays there."""
+    sc, h = _box_stack(1, warm_start=1)
+    om = 2 * math.pi * sc.params["contact_hertz"]
+    o = oracle.Oracle(sc)
+    o.step(400)
+    st = o.state()
+    assert abs(st[1, 2] - (h - 9.81 / om ** 2)) < 1e-9
+    assert np.abs(st[1, 7:13]).max() < 1e-9
+
+
+def test_stack_at_workload_settings_settles_at_its_spring_equilibrium_and_stays():
+    """Three touching boxes (0.02 m, 0.1 kg) on the plane at the small
+    workload's settings (dt 0.01, 4 substeps, 8 + 1 sweeps, soft contacts,
+    warm start): the contacts are springs of m_eff omega^2 with m_eff = m
+    (box - plane) and m / 2 (box - box), carrying 3, 2 and 1 weights, so the
+    boxes sink by 3, 3 + 4 and 3 + 4 + 2 times g / omega^2.  Each box stays
+    within 1e-4 m of that rest pose over 1000 steps."""
+    sc, h = _box_stack(3, warm_start=1)
+    p = sc.params
+    assert (p["dt"], p["substeps"], p["pos_iters"], p["vel_iters"]) == (0.01, 4, 8, 1)
+    om = 2 * math.pi * p["contact_hertz"]
+    s = 9.81 / om ** 2
+    rest = sc.bodies["pos"].astype(np.float64)[1:].copy()
+    rest[:, 2] -= np.array([3, 7, 9]) * s
+    o = oracle.Oracle(sc)
+    o.step(200)                                      # settling
+    worst = 0.0
+    for _ in range(10):
+        o.step(100)
+        st = o.state()
+        worst = max(worst, np.abs(st[1:, 0:3] - rest).max())
+    assert worst < 1e-4, worst
+    # the settled state is the spring equilibrium itself, far tighter than the bar
+    assert np.abs(o.state()[1:, 2] - rest[:, 2]).max() < 1e-6
+
+
+@pytest.mark.parametrize("warm", [0, 1])
+def test_arm_workload_stays_bounded(warm):
+    """The arm workload's light fingers (0.05 kg on 0.5-3 kg links) do not
+    gain speed with soft joint rows, cold or warm started: every body stays
+    below 10 m/s over 200 steps of random targets (rigid joint rows reach
+    100+ m/s in most envs)."""
+    sc = scenegen.make_scene("arm", n_envs=32)
+    sc.params = dict(sc.params, warm_start=warm)
+    o = oracle.Oracle(sc)
+    top = 0.0
+    for k in range(4):
+        o.step(50, actions=sc.actions(50 * k, 50), threads=8)
+        top = max(top, np.linalg.norm(o.state()[:, 7:10], axis=1).max())
+    assert top < 10.0, top
