@@ -708,3 +708,26 @@ def test_arm_workload_stays_bounded(warm):
         o.step(50, actions=sc.actions(50 * k, 50), threads=8)
         top = max(top, np.linalg.norm(o.state()[:, 7:10], axis=1).max())
     assert top < 10.0, top
+
+
+@pytest.mark.parametrize("u", [1.0, 0.3])
+def test_speculative_soft_contact_closed_form(u):
+    """A sphere a gap d above the plane, approaching at speed u, g = 0, one
+    substep of one position sweep: the soft normal row keeps the speculative
+    bias d / h, so it acts only if u > d / h and then leaves the normal
+    speed -u + ms (u - d / h), ms = a2 / (1 + a2) the contact mass scale."""
+    from scenegen import PLANE, SPHERE, body, pack
+    h, d, r, hz, zeta = 0.0025, 0.001, 0.02, 30.0, 10.0
+    sc = pack("spec", [[body(PLANE, (0, 0, 0), 0.0, (0, 0, 0)),
+                        body(SPHERE, (r, 0, 0), 0.1, (0, 0, r + d), linvel=(0, 0, -u))]], [[]],
+              scenegen.default_params(dt=h, substeps=1, pos_iters=1, vel_iters=0, gravity=(0.0, 0.0, 0.0),
+                                      contact_hertz=hz, contact_damping_ratio=zeta), 0, 0)
+    rows = oracle.body_rows(sc.bodies)
+    d, u = rows[1, 7] - rows[1, 1], -rows[1, 14]                # as stored (float32)
+    o = oracle.Oracle(sc)
+    o.step(1)
+    om = 2 * math.pi * hz
+    a2 = h * om * (2 * zeta + h * om)
+    ms = a2 / (1 + a2)
+    vz = -u + ms * (u - d / h) if u > d / h else -u
+    assert abs(o.state()[1, 9] - vz) < 1e-12
