@@ -84,6 +84,7 @@ struct ms_batch {
     int fused_threads = 0, fused_grid = 0, fused_ctas_per_sm = 0;
     size_t fused_smem = 0;
     bool fused_ready = false;
+    bool fused_lean = false;          // the configured kernel is k_fused<G, true>
     std::map<long long, GraphEntry> graphs;
     // recorded after the batch's last enqueued work, on whatever stream it
     // went to: waiting on it never touches a stream the caller may have
@@ -131,6 +132,13 @@ static void drop_graphs(ms_batch* b) {
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     b->graphs.clear();
+}
+
+// The batch's use of a task, contact forces or a contact record changed:
+// the batched kernel (lean or not) is chosen again at the next step.
+static void kernel_choice_changed(ms_batch* b) {
+    b->fused_ready = false;
+    drop_graphs(b);
 }
 
 static void free_all(ms_batch* b) {
@@ -578,6 +586,7 @@ extern "C" ms_status ms_step_plain(ms_batch* b, const float* actions, int n_step
 // ------------------------------------------------------------- batched path
 static ms_status configure_fused(ms_batch* b) {
     if (b->fused_ready) return MS_OK;
+    b->fused_lean = fused_lean(b->D);
     const ms_sim_params& p = b->params;
     Tuning& t = b->tune;
     int K = 32 / t.G;                               // envs per warp
@@ -592,7 +601,7 @@ static ms_status configure_fused(ms_batch* b) {
         size_t sm = (size_t)Lc.s_bytes * envs_per_cta;
         if (sm > b->smem_optin) return 0;
         int n = 0;
-        if (fused_occupancy(t.G, threads, sm, &n) != cudaSuccess) return 0;
+        if (fused_occupancy(t.G, b->fused_lean, threads, sm, &n) != cudaSuccess) return 0;
         return n;
     };
     // Placement.  rows_smem: every row on chip if one CTA fits.  Otherwise
@@ -620,7 +629,7 @@ static ms_status configure_fused(ms_batch* b) {
     }
     size_t smem = (size_t)L.s_bytes * envs_per_cta;
     int per_sm = 0;
-    CK(fused_occupancy(t.G, threads, smem, &per_sm));
+    CK(fused_occupancy(t.G, b->fused_lean, threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
     int grid = per_sm * b->sm_count;
     int need = (b->E + envs_per_cta - 1) / envs_per_cta;
@@ -661,8 +670,8 @@ static DevBatch call_view(const ms_batch* b, float* out) {
 
 static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, float* out, cudaStream_t st) {
     CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
-    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_grid, b->fused_threads,
-                    b->fused_smem, st));
+    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_lean, b->fused_grid,
+                    b->fused_threads, b->fused_smem, st));
     return MS_OK;
 }
 
@@ -759,6 +768,7 @@ extern "C" ms_status ms_set_task(ms_batch* b, const ms_task_desc* t, void* strea
     if (!b) return fail(MS_ERR_INVALID_ARG, "batch is NULL");
     if (!t) {
         b->D.T = DevTask{};
+        kernel_choice_changed(b);
         return MS_OK;
     }
     if (t->n_joints != b->A) return fail(MS_ERR_INVALID_ARG, "task n_joints %d != the batch's A %d", t->n_joints, b->A);
@@ -799,6 +809,7 @@ extern "C" ms_status ms_set_task(ms_batch* b, const ms_task_desc* t, void* strea
     T.out = nullptr;
     T.D = 10 + 2 * b->A;
     b->D.T = T;
+    kernel_choice_changed(b);
     launch_task_reset(b->D, nullptr, st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));           // the host copy of the bounds is reused by the next call
@@ -941,7 +952,7 @@ extern "C" ms_status ms_set_record_contacts(ms_batch* b, int record) {
     } else {
         b->D.rec_man = nullptr; b->D.rec_pts = nullptr; b->D.rec_cnt = nullptr; b->D.rec_col = nullptr;
     }
-    drop_graphs(b);
+    kernel_choice_changed(b);
     return MS_OK;
 }
 
@@ -956,7 +967,7 @@ extern "C" ms_status ms_enable_contact_forces(ms_batch* b, int on) {
         b->d_force = (float4*)f;
     }
     b->D.force = on ? b->d_force : nullptr;
-    drop_graphs(b);
+    kernel_choice_changed(b);
     return MS_OK;
 }
 

@@ -872,6 +872,8 @@ MSD void np_ch(const Shape& A, const Shape& B, float m, CandSet& cs) {
 }
 
 // Narrowphase of the ordered pair (A, B): up to 4 kept points in out.
+// HULLS = false compiles the hull routines out (a batch without hulls).
+template <bool HULLS = true>
 MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
     CandSet cs;
     cs.n = 0;
@@ -882,22 +884,24 @@ MSD int collide(const Shape& A, const Shape& B, float m, Cand* out) {
         if (tb == SH_SPHERE) np_ss(A, B, cs);
         else if (tb == SH_CAPSULE) np_sc(A, B, cs);
         else if (tb == SH_BOX) np_sb(A, B, cs);
-        else if (tb == SH_HULL) { if (B.hull.v) np_sh(A, B, cs); }
+        else if (tb == SH_HULL) { if constexpr (HULLS) { if (B.hull.v) np_sh(A, B, cs); } }
         else np_sp(A, B, cs);
     } else if (ta == SH_CAPSULE) {
         if (tb == SH_CAPSULE) np_cc(A, B, cs);
         else if (tb == SH_BOX) np_cb(A, B, m, cs);
         else if (tb == SH_PLANE) np_cp(A, B, cs);
-        else if (tb == SH_HULL) { if (B.hull.v) np_ch(A, B, m, cs); }
+        else if (tb == SH_HULL) { if constexpr (HULLS) { if (B.hull.v) np_ch(A, B, m, cs); } }
     } else if (ta == SH_BOX) {
         if (tb == SH_BOX) np_bb(A, B, m, cs);
-        else if (tb == SH_HULL) poly = B.hull.v != nullptr;
+        else if (tb == SH_HULL) poly = HULLS && B.hull.v != nullptr;
         else np_bp(A, B, cs);
-    } else if (ta == SH_HULL && A.hull.v) {
+    } else if (HULLS && ta == SH_HULL && A.hull.v) {
         if (tb == SH_HULL) poly = B.hull.v != nullptr;
         else if (tb == SH_PLANE) np_hp(A, B, m, cs);
     }
-    if (poly) np_poly(A, B, m, cs);
+    if constexpr (HULLS) {
+        if (poly) np_poly(A, B, m, cs);
+    }
     Cand kept[16];
     int nk = 0;
     for (int i = 0; i < cs.n; i++)

@@ -262,6 +262,7 @@ MSD void stage_broadphase(EnvView& e, const Grp& g, const Params& P) {
 }
 
 // ------------------------------------------------------------ narrowphase
+template <bool HULLS = true>
 MSD Shape shape_at(const EnvView& e, int i) {
     Shape s;
     s.x = xyz(e.x[i]);
@@ -270,7 +271,7 @@ MSD Shape shape_at(const EnvView& e, int i) {
     float4 p = e.shape[i];
     s.p0 = p.x; s.p1 = p.y; s.p2 = p.z;
     s.hull = HullRef{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
-    if (s.type == SH_HULL && e.hulls) {
+    if (HULLS && s.type == SH_HULL && e.hulls) {
         const HullLib& L = *e.hulls;
         int h = (int)p.x;
         int v0 = L.vo[h], t0 = L.to[h], e0 = L.eo[h];
@@ -336,6 +337,8 @@ MSD void stage_check_bounds(EnvView& e, const Grp& g, const Params& P, bool afte
 #define MS_CHECK_BOUNDS(e, g, P, after_color) ((void)0)
 #endif
 
+// HULLS = false: a batch without hulls (the hull routines compiled out)
+template <bool HULLS = true>
 MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
     int npairs = e.nb > 0 ? e.cnt[C_NPAIRS] : 0;
     int pmax = g.wmax(npairs);
@@ -351,9 +354,9 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
             int i = pr & 0xffff, j = pr >> 16;
             a = i; b = j;
             if (shape_rank(shape_type(e, j)) < shape_rank(shape_type(e, i))) { a = j; b = i; }
-            SA = shape_at(e, a);
-            SB = shape_at(e, b);
-            n = collide(SA, SB, P.margin, pts);
+            SA = shape_at<HULLS>(e, a);
+            SB = shape_at<HULLS>(e, b);
+            n = collide<HULLS>(SA, SB, P.margin, pts);
         }
         int incl = g.incl_scan(n);
         int chunk_total = g.shfl(incl, g.size - 1);
@@ -1158,15 +1161,19 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
 
 // One substep: prep, warm start, position sweeps, integration, relax
 // sweeps, the contact impulse record and (last substep) restitution, unscale.
+// RESTIT = false compiles restitution out (a batch without it).
+template <bool RESTIT = true>
 MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
     stage_prep(e, g, P);
     stage_sweep(e, g, 0, P);
     for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1, P);
     stage_integrate(e, g, P);
     for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2, P);
-    if (P.restit) {
-        stage_track_impulse(e, g);
-        if (last) stage_restitution(e, g, P);
+    if constexpr (RESTIT) {
+        if (P.restit) {
+            stage_track_impulse(e, g);
+            if (last) stage_restitution(e, g, P);
+        }
     }
     stage_unscale(e, g);
 }
