@@ -227,7 +227,9 @@ def dist_setup():
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        # the step has no collective: gloo carries only the barrier and the
+        # max over ranks of the timed region
+        dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -236,7 +238,7 @@ def reduce_max(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -247,61 +249,79 @@ def barrier(ws):
         dist.barrier()
 
 
-def time_cpu_baseline(name, n_envs, steps, one_core=False, variants=False):
-    """The oracle as it stands, on every host core, on a bounded sample."""
+def oracle_rate(name, n_envs, settle, steps, variants=False, threads=None):
+    """The oracle as it stands, timed on the host cores: one oracle over the
+    first n_envs envs of the workload (per-env seeding: the same envs the
+    GPU steps), advanced `settle` steps untimed, then `steps` steps timed one
+    call each.  Returns (env-steps/s, seconds per step list, threads)."""
     import oracle
     sc = make_workload(name, variants, n_envs=n_envs)
     o = oracle.Oracle(sc)
-    acts = sc.actions(0, steps)
-    cores = os.cpu_count() or 1
+    th = threads or os.cpu_count() or 1
+    task = sc.task is not None
+    if task:
+        o.set_task(sc.task)
+    acts = sc.actions(0, settle + steps)
 
-    def run(o, n, a, th):
-        if sc.task is not None:
-            o.set_task(sc.task)
+    def adv(k0, n):
+        a = None if acts is None else np.ascontiguousarray(acts[k0:k0 + n])
+        if task:
             o.step_task(n, actions=a, threads=th)
         else:
             o.step(n, actions=a, threads=th)
-    t0 = time.perf_counter()
-    run(o, steps, acts, cores)
-    dt = time.perf_counter() - t0
-    out = {"value": n_envs * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-           "sample": f"{n_envs} envs x {steps} steps of the {name} workload, FP64, {cores} threads "
-                     f"({dt:.1f} s)"}
-    if one_core:
-        # the same oracle on one core, on a sixteenth of the sample
-        n1 = max(1, n_envs // 16)
-        o1 = oracle.Oracle(sc.subset(range(n1)))
+    if settle:
+        adv(0, settle)
+    times = []
+    for k in range(steps):
         t0 = time.perf_counter()
-        run(o1, steps, None if acts is None else np.ascontiguousarray(acts[:, :n1]), 1)
-        d1 = time.perf_counter() - t0
-        out["value_1core"] = n1 * steps / d1
-        out["sample_1core"] = f"{n1} envs x {steps} steps, 1 thread ({d1:.1f} s)"
+        adv(settle + k, 1)
+        times.append(time.perf_counter() - t0)
+    return n_envs * steps / sum(times), times, th
+
+
+def oracle_sample_envs(name):
+    """Envs of the bounded oracle sample of a workload (about 10-30 s of
+    CPU work for the default run; rates extrapolate linearly in envs)."""
+    return min(scenegen.CONFIG_SIZES[name], 1024)
+
+
+def time_cpu_baseline(name, settle, steps, one_core=False, variants=False):
+    """cpu_baseline of the JSON line: the oracle on every host core on the
+    bounded sample at the same settled state as the GPU timing, and on one
+    core on a sixteenth of it."""
+    n = oracle_sample_envs(name)
+    v, times, th = oracle_rate(name, n, settle, steps, variants)
+    out = {"value": v, "unit": "env-steps/s", "cores": th, "kind": "oracle",
+           "sample": f"{n} envs of the {name} workload, {settle} settling steps, then {steps} timed steps "
+                     f"(one call each), FP64, {th} threads ({sum(times):.2f} s timed)"}
+    if one_core:
+        n1 = max(1, n // 16)
+        v1, t1, _ = oracle_rate(name, n1, settle, steps, variants, threads=1)
+        out["value_1core"] = v1
+        out["sample_1core"] = f"{n1} envs, {settle} settling + {steps} timed steps, 1 thread ({sum(t1):.2f} s timed)"
     return out
 
 
 def run_reference(args, ws, rank):
-    """The reference arm: the FP64 oracle on the host cores, same metric.
-    Each timed step advances a bounded sample of the workload by one step."""
+    """The reference arm: the FP64 oracle on the host cores, same metric and
+    the same bounded sample and settled state as the cpu_baseline of the
+    GPU line.  Each timed step advances the sample by one step."""
     if rank != 0:
         return
     E = scenegen.CONFIG_SIZES[args.config]
-    sample_envs = min(E, 512)
-    time_cpu_baseline(args.config, min(sample_envs, 64), 1)        # warm-up (page-in, build)
-    vals = [time_cpu_baseline(args.config, sample_envs, 1, variants=args.variants)["value"]
-            for _ in range(args.steps)]
-    v = statistics.median(vals)
-    cores = os.cpu_count() or 1
+    n = oracle_sample_envs(args.config)
+    v, times, th = oracle_rate(args.config, n, args.settle + args.warmup, args.steps, args.variants)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * E / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded scenegen scenes)",
             "config": {"workload": WORKLOADS[args.config], "n_envs": E, "n_per_call": 1,
-                       "l2": "not applicable (CPU)",
+                       "settle_steps": args.settle, "l2": "not applicable (CPU)",
                        "variants": (dict(VARIANT_PARAMS, restitution=VARIANT_RESTITUTION) if args.variants
                                     else None)},
-            "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{sample_envs} of {E} envs x 1 step per timed step, "
-                                       f"median of {args.steps}, {cores} threads"},
+            "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": th, "kind": "oracle",
+                             "sample": f"{n} of {E} envs, {args.settle + args.warmup} untimed steps, then "
+                                       f"{args.steps} timed steps of one call each, {th} threads"},
             "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -433,6 +453,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--settle", type=int, default=100,
+                    help="untimed calls before the warm-up: every timing starts from the settled workload")
     ap.add_argument("--config", default="arm", choices=sorted(WORKLOADS))
     ap.add_argument("--n-per-call", type=int, default=1)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -478,7 +500,8 @@ def main():
     E = scenegen.CONFIG_SIZES[name]
     sc = make_workload(name, args.variants, seed=None if rank == 0 else 1000 + rank)
     n = args.n_per_call
-    total_calls = args.warmup + args.steps
+    S = args.settle                 # untimed calls that bring the workload to its steady state
+    total_calls = S + args.warmup + args.steps
     acts_np = sc.actions(0, n * total_calls)
     acts = None if acts_np is None else torch.from_numpy(acts_np).to(dev)
     stream = torch.cuda.Stream(device=dev)
@@ -486,6 +509,15 @@ def main():
 
     def act(i):
         return None if acts is None else acts[i * n:(i + 1) * n]
+
+    def settle(bb):
+        """The first S calls, untimed (batched path; the plain path gives
+        bit-identical states), so every timing starts from the same settled
+        state: arms on the floor and at the cube, objects landed."""
+        with torch.cuda.stream(stream):
+            for i in range(S):
+                bb.step(act(i), n, stream=stream, out=None)
+        stream.synchronize()
 
     b = Batch(sc)
     if sc.task is not None:
@@ -496,15 +528,11 @@ def main():
         b.set_tuning(G, W, R)
         tuning = b.tuning()
     elif not args.no_autotune:
-        # tune on a state of the workload (arms moving, objects landed and in
+        # tune on the settled state (arms moving, objects landed and in
         # contact), not on the initial poses: the trials restore this state
-        # after each candidate.  60 steps: dropped objects have landed by then
-        # (tuned on the falling phase, the hulls workload picked a launch
-        # shape 1.5x slower over the run)
-        with torch.cuda.stream(stream):
-            for i in range(min(args.warmup + 60, total_calls)):
-                b.step(act(i), n, stream=stream)
-        stream.synchronize()
+        # after each candidate (tuned on the falling phase, the hulls
+        # workload picked a launch shape 1.5x slower over the run)
+        settle(b)
         tuning = b.autotune(n, cache_path=os.path.join(ROOT, "paper_2410_00425_b300", "tuning_cache.json"),
                             stream=stream)
     else:
@@ -523,9 +551,10 @@ def main():
             bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
         rec = (torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev)
                if sc.task is not None else None)
+        settle(bb)
         with torch.cuda.stream(stream):
             for i in range(args.warmup):
-                bb.step(act(i), n, stream=stream, plain=plain, out=rec)
+                bb.step(act(S + i), n, stream=stream, plain=plain, out=rec)
         stream.synchronize()
         times = []
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -537,7 +566,7 @@ def main():
                 flush.fill_(float(i))                      # L2 flush, outside the events
                 stream.wait_stream(torch.cuda.current_stream())
                 ev[i][0].record(stream)
-                bb.step(act(args.warmup + i), n, stream=stream, plain=plain, out=rec)
+                bb.step(act(S + args.warmup + i), n, stream=stream, plain=plain, out=rec)
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
         barrier(ws)
@@ -546,6 +575,9 @@ def main():
         bb.close()
         return sum(times) / 1e3, times, clk.summary(), code, launches_per_call * args.steps
 
+    from paper_2410_00425_b300 import _ffi as _ffi_peak
+    fp32_flops, _, fp32_s = _ffi_peak.ms_measure_fp32_peak(0.5)
+    fp32_peak = fp32_flops / 1e12
     t_b, times_b, clocks, code, launches = timed(False, 1)
     t_b = reduce_max(t_b, ws)
     value = ws * E * n * args.steps / t_b
@@ -577,16 +609,17 @@ def main():
             h_rec.copy_(d_rec, non_blocking=True)
         else:
             bb.state_to_host(h_state, stream=stream)
+    settle(bb)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            e2e_step(i)
+            e2e_step(S + i)
     stream.synchronize()
     barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
-            e2e_step(args.warmup + i)
+            e2e_step(S + args.warmup + i)
     e1.record(stream)
     stream.synchronize()
     t_e = reduce_max(e0.elapsed_time(e1) / 1e3, ws)
@@ -611,9 +644,10 @@ def main():
         rec = (torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev)
                if sc.task is not None else None)
         reps = min(args.steps, 50)
+        settle(bb)
         with torch.cuda.stream(stream):
             for i in range(args.warmup):
-                bb.step(act(i), n, stream=stream, out=rec)
+                bb.step(act(S + i), n, stream=stream, out=rec)
                 _ffi.ms_render(bb.h, o_rgba, o_depth, o_seg, stream)
         stream.synchronize()
         ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -629,7 +663,7 @@ def main():
             flush.fill_(float(i))
             stream.wait_stream(torch.cuda.current_stream())
             ev_s[i][0].record(stream)
-            bb.step(act(args.warmup + i), n, stream=stream, out=rec)
+            bb.step(act(S + args.warmup + i), n, stream=stream, out=rec)
             _ffi.ms_render(bb.h, o_rgba, o_depth, o_seg, stream)
             ev_s[i][1].record(stream)
         torch.cuda.synchronize()
@@ -652,8 +686,8 @@ def main():
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    fl, _ = algorithmic_flops_per_env_step(name, args.warmup, args.steps, variants=args.variants)
+    unit_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fl, _ = algorithmic_flops_per_env_step(name, S + args.warmup, args.steps, variants=args.variants)
     kernel_s = statistics.mean(times_b) / 1e3
     achieved = fl * E * n / kernel_s / 1e12
     line = {
@@ -661,14 +695,16 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenegen scenes)",
         "config": {"workload": WORKLOADS[name], "n_envs": E, "n_per_call": n, "path": "batched",
-                   "tuning": tuning, "l2": "flushed (256 MB write) before every timed step",
+                   "settle_steps": S * n, "tuning": tuning, "l2": "flushed (256 MB write) before every timed step",
                    "variants": (dict(VARIANT_PARAMS, restitution=VARIANT_RESTITUTION) if args.variants else None)},
         "plain_value": plain_value,
         "batched_over_plain": None if not plain_value else value / plain_value,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": ncu_traffic(name, tuning, args.variants),
-                     "peak_note": f"FP32 FMA peak = {props.multi_processor_count} SMs x 128 lanes x 2 x "
-                                  f"{sm_max:.0f} MHz (unit counts and max clock)",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": ncu_traffic(name, tuning, args.variants),
+                     "peak_note": f"measured FP32 FMA rate of this GPU (ms_measure_fp32_peak: 8 dependent-FMA "
+                                  f"chains per thread, full occupancy, {fp32_s:.2f} s); from unit counts "
+                                  f"{props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz = "
+                                  f"{unit_tflops:.1f} TFLOP/s",
                      "flops_per_env_step": fl},
         "e2e": {"value": ws * E * n * args.steps / t_e, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -688,7 +724,8 @@ def main():
                           "overload_10k_merged": serve_run(10000, 3.0, True, pools=pools),
                           "overload_10k_one_launch_per_request": serve_run(10000, 3.0, False, pools=pools)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_cpu_baseline(name, min(E, 4096), 20, one_core=True, variants=args.variants)
+        line["cpu_baseline"] = time_cpu_baseline(name, S * n + args.warmup, 20, one_core=True,
+                                                 variants=args.variants)
     print(json.dumps(line), flush=True)
 
 

@@ -470,10 +470,17 @@ ms_status ms_measure_fp32_peak(double seconds, double* flops_per_s, int* sm_coun
  *     and w unused; v.w receives the inverse mass).  q must hold unit
  *     quaternions.
  *   targets: float [n_joints] drive targets, read and written in place.
- *   status: uint32 [n_envs] status bits (MS_ENV_*), read and written; an env
- *     whose counts exceed the maxima below or whose joints name bodies out
- *     of range gets MS_ENV_INVALID and is left untouched.  The offsets must
- *     lie inside the caller's arrays.
+ *   status: uint32 [n_envs] status bits (MS_ENV_*), read and written.  An
+ *     env whose counts exceed the maxima below, or whose descriptors break a
+ *     rule ms_create_batch enforces (a body type other than sphere, capsule,
+ *     box or plane; a shape size not > 0; a negative or non-finite mass or
+ *     mu; restitution outside [0, 1]; a joint of unknown type, naming bodies
+ *     out of range or itself, with non-finite frames or limits or gains,
+ *     lower > upper, a negative gain or a zero frame quaternion) gets
+ *     MS_ENV_INVALID and is skipped whole: its x, q, v, w, targets are left
+ *     untouched.  The bit is or-ed into the word and stays set -- the env
+ *     stays skipped -- until the caller clears status[env]; so does
+ *     MS_ENV_NAN.  The offsets must lie inside the caller's arrays.
  *   max_bodies_per_env in [1, 64] and max_joints_per_env in [0, 512] bound
  *   every env; actions rows are max_joints_per_env wide. */
 typedef struct {
@@ -496,7 +503,11 @@ typedef struct {
  * fixed arena), or a control loop that cannot afford an allocation's
  * implicit synchronisation and latency.  It advances every env n_steps
  * steps with the same stages and results as ms_step, on `stream`, calling no
- * cudaMalloc, cudaFree or allocating library routine.
+ * cudaMalloc, cudaFree or allocating library routine.  It covers primitive
+ * shapes only: no hull library, no warm start across steps (no memory
+ * between calls; warm_start = 1 is rejected), no pick task and no contact
+ * forces or contact record.  The inertia of each body is derived from its
+ * descriptor by ms_create_batch's formula.
  *
  * The kernel's workspace is a fixed 32 MiB array inside the library, held by
  * every GPU that loads the library until the process exits.  A call whose

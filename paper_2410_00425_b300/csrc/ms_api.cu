@@ -166,27 +166,9 @@ static bool finite3(const float* v, int n) {
 
 // Body-frame principal inertia of a uniform solid of the given mass.
 static void body_inertia(const ms_body_desc& d, float out[3]) {
-    double m = d.mass;
-    if (d.type == MS_SPHERE) {
-        double r = d.p[0];
-        out[0] = out[1] = out[2] = (float)(0.4 * m * r * r);
-    } else if (d.type == MS_BOX) {
-        double x = d.p[0], y = d.p[1], z = d.p[2];
-        out[0] = (float)(m * (y * y + z * z) / 3.0);
-        out[1] = (float)(m * (x * x + z * z) / 3.0);
-        out[2] = (float)(m * (x * x + y * y) / 3.0);
-    } else {  // capsule along z: cylinder of length 2l + two hemispherical caps
-        const double pi = 3.14159265358979323846;
-        double r = d.p[0], l = d.p[1];
-        double vcyl = 2.0 * pi * r * r * l, vsph = 4.0 * pi * r * r * r / 3.0;
-        double mcyl = m * vcyl / (vcyl + vsph), msph = m - mcyl;
-        // a cap's centroid lies 3r/8 past the segment end; about the capsule
-        // centre each cap contributes m_cap (2r^2/5 + l^2 + 3lr/4)
-        double ixx = mcyl * (3.0 * r * r + 4.0 * l * l) / 12.0 + msph * (0.4 * r * r + l * l + 0.75 * l * r);
-        double izz = 0.5 * mcyl * r * r + 0.4 * msph * r * r;
-        out[0] = out[1] = (float)ixx;
-        out[2] = (float)izz;
-    }
+    double I[3];
+    primitive_inertia(d.type, d.mass, d.p[0], d.p[1], d.p[2], I);
+    for (int k = 0; k < 3; k++) out[k] = (float)I[k];
 }
 
 // ------------------------------------------------------------------- hulls
@@ -294,42 +276,18 @@ static ms_status validate_env(int e, const ms_body_desc* bd, int nb, const ms_jo
     if (nj < 0 || nj > 512) return fail(MS_ERR_INVALID_ARG, "env %d: n_joints %d not in [0, 512]", e, nj);
     if (!bd) return fail(MS_ERR_INVALID_ARG, "env %d: bodies is NULL", e);
     if (nj > 0 && !jd) return fail(MS_ERR_INVALID_ARG, "env %d: joints is NULL", e);
+    static const char* body_rule[] = {"", "bad type", "hull index not in the library", "non-finite field",
+                                      "zero quaternion", "negative mass", "negative mu", "restitution not in [0, 1]",
+                                      "shape size must be > 0"};
+    static const char* joint_rule[] = {"", "bad type", "bad parent/child", "non-finite field", "lower > upper",
+                                       "negative gain", "zero frame quaternion"};
     for (int i = 0; i < nb; i++) {
-        const ms_body_desc& d = bd[i];
-        if (d.type < MS_SPHERE || d.type > MS_HULL) return fail(MS_ERR_INVALID_ARG, "env %d body %d: bad type %d", e, i, d.type);
-        if (d.type == MS_HULL && !(d.p[0] >= 0.f && d.p[0] < (float)n_hulls && d.p[0] == std::floor(d.p[0])))
-            return fail(MS_ERR_INVALID_ARG, "env %d body %d: hull index %g not in the library (%d hulls)", e, i, d.p[0],
-                        n_hulls);
-        if (!finite3(d.pos, 3) || !finite3(d.quat, 4) || !finite3(d.linvel, 3) || !finite3(d.angvel, 3) ||
-            !std::isfinite(d.mass) || !std::isfinite(d.mu))
-            return fail(MS_ERR_INVALID_ARG, "env %d body %d: non-finite field", e, i);
-        double qn = (double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] + (double)d.quat[2] * d.quat[2] +
-                    (double)d.quat[3] * d.quat[3];
-        if (qn < 1e-12) return fail(MS_ERR_INVALID_ARG, "env %d body %d: zero quaternion", e, i);
-        if (d.mass < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mass", e, i);
-        if (d.mu < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d body %d: negative mu", e, i);
-        if (!(d.restitution >= 0.f && d.restitution <= 1.f))
-            return fail(MS_ERR_INVALID_ARG, "env %d body %d: restitution not in [0, 1]", e, i);
-        int need = d.type == MS_SPHERE ? 1 : (d.type == MS_CAPSULE ? 2 : (d.type == MS_BOX ? 3 : 0));
-        for (int k = 0; k < need; k++)
-            if (!(d.p[k] > 0.f) || !std::isfinite(d.p[k]))
-                return fail(MS_ERR_INVALID_ARG, "env %d body %d: shape size p[%d] must be > 0", e, i, k);
+        int r = body_desc_check(bd[i], n_hulls, true);
+        if (r) return fail(MS_ERR_INVALID_ARG, "env %d body %d: %s", e, i, body_rule[r]);
     }
     for (int j = 0; j < nj; j++) {
-        const ms_joint_desc& d = jd[j];
-        if (d.type != MS_REVOLUTE && d.type != MS_PRISMATIC) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: bad type", e, j);
-        if (d.parent < -1 || d.parent >= nb || d.child < 0 || d.child >= nb || d.parent == d.child)
-            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: bad parent/child %d/%d", e, j, d.parent, d.child);
-        if (!finite3(d.parent_frame, 7) || !finite3(d.child_frame, 7) || !std::isfinite(d.lower) ||
-            !std::isfinite(d.upper) || !std::isfinite(d.kp) || !std::isfinite(d.kd) || !std::isfinite(d.target0))
-            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: non-finite field", e, j);
-        if (d.lower > d.upper) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: lower > upper", e, j);
-        if (d.kp < 0.f || d.kd < 0.f) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: negative gain", e, j);
-        const float* qa = d.parent_frame + 3;
-        const float* qb = d.child_frame + 3;
-        if (qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3] < 1e-12f ||
-            qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3] < 1e-12f)
-            return fail(MS_ERR_INVALID_ARG, "env %d joint %d: zero frame quaternion", e, j);
+        int r = joint_desc_check(jd[j], nb);
+        if (r) return fail(MS_ERR_INVALID_ARG, "env %d joint %d: %s", e, j, joint_rule[r]);
     }
     return MS_OK;
 }

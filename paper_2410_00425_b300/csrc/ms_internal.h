@@ -67,6 +67,78 @@ struct DevParams {
     float j_rate, j_ms, j_is, j_ims;     // joint equality rows
 };
 
+// Principal inertia (body frame) of a uniform solid primitive of mass m:
+// sphere radius p0; box half-extents p0, p1, p2; capsule radius p0 and
+// half-length p1 along z -- a cylinder of length 2 p1 and two hemispherical
+// caps whose centroids sit 3 p0 / 8 past the segment ends (parallel-axis
+// theorem).  The one formula of ms_create_batch and ms_step_noalloc.
+__host__ __device__ inline void primitive_inertia(int type, double m, double p0, double p1, double p2, double I[3]) {
+    if (type == MS_SPHERE) {
+        I[0] = I[1] = I[2] = 0.4 * m * p0 * p0;
+    } else if (type == MS_BOX) {
+        I[0] = m * (p1 * p1 + p2 * p2) / 3.0;
+        I[1] = m * (p0 * p0 + p2 * p2) / 3.0;
+        I[2] = m * (p0 * p0 + p1 * p1) / 3.0;
+    } else {
+        const double pi = 3.14159265358979323846;
+        double r = p0, l = p1;
+        double vcyl = 2.0 * pi * r * r * l, vsph = 4.0 * pi * r * r * r / 3.0;
+        double mcyl = m * vcyl / (vcyl + vsph), msph = m - mcyl;
+        // about the capsule centre each cap contributes m_cap (2r^2/5 + l^2 + 3lr/4)
+        I[0] = I[1] = mcyl * (3.0 * r * r + 4.0 * l * l) / 12.0 + msph * (0.4 * r * r + l * l + 0.75 * l * r);
+        I[2] = 0.5 * mcyl * r * r + 0.4 * msph * r * r;
+    }
+}
+
+__host__ __device__ inline bool finite_f(float x) { return x == x && x - x == 0.f; }
+
+// Per-field checks of a body descriptor, the rules ms_create_batch and
+// ms_step_noalloc share (0: valid; otherwise which rule failed, BD_*).
+// state: also the pose and velocity fields (read by ms_create_batch only);
+// n_hulls: hulls in the batch's library (0: a hull body is invalid).
+enum { BD_TYPE = 1, BD_HULL, BD_NONFINITE, BD_QUAT, BD_MASS, BD_MU, BD_RESTITUTION, BD_SIZE };
+__host__ __device__ inline int body_desc_check(const ms_body_desc& d, int n_hulls, bool state) {
+    if (d.type < MS_SPHERE || d.type > MS_HULL) return BD_TYPE;
+    if (d.type == MS_HULL && !(d.p[0] >= 0.f && d.p[0] < (float)n_hulls && d.p[0] == (float)(int)d.p[0]))
+        return BD_HULL;
+    if (!finite_f(d.mass) || !finite_f(d.mu)) return BD_NONFINITE;
+    if (state) {
+        for (int k = 0; k < 3; k++)
+            if (!finite_f(d.pos[k]) || !finite_f(d.linvel[k]) || !finite_f(d.angvel[k])) return BD_NONFINITE;
+        for (int k = 0; k < 4; k++)
+            if (!finite_f(d.quat[k])) return BD_NONFINITE;
+        double qn = (double)d.quat[0] * d.quat[0] + (double)d.quat[1] * d.quat[1] + (double)d.quat[2] * d.quat[2] +
+                    (double)d.quat[3] * d.quat[3];
+        if (qn < 1e-12) return BD_QUAT;
+    }
+    if (d.mass < 0.f) return BD_MASS;
+    if (d.mu < 0.f) return BD_MU;
+    if (!(d.restitution >= 0.f && d.restitution <= 1.f)) return BD_RESTITUTION;
+    int need = d.type == MS_SPHERE ? 1 : (d.type == MS_CAPSULE ? 2 : (d.type == MS_BOX ? 3 : 0));
+    for (int k = 0; k < need; k++)
+        if (!(d.p[k] > 0.f) || !finite_f(d.p[k])) return BD_SIZE;
+    return 0;
+}
+
+// The same for a joint of an env of nb bodies (JD_*).
+enum { JD_TYPE = 1, JD_BODIES, JD_NONFINITE, JD_LIMITS, JD_GAINS, JD_QUAT };
+__host__ __device__ inline int joint_desc_check(const ms_joint_desc& d, int nb) {
+    if (d.type != MS_REVOLUTE && d.type != MS_PRISMATIC) return JD_TYPE;
+    if (d.parent < -1 || d.parent >= nb || d.child < 0 || d.child >= nb || d.parent == d.child) return JD_BODIES;
+    for (int k = 0; k < 7; k++)
+        if (!finite_f(d.parent_frame[k]) || !finite_f(d.child_frame[k])) return JD_NONFINITE;
+    if (!finite_f(d.lower) || !finite_f(d.upper) || !finite_f(d.kp) || !finite_f(d.kd) || !finite_f(d.target0))
+        return JD_NONFINITE;
+    if (d.lower > d.upper) return JD_LIMITS;
+    if (d.kp < 0.f || d.kd < 0.f) return JD_GAINS;
+    const float* qa = d.parent_frame + 3;
+    const float* qb = d.child_frame + 3;
+    if (qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3] < 1e-12f ||
+        qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3] < 1e-12f)
+        return JD_QUAT;
+    return 0;
+}
+
 // Soft-row parameters are finite and >= 0 (host).
 inline bool soft_params_ok(const ms_sim_params* p) {
     const float v[4] = {p->contact_hertz, p->contact_damping_ratio, p->joint_hertz, p->joint_damping_ratio};

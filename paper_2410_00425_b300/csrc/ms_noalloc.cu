@@ -58,28 +58,14 @@ __device__ __forceinline__ float4 desc_quat(const float* q) {
     return make_float4((float)(q[0] / n), (float)(q[1] / n), (float)(q[2] / n), (float)(q[3] / n));
 }
 
-// 1/I (body frame) and 1/m of a descriptor, in double like ms_create_batch
+// 1/I (body frame) and 1/m of a descriptor: the inertia formula of
+// ms_create_batch (primitive_inertia), in double
 __device__ __forceinline__ float4 desc_inverse_mass(const ms_body_desc& d, bool dyn) {
     if (!dyn) return make_float4(0.f, 0.f, 0.f, 0.f);
-    double m = d.mass;
-    float I0, I1, I2;
-    if (d.type == MS_SPHERE) {
-        double r = d.p[0];
-        I0 = I1 = I2 = (float)(0.4 * m * r * r);
-    } else if (d.type == MS_BOX) {
-        double x = d.p[0], y = d.p[1], z = d.p[2];
-        I0 = (float)(m * (y * y + z * z) / 3.0);
-        I1 = (float)(m * (x * x + z * z) / 3.0);
-        I2 = (float)(m * (x * x + y * y) / 3.0);
-    } else {
-        const double pi = 3.14159265358979323846;
-        double r = d.p[0], l = d.p[1];
-        double vcyl = 2.0 * pi * r * r * l, vsph = 4.0 * pi * r * r * r / 3.0;
-        double mcyl = m * vcyl / (vcyl + vsph), msph = m - mcyl;
-        I0 = I1 = (float)(mcyl * (3.0 * r * r + 4.0 * l * l) / 12.0 + msph * (0.4 * r * r + l * l + 0.75 * l * r));
-        I2 = (float)(0.5 * mcyl * r * r + 0.4 * msph * r * r);
-    }
-    return make_float4(1.f / I0, 1.f / I1, 1.f / I2, (float)(1.0 / m));
+    double I[3];
+    primitive_inertia(d.type, d.mass, d.p[0], d.p[1], d.p[2], I);
+    float I0 = (float)I[0], I1 = (float)I[1], I2 = (float)I[2];
+    return make_float4(1.f / I0, 1.f / I1, 1.f / I2, (float)(1.0 / (double)d.mass));
 }
 
 // Same stages and lockstep env loop as the batched kernel; the env's
@@ -135,14 +121,20 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
             // counts exceed the declared maxima would overrun its slot
             if (nb < 1 || nb > D.max_nb || nj < 0 || nj > D.max_nj) { invalid = true; nb = 0; nj = 0; }
         }
-        // primitives only (no hull library here): any other type invalidates the env
-        bool badtype = false;
-        int nbm = g.wmax(nb);
+        // every field the step reads, checked by the rules ms_create_batch
+        // applies (no hull library here: a hull body is invalid), before
+        // anything of the env is loaded; an invalid env is skipped whole
+        bool bad = false;
+        int nbm = g.wmax(nb), njm = g.wmax(nj);
         for (int i0 = 0; i0 < nbm; i0 += G) {
             int i = i0 + g.lane;
-            if (i < nb) { int t = D.bodies[b0 + i].type; badtype |= t < MS_SPHERE || t > MS_PLANE; }
+            if (i < nb) bad |= body_desc_check(D.bodies[b0 + i], 0, false) != 0;
         }
-        if (g.any(badtype)) { invalid = true; nb = 0; nj = 0; }
+        for (int k0 = 0; k0 < njm; k0 += G) {
+            int j = k0 + g.lane;
+            if (j < nj) bad |= joint_desc_check(D.joints[j0 + j], nb) != 0;
+        }
+        if (g.any(bad)) { invalid = true; nb = 0; nj = 0; }
         int nbmax = g.wmax(nb), njmax = g.wmax(nj);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
@@ -177,14 +169,13 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
                 jf[4 * j + 3] = desc_quat(d.child_frame + 3);
                 jp[j] = make_float4(d.lower, d.upper, d.kp, d.kd);
                 jm[j] = make_int4(d.type, d.parent, d.child, 0);
-                bool ok = (d.type == MS_REVOLUTE || d.type == MS_PRISMATIC) && d.parent >= -1 && d.parent < nb &&
-                          d.child >= 0 && d.child < nb && d.parent != d.child;
-                invalid |= !ok;
                 e.jt[j] = D.targets[j0 + j];
             }
         }
-        bool bad = g.any(invalid);
-        if (g.lane == 0) *e.status = active ? (D.status[env] | (bad ? (unsigned)MS_ENV_INVALID : 0u)) : 0u;
+        // MS_ENV_INVALID is or-ed into the caller's status word and stays
+        // set (the env is skipped) until the caller clears it
+        bool inv = g.any(invalid);
+        if (g.lane == 0) *e.status = active ? (D.status[env] | (inv ? (unsigned)MS_ENV_INVALID : 0u)) : 0u;
         g.sync();
         bool frozen = (*e.status & (ST_NAN | MS_ENV_INVALID)) != 0;
         e.nb = frozen ? 0 : nb;
