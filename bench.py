@@ -152,14 +152,24 @@ class ClockSampler:
         self.stop = threading.Event()
 
     def _nvml_handle(self):
+        """The NVML handle of this process's CUDA device: by UUID, else by PCI
+        bus id, else by index (NVML ignores CUDA_VISIBLE_DEVICES)."""
         import pynvml
         import torch
         pynvml.nvmlInit()
         p = torch.cuda.get_device_properties(self.index)
-        bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        uuid = getattr(p, "uuid", None)
+        if uuid is not None:
+            u = str(uuid)
+            for cand in (u if u.startswith("GPU-") else "GPU-" + u, u):
+                try:
+                    return pynvml, pynvml.nvmlDeviceGetHandleByUUID(cand.encode())
+                except Exception:
+                    pass
         try:
+            bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
             return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
-        except pynvml.NVMLError:
+        except Exception:
             return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
 
     def _poll_nvml(self):
@@ -216,7 +226,8 @@ class ClockSampler:
         sm = [x[0] for x in self.samples]
         reasons = set().union(*[x[2] for x in self.samples])
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
-                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml" if self.nvml else "nvidia-smi"}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml" if self.nvml else "nvidia-smi",
+                "window": "the settling, warm-up and timed steps of the batched timing (one kernel, one load)"}
 
 
 def dist_setup():
@@ -326,14 +337,18 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, pools=None, life_mean=500.0):
+def serve_run(rate, duration, merge, seed=5, n_sessions=128, budget=120 << 30, pools=None, life_mean=50.0,
+              max_inflight=32, openers=4):
     """Open-loop Poisson load on the step server.
 
     Sessions own 1..1024 envs (log-uniform) of a scene type drawn uniformly
     from {arm, clutter, hand}, live for a geometric number of requests (mean
     life_mean, an episode) and are replaced by fresh sessions; each request
-    steps its session once with fresh drive targets.  Returns latency percentiles (host
-    arrival -> completion) and the env-steps/s the server sustained."""
+    steps its session once with fresh drive targets.  A closed session's
+    replacement is opened by one of `openers` client threads (session
+    creation, admission and upload are part of the served work).  Returns
+    latency percentiles (host arrival -> completion) and the env-steps/s the
+    server sustained."""
     import queue as _q
     from paper_2410_00425_b300.server import Server
     g = np.random.default_rng(seed)
@@ -341,7 +356,7 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
     if pools is None:
         pools = {t: scenegen.make_scene(t, n_envs=1024) for t in types}
     act_pool = {t: (pools[t].actions(0, 8) if pools[t].n_act else None) for t in types}
-    srv = Server(budget, merge=merge)
+    srv = Server(budget, merge=merge, max_inflight=max_inflight)
     g_open = np.random.default_rng(seed + 1)      # the opener thread's own generator
 
     def new_session(g):
@@ -365,32 +380,38 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
     # replacement sessions are cut from the pools before the timed region, so
     # the opener thread only makes the (GIL-free) library calls
     spare = []
-    for _ in range(int(rate * duration / 40) + 64):
+    for _ in range(int(rate * duration / max(life_mean, 1.0) * 1.5) + 64):
         t = types[int(g_open.integers(0, 3))]
         n = max(1, min(1024, int(np.exp(g_open.uniform(0.0, np.log(1024.0))))))
         a0 = int(g_open.integers(0, 1024 - n + 1))
         spare.append((t, a0, n, pools[t].subset(range(a0, a0 + n)), int(g_open.geometric(1.0 / life_mean))))
 
     open_s = []
+    spare_it = iter(spare)
+    spare_mu = threading.Lock()
 
     def opener():
-        k = 0
         while not stop.is_set():
             try:
                 sid = closing.get(timeout=0.05)
             except _q.Empty:
                 continue
             srv.close_session(sid)
-            if k < len(spare):
-                t, a0, n, sc, life = spare[k]
-                k += 1
+            with spare_mu:
+                nxt_spare = next(spare_it, None)
+            if nxt_spare is not None:
+                t, a0, n, sc, life = nxt_spare
                 t_open = time.perf_counter()
                 sid2 = srv.open(sc)
                 open_s.append(time.perf_counter() - t_open)
                 if sid2 is not None:
                     repl.put([sid2, t, a0, n, life])
-    th = threading.Thread(target=opener, daemon=True)
-    th.start()
+    # the arrival loop and the openers share the interpreter: switch often
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(2e-4)
+    ths = [threading.Thread(target=opener, daemon=True) for _ in range(max(1, openers))]
+    for th in ths:
+        th.start()
     # warm-up: one request per session (first launches, graph capture)
     for s_ in active:
         srv.submit(s_[0], None)
@@ -412,8 +433,12 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
             if submitted - srv.stats()["requests_done"] > 2.0 * rate:
                 saturated = True
                 break
-        while time.perf_counter() < nxt:
-            pass
+        while True:                      # sleep to the arrival, spin the last 0.2 ms
+            left = nxt - time.perf_counter()
+            if left <= 0:
+                break
+            if left > 3e-4:
+                time.sleep(left - 2e-4)
         while not repl.empty():
             active.append(repl.get())
         arrivals += 1
@@ -433,7 +458,9 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
     wall = time.perf_counter() - t0
     st = srv.stats()
     stop.set()
-    th.join()
+    for th in ths:
+        th.join()
+    sys.setswitchinterval(old_switch)
     srv.close()
     return {"rate_req_s": rate, "duration_s": duration, "merge": merge, "arrivals": arrivals,
             "lost_no_session": no_session, "requests": int(st["requests_done"]),
@@ -445,7 +472,7 @@ def serve_run(rate, duration, merge, seed=5, n_sessions=32, budget=120 << 30, po
             "launch_p99_ms": 1e3 * st["launch_p99"], "launch_max_ms": 1e3 * st["launch_max"],
             "queue_p50_ms": 1e3 * st["queue_p50"], "queue_p99_ms": 1e3 * st["queue_p99"],
             "stage_p99_ms": 1e3 * st["stage_p99"], "stage_max_ms": 1e3 * st["stage_max"], "life_mean": life_mean,
-            "saturated": saturated}
+            "max_inflight": max_inflight, "sessions": n_sessions, "openers": openers, "saturated": saturated}
 
 
 def main():
@@ -465,7 +492,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving sweep only (rates x merge modes)")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000", help="arrival rates (requests/s) of --serve")
-    ap.add_argument("--serve-life", type=float, default=500.0, help="mean session lifetime (requests) of --serve")
+    ap.add_argument("--serve-life", type=float, default=50.0, help="mean session lifetime (requests) of --serve")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-render", action="store_true", help="skip the camera-rendering measurement")
     ap.add_argument("--variants", action="store_true",
@@ -551,6 +578,8 @@ def main():
             bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
         rec = (torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev)
                if sc.task is not None else None)
+        clk = ClockSampler(local)
+        clk.__enter__()
         settle(bb)
         with torch.cuda.stream(stream):
             for i in range(args.warmup):
@@ -561,7 +590,7 @@ def main():
               for _ in range(args.steps)]
         barrier(ws)
         torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
+        try:
             for i in range(args.steps):
                 flush.fill_(float(i))                      # L2 flush, outside the events
                 stream.wait_stream(torch.cuda.current_stream())
@@ -569,6 +598,8 @@ def main():
                 bb.step(act(S + args.warmup + i), n, stream=stream, plain=plain, out=rec)
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
+        finally:
+            clk.__exit__(None, None, None)
         barrier(ws)
         times = [a.elapsed_time(z) for a, z in ev]
         code, status = bb.sync()
@@ -687,7 +718,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     unit_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    fl, _ = algorithmic_flops_per_env_step(name, S + args.warmup, args.steps, variants=args.variants)
+    fl, _ = algorithmic_flops_per_env_step(name, (S + args.warmup) * n, args.steps * n, variants=args.variants)
     kernel_s = statistics.mean(times_b) / 1e3
     achieved = fl * E * n / kernel_s / 1e12
     line = {
@@ -724,7 +755,7 @@ def main():
                           "overload_10k_merged": serve_run(10000, 3.0, True, pools=pools),
                           "overload_10k_one_launch_per_request": serve_run(10000, 3.0, False, pools=pools)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_cpu_baseline(name, S * n + args.warmup, 20, one_core=True,
+        line["cpu_baseline"] = time_cpu_baseline(name, S * n + args.warmup, 100, one_core=True,
                                                  variants=args.variants)
     print(json.dumps(line), flush=True)
 

@@ -38,7 +38,7 @@ typedef struct {
     int32_t merge;              /* 1: merge pending requests into one launch; 0: one launch per request */
     int32_t max_requests;       /* at most this many requests per merged launch (<= 0: no limit) */
     double coalesce_us;         /* after the first pending request, wait up to this long for more */
-    int32_t max_inflight;       /* launches running at once, 1..64 (0: 4) */
+    int32_t max_inflight;       /* launches running at once, 1..64 (0: 16) */
 } ms_server_options;
 
 typedef struct {

@@ -696,6 +696,16 @@ extern "C" ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, 
     return MS_OK;
 }
 
+ms_status ms::batch_step_eager(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
+    ms_status s = check_step_args(b, n_steps);
+    if (s) return s;
+    if (n_steps == 0) return MS_OK;
+    if ((s = configure_fused(b)) != MS_OK) return s;
+    if ((s = enqueue_fused(b, actions, n_steps, nullptr, st)) != MS_OK) return s;
+    CK(cudaEventRecord(b->done, st));
+    return MS_OK;
+}
+
 extern "C" ms_status ms_step(ms_batch* b, const float* actions, int n_steps, void* stream) {
     return ms_step_ex(b, actions, n_steps, nullptr, 0, stream);
 }

@@ -265,6 +265,9 @@ const DevBatch& batch_dev(const ::ms_batch* b);
 void batch_dims(const ::ms_batch* b, int* E, int* A, int* max_nb, int* max_nj);
 // true when ms_step(b, ., n_steps, stream) will replay a graph (no capture)
 bool batch_has_graph(const ::ms_batch* b, int n_steps);
+// ms_step without a CUDA graph (queue reset + launch enqueued directly): for
+// short-lived batches, where capturing a graph per batch costs more than it saves
+ms_status batch_step_eager(::ms_batch* b, const float* actions, int n_steps, cudaStream_t stream);
 void launch_unpack_state(const DevBatch& D, const float* in, const uint8_t* mask, const int* body_env,
                          cudaStream_t s);
 

@@ -203,11 +203,24 @@ int bucket(int v, std::initializer_list<int> sizes) {
     return v;
 }
 
+// Requests whose sessions fall in one cost class are merged into one launch:
+// the solver's sweeps per step and the bucketed env size (the same buckets
+// as a merged launch's workspace layout), so the envs of a launch take
+// similar time.
+uint64_t cost_class(const Session* se) {
+    uint64_t k = (uint64_t)se->p.substeps;
+    k = k * 4099 + (uint64_t)(se->p.pos_iters + 1) * 131 + (uint64_t)se->p.vel_iters;
+    k = k * 131 + (uint64_t)bucket(se->max_nb, {4, 8, 12, 16, 24, 32, 48, 64});
+    k = k * 131 + (uint64_t)bucket(se->max_nj, {0, 4, 8, 12, 16, 24, 32, 48, 64});
+    k = k * 2053 + (uint64_t)bucket(se->p.contact_capacity, {8, 16, 32, 64, 128, 256, 512, 1024});
+    return k;
+}
+
 }  // namespace
 
 struct ms_server {
     size_t budget = 0, used = 0;
-    ms_server_options opt{1, 0, 0.0, 4};
+    ms_server_options opt{1, 0, 0.0, 16};
     int device = 0, sm_count = 0, smem_optin = 0;
     std::mutex mu;
     // Serialises the worker's stream captures with the client threads'
@@ -436,14 +449,9 @@ static int launch_single(ms_server* s, Slot& sl) {
         cudaMemcpyAsync(sl.d_act, sl.h_act, r->act.size() * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
         act = sl.d_act;
     }
-    int st;
-    if (batch_has_graph(se->b, 1)) {
-        st = ms_step(se->b, act, 1, sl.stream);
-    } else {                                  // the first step of a session captures its graph
-        std::lock_guard<std::mutex> dk(s->dev_mu);
-        st = ms_step(se->b, act, 1, sl.stream);
-        s->graph_captures++;
-    }
+    // sessions are short-lived (tens of requests): launched directly, no
+    // graph captured per session
+    int st = batch_step_eager(se->b, act, 1, sl.stream);
     if (st) return st;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return sfail(MS_ERR_CUDA, "event record failed");
     sl.envs = se->E;
@@ -493,18 +501,22 @@ static void worker_loop(ms_server* s) {
             progress = true;
         }
         if (progress) s->done_cv.notify_all();
-        // 2. start a launch on a free slot: pending requests in arrival
-        //    order, at most one per session, none of a running session
-        Slot* free_slot = nullptr;
+        // 2. start launches on the free slots: pending requests in arrival
+        //    order, at most one per session, none of a running session.
+        //    Merged: requests of one cost class (solver settings and size
+        //    bucket, see cost_class) share a launch, one launch per class --
+        //    a launch lasts as long as its slowest env, so a light session
+        //    never waits on a heavy one.  Unmerged: one launch per request.
+        std::vector<Slot*> free_slots;
         for (auto& sl : s->slots)
-            if (!sl.busy) { free_slot = &sl; break; }
+            if (!sl.busy) free_slots.push_back(&sl);
         bool wait_coalesce = false;
-        if (free_slot && !s->pending.empty() && s->opt.coalesce_us > 0.0 && !s->stop) {
+        if (!free_slots.empty() && !s->pending.empty() && s->opt.coalesce_us > 0.0 && !s->stop) {
             const Req& first = s->reqs[s->pending.front()];
             wait_coalesce = now_s() < first.t_arrive + s->opt.coalesce_us * 1e-6;
         }
-        if (free_slot && !s->pending.empty() && !wait_coalesce) {
-            std::vector<std::pair<Req*, Session*>> batch;
+        if (!free_slots.empty() && !s->pending.empty() && !wait_coalesce) {
+            std::vector<std::pair<uint64_t, std::vector<std::pair<Req*, Session*>>>> groups;
             std::deque<uint64_t> keep;
             while (!s->pending.empty()) {
                 uint64_t t = s->pending.front();
@@ -517,16 +529,22 @@ static void worker_loop(ms_server* s) {
                     continue;
                 }
                 Session* se = sit->second;
-                bool full = (s->opt.max_requests > 0 && (int)batch.size() >= s->opt.max_requests) ||
-                            (!s->opt.merge && !batch.empty());
-                if (se->running || full) { keep.push_back(t); continue; }
+                if (se->running) { keep.push_back(t); continue; }
+                uint64_t k = s->opt.merge ? cost_class(se) : t;
+                size_t gi = 0;
+                while (gi < groups.size() && groups[gi].first != k) gi++;
+                bool full = gi < groups.size() ? (!s->opt.merge || (s->opt.max_requests > 0 &&
+                                                                    (int)groups[gi].second.size() >= s->opt.max_requests))
+                                               : groups.size() >= free_slots.size();
+                if (full) { keep.push_back(t); continue; }
+                if (gi == groups.size()) groups.emplace_back(k, std::vector<std::pair<Req*, Session*>>());
                 se->running = true;
-                batch.emplace_back(&r, se);
+                groups[gi].second.emplace_back(&r, se);
             }
             s->pending = std::move(keep);
-            if (!batch.empty()) {
-                Slot& sl = *free_slot;
-                sl.batch = std::move(batch);
+            for (size_t gi = 0; gi < groups.size(); gi++) {
+                Slot& sl = *free_slots[gi];
+                sl.batch = std::move(groups[gi].second);
                 sl.busy = true;
                 sl.status = MS_OK;
                 sl.envs = 0;
@@ -566,7 +584,7 @@ extern "C" ms_status ms_server_create(size_t budget, const ms_server_options* op
     ms_server* s = new ms_server();
     s->budget = budget;
     if (opt) s->opt = *opt;
-    if (s->opt.max_inflight == 0) s->opt.max_inflight = 4;
+    if (s->opt.max_inflight == 0) s->opt.max_inflight = 16;
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
     cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
