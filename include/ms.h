@@ -410,12 +410,19 @@ ms_status ms_contact_forces(ms_batch* b, float* out, void* stream);
 
 /* Batched-path launch shape.  lanes_per_env in {1, 2, 4, 8, 16, 32}: a warp
  * steps 32 / lanes_per_env envs in lockstep; warps_per_cta in [1, 8];
- * rows_in_smem: 1 keeps every constraint row in shared memory when one
- * CTA fits (else as 0); 0 keeps the joint rows in shared memory together
- * with the rows of as many contact points per env as leave enough CTAs
- * resident for all envs to be in flight at once, the other contact rows in
- * an L2-resident global slot per lane group.  Any choice gives
- * bit-identical results. */
+ * rows_in_smem (placement of the constraint lists, impulses and rows):
+ *   1  every row in shared memory when one CTA fits (else as 0);
+ *   0  per-env slots sized for the capacities (lists, impulses, joint rows
+ *      and the rows of as many contact points as leave enough CTAs resident
+ *      for all envs to be in flight at once) when that holds every contact
+ *      point; otherwise the dynamic placement at that residency: each warp's
+ *      envs share a shared-memory arena, handed out after every step's
+ *      narrowphase by the counts of that step (lists and impulses first,
+ *      then joint rows, then contact rows levelled across the envs);
+ *   2  the dynamic placement with one CTA per SM.
+ * Whatever is not in shared memory stays in an L2-resident global slot per
+ * lane group.  Any choice gives bit-identical results; other values of
+ * rows_in_smem are MS_ERR_INVALID_ARG. */
 typedef struct {
     int32_t lanes_per_env;
     int32_t warps_per_cta;

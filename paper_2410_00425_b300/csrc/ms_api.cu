@@ -562,18 +562,26 @@ static ms_status configure_fused(ms_batch* b) {
         if (fused_occupancy(t.G, b->fused_lean, threads, sm, &n) != cudaSuccess) return 0;
         return n;
     };
-    // Placement.  rows_smem: every row on chip if one CTA fits.  Otherwise
-    // (or by choice) joint rows, lists and impulses on chip, with the rows of
+    // Placement.  rows_smem 1: every row on chip if one CTA fits.  0: slots
+    // sized for the capacities -- lists, impulses, joint rows and the rows of
     // as many contact points as keep enough CTAs resident for every env to
-    // be in flight at once; then joint rows, then the lists, move to the
-    // global part if a CTA does not fit.
+    // be in flight at once -- when that holds every contact point; else the
+    // dynamic placement: slots hold only the envs' bodies, and each warp's
+    // envs share an arena, as large as those resident CTAs allow, that holds
+    // what the envs use in each step.  2: the dynamic placement with one CTA
+    // per SM (its warps share all of the SM's shared memory).
     bool all_rows = false;
     Layout L;
-    if (t.rows_smem && occ(L = lay(true, cc, true)) >= 1) {
+    int need = (b->E + envs_per_cta - 1) / envs_per_cta;
+    int want_sm = (need + b->sm_count - 1) / b->sm_count;    // CTAs per SM for one wave
+    bool fixed = false;
+    if (t.rows_smem == 1 && occ(L = lay(true, cc, true)) >= 1) {
         all_rows = true;
+        fixed = true;
+    } else if (t.rows_smem == 2) {
+        want_sm = 1;
     } else if (int o0 = occ(L = lay(true, 0, true))) {
-        int need = (b->E + envs_per_cta - 1) / envs_per_cta;
-        int want = std::min(o0, (need + b->sm_count - 1) / b->sm_count);
+        int want = std::min(o0, want_sm);
         int lo = 0, hi = cc;
         while (lo < hi) {
             int mid = (lo + hi + 1) / 2;
@@ -581,16 +589,38 @@ static ms_status configure_fused(ms_batch* b) {
             else hi = mid - 1;
         }
         L = lay(true, lo, true);
-    } else if (occ(L = lay(false, 0, true)) < 1 && occ(L = lay(false, 0, false)) < 1) {
-        return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)",
-                    (size_t)L.s_bytes * envs_per_cta, b->smem_optin);
+        fixed = lo == cc;
     }
     size_t smem = (size_t)L.s_bytes * envs_per_cta;
+    if (!fixed) {
+        L = lay(false, 0, false);
+        size_t base = (size_t)L.s_bytes * envs_per_cta;
+        int o1 = occ(L);
+        if (o1 < 1)
+            return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)", base,
+                        b->smem_optin);
+        int n_cta = std::max(1, std::min(o1, want_sm));
+        // the largest arena per warp (16-byte multiple) that keeps n_cta CTAs resident
+        size_t lo = 0, hi = (b->smem_optin - base) / (size_t)t.warps / 16;
+        auto occ_a = [&](size_t a16) {
+            int n = 0;
+            size_t sm = base + a16 * 16 * t.warps;
+            if (sm > b->smem_optin) return 0;
+            if (fused_occupancy(t.G, b->fused_lean, threads, sm, &n) != cudaSuccess) return 0;
+            return n;
+        };
+        while (lo < hi) {
+            size_t mid = (lo + hi + 1) / 2;
+            if (occ_a(mid) >= n_cta) lo = mid;
+            else hi = mid - 1;
+        }
+        L.arena_bytes = (int)(lo * 16);
+        smem = base + (size_t)L.arena_bytes * t.warps;
+    }
     int per_sm = 0;
     CK(fused_occupancy(t.G, b->fused_lean, threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
     int grid = per_sm * b->sm_count;
-    int need = (b->E + envs_per_cta - 1) / envs_per_cta;
     if (grid > need) grid = need;
     size_t gbytes = (size_t)grid * envs_per_cta * L.g_bytes;
     if (gbytes > b->gscratch_bytes) {
@@ -600,7 +630,7 @@ static ms_status configure_fused(ms_batch* b) {
         b->d_gscratch = (char*)p2;
         b->gscratch_bytes = gbytes;
     }
-    t.rows_smem = all_rows ? 1 : 0;
+    if (t.rows_smem == 1 && !all_rows) t.rows_smem = 0;
     b->fused_layout = L;
     b->fused_threads = threads;
     b->fused_grid = grid;
@@ -998,7 +1028,8 @@ extern "C" ms_status ms_set_tuning(ms_batch* b, const ms_tuning* t) {
     Tuning old = b->tune;
     b->tune.G = t->lanes_per_env;
     b->tune.warps = t->warps_per_cta;
-    b->tune.rows_smem = t->rows_in_smem ? 1 : 0;
+    if (t->rows_in_smem < 0 || t->rows_in_smem > 2) return fail(MS_ERR_INVALID_ARG, "rows_in_smem must be 0, 1 or 2");
+    b->tune.rows_smem = t->rows_in_smem;
     b->fused_ready = false;
     drop_graphs(b);
     ms_status s = configure_fused(b);
@@ -1095,7 +1126,7 @@ extern "C" ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_pat
     const int Ws[] = {1, 2, 4, 8};
     for (int G : Gs)
         for (int W : Ws)
-            for (int R = 1; R >= 0; R--) {
+            for (int R : {1, 0, 2}) {
                 ms_tuning c = {G, W, R, 0};
                 if (ms_set_tuning(b, &c) != MS_OK) continue;
                 if (R == 1 && b->tune.rows_smem == 0) continue;   // rows did not fit: same as R = 0

@@ -8,7 +8,9 @@
 // Each warp pops 32 / G env tickets at once from a queue ordered
 // longest-first, copies those envs' bodies into shared-memory slots, runs
 // all n_steps for all of them in lockstep (G lanes per env) and writes the
-// state back once.  No wait spins on another thread.
+// state back once.  No wait spins on another thread.  With a dynamic
+// placement (arena_bytes > 0) the warp's envs share an arena for their
+// lists, impulses and rows, placed anew after each step's narrowphase.
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -31,6 +33,11 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
     char* s = smem + (size_t)slot_id * L.s_bytes;
     size_t gslot = ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * K + gi;
     char* gl = C.gscratch + gslot * (size_t)L.g_bytes;
+
+    // dynamic placement: the warp's share of the arena after the CTA's slots
+    char* arena = L.arena_bytes > 0
+                      ? smem + (size_t)(blockDim.x >> 5) * K * L.s_bytes + (size_t)warp * L.arena_bytes
+                      : nullptr;
 
     EnvView e;
     e.x = at<float4>(s, L.x); e.q = at<float4>(s, L.q); e.v = at<float4>(s, L.v); e.w = at<float4>(s, L.w);
@@ -68,6 +75,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             stage_actions(e, g, act, D.A, (!LEAN && D.T.on) ? D.T.half : nullptr);
             stage_broadphase(e, g, D.P);
             stage_narrowphase<!LEAN>(e, g, D.P);
+            if (arena) place_dynamic(e, g, arena, L.arena_bytes, gl, L);
             if constexpr (LEAN) {
                 stage_color(e, g);
                 MS_CHECK_BOUNDS(e, g, D.P, true);

@@ -42,6 +42,10 @@ struct Layout {
     int aabb, pairs, man, pts;
     int rows_cg;                             // rows of every contact point (those >= pts_s are used), or -1
     int shape, inv, meta, adj, jf, jp, jm, jt, rest;   // parameter copies (no-allocation path only), or -1
+    // batched path, dynamic placement: bytes of shared memory per warp, after
+    // the CTA's slots, that the warp's envs share each step for their lists,
+    // impulses and rows (0: the placement above, fixed by the capacities)
+    int arena_bytes;
 };
 
 // with_state: x, q, v, w copied into the shared part; with_params: body and

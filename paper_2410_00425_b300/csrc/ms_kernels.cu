@@ -87,6 +87,7 @@ Layout make_layout(int max_nb, int max_nj, int pair_cap, int contact_cap, bool w
         L.shape = L.inv = L.meta = L.adj = L.jf = L.jp = L.jm = L.jt = L.rest = -1;
     }
     L.g_bytes = align_up(o, 16);
+    L.arena_bytes = 0;
     return L;
 }
 

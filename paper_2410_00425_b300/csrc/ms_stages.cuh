@@ -401,6 +401,91 @@ MSD void stage_narrowphase(EnvView& e, const Grp& g, const Params& P) {
     MS_CHECK_BOUNDS(e, g, P, false);
 }
 
+// ------------------------------------------------- dynamic row placement
+// The batched kernel's placement when slots sized for the capacities do not
+// fit on chip.  The envs of a warp share one shared-memory arena, handed out
+// after each step's narrowphase by what the envs hold in that step: first
+// the colour-ordered list and the impulses of every env (in env order), then
+// the joint rows, then the contact rows, levelled so that every env keeps
+// the rows of the same number of points on chip, or all of its own.  What
+// does not fit stays in the env's global slot, laid out for the capacities.
+// The colouring scratch goes over an env's on-chip rows when they are large
+// enough (the rows are written after the colouring).  Every lane computes
+// the same placement from the counts of all envs of the warp, so the loops
+// and shuffles are warp-uniform.
+MSD int pad16(int b) { return (b + 15) & ~15; }
+
+MSD void place_dynamic(EnvView& e, const Grp& g, char* arena, int abytes, char* gl, const Layout& L) {
+    e.scons = at<int4>(gl, L.scons);
+    e.lam = at<float>(gl, L.lam);
+    e.rows_j = at<Row>(gl, L.rows_j);
+    e.rows_cs = nullptr;
+    e.pts_s = 0;
+    e.cons = at<int4>(gl, L.cons);
+    e.colr = at<int>(gl, L.colr);
+    e.used = at<unsigned long long>(gl, L.used);
+    bool live = e.nb > 0;
+    int ncons = live ? e.nj + e.cnt[C_NMAN] : 0;
+    int npts = live ? e.cnt[C_NPTS] : 0;
+    int blist = pad16(16 * ncons), blam = pad16(4 * (8 * e.njs + 3 * npts));
+    int bl = live ? blist + blam : 0;
+    int bj = live && e.nj > 0 ? (int)sizeof(Row) * 8 * e.njs : 0;
+    const int BP = 3 * (int)sizeof(Row);                // the rows of one contact point
+    const int K = 32 / g.size;
+    int A = abytes;
+    unsigned inl = 0u, inj = 0u;
+    for (int k = 0; k < K; k++) {
+        int b = __shfl_sync(FULL_MASK, bl, k * g.size);
+        if (b > 0 && b <= A) { A -= b; inl |= 1u << k; }
+    }
+    for (int k = 0; k < K; k++) {
+        int b = __shfl_sync(FULL_MASK, bj, k * g.size);
+        if (b > 0 && b <= A) { A -= b; inj |= 1u << k; }
+    }
+    // the level: the most points per env whose rows, summed over the envs
+    // (each env at most its own count), fit in what is left
+    int lo = 0, hi = g.wmax(npts);
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int n = 0;
+        for (int k = 0; k < K; k++) n += min(__shfl_sync(FULL_MASK, npts, k * g.size), mid);
+        if (n <= A / BP) lo = mid;
+        else hi = mid - 1;
+    }
+    // this env's region starts after those of the envs before it
+    int gi = g.base / g.size, start = 0;
+    for (int k = 0; k < K; k++) {
+        int src = k * g.size;
+        int b0 = __shfl_sync(FULL_MASK, bl, src), b1 = __shfl_sync(FULL_MASK, bj, src);
+        int p = __shfl_sync(FULL_MASK, npts, src);
+        int sz = (((inl >> k) & 1u) ? b0 : 0) + (((inj >> k) & 1u) ? b1 : 0) + BP * min(p, lo);
+        if (k < gi) start += sz;
+    }
+    char* p = arena + start;
+    if ((inl >> gi) & 1u) {
+        e.scons = reinterpret_cast<int4*>(p);
+        e.lam = reinterpret_cast<float*>(p + blist);
+        p += bl;
+    }
+    char* r0 = p;
+    if ((inj >> gi) & 1u) {
+        e.rows_j = reinterpret_cast<Row*>(p);
+        p += bj;
+    }
+    int ps = min(npts, lo);
+    if (ps > 0) {
+        e.rows_cs = reinterpret_cast<Row*>(p);
+        e.pts_s = ps;
+        p += BP * ps;
+    }
+    int bcol = pad16(4 * ncons);
+    if (live && (int)(p - r0) >= blist + bcol + 8 * e.nb) {
+        e.cons = reinterpret_cast<int4*>(r0);
+        e.colr = reinterpret_cast<int*>(r0 + blist);
+        e.used = reinterpret_cast<unsigned long long*>(r0 + blist + bcol);
+    }
+}
+
 // -------------------------------------------------------------- colouring
 // Constraint list = joints (index order) then manifolds (pair order).  Each
 // takes the lowest colour free on both of its dynamic bodies (static bodies
