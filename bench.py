@@ -125,10 +125,10 @@ def algorithmic_flops_per_env_step(name, warmup, steps, sample_envs=32, variants
         o.set_task(sc.task)
     stepper = o.step_task if sc.task is not None else o.step
     if warmup:
-        stepper(warmup, threads=th)
+        stepper(warmup, actions=sc.actions(0, warmup), threads=th)
     c0 = o.counters()
     n = max(1, min(steps, 200))
-    stepper(n, threads=th)
+    stepper(n, actions=sc.actions(warmup, n), threads=th)
     c1 = o.counters()
     c = {k: c1[k] - c0[k] for k in c1}
     flops = sum(FLOP_WEIGHTS[k] * c[k] for k in FLOP_WEIGHTS)

@@ -28,8 +28,13 @@ HEADERS = ["ms_math.cuh", "ms_narrow.cuh", "ms_stages.cuh", "ms_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: every fused multiply-add is written out in the source, so the
-# rounding does not depend on how a stage is inlined into a kernel
-FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# rounding does not depend on how a stage is inlined into a kernel.
+# -prec-div=false: the compiler's approximate float division (at most 2 ulp
+# from the rounded quotient) instead of IEEE-rounded division; every kernel
+# of the library is built the same way, so the plain, batched, server and
+# no-allocation paths keep agreeing bit for bit.
+FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-prec-div=false", "-Xcompiler", "-fPIC",
+                "--expt-relaxed-constexpr"]
 
 
 def _newest_input() -> float:
