@@ -84,7 +84,8 @@ struct ms_batch {
     int fused_threads = 0, fused_grid = 0, fused_ctas_per_sm = 0;
     size_t fused_smem = 0;
     bool fused_ready = false;
-    bool fused_lean = false;          // the configured kernel is k_fused<G, true>
+    bool fused_lean = false;          // the configured kernel is k_fused<G, true, DYN>
+    bool fused_dyn = false;           // ... and k_fused<G, LEAN, true>: the dynamic placement
     std::map<long long, GraphEntry> graphs;
     // recorded after the batch's last enqueued work, on whatever stream it
     // went to: waiting on it never touches a stream the caller may have
@@ -559,7 +560,7 @@ static ms_status configure_fused(ms_batch* b) {
         size_t sm = (size_t)Lc.s_bytes * envs_per_cta;
         if (sm > b->smem_optin) return 0;
         int n = 0;
-        if (fused_occupancy(t.G, b->fused_lean, threads, sm, &n) != cudaSuccess) return 0;
+        if (fused_occupancy(t.G, b->fused_lean, false, threads, sm, &n) != cudaSuccess) return 0;
         return n;
     };
     // Placement.  rows_smem 1: every row on chip if one CTA fits.  0: slots
@@ -595,20 +596,21 @@ static ms_status configure_fused(ms_batch* b) {
     if (!fixed) {
         L = lay(false, 0, false);
         size_t base = (size_t)L.s_bytes * envs_per_cta;
-        int o1 = occ(L);
+        // resident CTAs of the dynamic-placement kernel with an arena of a16 * 16 bytes per warp
+        auto occ_a = [&](size_t a16) {
+            int n = 0;
+            size_t sm = base + a16 * 16 * t.warps;
+            if (sm > b->smem_optin) return 0;
+            if (fused_occupancy(t.G, b->fused_lean, true, threads, sm, &n) != cudaSuccess) return 0;
+            return n;
+        };
+        int o1 = occ_a(0);
         if (o1 < 1)
             return fail(MS_ERR_INVALID_ARG, "tuning needs %zu B of shared memory per CTA (max %zu)", base,
                         b->smem_optin);
         int n_cta = std::max(1, std::min(o1, want_sm));
         // the largest arena per warp (16-byte multiple) that keeps n_cta CTAs resident
         size_t lo = 0, hi = (b->smem_optin - base) / (size_t)t.warps / 16;
-        auto occ_a = [&](size_t a16) {
-            int n = 0;
-            size_t sm = base + a16 * 16 * t.warps;
-            if (sm > b->smem_optin) return 0;
-            if (fused_occupancy(t.G, b->fused_lean, threads, sm, &n) != cudaSuccess) return 0;
-            return n;
-        };
         while (lo < hi) {
             size_t mid = (lo + hi + 1) / 2;
             if (occ_a(mid) >= n_cta) lo = mid;
@@ -618,7 +620,8 @@ static ms_status configure_fused(ms_batch* b) {
         smem = base + (size_t)L.arena_bytes * t.warps;
     }
     int per_sm = 0;
-    CK(fused_occupancy(t.G, b->fused_lean, threads, smem, &per_sm));
+    bool dyn = L.arena_bytes > 0;
+    CK(fused_occupancy(t.G, b->fused_lean, dyn, threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
     int grid = per_sm * b->sm_count;
     if (grid > need) grid = need;
@@ -632,6 +635,7 @@ static ms_status configure_fused(ms_batch* b) {
     }
     if (t.rows_smem == 1 && !all_rows) t.rows_smem = 0;
     b->fused_layout = L;
+    b->fused_dyn = dyn;
     b->fused_threads = threads;
     b->fused_grid = grid;
     b->fused_smem = smem;
@@ -658,7 +662,7 @@ static DevBatch call_view(const ms_batch* b, float* out) {
 
 static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, float* out, cudaStream_t st) {
     CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
-    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_lean, b->fused_grid,
+    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_lean, b->fused_dyn, b->fused_grid,
                     b->fused_threads, b->fused_smem, st));
     return MS_OK;
 }

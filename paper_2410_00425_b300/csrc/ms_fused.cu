@@ -8,9 +8,11 @@
 // Each warp pops 32 / G env tickets at once from a queue ordered
 // longest-first, copies those envs' bodies into shared-memory slots, runs
 // all n_steps for all of them in lockstep (G lanes per env) and writes the
-// state back once.  No wait spins on another thread.  With a dynamic
-// placement (arena_bytes > 0) the warp's envs share an arena for their
-// lists, impulses and rows, placed anew after each step's narrowphase.
+// state back once.  No wait spins on another thread.  DYN = true is the
+// kernel of the dynamic placement (arena_bytes > 0): the warp's envs share
+// an arena for their lists, impulses and rows, placed anew after each
+// step's narrowphase; that code is compiled out of the DYN = false kernel,
+// which runs the capacity-sized slots.
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -20,7 +22,7 @@
 
 namespace ms {
 
-template <int G, bool LEAN>
+template <int G, bool LEAN, bool DYN>
 __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
     char* gl = C.gscratch + gslot * (size_t)L.g_bytes;
 
     // dynamic placement: the warp's share of the arena after the CTA's slots
-    char* arena = L.arena_bytes > 0
+    char* arena = DYN
                       ? smem + (size_t)(blockDim.x >> 5) * K * L.s_bytes + (size_t)warp * L.arena_bytes
                       : nullptr;
 
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             stage_actions(e, g, act, D.A, (!LEAN && D.T.on) ? D.T.half : nullptr);
             stage_broadphase(e, g, D.P);
             stage_narrowphase<!LEAN>(e, g, D.P);
-            if (arena) place_dynamic(e, g, arena, L.arena_bytes, gl, L);
+            if constexpr (DYN) place_dynamic(e, g, arena, L.arena_bytes, gl, L);
             if constexpr (LEAN) {
                 stage_color(e, g);
                 MS_CHECK_BOUNDS(e, g, D.P, true);
@@ -106,8 +108,9 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
 
 #define MS_CAT_(a, b) a##b
 #define MS_CAT(a, b) MS_CAT_(a, b)
-const void* MS_CAT(fused_kernel_, MS_FUSED_G)(bool lean) {
-    return lean ? (const void*)k_fused<MS_FUSED_G, true> : (const void*)k_fused<MS_FUSED_G, false>;
+const void* MS_CAT(fused_kernel_, MS_FUSED_G)(bool lean, bool dyn) {
+    if (dyn) return lean ? (const void*)k_fused<MS_FUSED_G, true, true> : (const void*)k_fused<MS_FUSED_G, false, true>;
+    return lean ? (const void*)k_fused<MS_FUSED_G, true, false> : (const void*)k_fused<MS_FUSED_G, false, false>;
 }
 
 }  // namespace ms

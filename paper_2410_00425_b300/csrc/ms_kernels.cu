@@ -211,26 +211,26 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
 
 // ----------------------------------------------------------- batched path
 // k_fused<G> lives in ms_fused.cu, one translation unit per G.
-static const void* fused_fn(int G, bool lean) {
+static const void* fused_fn(int G, bool lean, bool dyn) {
     switch (G) {
-    case 1: return fused_kernel_1(lean);
-    case 2: return fused_kernel_2(lean);
-    case 4: return fused_kernel_4(lean);
-    case 8: return fused_kernel_8(lean);
-    case 16: return fused_kernel_16(lean);
-    case 32: return fused_kernel_32(lean);
+    case 1: return fused_kernel_1(lean, dyn);
+    case 2: return fused_kernel_2(lean, dyn);
+    case 4: return fused_kernel_4(lean, dyn);
+    case 8: return fused_kernel_8(lean, dyn);
+    case 16: return fused_kernel_16(lean, dyn);
+    case 32: return fused_kernel_32(lean, dyn);
     default: return nullptr;
     }
 }
 
-bool fused_supported(int G) { return fused_fn(G, false) != nullptr; }
+bool fused_supported(int G) { return fused_fn(G, false, false) != nullptr; }
 
 bool fused_lean(const DevBatch& D) {
     return !D.hulls && !D.T.on && !D.force && !D.P.restit && !D.P.warm && !D.rec_man;
 }
 
-cudaError_t fused_occupancy(int G, bool lean, int threads, size_t smem, int* blocks_per_sm) {
-    const void* fn = fused_fn(G, lean);
+cudaError_t fused_occupancy(int G, bool lean, bool dyn, int threads, size_t smem, int* blocks_per_sm) {
+    const void* fn = fused_fn(G, lean, dyn);
     if (!fn) return cudaErrorInvalidValue;
     // The limit is a property of the kernel function shared by every batch
     // (and every captured graph), so it is raised once to the device maximum
@@ -244,9 +244,9 @@ cudaError_t fused_occupancy(int G, bool lean, int threads, size_t smem, int* blo
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, bool lean,
+cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, bool lean, bool dyn,
                          int grid, int threads, size_t smem, cudaStream_t s) {
-    const void* fn = fused_fn(G, lean);
+    const void* fn = fused_fn(G, lean, dyn);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&D, (void*)&actions, (void*)&n_steps, (void*)&C};
     NvtxRange r("ms_step (fused)");
