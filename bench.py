@@ -78,10 +78,13 @@ def make_workload(name, variants=False, **kw):
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 30.434e6, "kernel_sha": "beab9487222cc3de", "kernel": "k_fused<8, lean>"},
-    ("arm", "4,1,0"): {"bytes": 17.915e6, "kernel_sha": "beab9487222cc3de", "kernel": "k_fused<4, lean>"},
-    ("clutter", "16,4,0"): {"bytes": 543.869e6, "kernel_sha": "beab9487222cc3de", "kernel": "k_fused<16, lean>"},
-    ("hand", "8,4,2"): {"bytes": 33.537e6, "kernel_sha": "beab9487222cc3de", "kernel": "k_fused<8, lean>"},
+    ("arm", "8,1,0"): {"bytes": 3.0255e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
+    ("arm", "4,1,0"): {"bytes": 1.7944e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<4, lean, dynamic>"},
+    ("arm", "8,2,0"): {"bytes": 3.0235e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
+    ("clutter", "16,8,2"): {"bytes": 5.43285e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
+    ("clutter", "16,8,0"): {"bytes": 5.45147e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
+    ("clutter", "16,4,0"): {"bytes": 5.45955e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
+    ("hand", "8,4,2"): {"bytes": 3.365e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
 }
 KERNEL_SOURCES = ("ms_fused.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
