@@ -66,6 +66,7 @@ def test_rollout_non_chaotic():
     o = oracle_run(sc, 100)
     _, st, _ = gpu_run(sc, 100)
     clean = calm & tie_free(o, sc)
+    print(f"hulls: {clean.sum()} of 128 envs non-chaotic and tie-free")
     assert clean.sum() >= 3
     err = env_errors(sc, st, ost)
     ok = within(err, 10.0)
