@@ -631,21 +631,16 @@ def main():
     bb = new_batch()
     if tuning:
         bb.set_tuning(tuning["lanes_per_env"], tuning["warps_per_cta"], tuning["rows_in_smem"])
+    # one C-ABI call per step (ms_step_host): pinned host actions in, pinned
+    # host state (or the task records) out, both copies on the stream
     h_act = None if acts_np is None else torch.from_numpy(acts_np).pin_memory()
-    d_act = None if acts is None else torch.empty_like(acts[:n])
     task = sc.task is not None
     h_state = torch.empty((bb.NB, 13), dtype=torch.float32).pin_memory()
-    d_rec = torch.empty((n, E, bb.record_len()), dtype=torch.float32, device=dev) if task else None
     h_rec = torch.empty((n, E, bb.record_len()), dtype=torch.float32).pin_memory() if task else None
 
     def e2e_step(j):
-        if d_act is not None:
-            d_act.copy_(h_act[j * n:(j + 1) * n], non_blocking=True)
-        bb.step(d_act, n, stream=stream, out=d_rec)
-        if task:
-            h_rec.copy_(d_rec, non_blocking=True)
-        else:
-            bb.state_to_host(h_state, stream=stream)
+        a = None if h_act is None else h_act[j * n:(j + 1) * n]
+        bb.step_host(a, n, h_rec if task else h_state, records=task, stream=stream)
     settle(bb)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -661,7 +656,7 @@ def main():
     stream.synchronize()
     t_e = reduce_max(e0.elapsed_time(e1) / 1e3, ws)
     bb.close()
-    h2d = 0 if d_act is None else d_act.numel() * 4
+    h2d = 0 if h_act is None else n * E * sc.n_act * 4
     d2h = (h_rec.numel() if task else h_state.numel()) * 4
 
     # batched camera rendering (one 128 x 128 camera per env): the render

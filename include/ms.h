@@ -326,6 +326,20 @@ ms_status ms_task_observe(ms_batch* b, float* out, void* stream);
 enum { MS_STEP_PLAIN = 1 };
 ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, float* out, int flags, void* stream);
 
+/* ms_step with host buffers on both sides, for callers whose actions and
+ * results live in host memory: copies actions (host float
+ * [n_steps][n_envs][n_act], nullable = keep every target) into a device
+ * buffer the batch owns, steps n_steps, and copies into out (host) either
+ * the state afterwards (out_kind 0: float [n_bodies][13], as ms_copy_state)
+ * or the task records of every step (out_kind 1: float
+ * [n_steps][n_envs][ms_task_record_len]; needs a task).  All copies and the
+ * step are ordered on `stream`; pinned host buffers let the call return
+ * before they finish, and both must stay valid until the stream reaches the
+ * copies.  The batch's device buffers are shared by its calls: calls on
+ * different streams must be ordered by the caller.  MS_ERR_INVALID_ARG for
+ * a NULL out or an unknown out_kind; MS_ERR_OOM if a buffer cannot grow. */
+ms_status ms_step_host(ms_batch* b, const float* actions, int n_steps, float* out, int out_kind, void* stream);
+
 /* ----------------------------------------------------------------------- */
 /* Batched camera rendering                                                 */
 /* ----------------------------------------------------------------------- */

@@ -109,6 +109,12 @@ class Batch:
         _ffi.ms_copy_state(self.h, out, 1, stream)
         return out
 
+    def step_host(self, actions, n_steps, out, records=False, stream=None):
+        """Host actions in, host state (or, records=True, task records) out,
+        through one C-ABI call (ms_step_host)."""
+        _ffi.ms_step_host(self.h, actions, n_steps, out, 1 if records else 0, stream)
+        return out
+
     def state_to_host(self, out, stream=None):
         """Copy the state into a (pinned) host tensor [n_bodies, 13]."""
         _ffi.ms_copy_state(self.h, out, 0, stream)

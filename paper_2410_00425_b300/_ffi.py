@@ -116,6 +116,7 @@ _SIGS = [
     ("ms_task_record_len", C.c_int, [C.c_void_p]),
     ("ms_task_observe", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_step_ex", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_step_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     ("ms_set_camera", C.c_int, [C.c_void_p, C.POINTER(ms_camera_desc)]),
     ("ms_create_batch_hulls", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                         C.POINTER(ms_sim_params), C.POINTER(ms_hull_lib), C.POINTER(C.c_void_p)]),
@@ -235,6 +236,11 @@ def ms_step_plain(b, actions=None, n_steps=1, stream=None):
 
 def ms_step_ex(b, actions=None, n_steps=1, out=None, flags=0, stream=None):
     return check(load().ms_step_ex(b, _ptr(actions), n_steps, _ptr(out), flags, _stream(stream)))
+
+
+def ms_step_host(b, actions=None, n_steps=1, out=None, out_kind=0, stream=None):
+    """actions, out: host buffers (pinned tensors or arrays)."""
+    return check(load().ms_step_host(b, _ptr(actions), n_steps, _ptr(out), out_kind, _stream(stream)))
 
 
 def ms_set_task(b, task, stream=None):

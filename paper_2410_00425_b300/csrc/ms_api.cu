@@ -74,6 +74,10 @@ struct ms_batch {
     int* d_order = nullptr;
     char* d_gscratch = nullptr;
     size_t gscratch_bytes = 0;
+    float* d_hact = nullptr;          // ms_step_host: device copy of the host actions
+    size_t hact_cap = 0;              //   its capacity in floats
+    float* d_hrec = nullptr;          // ms_step_host: device task records before the copy out
+    size_t hrec_cap = 0;
     size_t bytes = 0;
     bool record = false;
     void* rec_keep[4] = {nullptr, nullptr, nullptr, nullptr};   // record buffers, kept while recording is off
@@ -728,6 +732,48 @@ extern "C" ms_status ms_step_ex(ms_batch* b, const float* actions, int n_steps, 
     if ((s = step_enqueue(b, actions, n_steps, out, st)) != MS_OK) return s;
     CK(cudaEventRecord(b->done, st));
     return MS_OK;
+}
+
+// grows a batch-owned device buffer to at least n floats (the old one stays
+// allocated until the batch is destroyed: calls already enqueued may use it)
+static ms_status grow_floats(ms_batch* b, float** p, size_t* cap, size_t n) {
+    if (n <= *cap) return MS_OK;
+    void* q = nullptr;
+    ms_status s = dmalloc(b, &q, sizeof(float) * n);
+    if (s) return s;
+    *p = (float*)q;
+    *cap = n;
+    return MS_OK;
+}
+
+extern "C" ms_status ms_step_host(ms_batch* b, const float* actions, int n_steps, float* out, int out_kind,
+                                  void* stream) {
+    ms_status s = check_step_args(b, n_steps);
+    if (s) return s;
+    if (!out) return fail(MS_ERR_INVALID_ARG, "out is NULL");
+    if (out_kind != 0 && out_kind != 1) return fail(MS_ERR_INVALID_ARG, "out_kind must be 0 (state) or 1 (records)");
+    if (out_kind == 1 && !b->D.T.on) return fail(MS_ERR_INVALID_ARG, "task records requested but no task is set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const float* dact = nullptr;
+    size_t na = actions ? (size_t)n_steps * b->E * b->A : 0;
+    if (na > 0) {
+        if ((s = grow_floats(b, &b->d_hact, &b->hact_cap, na)) != MS_OK) return s;
+        CK(cudaMemcpyAsync(b->d_hact, actions, sizeof(float) * na, cudaMemcpyHostToDevice, st));
+        dact = b->d_hact;
+    }
+    float* drec = nullptr;
+    size_t nr = out_kind == 1 ? (size_t)n_steps * b->E * b->D.T.D : 0;
+    if (nr > 0) {
+        if ((s = grow_floats(b, &b->d_hrec, &b->hrec_cap, nr)) != MS_OK) return s;
+        drec = b->d_hrec;
+    }
+    if ((s = ms_step_ex(b, dact, n_steps, drec, 0, stream)) != MS_OK) return s;
+    if (out_kind == 1) {
+        if (nr > 0) CK(cudaMemcpyAsync(out, drec, sizeof(float) * nr, cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(b->done, st));
+        return MS_OK;
+    }
+    return ms_copy_state(b, out, 0, stream);
 }
 
 ms_status ms::batch_step_eager(ms_batch* b, const float* actions, int n_steps, cudaStream_t st) {
