@@ -12,7 +12,8 @@
 // kernel of the dynamic placement (arena_bytes > 0): the warp's envs share
 // an arena for their lists, impulses and rows, placed anew after each
 // step's narrowphase; that code is compiled out of the DYN = false kernel,
-// which runs the capacity-sized slots.
+// which runs the capacity-sized slots.  JOINTS = false (lean kernels only)
+// is the kernel of a batch without joints: the joint rows are compiled out.
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -22,7 +23,7 @@
 
 namespace ms {
 
-template <int G, bool LEAN, bool DYN>
+template <int G, bool LEAN, bool DYN, bool JOINTS>
 __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             } else {
                 begin_step_solve(e, g, D.P);
             }
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep<!LEAN>(e, g, D.P, sub == D.P.substeps - 1);
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep<!LEAN, JOINTS>(e, g, D.P, sub == D.P.substeps - 1);
             if constexpr (!LEAN) {
                 end_step_solve(e, g, D.P);
                 if (D.force) stage_contact_forces(e, g, D.P);
@@ -108,9 +109,13 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
 
 #define MS_CAT_(a, b) a##b
 #define MS_CAT(a, b) MS_CAT_(a, b)
-const void* MS_CAT(fused_kernel_, MS_FUSED_G)(bool lean, bool dyn) {
-    if (dyn) return lean ? (const void*)k_fused<MS_FUSED_G, true, true> : (const void*)k_fused<MS_FUSED_G, false, true>;
-    return lean ? (const void*)k_fused<MS_FUSED_G, true, false> : (const void*)k_fused<MS_FUSED_G, false, false>;
+// joints = false (a batch without joints) has a kernel of its own only when lean
+const void* MS_CAT(fused_kernel_, MS_FUSED_G)(bool lean, bool dyn, bool joints) {
+    constexpr int G = MS_FUSED_G;
+    if (lean && !joints)
+        return dyn ? (const void*)k_fused<G, true, true, false> : (const void*)k_fused<G, true, false, false>;
+    if (dyn) return lean ? (const void*)k_fused<G, true, true, true> : (const void*)k_fused<G, false, true, true>;
+    return lean ? (const void*)k_fused<G, true, false, true> : (const void*)k_fused<G, false, false, true>;
 }
 
 }  // namespace ms

@@ -718,6 +718,7 @@ MSD Row* cons_rows(const EnvView& e, int4 c) {
     return (place == CP_JOINT ? e.rows_j : (place == CP_MAN_S ? e.rows_cs : e.rows_cg)) + c.z;
 }
 
+template <bool JOINTS = true>
 MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     bool joint = (c.w & 3) == CP_JOINT;
     int idx = c.w >> 8;
@@ -750,6 +751,7 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
         }
         return;
     }
+    if constexpr (!JOINTS) return;              // a batch without joints
     const int J = e.njs;                        // joint row stride
     int4 jm = e.jm[idx];
     float4 jp = e.jp[idx];
@@ -807,6 +809,7 @@ MSD void prep_constraint(EnvView& e, int4 c, const Params& P) {
     }
 }
 
+template <bool JOINTS = true>
 MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
     float h = P.h;
     int nb = e.nb;
@@ -849,7 +852,7 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
     int cmax = g.wmax(ncons);
     for (int c0 = 0; c0 < cmax; c0 += g.size) {
         int ci = c0 + g.lane;
-        if (ci < ncons) prep_constraint(e, e.scons[ci], P);
+        if (ci < ncons) prep_constraint<JOINTS>(e, e.scons[ci], P);
     }
     g.sync();
 }
@@ -888,14 +891,17 @@ MSD SolveCtx solve_ctx(const EnvView& e, const Params& P) {
 // own count, and lanes without a constraint (has = false), change nothing.
 // Lanes that diverged on a trip count or a row kind would run their paths
 // one after the other.
-template <int MODE>
+template <int MODE, bool JOINTS = true>
 MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
     int place = c.w & 3, np = (c.w >> 2) & 7;
-    bool joint = place == CP_JOINT;
+    bool joint = JOINTS && place == CP_JOINT;
     int nrows = has ? (joint ? 8 : 3 * np) : 0;
-    const Row* R = (joint ? x.rj : (place == CP_MAN_S ? x.rcs : x.rcg)) + c.z;
-    float* L = x.lam + (joint ? c.z : 8 * x.njs + c.z);
-    int st = joint ? x.njs : 1;                         // row stride
+    // addressing by the record's place (an idle lane's null record is a
+    // joint record, valid in every batch), row kinds by `joint`
+    bool jplace = place == CP_JOINT;
+    const Row* R = (jplace ? x.rj : (place == CP_MAN_S ? x.rcs : x.rcg)) + c.z;
+    float* L = x.lam + (jplace ? c.z : 8 * x.njs + c.z);
+    int st = jplace ? x.njs : 1;                        // row stride
     int last = max(nrows - 1, 0);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 va = c.x >= 0 ? x.v[c.x] : z4, wa4 = c.x >= 0 ? x.w[c.x] : z4;
@@ -957,7 +963,7 @@ MSD void solve_constraint(const SolveCtx& x, int4 c, bool has, int nrmax) {
     if (has && dynB) { x.v[c.y] = f4(vA - dv, imB); x.w[c.y] = f4(wB, wb4.w); }
 }
 
-template <int MODE>
+template <int MODE, bool JOINTS = true>
 MSD void sweep_mode(EnvView& e, const Grp& g, const Params& P) {
     SolveCtx x = solve_ctx(e, P);
     const int4* sc = e.scons;
@@ -974,20 +980,22 @@ MSD void sweep_mode(EnvView& e, const Grp& g, const Params& P) {
             bool has = k < k1;
             int4 c = has ? sc[k] : none;
             int nr = has ? ((c.w & 3) == CP_JOINT ? 8 : 3 * ((c.w >> 2) & 7)) : 0;
-            solve_constraint<MODE>(x, c, has, g.wmax(nr));
+            solve_constraint<MODE, JOINTS>(x, c, has, g.wmax(nr));
         }
         g.sync();
         k0 = k1;
     }
 }
 
+template <bool JOINTS = true>
 MSD void stage_sweep(EnvView& e, const Grp& g, int mode, const Params& P) {
-    if (mode == 0) sweep_mode<0>(e, g, P);
-    else if (mode == 1) sweep_mode<1>(e, g, P);
-    else sweep_mode<2>(e, g, P);
+    if (mode == 0) sweep_mode<0, JOINTS>(e, g, P);
+    else if (mode == 1) sweep_mode<1, JOINTS>(e, g, P);
+    else sweep_mode<2, JOINTS>(e, g, P);
 }
 
 // -------------------------------------------------------------- integrate
+template <bool JOINTS = true>
 MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
     bool joint = (c.w & 3) == CP_JOINT;
     int idx = c.w >> 8;
@@ -1002,7 +1010,7 @@ MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
             float d = contact_sep(e.pts + 3 * (M.w + k), A, B, FA, FB, rA, rB);
             R[k].c.w = fmaxf(d, 0.f) / h;
         }
-    } else {
+    } else if constexpr (JOINTS) {
         int4 jm = e.jm[idx];
         float4 jp = e.jp[idx];
         JointGeo gj = joint_geo(e, idx, jm.x, A, B);
@@ -1012,6 +1020,7 @@ MSD void relax_constraint(EnvView& e, int4 c, const Params& P) {
 }
 
 // symplectic Euler with w = S w^; e.w keeps w^ for the relax sweeps
+template <bool JOINTS = true>
 MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
     float h = P.h;
     int nb = e.nb;
@@ -1035,7 +1044,7 @@ MSD void stage_integrate(EnvView& e, const Grp& g, const Params& P) {
     int cmax = g.wmax(ncons);
     for (int c0 = 0; c0 < cmax; c0 += g.size) {
         int ci = c0 + g.lane;
-        if (ci < ncons) relax_constraint(e, e.scons[ci], P);
+        if (ci < ncons) relax_constraint<JOINTS>(e, e.scons[ci], P);
     }
     g.sync();
 }
@@ -1246,14 +1255,15 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
 
 // One substep: prep, warm start, position sweeps, integration, relax
 // sweeps, the contact impulse record and (last substep) restitution, unscale.
-// RESTIT = false compiles restitution out (a batch without it).
-template <bool RESTIT = true>
+// RESTIT = false compiles restitution out (a batch without it); JOINTS =
+// false the joint rows (a batch without joints).
+template <bool RESTIT = true, bool JOINTS = true>
 MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
-    stage_prep(e, g, P);
-    stage_sweep(e, g, 0, P);
-    for (int it = 0; it < P.pos_iters; it++) stage_sweep(e, g, 1, P);
-    stage_integrate(e, g, P);
-    for (int it = 0; it < P.vel_iters; it++) stage_sweep(e, g, 2, P);
+    stage_prep<JOINTS>(e, g, P);
+    stage_sweep<JOINTS>(e, g, 0, P);
+    for (int it = 0; it < P.pos_iters; it++) stage_sweep<JOINTS>(e, g, 1, P);
+    stage_integrate<JOINTS>(e, g, P);
+    for (int it = 0; it < P.vel_iters; it++) stage_sweep<JOINTS>(e, g, 2, P);
     if constexpr (RESTIT) {
         if (P.restit) {
             stage_track_impulse(e, g);
