@@ -88,9 +88,7 @@ struct ms_batch {
     int fused_threads = 0, fused_grid = 0, fused_ctas_per_sm = 0;
     size_t fused_smem = 0;
     bool fused_ready = false;
-    bool fused_lean = false;          // the configured kernel is k_fused<G, true, DYN>
-    bool fused_dyn = false;           // ... and k_fused<G, LEAN, true>: the dynamic placement
-    bool fused_joints = true;         // ... and k_fused<G, LEAN, DYN, false>: a batch without joints
+    unsigned fused_var = 0;           // the configured kernel variant (FV_* bits)
     std::map<long long, GraphEntry> graphs;
     // recorded after the batch's last enqueued work, on whatever stream it
     // went to: waiting on it never touches a stream the caller may have
@@ -550,8 +548,13 @@ extern "C" ms_status ms_step_plain(ms_batch* b, const float* actions, int n_step
 // ------------------------------------------------------------- batched path
 static ms_status configure_fused(ms_batch* b) {
     if (b->fused_ready) return MS_OK;
-    b->fused_lean = fused_lean(b->D);
-    b->fused_joints = b->NJ > 0;
+    // the variant without the code this batch does not use (FV_DYN added below)
+    unsigned var = FV_JOINTS | FV_HULLS;
+    if (fused_lean(b->D)) {
+        var = FV_LEAN;
+        if (b->NJ > 0) var |= FV_JOINTS;
+        if (b->D.hulls) var |= FV_HULLS;
+    }
     const ms_sim_params& p = b->params;
     Tuning& t = b->tune;
     int K = 32 / t.G;                               // envs per warp
@@ -566,7 +569,7 @@ static ms_status configure_fused(ms_batch* b) {
         size_t sm = (size_t)Lc.s_bytes * envs_per_cta;
         if (sm > b->smem_optin) return 0;
         int n = 0;
-        if (fused_occupancy(t.G, b->fused_lean, false, b->fused_joints, threads, sm, &n) != cudaSuccess) return 0;
+        if (fused_occupancy(t.G, var, threads, sm, &n) != cudaSuccess) return 0;
         return n;
     };
     // Placement.  rows_smem 1: every row on chip if one CTA fits.  0: slots
@@ -607,7 +610,7 @@ static ms_status configure_fused(ms_batch* b) {
             int n = 0;
             size_t sm = base + a16 * 16 * t.warps;
             if (sm > b->smem_optin) return 0;
-            if (fused_occupancy(t.G, b->fused_lean, true, b->fused_joints, threads, sm, &n) != cudaSuccess) return 0;
+            if (fused_occupancy(t.G, var | FV_DYN, threads, sm, &n) != cudaSuccess) return 0;
             return n;
         };
         int o1 = occ_a(0);
@@ -627,7 +630,7 @@ static ms_status configure_fused(ms_batch* b) {
     }
     int per_sm = 0;
     bool dyn = L.arena_bytes > 0;
-    CK(fused_occupancy(t.G, b->fused_lean, dyn, b->fused_joints, threads, smem, &per_sm));
+    CK(fused_occupancy(t.G, var | (dyn ? FV_DYN : 0u), threads, smem, &per_sm));
     if (per_sm < 1) return fail(MS_ERR_INVALID_ARG, "tuning does not fit on an SM");
     int grid = per_sm * b->sm_count;
     if (grid > need) grid = need;
@@ -641,7 +644,7 @@ static ms_status configure_fused(ms_batch* b) {
     }
     if (t.rows_smem == 1 && !all_rows) t.rows_smem = 0;
     b->fused_layout = L;
-    b->fused_dyn = dyn;
+    b->fused_var = var | (dyn ? FV_DYN : 0u);
     b->fused_threads = threads;
     b->fused_grid = grid;
     b->fused_smem = smem;
@@ -668,8 +671,7 @@ static DevBatch call_view(const ms_batch* b, float* out) {
 
 static ms_status enqueue_fused(ms_batch* b, const float* actions, int n_steps, float* out, cudaStream_t st) {
     CK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
-    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_lean, b->fused_dyn,
-                    b->fused_joints, b->fused_grid,
+    CK(launch_fused(call_view(b, out), actions, n_steps, fused_cfg(b), b->tune.G, b->fused_var, b->fused_grid,
                     b->fused_threads, b->fused_smem, st));
     return MS_OK;
 }

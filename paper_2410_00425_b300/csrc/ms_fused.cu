@@ -1,9 +1,11 @@
-// The batched path's persistent kernel, k_fused<G, LEAN>, for one lane-group
-// size G (lanes per env) per translation unit: the build compiles this file
-// once per G with -DMS_FUSED_G=G, so the instantiations compile in parallel.
-// LEAN = true is the kernel of a batch that uses no hull, pick task, contact
-// force, restitution, warm start or contact record: that code is compiled
-// out (a smaller kernel: fewer instruction-cache misses), results identical.
+// The batched path's persistent kernel, k_fused<G, LEAN, DYN, JOINTS, HULLS>,
+// for one lane-group size G (lanes per env) per translation unit: the build
+// compiles this file once per G with -DMS_FUSED_G=G, so the instantiations
+// compile in parallel.  Code a batch does not use is compiled out of its
+// kernel (a smaller kernel: fewer registers and instruction-cache misses),
+// results identical: LEAN = true has no pick-task, contact-force,
+// restitution, warm-start or contact-record code; JOINTS = false no joint
+// rows; HULLS = false no hull routines (both only in lean kernels).
 //
 // Each warp pops 32 / G env tickets at once from a queue ordered
 // longest-first, copies those envs' bodies into shared-memory slots, runs
@@ -12,8 +14,7 @@
 // kernel of the dynamic placement (arena_bytes > 0): the warp's envs share
 // an arena for their lists, impulses and rows, placed anew after each
 // step's narrowphase; that code is compiled out of the DYN = false kernel,
-// which runs the capacity-sized slots.  JOINTS = false (lean kernels only)
-// is the kernel of a batch without joints: the joint rows are compiled out.
+// which runs the capacity-sized slots.
 #include "ms_internal.h"
 #include "ms_stages.cuh"
 
@@ -23,7 +24,7 @@
 
 namespace ms {
 
-template <int G, bool LEAN, bool DYN, bool JOINTS>
+template <int G, bool LEAN, bool DYN, bool JOINTS, bool HULLS>
 __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actions, int n_steps, FusedCfg C) {
     extern __shared__ __align__(16) char smem[];
     const Layout& L = C.layout;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             nb = D.body_off[env + 1] - b0; nj = D.joint_off[env + 1] - j0;
         }
         view_params(e, D, b0, j0, env, active && !LEAN);
-        if constexpr (LEAN) e.hulls = nullptr;
+        if constexpr (!HULLS) e.hulls = nullptr;
         int nbmax = g.wmax(nb);
         for (int i0 = 0; i0 < nbmax; i0 += G) {
             int i = i0 + g.lane;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             const float* act = (actions && active) ? actions + ((size_t)k * D.E + env) * D.A : nullptr;
             stage_actions(e, g, act, D.A, (!LEAN && D.T.on) ? D.T.half : nullptr);
             stage_broadphase(e, g, D.P);
-            stage_narrowphase<!LEAN>(e, g, D.P);
+            stage_narrowphase<HULLS>(e, g, D.P);
             if constexpr (DYN) place_dynamic(e, g, arena, L.arena_bytes, gl, L);
             if constexpr (LEAN) {
                 stage_color(e, g);
@@ -109,13 +110,17 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
 
 #define MS_CAT_(a, b) a##b
 #define MS_CAT(a, b) MS_CAT_(a, b)
-// joints = false (a batch without joints) has a kernel of its own only when lean
-const void* MS_CAT(fused_kernel_, MS_FUSED_G)(bool lean, bool dyn, bool joints) {
-    constexpr int G = MS_FUSED_G;
-    if (lean && !joints)
-        return dyn ? (const void*)k_fused<G, true, true, false> : (const void*)k_fused<G, true, false, false>;
-    if (dyn) return lean ? (const void*)k_fused<G, true, true, true> : (const void*)k_fused<G, false, true, true>;
-    return lean ? (const void*)k_fused<G, true, false, true> : (const void*)k_fused<G, false, false, true>;
+template <bool L, bool D, bool J, bool H>
+static const void* kf() { return (const void*)k_fused<MS_FUSED_G, L, D, J, H>; }
+
+// the kernel of a variant (FV_* bits); a variant without FV_LEAN has joints and hulls
+const void* MS_CAT(fused_kernel_, MS_FUSED_G)(unsigned v) {
+    bool dyn = v & FV_DYN, joints = v & FV_JOINTS, hulls = v & FV_HULLS;
+    if (!(v & FV_LEAN)) return dyn ? kf<false, true, true, true>() : kf<false, false, true, true>();
+    if (joints && hulls) return dyn ? kf<true, true, true, true>() : kf<true, false, true, true>();
+    if (joints) return dyn ? kf<true, true, true, false>() : kf<true, false, true, false>();
+    if (hulls) return dyn ? kf<true, true, false, true>() : kf<true, false, false, true>();
+    return dyn ? kf<true, true, false, false>() : kf<true, false, false, false>();
 }
 
 }  // namespace ms

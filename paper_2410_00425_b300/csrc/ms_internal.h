@@ -233,20 +233,22 @@ struct FusedCfg {
 
 int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStream_t s);
 // k_fused<G, lean> of each lane-group size (ms_fused.cu, one translation unit per G)
-const void* fused_kernel_1(bool lean, bool dyn, bool joints);
-const void* fused_kernel_2(bool lean, bool dyn, bool joints);
-const void* fused_kernel_4(bool lean, bool dyn, bool joints);
-const void* fused_kernel_8(bool lean, bool dyn, bool joints);
-const void* fused_kernel_16(bool lean, bool dyn, bool joints);
-const void* fused_kernel_32(bool lean, bool dyn, bool joints);
-// lean: the kernel without hull, task, force, restitution, warm-start and
-// record code (fused_lean tells whether a batch can use it)
-cudaError_t fused_occupancy(int G, bool lean, bool dyn, bool joints, int threads, size_t smem,
-                           int* blocks_per_sm);
+const void* fused_kernel_1(unsigned variant);
+const void* fused_kernel_2(unsigned variant);
+const void* fused_kernel_4(unsigned variant);
+const void* fused_kernel_8(unsigned variant);
+const void* fused_kernel_16(unsigned variant);
+const void* fused_kernel_32(unsigned variant);
+// kernel variant bits of k_fused: FV_LEAN (no task, contact force,
+// restitution, warm start or record code), FV_DYN (dynamic placement),
+// FV_JOINTS (joint rows), FV_HULLS (hull routines); a variant without
+// FV_LEAN always has FV_JOINTS and FV_HULLS.
+enum : unsigned { FV_LEAN = 1u, FV_DYN = 2u, FV_JOINTS = 4u, FV_HULLS = 8u };
+cudaError_t fused_occupancy(int G, unsigned variant, int threads, size_t smem, int* blocks_per_sm);
 bool fused_supported(int G);
-bool fused_lean(const DevBatch& D);
-cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, bool lean, bool dyn,
-                         bool joints, int grid, int threads, size_t smem, cudaStream_t s);
+bool fused_lean(const DevBatch& D);   // whether a batch can run an FV_LEAN variant
+cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, unsigned variant,
+                         int grid, int threads, size_t smem, cudaStream_t s);
 void launch_pack_state(const DevBatch& D, float* out, cudaStream_t s);
 // pick task: controller reset of the masked envs (all if mask is null) and
 // the records of every env at the current state

@@ -211,27 +211,26 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
 
 // ----------------------------------------------------------- batched path
 // k_fused<G> lives in ms_fused.cu, one translation unit per G.
-static const void* fused_fn(int G, bool lean, bool dyn, bool joints) {
+static const void* fused_fn(int G, unsigned v) {
     switch (G) {
-    case 1: return fused_kernel_1(lean, dyn, joints);
-    case 2: return fused_kernel_2(lean, dyn, joints);
-    case 4: return fused_kernel_4(lean, dyn, joints);
-    case 8: return fused_kernel_8(lean, dyn, joints);
-    case 16: return fused_kernel_16(lean, dyn, joints);
-    case 32: return fused_kernel_32(lean, dyn, joints);
+    case 1: return fused_kernel_1(v);
+    case 2: return fused_kernel_2(v);
+    case 4: return fused_kernel_4(v);
+    case 8: return fused_kernel_8(v);
+    case 16: return fused_kernel_16(v);
+    case 32: return fused_kernel_32(v);
     default: return nullptr;
     }
 }
 
-bool fused_supported(int G) { return fused_fn(G, false, false, true) != nullptr; }
+bool fused_supported(int G) { return fused_fn(G, FV_JOINTS | FV_HULLS) != nullptr; }
 
 bool fused_lean(const DevBatch& D) {
-    return !D.hulls && !D.T.on && !D.force && !D.P.restit && !D.P.warm && !D.rec_man;
+    return !D.T.on && !D.force && !D.P.restit && !D.P.warm && !D.rec_man;
 }
 
-cudaError_t fused_occupancy(int G, bool lean, bool dyn, bool joints, int threads, size_t smem,
-                           int* blocks_per_sm) {
-    const void* fn = fused_fn(G, lean, dyn, joints);
+cudaError_t fused_occupancy(int G, unsigned variant, int threads, size_t smem, int* blocks_per_sm) {
+    const void* fn = fused_fn(G, variant);
     if (!fn) return cudaErrorInvalidValue;
     // The limit is a property of the kernel function shared by every batch
     // (and every captured graph), so it is raised once to the device maximum
@@ -245,9 +244,9 @@ cudaError_t fused_occupancy(int G, bool lean, bool dyn, bool joints, int threads
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, bool lean, bool dyn,
-                         bool joints, int grid, int threads, size_t smem, cudaStream_t s) {
-    const void* fn = fused_fn(G, lean, dyn, joints);
+cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, unsigned variant,
+                         int grid, int threads, size_t smem, cudaStream_t s) {
+    const void* fn = fused_fn(G, variant);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&D, (void*)&actions, (void*)&n_steps, (void*)&C};
     NvtxRange r("ms_step (fused)");
