@@ -78,13 +78,19 @@ def make_workload(name, variants=False, **kw):
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 3.0255e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
-    ("arm", "4,1,0"): {"bytes": 1.7944e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<4, lean, dynamic>"},
-    ("arm", "8,2,0"): {"bytes": 3.0235e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
-    ("clutter", "16,8,2"): {"bytes": 5.43285e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
-    ("clutter", "16,8,0"): {"bytes": 5.45147e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
-    ("clutter", "16,4,0"): {"bytes": 5.45955e+08, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<16, lean, dynamic>"},
-    ("hand", "8,4,2"): {"bytes": 3.365e+07, "kernel_sha": "1f62c4675efa21be", "kernel": "k_fused<8, lean, dynamic>"},
+    ("arm", "8,1,0"): {"bytes": 3.0277e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
+    ("arm", "4,1,0"): {"bytes": 1.8032e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<4, lean, dynamic>"},
+    ("arm", "8,2,0"): {"bytes": 3.0149e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
+    ("pick", "8,1,0"): {"bytes": 3.0911e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, full, dynamic>"},
+    ("clutter", "16,8,0"): {"bytes": 5.5026e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("clutter", "16,8,2"): {"bytes": 5.51143e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("clutter", "16,4,0"): {"bytes": 5.52079e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("hand", "8,4,2"): {"bytes": 3.3445e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
+    ("hand", "8,4,0"): {"bytes": 8.5148e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
+    ("hulls", "16,8,2"): {"bytes": 2.95903e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
+    ("hulls", "16,8,0"): {"bytes": 2.95121e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
+    ("mixed", "16,4,2"): {"bytes": 3.4084e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic>"},
+    ("mixed", "32,8,0"): {"bytes": 7.5235e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<32, lean, dynamic>"},
 }
 KERNEL_SOURCES = ("ms_fused.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
