@@ -627,7 +627,9 @@ def main():
     plain_value = None
     if not args.no_plain:
         p = sc.params
-        lp = n * (3 + p["substeps"] * (4 + p["pos_iters"] + p["vel_iters"]) + 1)
+        # launches per step: begin, narrow, colour; per substep prep, warm start
+        # (not on the first substep without warm_start), sweeps, integrate, end; check
+        lp = n * (3 + p["substeps"] * (4 + p["pos_iters"] + p["vel_iters"]) + 1 - (0 if p.get("warm_start") else 1))
         t_p, _, _, _, _ = timed(True, lp)
         t_p = reduce_max(t_p, ws)
         plain_value = ws * E * n * args.steps / t_p

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 1) k_fused(DevBatch D, const float* actio
             } else {
                 begin_step_solve(e, g, D.P);
             }
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep<!LEAN, JOINTS>(e, g, D.P, sub == D.P.substeps - 1);
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep<!LEAN, JOINTS>(e, g, D.P, sub == 0, sub == D.P.substeps - 1);
             if constexpr (!LEAN) {
                 end_step_solve(e, g, D.P);
                 if (D.force) stage_contact_forces(e, g, D.P);

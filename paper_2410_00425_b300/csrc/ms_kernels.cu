@@ -186,8 +186,11 @@ int launch_plain(const DevBatch& D, const float* actions, int n_steps, cudaStrea
             {
                 NvtxRange r("prep+warm");
                 k_prep<<<grid, block, 0, s>>>(D);
-                k_sweep<<<grid, block, 0, s>>>(D, 0);
-                launches += 2;
+                launches++;
+                if (sub > 0 || D.P.warm) {      // the first substep's warm start has nothing to apply without warm_start
+                    k_sweep<<<grid, block, 0, s>>>(D, 0);
+                    launches++;
+                }
             }
             {
                 NvtxRange r("position sweeps");

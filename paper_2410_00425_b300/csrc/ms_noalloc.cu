@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_noalloc(NoallocArgs D, const float* act
             stage_narrowphase(e, g, D.P);
             stage_color(e, g);
             MS_CHECK_BOUNDS(e, g, D.P, true);
-            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == D.P.substeps - 1);
+            for (int sub = 0; sub < D.P.substeps; sub++) run_substep(e, g, D.P, sub == 0, sub == D.P.substeps - 1);
             stage_check(e, g);
             if (*e.status & ST_NAN) { e.nb = 0; e.nj = 0; }
         }

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256, 1) k_multi(const DevBatch* __restrict__ b
         stage_broadphase(e, g, P);
         stage_narrowphase(e, g, P);
         begin_step_solve(e, g, P);
-        for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P, sub == P.substeps - 1);
+        for (int sub = 0; sub < P.substeps; sub++) run_substep(e, g, P, sub == 0, sub == P.substeps - 1);
         end_step_solve(e, g, P);
         stage_check(e, g);
         for (int i0 = 0; i0 < nbmax; i0 += G) {

@@ -1257,10 +1257,13 @@ MSD void stage_restitution(EnvView& e, const Grp& g, const Params& P) {
 // sweeps, the contact impulse record and (last substep) restitution, unscale.
 // RESTIT = false compiles restitution out (a batch without it); JOINTS =
 // false the joint rows (a batch without joints).
+// The first substep's warm start applies impulses that the colouring has
+// just zeroed unless they are carried across steps (warm_start): it is
+// skipped (first = true), which changes no value.
 template <bool RESTIT = true, bool JOINTS = true>
-MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool last) {
+MSD void run_substep(EnvView& e, const Grp& g, const Params& P, bool first, bool last) {
     stage_prep<JOINTS>(e, g, P);
-    stage_sweep<JOINTS>(e, g, 0, P);
+    if (!first || P.warm) stage_sweep<JOINTS>(e, g, 0, P);
     for (int it = 0; it < P.pos_iters; it++) stage_sweep<JOINTS>(e, g, 1, P);
     stage_integrate<JOINTS>(e, g, P);
     for (int it = 0; it < P.vel_iters; it++) stage_sweep<JOINTS>(e, g, 2, P);
