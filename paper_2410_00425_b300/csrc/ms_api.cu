@@ -374,12 +374,13 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
                 int h = (int)d.p[0];
                 double rho = (double)d.mass / hh.vol[h];
                 const double* c2 = &hh.c2[3 * h];
-                inv[k] = make_float4((float)(1.0 / (rho * (c2[1] + c2[2]))), (float)(1.0 / (rho * (c2[0] + c2[2]))),
-                                     (float)(1.0 / (rho * (c2[0] + c2[1]))), (float)(1.0 / (double)d.mass));
+                inv[k] = make_float4(sqrtf((float)(1.0 / (rho * (c2[1] + c2[2])))),
+                                     sqrtf((float)(1.0 / (rho * (c2[0] + c2[2])))),
+                                     sqrtf((float)(1.0 / (rho * (c2[0] + c2[1])))), (float)(1.0 / (double)d.mass));
             } else if (dyn) {
                 float I[3];
                 body_inertia(d, I);
-                inv[k] = make_float4(1.f / I[0], 1.f / I[1], 1.f / I[2], (float)(1.0 / (double)d.mass));
+                inv[k] = make_float4(sqrtf(1.f / I[0]), sqrtf(1.f / I[1]), sqrtf(1.f / I[2]), (float)(1.0 / (double)d.mass));
             } else {
                 inv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }

@@ -201,7 +201,7 @@ struct DevBatch {
     const int* joint_off;
     float4 *x, *q, *v, *w;
     const float4* shape;
-    const float4* inv;
+    const float4* inv;                 // sqrt(1/Ixx), sqrt(1/Iyy), sqrt(1/Izz), 1/m (0 = static)
     const int2* meta;
     const unsigned long long* adj;
     const float4* jf;

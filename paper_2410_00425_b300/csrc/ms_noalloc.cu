@@ -58,16 +58,17 @@ __device__ __forceinline__ float4 desc_quat(const float* q) {
     return make_float4((float)(q[0] / n), (float)(q[1] / n), (float)(q[2] / n), (float)(q[3] / n));
 }
 
-// 1/I (body frame) and 1/m of a descriptor: the inertia formula of
-// ms_create_batch (primitive_inertia), in double, and its float reciprocals
+// sqrt(1/I) (body frame) and 1/m of a descriptor: the inertia formula of
+// ms_create_batch (primitive_inertia), in double, its float reciprocals
 // rounded to nearest as the host rounds them (the kernels are built with
-// approximate float division; __frcp_rn is the IEEE-rounded reciprocal)
+// approximate float division; __frcp_rn is the IEEE-rounded reciprocal), and
+// their IEEE square roots, as stored by ms_create_batch
 __device__ __forceinline__ float4 desc_inverse_mass(const ms_body_desc& d, bool dyn) {
     if (!dyn) return make_float4(0.f, 0.f, 0.f, 0.f);
     double I[3];
     primitive_inertia(d.type, d.mass, d.p[0], d.p[1], d.p[2], I);
     float I0 = (float)I[0], I1 = (float)I[1], I2 = (float)I[2];
-    return make_float4(__frcp_rn(I0), __frcp_rn(I1), __frcp_rn(I2), (float)(1.0 / (double)d.mass));
+    return make_float4(sqrtf(__frcp_rn(I0)), sqrtf(__frcp_rn(I1)), sqrtf(__frcp_rn(I2)), (float)(1.0 / (double)d.mass));
 }
 
 // Same stages and lockstep env loop as the batched kernel; the env's

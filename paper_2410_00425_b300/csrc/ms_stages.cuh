@@ -64,7 +64,7 @@ struct EnvView {
     int nb, nj;                       // counts the stages see (0: inactive or frozen)
     float4 *x, *q, *v, *w;            // state; v.w = inverse mass (0 = static); w holds w^ during a substep
     const float4* shape;              // p0, p1, p2, mu
-    const float4* inv;                // 1/Ixx, 1/Iyy, 1/Izz, 1/m (0 = static)
+    const float4* inv;                // sqrt(1/Ixx), sqrt(1/Iyy), sqrt(1/Izz), 1/m (0 = static)
     const int2* meta;                 // x: type | dyn << 8; y: group | mask << 16
     const unsigned long long* adj;    // joint adjacency bit mask per body
     const float4* jf;                 // 4 per joint: parent pos, parent quat, child pos, child quat
@@ -828,7 +828,7 @@ MSD void stage_prep(EnvView& e, const Grp& g, const Params& P) {
         }
         if (is_dyn(e, i) && e.x[i].w != 0.f) {
             float4 iv = e.inv[i];
-            float3 sd = f3(sqrtf(iv.x), sqrtf(iv.y), sqrtf(iv.z));
+            float3 sd = xyz(iv);                        // (principal inverse inertia)^(1/2), stored
             M3 R = qmat(e.q[i]);
             S3 S = rdrt(R, sd);
             S3 Si = rdrt(R, f3(1.f / sd.x, 1.f / sd.y, 1.f / sd.z));
