@@ -246,6 +246,7 @@ const void* fused_kernel_32(unsigned variant);
 enum : unsigned { FV_LEAN = 1u, FV_DYN = 2u, FV_JOINTS = 4u, FV_HULLS = 8u };
 cudaError_t fused_occupancy(int G, unsigned variant, int threads, size_t smem, int* blocks_per_sm);
 bool fused_supported(int G);
+void fused_preload();
 bool fused_lean(const DevBatch& D);   // whether a batch can run an FV_LEAN variant
 cudaError_t launch_fused(const DevBatch& D, const float* actions, int n_steps, const FusedCfg& C, int G, unsigned variant,
                          int grid, int threads, size_t smem, cudaStream_t s);

@@ -228,6 +228,17 @@ static const void* fused_fn(int G, unsigned v) {
 
 bool fused_supported(int G) { return fused_fn(G, FV_JOINTS | FV_HULLS) != nullptr; }
 
+// Loads every variant of the batched kernel now (a kernel's first use
+// otherwise loads it then, which a long-running caller such as the step
+// server would see as one slow launch).
+void fused_preload() {
+    cudaFuncAttributes a;
+    for (int G : {1, 2, 4, 8, 16, 32})
+        for (unsigned v = 0; v < 16u; v++)
+            if (const void* fn = fused_fn(G, v)) cudaFuncGetAttributes(&a, fn);
+    cudaGetLastError();
+}
+
 bool fused_lean(const DevBatch& D) {
     return !D.T.on && !D.force && !D.P.restit && !D.P.warm && !D.rec_man;
 }

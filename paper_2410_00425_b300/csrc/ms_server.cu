@@ -590,6 +590,7 @@ extern "C" ms_status ms_server_create(size_t budget, const ms_server_options* op
     cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     // raised to the device maximum once: graphs of every layout stay valid
     cudaFuncSetAttribute((const void*)k_multi<MULTI_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+    fused_preload();                         // no module load on the worker's first launch of a kernel
     // sessions come and go: keep freed pool memory for the next session
     // instead of returning it to the driver at every synchronisation
     cudaMemPool_t pool;
@@ -634,6 +635,14 @@ extern "C" ms_status ms_server_open(ms_server* s, const ms_body_desc* bodies, co
     {
         std::lock_guard<std::mutex> dk(s->dev_mu);
         st = ms_create_batch_flat(bodies, body_off, joints, joint_off, n_envs, p, &b);
+        // choose the kernel and its placement here, on the client's thread,
+        // not at the session's first step on the worker (occupancy queries,
+        // its workspace allocation)
+        ms_tuning t{};
+        if (st == MS_OK && (st = ms_get_tuning(b, &t)) != MS_OK) {
+            ms_destroy(b);
+            b = nullptr;
+        }
     }
     std::lock_guard<std::mutex> lk(s->mu);
     if (st != MS_OK) {
