@@ -78,19 +78,19 @@ def make_workload(name, variants=False, **kw):
 # by workload and tuning.  Valid only while the kernel sources hash to the
 # recorded value; otherwise the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("arm", "8,1,0"): {"bytes": 3.0277e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
-    ("arm", "4,1,0"): {"bytes": 1.8032e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<4, lean, dynamic>"},
-    ("arm", "8,2,0"): {"bytes": 3.0149e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
-    ("pick", "8,1,0"): {"bytes": 3.0911e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, full, dynamic>"},
-    ("clutter", "16,8,0"): {"bytes": 5.5026e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
-    ("clutter", "16,8,2"): {"bytes": 5.51143e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
-    ("clutter", "16,4,0"): {"bytes": 5.52079e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, no joints>"},
-    ("hand", "8,4,2"): {"bytes": 3.3445e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
-    ("hand", "8,4,0"): {"bytes": 8.5148e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<8, lean, dynamic>"},
-    ("hulls", "16,8,2"): {"bytes": 2.95903e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
-    ("hulls", "16,8,0"): {"bytes": 2.95121e+08, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
-    ("mixed", "16,4,2"): {"bytes": 3.4084e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<16, lean, dynamic>"},
-    ("mixed", "32,8,0"): {"bytes": 7.5235e+07, "kernel_sha": "33b3fdbe522520e4", "kernel": "k_fused<32, lean, dynamic>"},
+    ("arm", "4,1,0"): {"bytes": 1.80493e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<4, lean, dynamic>"},
+    ("arm", "8,1,0"): {"bytes": 3.04064e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<8, lean, dynamic>"},
+    ("arm", "8,2,0"): {"bytes": 3.02684e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<8, lean, dynamic>"},
+    ("clutter", "16,4,0"): {"bytes": 5.51108e+08, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("clutter", "16,8,0"): {"bytes": 5.5136e+08, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("clutter", "16,8,2"): {"bytes": 5.51332e+08, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic, no joints>"},
+    ("hand", "8,4,2"): {"bytes": 3.33629e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<8, lean, dynamic>"},
+    ("hulls", "16,8,0"): {"bytes": 2.958e+08, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
+    ("hulls", "16,8,2"): {"bytes": 2.95881e+08, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic, hulls, no joints>"},
+    ("mixed", "16,4,2"): {"bytes": 3.39876e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, dynamic>"},
+    ("pick", "8,1,0"): {"bytes": 3.09965e+07, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<8, full, dynamic>"},
+    ("small", "16,2,0"): {"bytes": 179712, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<16, lean, capacity slots, no joints>"},
+    ("small", "32,2,0"): {"bytes": 187648, "kernel_sha": "d66443322403c88d", "kernel": "k_fused<32, lean, capacity slots, no joints>"},
 }
 KERNEL_SOURCES = ("ms_fused.cu", "ms_stages.cuh", "ms_narrow.cuh", "ms_math.cuh", "ms_internal.h", "../build.py")
 
