@@ -453,6 +453,22 @@ ms_status ms_get_tuning(ms_batch* b, ms_tuning* t);
  * updated after tuning.  best (nullable) receives the choice. */
 ms_status ms_autotune(ms_batch* b, int n_steps, const char* cache_path, ms_tuning* best, void* stream);
 
+/* Device-memory hook, for callers whose device memory belongs to another
+ * allocator (a framework's caching allocator).  Every device allocation of a
+ * batch created after the call -- its state, parameters, workspaces, record,
+ * task and staging buffers -- comes from alloc(bytes, device, stream, user),
+ * stream being the batch's own setup stream, and goes back through
+ * free(ptr, device, stream, user) when the batch is destroyed, after the
+ * batch's work has finished.  alloc returns NULL on failure (the creating
+ * call then fails with MS_ERR_OOM).  A batch keeps the hook it was created
+ * under, so the functions and user must outlive it; ms_set_allocator(NULL,
+ * NULL, NULL) restores the library's own stream-ordered pool for later
+ * batches.  Setting only one function is MS_ERR_INVALID_ARG.  The tuner's
+ * temporary state copies still use the library's pool. */
+typedef void* (*ms_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*ms_free_fn)(void* ptr, int device, void* stream, void* user);
+ms_status ms_set_allocator(ms_alloc_fn alloc, ms_free_fn free_fn, void* user);
+
 /* Device bytes held by the batch (state, parameters, workspaces). */
 ms_status ms_memory_bytes(ms_batch* b, size_t* bytes);
 

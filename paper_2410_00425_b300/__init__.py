@@ -158,3 +158,17 @@ class Batch:
 
     def memory_bytes(self):
         return _ffi.ms_memory_bytes(self.h)
+
+
+def use_torch_allocator(on=True):
+    """Route the device memory of batches created from now on through
+    PyTorch's caching allocator (on=False: back to the library's pool).
+    Batches keep the allocator they were created with."""
+    import torch
+    from . import _ffi
+    if not on:
+        _ffi.ms_set_allocator(None, None)
+        return
+    _ffi.ms_set_allocator(lambda n, d, st: torch.cuda.caching_allocator_alloc(n, d, st),
+                          lambda p, d, st: torch.cuda.caching_allocator_delete(p))
+

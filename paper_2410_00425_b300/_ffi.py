@@ -117,6 +117,7 @@ _SIGS = [
     ("ms_task_observe", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_step_ex", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     ("ms_step_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
+    ("ms_set_allocator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ms_set_camera", C.c_int, [C.c_void_p, C.POINTER(ms_camera_desc)]),
     ("ms_create_batch_hulls", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                         C.POINTER(ms_sim_params), C.POINTER(ms_hull_lib), C.POINTER(C.c_void_p)]),
@@ -241,6 +242,25 @@ def ms_step_ex(b, actions=None, n_steps=1, out=None, flags=0, stream=None):
 def ms_step_host(b, actions=None, n_steps=1, out=None, out_kind=0, stream=None):
     """actions, out: host buffers (pinned tensors or arrays)."""
     return check(load().ms_step_host(b, _ptr(actions), n_steps, _ptr(out), out_kind, _stream(stream)))
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p)
+_hook = None                                   # the installed callbacks, kept alive
+
+
+def ms_set_allocator(alloc=None, free=None):
+    """alloc(bytes, device, stream) -> int pointer (0 on failure), free(ptr,
+    device, stream): Python callables, or None and None for the library's pool."""
+    global _hook
+    if alloc is None and free is None:
+        check(load().ms_set_allocator(None, None, None))
+        _hook = None
+        return
+    a = ALLOC_FN(lambda n, d, st, u: alloc(n, d, st) or None)
+    f = FREE_FN(lambda p, d, st, u: free(p, d, st))
+    check(load().ms_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None))
+    _hook = (a, f)
 
 
 def ms_set_task(b, task, stream=None):

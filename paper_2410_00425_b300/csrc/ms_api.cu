@@ -15,6 +15,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <sstream>
 #include <string>
@@ -95,6 +96,9 @@ struct ms_batch {
     // destroyed since
     cudaEvent_t done = nullptr;
     cudaStream_t setup = nullptr;     // non-blocking stream for allocation and uploads
+    ms_alloc_fn alloc_fn = nullptr;   // the device-memory hook the batch was created under (null: own pool)
+    ms_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
     int sm_count = 0;
     size_t smem_optin = 0;
     std::vector<int> h_body_off, h_joint_off;
@@ -108,11 +112,33 @@ struct ms_batch {
     float4* d_force = nullptr;        // contact forces per body (allocated on first use)
 };
 
+// The device-memory hook of batches created from now on (ms_set_allocator).
+static std::mutex g_alloc_mu;
+static ms_alloc_fn g_alloc_fn = nullptr;
+static ms_free_fn g_free_fn = nullptr;
+static void* g_alloc_user = nullptr;
+
+extern "C" ms_status ms_set_allocator(ms_alloc_fn alloc, ms_free_fn free_, void* user) {
+    if ((alloc == nullptr) != (free_ == nullptr)) return fail(MS_ERR_INVALID_ARG, "set both functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_fn = alloc;
+    g_free_fn = free_;
+    g_alloc_user = user;
+    return MS_OK;
+}
+
 // Device memory comes from the device's stream-ordered pool on the batch's
 // own non-blocking stream: creating a batch (or a server session) neither
 // waits for nor stalls work running on other streams.
 static ms_status dmalloc(ms_batch* b, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (b->alloc_fn) {
+        *p = b->alloc_fn(bytes, b->device, (void*)b->setup, b->alloc_user);
+        if (!*p) return fail(MS_ERR_OOM, "the device-memory hook returned NULL for %zu bytes", bytes);
+        b->allocs.push_back(*p);
+        b->bytes += bytes;
+        return MS_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, b->setup);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->setup);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA,
@@ -149,7 +175,12 @@ static void free_all(ms_batch* b) {
     drop_graphs(b);
     render_destroy(b->render);
     b->render = nullptr;
-    for (void* p : b->allocs) cudaFreeAsync(p, b->setup);
+    if (b->free_fn) {
+        if (b->setup) cudaStreamSynchronize(b->setup);
+        for (void* p : b->allocs) b->free_fn(p, b->device, (void*)b->setup, b->alloc_user);
+    } else {
+        for (void* p : b->allocs) cudaFreeAsync(p, b->setup);
+    }
     b->allocs.clear();
     if (b->setup) {
         cudaStreamSynchronize(b->setup);
@@ -319,6 +350,12 @@ static ms_status create_impl(const ms_body_desc* const* bodies_of, const int* nb
     b->params = *p;
     cudaGetDevice(&b->device);
     {
+        {
+            std::lock_guard<std::mutex> lk(g_alloc_mu);
+            b->alloc_fn = g_alloc_fn;
+            b->free_fn = g_free_fn;
+            b->alloc_user = g_alloc_user;
+        }
         cudaError_t e = cudaStreamCreateWithFlags(&b->setup, cudaStreamNonBlocking);
         if (e != cudaSuccess) { delete b; return fail(MS_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); }
         e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
